@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the Helios-r2 forward model + likelihood on B300.
+
+One step = forward_model_batch + log_likelihood_batch over one batch of
+synthetic parameter samples (FP16-offset tables, FP32 solve, FP64 lnL) on
+the 1024-sample, 100-layer, 6-absorber, 8501-wavenumber workload (4 Gauss
+nodes, R = 300, 300 bins).  Inputs are resident in HBM; L2 is flushed (a
+256 MB write) between timed steps, outside the timed events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hr2|reference]
+
+Under torchrun (N > 1) every rank runs the same per-GPU workload on its own
+GPU with its own samples (weak scaling, no data-path collective); rank 0
+prints one JSON line with the whole-job throughput over the slowest rank.
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "forward models/sec and HBM-roofline fraction at 1e-4 rel. flux error; p50/p99 latency"
+WORKLOAD = "batch1024_l100_k6_nu8501"
+PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="hr2", choices=["hr2", "reference"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-samples", type=int, default=64)
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ helpers
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def mufu_ops_per_model(setup, n_cia: int) -> float:
+    """Exponentials the method needs per model: per wavenumber, one per absorber,
+    CIA pair and Planck source on every level, and one transmission factor per
+    layer and angle node."""
+    L = setup.n_layers
+    K = len(setup.species)
+    return float(setup.n_nu) * ((L + 1) * (K + n_cia + 1) + L * setup.n_mu)
+
+
+def cpu_baseline(wl, n_samples: int):
+    """The FP64 oracle, as it stands, on the host cores over a bounded sample."""
+    import oracle
+    from paper_1910_01070_b300 import workloads as W
+    oracle.build()
+    tabs = W.make_tables(wl.table)
+    om = oracle.Model(tabs, wl.setups[0].as_dict())
+    theta, _ = wl.params(n_samples, seed_offset=99)
+    om.forward_batch(theta[:2], n_threads=0)          # warm-up (page-in)
+    t0 = time.perf_counter()
+    om.forward_batch(theta, n_threads=0)
+    dt = time.perf_counter() - t0
+    return {"value": n_samples / dt, "unit": "models/s", "cores": int(om.last_threads), "kind": "oracle",
+            "sample": "%d samples of %s (full spectra + bins), FP64, OpenMP over samples, %.1f s wall"
+                      % (n_samples, wl.name, dt)}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_1910_01070_b300 import workloads as W
+    import oracle
+    wl = W.WORKLOADS[args.workload]()
+    oracle.build()
+    tabs = W.make_tables(wl.table)
+    om = oracle.Model(tabs, wl.setups[0].as_dict())
+    per_step = max(1, args.cpu_samples // 4)
+    times = []
+    for k in range(args.warmup + args.steps):
+        theta, _ = wl.params(per_step, seed_offset=1000 + k)
+        t0 = time.perf_counter()
+        om.forward_batch(theta, n_threads=0)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    total = sum(times)
+    value = per_step * len(times) / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "models/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "samples_per_step": per_step,
+                       "note": "each step a bounded sample of the workload's batch"},
+            "cpu_baseline": {"value": value, "unit": "models/s", "cores": int(om.last_threads), "kind": "oracle",
+                             "sample": "%d samples per step of %s" % (per_step, wl.name)},
+            "e2e": {"value": value, "unit": "models/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ hr2 arm
+def run_hr2(args, world, rank, local):
+    import torch
+
+    from paper_1910_01070_b300 import hr2
+    from paper_1910_01070_b300 import workloads as W
+    from paper_1910_01070_b300.build import build
+    from paper_1910_01070_b300.engine import Engine
+
+    build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl = W.WORKLOADS[args.workload]()
+    setup = wl.setups[0]
+    n = wl.n_samples
+    tabs = W.make_tables(wl.table)
+    eng = Engine(local)
+    t16 = eng.add_tables(wl.table, "fp16", tabs)
+    s16 = eng.add_setup(t16, setup)
+    stream = torch.cuda.current_stream()
+
+    # mock observation: the model at a fixed "true" sample plus seeded noise
+    truth = torch.as_tensor(wl.truth(0)[None, :], device=dev)
+    sid1 = torch.zeros(1, dtype=torch.int32, device=dev)
+    tb = eng.forward([s16], sid1, truth)
+    D, sig = W.mock_observation(tb.double().cpu().numpy()[0], wl.seed)
+    eng.set_observation(s16, D, sig)
+
+    # a pool of distinct parameter batches resident in HBM (per-rank seeds)
+    pool = []
+    for p in range(4):
+        th, sid = wl.params(n, seed_offset=17 * rank + p)
+        pool.append((torch.as_tensor(th, device=dev), torch.as_tensor(sid, device=dev)))
+    bins = torch.empty((n, setup.n_bins), dtype=torch.float32, device=dev)
+    lnl = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step(k, setups):
+        th, sid = pool[k % len(pool)]
+        hr2.forward_model_batch(eng.ctx, setups, sid, th, bins, None, None, stream)
+        hr2.log_likelihood_batch(eng.ctx, setups, sid, bins, lnl, None, stream)
+
+    def timed(setups, steps, warmup):
+        for k in range(warmup):
+            step(k, setups)
+        torch.cuda.synchronize()
+        hr2.hr2_profile_read(eng.ctx, True)
+        hr2.hr2_profile_enable(eng.ctx, True)
+        evs = []
+        barrier(world)
+        torch.cuda.synchronize()
+        for k in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(k, setups)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        barrier(world)
+        hr2.hr2_profile_enable(eng.ctx, False)
+        kms, launches = hr2.hr2_profile_read(eng.ctx, True)
+        times = [a.elapsed_time(b) for a, b in evs]
+        return times, kms, launches
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, kms, launches = timed([s16], args.steps, args.warmup)
+    clk = clocks.stop()
+    total_ms = max_over_ranks(world, sum(times))
+    ms_step = total_ms / args.steps
+    value = world * n * args.steps / (total_ms / 1e3)
+    lat = np.asarray(times)
+    n_cia = int(wl.table.cia) * 2
+    ops = mufu_ops_per_model(setup, n_cia) * n
+    kernel_ms = kms / max(launches, 1)
+    props = torch.cuda.get_device_properties(local)
+    peak_ops = props.multi_processor_count * 32 * 2032e6 / 1e12     # ex2 per clock per SM (measured 32)
+    achieved = ops / (kernel_ms / 1e3) / 1e12
+    traffic = None
+    if os.path.exists(PROFILE_TRAFFIC):
+        with open(PROFILE_TRAFFIC) as f:
+            tr = json.load(f)
+        if tr.get("kernel_source_hash") == _kernel_hash():
+            traffic = tr.get("bytes_per_launch")
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Texp/s",
+                "frac": achieved / peak_ops, "traffic": traffic,
+                "kernel": "k_forward32", "kernel_ms": kernel_ms,
+                "note": "exponentials required by the method per launch / event-timed kernel time; peak = "
+                        "SMs x 32 ex2/clk/SM (measured) x 2032 MHz"}
+
+    # end to end through the host-buffer entry point (pinned buffers)
+    h_par = [torch.as_tensor(p[0].cpu().numpy()).pin_memory() for p in pool]
+    h_sid = [torch.as_tensor(p[1].cpu().numpy()).pin_memory() for p in pool]
+    h_out = torch.empty(n, dtype=torch.float64).pin_memory()
+    for k in range(2):
+        hr2.hr2_evaluate_host(eng.ctx, [s16], h_sid[k % 4], h_par[k % 4], h_out, None, None, stream)
+    e2e_t = []
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hr2.hr2_evaluate_host(eng.ctx, [s16], h_sid[k % 4], h_par[k % 4], h_out, None, None, stream)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = max_over_ranks(world, sum(e2e_t))
+    e2e = {"value": world * n * args.steps / e2e_total, "unit": "models/s",
+           "h2d_bytes_per_step": n * (8 * hr2.HR2_NPARAM + 4), "d2h_bytes_per_step": n * 8,
+           "ms_per_step": 1e3 * e2e_total / args.steps, "api": "hr2_evaluate_host (pinned host buffers)"}
+
+    fp64 = None
+    if not args.no_fp64:
+        t64 = eng.add_tables(wl.table, "fp64", tabs)
+        s64 = eng.add_setup(t64, setup)
+        eng.set_observation(s64, D, sig)
+        k64 = min(args.steps, 5)
+        t64s, kms64, l64 = timed([s64], k64, 3)
+        tot64 = max_over_ranks(world, sum(t64s))
+        fp64 = {"value": world * n * k64 / (tot64 / 1e3), "unit": "models/s", "steps": k64,
+                "p50_ms": float(np.percentile(t64s, 50)), "p99_ms": float(np.percentile(t64s, 99)),
+                "kernel_ms": kms64 / max(l64, 1), "tables": "fp64"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, args.cpu_samples)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "models/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "samples_per_gpu": n, "layers": setup.n_layers,
+                           "absorbers": len(setup.species), "wavenumbers": setup.n_nu, "gauss_nodes": setup.n_mu,
+                           "bins": setup.n_bins, "resolving_power": setup.resolving_power,
+                           "tables": "FP16 log10 sigma - integer offset per species",
+                           "l2": "flushed between timed steps (256 MB write outside the events)",
+                           "launch": list(hr2.hr2_get_launch_config(eng.ctx))},
+                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+                "fp64_path": fp64, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+                "gpu_launches": 5 * args.steps}
+        if fp64:
+            line["speedup_vs_fp64_path"] = value / fp64["value"]
+        print(json.dumps(line), flush=True)
+    eng.close()
+
+
+def _kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("kern_forward.cu", "hr2_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1910_01070_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_hr2(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

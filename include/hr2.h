@@ -1,0 +1,277 @@
+/*
+ * hr2.h -- C ABI of the B300 (sm_103a) Helios-r2 emission forward model.
+ *
+ * The library evaluates, for a batch of parameter samples, the forward model
+ * of Kitzmann et al. (2020), Sects. 2-3: finite-element temperature profile
+ * (Sect. 2.5.1, Eqs. 12-16), opacity interpolation onto each level's (T, p)
+ * and the abundance-weighted absorption coefficient (Sects. 2.3, 2.8), layer
+ * optical depths, the scattering-free short-characteristic solve with a
+ * linear Planck source over Gauss angle nodes (Sect. 2.1, Eqs. 1-8), the
+ * radius-distance scaling (Sect. 2.2, Eq. 9), the Gaussian instrument
+ * profile (Sect. 2.7, Eq. 17), binning to the observed bins (Sect. 2.8) and
+ * the Gaussian log-likelihood with optional error inflation (Sect. 3.1
+ * Eq. 19; Sect. 3.3 Eqs. 22-23).
+ *
+ * Conventions for every entry point
+ *   - Return value: HR2_OK (0) or a negative hr2_status.  No C++ exception
+ *     crosses the ABI.  hr2_last_error() gives a human-readable message for
+ *     the calling thread's last failure on that context.
+ *   - Device pointers are plain CUDA device addresses (e.g. a torch tensor's
+ *     data_ptr()); host pointers are ordinary process memory.  Every argument
+ *     says which it is.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Batch calls are asynchronous on that stream and do not
+ *     synchronise the host, except where stated.
+ *   - Ownership: the library owns contexts, tables and setups (create /
+ *     destroy pairs); the caller owns every parameter and output buffer.
+ *   - Units are cgs; wavenumbers in cm^-1; pressures in bar at the ABI.
+ *   - Physically invalid samples (non-positive T on any level, f <= 0,
+ *     d <= 0, absorber mixing ratios summing to >= 1, non-finite values)
+ *     do not fail the call: their spectrum is NaN, their status word is
+ *     non-zero and their log-likelihood is -inf.
+ */
+#ifndef HR2_H
+#define HR2_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+typedef enum {
+  HR2_OK = 0,
+  HR2_EINVAL = -1,    /* invalid argument; nothing was launched           */
+  HR2_ENOMEM = -2,    /* device allocation failed or memory budget hit    */
+  HR2_ECUDA = -3,     /* a CUDA runtime call failed                       */
+  HR2_ETIMEDOUT = -4, /* a bounded device-side wait gave up               */
+  HR2_EBUSY = -5      /* workspace cannot grow while the stream captures  */
+} hr2_status;
+
+/* per-sample status bits written by forward_model_batch */
+#define HR2_SAMPLE_BAD_T      1  /* a level temperature is <= 0 or not finite  */
+#define HR2_SAMPLE_BAD_ABUND  2  /* mixing ratios sum to >= 1 or are not finite */
+#define HR2_SAMPLE_BAD_SCALE  4  /* f, d or g not positive / finite            */
+#define HR2_SAMPLE_BAD_SETUP  8  /* setup index outside [0, n_setups)          */
+
+/* ---------------------------------------------------------------- limits */
+#define HR2_MAX_TNODES   16   /* finite-element temperature nodes, K_e q + 1  */
+#define HR2_MAX_SPECIES  16   /* absorbers per setup                          */
+#define HR2_MAX_MU        8   /* Gauss angle nodes                            */
+#define HR2_MAX_LEVELS  256   /* levels (layers + 1) per setup                */
+#define HR2_MAX_SETUPS   32   /* distinct setups in one batch call            */
+#define HR2_MAX_TGRID    64   /* points of a table's temperature grid         */
+#define HR2_MAX_PGRID    64   /* points of a table's pressure grid            */
+
+/* ------------------------------------------------ parameter vector layout
+ * One row of HR2_NPARAM doubles per sample ("theta", Table 1 of the paper,
+ * free-chemistry variant):
+ *   [HR2_P_LOGG]      log10 g, g in cm s^-2
+ *   [HR2_P_F]         calibration factor f of the radius-distance relation
+ *   [HR2_P_DIST]      distance d in parsec
+ *   [HR2_P_T0 + i]    finite-element nodal temperature i in K, i = 0 is the
+ *                     bottom of the atmosphere (T_1 of Sect. 2.5.1); the setup
+ *                     uses fe_elements*fe_order+1 of them
+ *   [HR2_P_X0 + s]    log10 volume mixing ratio of the setup's absorber s
+ * Unused entries are ignored.  hr2_nodes_from_b() converts (T_1, b_i) to
+ * nodal temperatures. */
+#define HR2_P_LOGG  0
+#define HR2_P_F     1
+#define HR2_P_DIST  2
+#define HR2_P_T0    3
+#define HR2_P_X0   19
+#define HR2_NPARAM 35
+
+/* ---------------------------------------------------------------- storage */
+#define HR2_STORE_FP16_OFFSET 1  /* FP16 of (log10 sigma - off_s), off_s integer */
+#define HR2_STORE_FP64        2  /* FP64 log10 sigma (the plain FP64 path)       */
+
+typedef struct hr2_ctx hr2_ctx;
+typedef struct hr2_tables hr2_tables;
+typedef struct hr2_setup hr2_setup;
+
+/* Opacity table description (Sect. 2.3: per-species cross-sections tabulated
+ * on a (T, p, nu) grid; CIA of H2-H2 and H2-He on (T, nu)).  All pointers
+ * are HOST memory read during the call only. */
+typedef struct {
+  int n_species;              /* absorbers in the table, 1..HR2_MAX_SPECIES     */
+  int n_T;                    /* 2..HR2_MAX_TGRID                               */
+  const double* T_grid;       /* [n_T] K, strictly ascending, > 0               */
+  int n_p;                    /* 2..HR2_MAX_PGRID                               */
+  const double* log10p_grid;  /* [n_p] log10(p / bar), strictly ascending       */
+  double nu0;                 /* wavenumber of column 0, cm^-1 (> 0)            */
+  double dnu;                 /* uniform spacing, cm^-1 (> 0)                   */
+  int n_nu;                   /* columns                                        */
+  const double* species_mass; /* [n_species] molecular mass in u                */
+  int has_cia_h2h2;           /* nonzero: an H2-H2 CIA table is supplied        */
+  int has_cia_h2he;           /* nonzero: an H2-He CIA table is supplied        */
+} hr2_table_desc;
+
+/* Spectral / atmospheric setup (Sects. 2, 2.1, 2.5.1, 2.7).  Pointers are
+ * HOST memory read during the call only. */
+typedef struct {
+  int nu_first;               /* first table column used                        */
+  int n_nu;                   /* columns used (>= 1)                            */
+  int n_layers;               /* L layers; L+1 levels equidistant in log p      */
+  double p_top, p_bot;        /* bar, 0 < p_top < p_bot                         */
+  int n_species;              /* absorbers used, 0..HR2_MAX_SPECIES             */
+  const int* species;         /* [n_species] table indices                      */
+  int n_mu;                   /* Gauss-Legendre angle nodes, 1..HR2_MAX_MU      */
+  int fe_elements;            /* K_e >= 1                                       */
+  int fe_order;               /* q >= 1, K_e q + 1 <= HR2_MAX_TNODES            */
+  double resolving_power;     /* R = nu / FWHM of the instrument; <= 0: none    */
+  int n_bins;                 /* >= 1; every bin must contain a grid point     */
+  const double* bin_edges;    /* [n_bins+1] cm^-1 ascending; a point nu belongs
+                                 to bin b if edge_b <= nu < edge_{b+1} (last bin
+                                 closed)                                         */
+  const double* obs_flux;     /* [n_bins] observed D_j, or NULL                 */
+  const double* obs_sigma;    /* [n_bins] observational errors sigma_j, or NULL */
+  double r_he;                /* n_He / n_H2 of the H2/He filling gas (> 0)     */
+  double radius_cm;           /* R_* of the radius-distance relation, cm        */
+} hr2_setup_desc;
+
+/* Launch shape of the persistent forward kernel (chosen by the autotuner). */
+typedef struct {
+  int warps_per_cta;          /* samples processed together per work item: 1..16 */
+  int ctas_per_sm;            /* persistent CTAs per SM: 1..8                     */
+} hr2_launch_cfg;
+
+/* ------------------------------------------------------------- contexts */
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the
+ * device memory the context may hold for tables, setups and workspace
+ * (0 = no cap beyond the device).  *out receives the handle. */
+int hr2_ctx_create(int device, size_t mem_budget_bytes, hr2_ctx** out);
+
+/* Destroy a context and every table, setup and workspace it still owns.
+ * The caller must have finished all work it launched with it. */
+int hr2_ctx_destroy(hr2_ctx* ctx);
+
+/* Message of the calling thread's last failure on ctx ("" if none).  The
+ * string is owned by the library and valid until the next call on ctx. */
+const char* hr2_last_error(const hr2_ctx* ctx);
+
+/* Device bytes currently held by ctx and its budget (0 = uncapped). */
+int hr2_ctx_memory(const hr2_ctx* ctx, size_t* used_bytes, size_t* budget_bytes);
+
+/* Set / read the persistent kernel's launch shape used by later calls. */
+int hr2_set_launch_config(hr2_ctx* ctx, const hr2_launch_cfg* cfg);
+int hr2_get_launch_config(const hr2_ctx* ctx, hr2_launch_cfg* cfg);
+
+/* Make sure the workspace of `stream` holds a batch of n samples whose
+ * setups span at most n_nu_max wavenumbers, so that a later batch call of
+ * that size allocates nothing (required before CUDA-graph capture). */
+int hr2_reserve(hr2_ctx* ctx, void* stream, int n, int n_nu_max);
+
+/* -------------------------------------------------------------- tables */
+
+/* create_opacity_tables: copy the cross-section tables to the device and
+ * keep them resident (Sects. 2.3, 2.8).
+ *   log10_sigma     HOST [n_species][n_T][n_p][n_nu] log10 sigma in cm^2, or
+ *                   NULL to upload each species later with
+ *                   hr2_tables_upload_species();
+ *   log10_cia_h2h2  HOST [n_T][n_nu] log10 k in cm^5, or NULL (required iff
+ *                   desc->has_cia_h2h2); log10_cia_h2he likewise;
+ *   storage         HR2_STORE_FP16_OFFSET: each species s (and each CIA
+ *                   table) is stored as IEEE binary16 of (value - off_s),
+ *                   rounded to nearest even, with off_s = rint((min+max)/2)
+ *                   over that species' values; HR2_STORE_FP64: stored as is.
+ * All values must be finite.  The wavenumber axis is padded on the device to
+ * a multiple of 64 columns.  *out receives the handle. */
+int create_opacity_tables(hr2_ctx* ctx, const hr2_table_desc* desc, const double* log10_sigma,
+                          const double* log10_cia_h2h2, const double* log10_cia_h2he, int storage,
+                          hr2_tables** out);
+
+/* Upload (or replace) species s: HOST [n_T][n_p][n_nu] log10 sigma.  Lets
+ * large tables be filled one species at a time.  Synchronous. */
+int hr2_tables_upload_species(hr2_ctx* ctx, hr2_tables* tables, int s, const double* log10_sigma_s);
+
+/* Offsets off_s (HOST [n_species + 2] out: species, then H2-H2, H2-He CIA)
+ * and device bytes of the stored table. */
+int hr2_tables_info(const hr2_tables* tables, double* offsets_out, size_t* device_bytes);
+
+int hr2_tables_destroy(hr2_ctx* ctx, hr2_tables* tables);
+
+/* --------------------------------------------------------------- setups */
+
+/* Build a setup on the device: level grid, Gauss-Legendre angle nodes,
+ * Gauss-Lobatto element nodes, per-level pressure interpolation weights and
+ * the combined instrument-profile + binning operator W (a banded sparse
+ * matrix, FP32 and FP64, Sects. 2.7-2.8), plus the observation if given.
+ * Synchronous.  The tables must outlive the setup. */
+int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tables, const hr2_setup_desc* desc, hr2_setup** out);
+
+/* Replace the observation (HOST [n_bins] each).  Synchronous. */
+int hr2_setup_set_observation(hr2_ctx* ctx, hr2_setup* setup, const double* obs_flux, const double* obs_sigma);
+
+/* Number of bins / wavenumbers / nonzeros of W of a setup. */
+int hr2_setup_info(const hr2_setup* setup, int* n_bins, int* n_nu, long long* w_nnz);
+
+int hr2_setup_destroy(hr2_ctx* ctx, hr2_setup* setup);
+
+/* ----------------------------------------------------------- batch calls */
+
+/* forward_model_batch: model spectra of n samples (Sects. 2.1-2.8).
+ *   setups           HOST [n_setups] handles, 1 <= n_setups <= HR2_MAX_SETUPS;
+ *                    all must share one table set and one storage type
+ *   setup_of_sample  DEVICE int [n]: index into `setups` per sample
+ *   params           DEVICE double [n][HR2_NPARAM] (layout above)
+ *   out_bins         DEVICE float [n][bins_ld]: D_m of sample i in its first
+ *                    n_bins entries (FP32), scaled by f (R_star/d)^2
+ *   out_highres      DEVICE float [n][highres_ld] or NULL: unscaled top-of-
+ *                    atmosphere flux F+ (Eq. 8) on the setup's n_nu points
+ *   out_status       DEVICE int [n] or NULL: HR2_SAMPLE_* bits per sample
+ * FP16-offset tables run the FP32 persistent kernel; FP64 tables run the
+ * plain FP64 kernel.  Results for a sample do not depend on the rest of the
+ * batch.  Asynchronous on `stream`; uses the stream's workspace. */
+int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
+                        const int* setup_of_sample, const double* params, int n, float* out_bins,
+                        int bins_ld, float* out_highres, int highres_ld, int* out_status, void* stream);
+
+/* log_likelihood_batch: Gaussian log-likelihood (Eq. 19), with error
+ * inflation s_j^2 = sigma_j^2 + 10^eps (Eqs. 22-23) where log_eps[i] is
+ * finite.  FP64 accumulation in a fixed order (deterministic).
+ *   model_bins   DEVICE float [n][bins_ld] (as written by forward_model_batch)
+ *   log_eps      DEVICE double [n] or NULL (NULL or NaN: no inflation)
+ *   out_lnL      DEVICE double [n]; -inf where any model bin is not finite
+ * Every setup used must have an observation.  Asynchronous on `stream`. */
+int log_likelihood_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
+                         const int* setup_of_sample, const float* model_bins, int bins_ld,
+                         const double* log_eps, int n, double* out_lnL, void* stream);
+
+/* hr2_evaluate_host: the call a sampler makes per batch of live points, with
+ * HOST buffers: copies setup_of_sample (int [n]), params (double
+ * [n][HR2_NPARAM]) and log_eps (double [n] or NULL) to the stream's
+ * workspace, runs forward_model_batch and log_likelihood_batch, and copies
+ * lnL (double [n]) and, if out_bins is not NULL, the model bins (float
+ * [n][bins_ld]) back.  Synchronises `stream` before returning.  Pinned host
+ * buffers make the copies asynchronous with respect to other streams. */
+int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
+                      const int* setup_of_sample, const double* params, const double* log_eps, int n,
+                      double* out_lnL, float* out_bins, int bins_ld, void* stream);
+
+/* -------------------------------------------------------- instrumentation
+ * (No counterpart in the paper.)  While enabled, every forward_model_batch
+ * records a pair of CUDA events on its stream around the launch of the main
+ * forward kernel (k_forward32 / k_forward64), so a caller can time that
+ * kernel alone inside a longer step.  hr2_profile_read waits for the
+ * recorded events, returns the summed kernel time in ms and the number of
+ * launches, and with reset != 0 forgets them. */
+int hr2_profile_enable(hr2_ctx* ctx, int on);
+int hr2_profile_read(hr2_ctx* ctx, int reset, double* kernel_ms, int* launches);
+
+/* ------------------------------------------------------------- helpers */
+
+/* Nodal temperatures from the retrieved bottom temperature T_1 and the
+ * ratios b_i (Sect. 2.5.1): node i+1 = b_i * node i.  HOST arrays:
+ * b [n_nodes-1], nodes_out [n_nodes]. */
+int hr2_nodes_from_b(int n_nodes, double T1, const double* b, double* nodes_out);
+
+/* Library version string. */
+const char* hr2_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HR2_H */

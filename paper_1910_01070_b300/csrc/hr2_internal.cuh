@@ -1,0 +1,193 @@
+// hr2_internal.cuh -- device-side data structures shared by the kernels and
+// the host implementation of the C ABI (include/hr2.h).
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hr2.h"
+
+namespace hr2 {
+
+// Wavenumber tile of one work item: 32 lanes x 2 consecutive points.
+constexpr int kTileNu = 64;
+constexpr int kMaxWarps = 16;
+constexpr int kCiaH2H2 = HR2_MAX_SPECIES;      // offset slot of the H2-H2 CIA table
+constexpr int kCiaH2He = HR2_MAX_SPECIES + 1;  // offset slot of the H2-He CIA table
+
+// CGS constants (CODATA 2018).
+constexpr double kH = 6.62607015e-27;         // erg s
+constexpr double kC = 2.99792458e10;          // cm s^-1
+constexpr double kKB = 1.380649e-16;          // erg K^-1
+constexpr double kAMU = 1.66053906660e-24;    // g
+constexpr double kParsec = 3.0856775814913673e18;  // cm
+constexpr double kBar = 1.0e6;                // dyn cm^-2
+constexpr double kMassH2 = 2.01588;           // u
+constexpr double kMassHe = 4.002602;          // u
+constexpr double kPi = 3.141592653589793;
+constexpr double kLog2_10 = 3.321928094887362;    // log2(10)
+constexpr double kLog2e = 1.4426950408889634;     // log2(e)
+constexpr double kLn2 = 0.6931471805599453;       // ln(2)
+// second radiation constant h c / k_B (cm K) and 2 h c^2 (erg cm^2 s^-1)
+constexpr double kC2 = kH * kC / kKB;
+constexpr double kC1 = 2.0 * kH * kC * kC;
+
+// Device copy of one opacity table set.
+struct TablesDev {
+  int storage;            // HR2_STORE_*
+  int n_species, n_T, n_p, n_nu, nu_pad;
+  double nu0, dnu;
+  const __half* sig16;    // [n_species][n_T][n_p][nu_pad]  (FP16 of value - off_s)
+  const __half* cia16;    // [2][n_T][nu_pad] (H2-H2, H2-He) or null
+  const double* sig64;    // [n_species][n_T][n_p][nu_pad]
+  const double* cia64;    // [2][n_T][nu_pad] or null
+  int has_cia[2];
+  // FP16 offsets off_s: [0, HR2_MAX_SPECIES) species, then kCiaH2H2, kCiaH2He
+  double off[HR2_MAX_SPECIES + 2];
+  float T_grid[HR2_MAX_TGRID];
+  double T_grid64[HR2_MAX_TGRID];
+  double log10p_grid64[HR2_MAX_PGRID];
+  double mass[HR2_MAX_SPECIES];
+};
+
+// Per-level data of a setup that does not depend on the sample.
+struct LevelDev {
+  int pcell;              // p-grid cell index b_j (clamped)
+  float wp;               // weight of log10p_grid[b_j + 1]
+  float p_dyn;            // level pressure, dyn cm^-2
+  float half_dp;          // (p_{j+1} - p_j) / 2 for layer j (0 for the last level)
+  double p_dyn64, half_dp64;
+  double wp64;
+};
+
+// Device descriptor of one setup (lives in device memory).
+struct SetupDev {
+  int nu_first, n_nu;     // table columns used
+  int tile0, n_tiles;     // 64-aligned tiles (in table columns) covering the range
+  int n_lev;              // levels = layers + 1
+  int n_species;
+  int species[HR2_MAX_SPECIES];
+  float mass[HR2_MAX_SPECIES];
+  double mass64[HR2_MAX_SPECIES];
+  int n_mu;
+  float mu_nlog2e[HR2_MAX_MU];   // -log2(e) / mu_k
+  float mu[HR2_MAX_MU];
+  float inv_mu[HR2_MAX_MU];
+  float wflux[HR2_MAX_MU];       // 2 pi w_k mu_k
+  double mu64[HR2_MAX_MU], wmu64[HR2_MAX_MU];  // Gauss-Legendre nodes and weights on [0,1]
+  int fe_elements, fe_order, n_tnodes;
+  double gll[HR2_MAX_TNODES];    // Gauss-Lobatto nodes on [0,1] (fe_order+1 of them)
+  double r_he, radius_cm;
+  int n_bins;
+  long long w_nnz;
+  const LevelDev* levels;        // [n_lev]
+  const long long* w_rowptr;     // [n_bins+1]
+  const int* w_col0;             // [n_bins] first setup point of row b
+  const float* w32;              // [nnz]
+  const double* w64;             // [nnz]
+  const double* obs_D;           // [n_bins] or null
+  const double* obs_sigma;       // [n_bins] or null
+  float cost;                    // relative cost of one work item (scheduling)
+  const TablesDev* tables;       // device copy
+};
+
+// Per-(sample, level) inputs of the FP32 forward kernel, written by the
+// prep kernel: table row, interpolation weights, CIA terms and Planck
+// factors.  Four 16-byte words.
+//
+// Exponents are kept small and exact in FP32: every exponent of the sample
+// is shifted by an integer power of two 2^shift (undone exactly in half_dp),
+// and each per-sample constant is split into an FP32 head and a tail that
+// enters as the factor (1 + ln2 * tail) on the exponential.
+struct __align__(16) LevRec {
+  int rowoff;        // a_j * n_p + b_j: row of corner (T cell a_j, p cell b_j)
+  float wT;          // weight of T_grid[a_j + 1]
+  float wp;          // weight of log10p_grid[b_j + 1]
+  float wTwp;        // wT * wp
+  float bh2h2;       // head of log2(x_H2^2 c n_j) + off_cia log2(10) - shift
+  float bh2he;       // head of log2(x_H2 x_He c n_j) + off_cia log2(10) - shift
+  float upl;         // head of -log2(e) h c / (k T_j): e^{-hc nu/kT} = 2^(upl nu)
+  float half_dp;     // 2^shift (p_{j+1} - p_j) / 2, dyn cm^-2 (layer j)
+  int acell;         // a_j
+  float upl_lo;      // tail of upl
+  float ch2h2;       // 1 + ln2 * (tail of bh2h2)
+  float ch2he;       // 1 + ln2 * (tail of bh2he)
+  float rdnu;        // e^{-h c dnu / (k T_j)}: Planck factor between neighbouring points
+  float pad0, pad1, pad2;
+};
+
+// Per-sample scalars written by the prep kernel.
+struct SampleDev {
+  float A[HR2_MAX_SPECIES];   // head of log2(x_s c) + off_s log2(10) - shift, c = 1/(mmw m_u g)
+  float Ac[HR2_MAX_SPECIES];  // 1 + ln2 * (its tail)
+  double scale;               // f (R_* / d)^2
+  int status;                 // HR2_SAMPLE_* bits
+  int setup;                  // setup index, -1 if invalid
+};
+
+// Work plan written by the planner kernel for one batch call.
+struct PlanDev {
+  int total_items;
+  int n_setups;
+  int order[HR2_MAX_SETUPS];        // setups in decreasing item cost
+  int count[HR2_MAX_SETUPS];        // samples per setup
+  int first[HR2_MAX_SETUPS];        // start of the setup's samples in perm
+  int n_sblocks[HR2_MAX_SETUPS];    // sample blocks per setup
+  int item_start[HR2_MAX_SETUPS + 1];  // by position in `order`
+};
+
+struct FwdArgs {
+  const SetupDev* setups[HR2_MAX_SETUPS];
+  int n_setups;
+  int n;
+  const int* setup_of_sample;
+  const double* params;
+  const int* perm;          // samples grouped by setup
+  const PlanDev* plan;
+  unsigned int* counter;    // work counter (reset by the planner)
+  float* highres;           // [n][highres_ld]: F+ (caller's or workspace)
+  int highres_ld;
+  double* highres64;        // FP64 path: F+ [n][highres64_ld] in the workspace
+  int highres64_ld;
+  float* user_highres;      // FP64 path: optional FP32 copy for the caller
+  int* status;              // [n] or null
+  LevRec* recs;             // [n][rec_ld]
+  int rec_ld;
+  SampleDev* samp;          // [n]
+  int warps;                // samples per work item
+};
+
+// Launchers (kern_*.cu).
+cudaError_t launch_prep(const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_plan(const FwdArgs& a, int* perm, PlanDev* plan, cudaStream_t s);
+cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, cudaStream_t s);
+cudaError_t launch_forward64(const FwdArgs& a, int max_nmu, int max_nu, cudaStream_t s);
+cudaError_t launch_bins(const FwdArgs& a, float* bins, int bins_ld, bool fp64, cudaStream_t s);
+struct LnlArgs {
+  const SetupDev* setups[HR2_MAX_SETUPS];
+  int n_setups;
+  const int* setup_of_sample;
+  const float* bins;
+  int bins_ld;
+  const double* log_eps;
+  int n;
+  double* lnl;
+};
+cudaError_t launch_lnl(const LnlArgs& a, cudaStream_t s);
+
+// Setup construction kernels (kern_setup.cu); asynchronous on s.
+cudaError_t build_setup_levels(int n_lev, double p_top, double p_bot, const TablesDev* d_tab, LevelDev* d_levels,
+                               cudaStream_t s);
+cudaError_t build_quadratures(int n_mu, int n_gll, double* d_out, cudaStream_t s);
+cudaError_t build_w_rows(const TablesDev* d_tab, int nu_first, int n_nu, double R, int n_bins, const double* d_edges,
+                         int* d_lo, int* d_hi, double* d_invz, int* d_bin, int* d_rowinfo, int* d_err,
+                         cudaStream_t s);
+cudaError_t build_w_values(const TablesDev* d_tab, int nu_first, double R, int n_bins, const int* d_lo,
+                           const int* d_hi, const double* d_invz, const int* d_rowinfo, const long long* d_rowptr,
+                           float* d_w32, double* d_w64, cudaStream_t s);
+cudaError_t quantise_fp16(const double* d_src, __half* d_dst, long long rows, int n_nu, int nu_pad, double off,
+                          cudaStream_t s);
+cudaError_t copy_pad_fp64(const double* d_src, double* d_dst, long long rows, int n_nu, int nu_pad,
+                          cudaStream_t s);
+
+}  // namespace hr2

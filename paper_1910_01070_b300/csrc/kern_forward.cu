@@ -1,0 +1,762 @@
+// kern_forward.cu -- the per-batch kernels of the forward model:
+//   k_prep       per (sample, level): T profile, interpolation cells and
+//                weights, CIA and Planck factors (FP64 math, FP32 records)
+//   k_plan       groups samples by setup and lays out the work items
+//   k_forward32  persistent FP32 kernel over (setup, wavenumber tile,
+//                sample block) items: opacity interpolation, absorption,
+//                optical depth, Planck source, short characteristics,
+//                angular quadrature -> F+
+//   k_forward64  the plain FP64 path: same steps in double, one thread per
+//                wavenumber, FP64 tables
+//   k_bins       instrument profile + binning via the setup's operator W
+//   k_lnl        Gaussian log-likelihood, FP64, fixed-order warp reduction
+#include <math.h>
+
+#include "hr2_internal.cuh"
+
+namespace hr2 {
+
+__device__ __forceinline__ float ex2f(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rcpf(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Continuous finite-element temperature at x in [0,1] (x = 0 bottom, 1 top):
+// element k of K_e, local coordinate on [0,1] with the Gauss-Lobatto nodes,
+// Lagrange basis (Sect. 2.5.1, Eqs. 12-16).  Node 0 is the bottom T_1.
+__device__ double fe_temperature(const SetupDev& S, const double* nodes, double x) {
+  const int Ke = S.fe_elements, q = S.fe_order;
+  int k = (int)floor(x * Ke);
+  k = k < 0 ? 0 : (k > Ke - 1 ? Ke - 1 : k);
+  const double loc = x * Ke - k;
+  double T = 0.0;
+  for (int i = 0; i <= q; ++i) {
+    double l = 1.0;
+    for (int m = 0; m <= q; ++m)
+      if (m != i) l *= (loc - S.gll[m]) / (S.gll[i] - S.gll[m]);
+    T += nodes[k * q + i] * l;
+  }
+  return T;
+}
+
+// Cell a with grid[a] <= v <= grid[a+1] and the weight of grid[a+1],
+// clamped to the grid ends (no extrapolation).
+__device__ void grid_cell(const double* grid, int n, double v, int& a, double& w) {
+  if (!(v > grid[0])) {
+    a = 0;
+    w = 0.0;
+    return;
+  }
+  if (v >= grid[n - 1]) {
+    a = n - 2;
+    w = 1.0;
+    return;
+  }
+  int lo = 0, hi = n - 1;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (grid[mid] < v) lo = mid;
+    else hi = mid;
+  }
+  a = lo;
+  w = (v - grid[lo]) / (grid[lo + 1] - grid[lo]);
+}
+
+// ------------------------------------------------------------------ prep
+// One warp per sample.  Free chemistry (Sect. 2.4): absorber mixing ratios
+// x_s, H2 and He fill the rest at n_He/n_H2 = r_he; the column factor
+// c = 1/(mmw m_u g) turns a cross-section per molecule into optical depth
+// per unit pressure (hydrostatic dm = dp/g).
+__global__ void k_prep(FwdArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= a.n) return;
+  SampleDev* sd = a.samp + i;
+  const int g = a.setup_of_sample[i];
+  if (g < 0 || g >= a.n_setups) {
+    if (lane == 0) {
+      sd->status = HR2_SAMPLE_BAD_SETUP;
+      sd->setup = -1;
+      sd->scale = 0.0;
+      if (a.status) a.status[i] = HR2_SAMPLE_BAD_SETUP;
+    }
+    return;
+  }
+  const SetupDev& S = *a.setups[g];
+  const TablesDev& T = *S.tables;
+  const double* th = a.params + (size_t)i * HR2_NPARAM;
+  int status = 0;
+  double sumx = 0.0, mabs = 0.0;
+  for (int s = 0; s < S.n_species; ++s) {
+    const double lx = th[HR2_P_X0 + s];
+    if (!isfinite(lx)) status |= HR2_SAMPLE_BAD_ABUND;
+    const double x = exp10(lx);
+    sumx += x;
+    mabs += x * S.mass64[s];
+  }
+  if (!(sumx < 1.0)) status |= HR2_SAMPLE_BAD_ABUND;
+  const double xh2 = (1.0 - sumx) / (1.0 + S.r_he);
+  const double xhe = S.r_he * xh2;
+  const double mmw = mabs + xh2 * kMassH2 + xhe * kMassHe;
+  const double grav = exp10(th[HR2_P_LOGG]);
+  const double f = th[HR2_P_F], dcm = th[HR2_P_DIST] * kParsec;
+  if (!(f > 0.0) || !(dcm > 0.0) || !isfinite(f) || !isfinite(dcm) || !isfinite(grav) || !(grav > 0.0))
+    status |= HR2_SAMPLE_BAD_SCALE;
+  const double c = 1.0 / (mmw * kAMU * grav);
+  const double lc = log2(c);
+  const double ratio = S.radius_cm / dcm;
+  // integer shift that centres the exponent of the dominant absorber
+  double amax = -1e300;
+  for (int s = 0; s < S.n_species; ++s)
+    amax = fmax(amax, th[HR2_P_X0 + s] * kLog2_10 + lc + T.off[S.species[s]] * kLog2_10);
+  const double shift = (S.n_species > 0 && isfinite(amax)) ? rint(amax) : 0.0;
+  if (lane < S.n_species) {
+    const double A = th[HR2_P_X0 + lane] * kLog2_10 + lc + T.off[S.species[lane]] * kLog2_10 - shift;
+    const float hi = (float)A;
+    sd->A[lane] = hi;
+    sd->Ac[lane] = (float)(1.0 + kLn2 * (A - (double)hi));
+  }
+
+  const int L = S.n_lev - 1;
+  LevRec* rec = a.recs + (size_t)i * a.rec_ld;
+  for (int j = lane; j <= L; j += 32) {
+    const double x = (double)(L - j) / (double)L;
+    const double Tj = fe_temperature(S, th + HR2_P_T0, x);
+    if (!(Tj > 0.0) || !isfinite(Tj)) status |= HR2_SAMPLE_BAD_T;
+    int acell;
+    double wT;
+    grid_cell(T.T_grid64, T.n_T, Tj, acell, wT);
+    const LevelDev lv = S.levels[j];
+    const double wp = lv.wp64;
+    LevRec r;
+    r.rowoff = acell * T.n_p + lv.pcell;
+    r.acell = acell;
+    r.wT = (float)wT;
+    r.wp = (float)wp;
+    r.wTwp = (float)(wT * wp);
+    const double ntot = lv.p_dyn64 / (kKB * Tj);
+    const double b0 = log2(xh2 * xh2 * c * ntot) + T.off[kCiaH2H2] * kLog2_10 - shift;
+    const double b1 = log2(xh2 * xhe * c * ntot) + T.off[kCiaH2He] * kLog2_10 - shift;
+    r.bh2h2 = (float)b0;
+    r.ch2h2 = (float)(1.0 + kLn2 * (b0 - (double)r.bh2h2));
+    r.bh2he = (float)b1;
+    r.ch2he = (float)(1.0 + kLn2 * (b1 - (double)r.bh2he));
+    const double upl = -kC2 * kLog2e / Tj;
+    r.upl = (float)upl;
+    r.upl_lo = (float)(upl - (double)r.upl);
+    r.half_dp = (float)ldexp(lv.half_dp64, (int)shift);
+    r.rdnu = (float)exp(-kC2 * T.dnu / Tj);
+    r.pad0 = r.pad1 = r.pad2 = 0.f;
+    rec[j] = r;
+  }
+  status = __reduce_or_sync(0xffffffffu, status);
+  if (lane == 0) {
+    sd->status = status;
+    sd->scale = f * ratio * ratio;
+    sd->setup = g;
+    if (a.status) a.status[i] = status;
+  }
+}
+
+cudaError_t launch_prep(const FwdArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  k_prep<<<(a.n + 7) / 8, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ plan
+// Counts samples per setup, orders setups by decreasing item cost, lays out
+// work items (setup, tile, sample block) with the sample block fastest so
+// that consecutive items share a wavenumber tile of the table, and writes
+// the samples of each setup contiguously (stable) into perm.
+__global__ void k_plan(FwdArgs a, int* perm, PlanDev* plan) {
+  __shared__ int cnt[HR2_MAX_SETUPS], base[HR2_MAX_SETUPS];
+  const int tid = threadIdx.x;
+  if (tid < HR2_MAX_SETUPS) cnt[tid] = 0;
+  __syncthreads();
+  for (int i = tid; i < a.n; i += blockDim.x) {
+    const int g = a.setup_of_sample[i];
+    if (g >= 0 && g < a.n_setups) atomicAdd(&cnt[g], 1);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int order[HR2_MAX_SETUPS];
+    for (int g = 0; g < a.n_setups; ++g) order[g] = g;
+    for (int p = 1; p < a.n_setups; ++p) {  // stable insertion sort, cost descending
+      int v = order[p], q = p - 1;
+      while (q >= 0 && a.setups[order[q]]->cost < a.setups[v]->cost) {
+        order[q + 1] = order[q];
+        --q;
+      }
+      order[q + 1] = v;
+    }
+    int first = 0;
+    for (int g = 0; g < a.n_setups; ++g) {
+      plan->first[g] = first;
+      base[g] = first;
+      plan->count[g] = cnt[g];
+      plan->n_sblocks[g] = (cnt[g] + a.warps - 1) / a.warps;
+      first += cnt[g];
+    }
+    int items = 0;
+    for (int p = 0; p < a.n_setups; ++p) {
+      const int g = order[p];
+      plan->order[p] = g;
+      plan->item_start[p] = items;
+      items += plan->n_sblocks[g] * a.setups[g]->n_tiles;
+    }
+    plan->item_start[a.n_setups] = items;
+    plan->total_items = items;
+    plan->n_setups = a.n_setups;
+    *a.counter = 0u;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const int lane = tid;
+    for (int c0 = 0; c0 < a.n; c0 += 32) {
+      const int i = c0 + lane;
+      const int g = (i < a.n) ? a.setup_of_sample[i] : -1;
+      const bool ok = g >= 0 && g < a.n_setups;
+      const int key = ok ? g : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int rank = __popc(peers & ((1u << lane) - 1u));
+      const int leader = __ffs(peers) - 1;
+      const int b = ok ? base[g] : 0;
+      __syncwarp();
+      if (ok) perm[b + rank] = i;
+      if (ok && lane == leader) base[g] = b + __popc(peers);
+      __syncwarp();
+    }
+  }
+}
+
+cudaError_t launch_plan(const FwdArgs& a, int* perm, PlanDev* plan, cudaStream_t s) {
+  k_plan<<<1, 1024, 0, s>>>(a, perm, plan);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- FP32 forward
+// Packed two-wide FP32 arithmetic (Blackwell f32x2): each lane carries two
+// neighbouring wavenumbers through the whole level sweep, so every FMA, add
+// and multiply of the path issues once for both.
+typedef unsigned long long v2;
+__device__ __forceinline__ v2 pk(float a, float b) {
+  v2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ v2 pk(float a) { return pk(a, a); }
+__device__ __forceinline__ float2 up(v2 r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ v2 fma2(v2 a, v2 b, v2 c) {
+  v2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ v2 add2(v2 a, v2 b) {
+  v2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ v2 sub2(v2 a, v2 b) {
+  v2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ v2 mul2(v2 a, v2 b) {
+  v2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ v2 ex2_2(v2 x) {
+  const float2 f = up(x);
+  return pk(ex2f(f.x), ex2f(f.y));
+}
+__device__ __forceinline__ v2 rcp_2(v2 x) {
+  const float2 f = up(x);
+  return pk(rcpf(f.x), rcpf(f.y));
+}
+__device__ __forceinline__ v2 h2f2(unsigned int h) {
+  const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&h));
+  return pk(f.x, f.y);
+}
+__device__ __forceinline__ unsigned int ldh2(const __half* p) {
+  return __ldg(reinterpret_cast<const unsigned int*>(p));
+}
+
+// log2(10) as an FP32 head and tail
+constexpr float kL2Hi = 3.32192802f;
+constexpr float kL2Lo = (float)(kLog2_10 - (double)kL2Hi);
+// below this optical thickness D the linear-source factor (1 - e^{-D}) / D
+// comes from its series instead of from 1 - e^{-D}
+constexpr float kThinD = 0.25f;
+
+// One warp computes one sample on one 64-point wavenumber tile (two points
+// per lane), sweeping the levels from the top (j = 0) to the bottom (j = L):
+//   log10 sigma_s: bilinear in (T, log10 p) written as corner 00 plus
+//                  weighted differences (exact partition of unity)
+//   chi_j = sum_s x_s c sigma_s + CIA     (Sects. 2.3, 2.8; 2^(A_s + ...))
+//   dtau_l = (chi_l + chi_{l+1}) (p_{l+1} - p_l) / 2
+//   S_j = B_nu(T_j) = c1 nu^3 t / (1 - t), t = e^{-hc nu / kT_j}      (Eq. 2)
+// Short characteristics with a linear source (Eqs. 4-7): layer l adds
+//   beta_l S_l + gamma_l S_{l+1},  beta = 1 - q, gamma = q - e^{-D},
+//   q = (1 - e^{-D}) / D,  D = dtau_l / mu,
+// to the intensity entering it from below, with B(T_L) entering the bottom.
+// Unrolling that recursion and collecting the terms of each S gives the same
+// emergent intensity as a telescoped sum over layers:
+//   I_0(mu) = S_0 + mu sum_l (E_l - E_{l+1}) (S_{l+1} - S_l) / dtau_l,
+//   E_l = e^{-tau_l / mu}, tau_l the optical depth of level l from the top,
+// i.e. the formal solution (Eq. 1) integrated by parts for a piecewise-
+// linear source.  Each E_l comes directly from the cumulative tau_l, so the
+// small bias of the hardware exponential cannot compound over the layers.
+// For optically thin layers (D < kThinD) the difference is taken as
+//   E_l - E_{l+1} = E_l D q(D),  q = 1 - D/2 + D^2/6 - ... (no cancellation).
+//   F+ = 2 pi sum_k w_k mu_k I_0(mu_k)                             (Eq. 8)
+template <int NMU>
+__device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
+                                           const v2* sA2, const v2* sAc2, const __half* const* sPtr,
+                                           const v2* sMnl, const v2* sImu) {
+  const int lane = threadIdx.x & 31;
+  const SampleDev& sd = a.samp[i];
+  float* out = a.highres + (size_t)i * a.highres_ld;
+  const int col = (S.tile0 + tile) * kTileNu + 2 * lane;  // table column of point 0
+  const int k0 = col - S.nu_first;
+  const bool in0 = k0 >= 0 && k0 < S.n_nu;
+  const bool in1 = k0 + 1 >= 0 && k0 + 1 < S.n_nu;
+  if (sd.status != 0) {
+    if (in0) out[k0] = __int_as_float(0x7fc00000);
+    if (in1) out[k0 + 1] = __int_as_float(0x7fc00000);
+    return;
+  }
+  const double nu0d = T.nu0 + (double)col * T.dnu, nu1d = T.nu0 + (double)(col + 1) * T.dnu;
+  const float nu0 = (float)nu0d;                       // head
+  const float nl0 = (float)(nu0d - (double)nu0);       // tail
+  const float nu_ratio = (float)(nu1d / nu0d);
+  const v2 c1n = pk((float)(kC1 * nu0d * nu0d * nu0d), (float)(kC1 * nu1d * nu1d * nu1d));
+  const int nmu = S.n_mu;
+  const float thin_dtau = kThinD * S.mu[nmu - 1];   // dtau below which some node is thin
+  const int K = S.n_species;
+  const int nu_pad = T.nu_pad;
+  const unsigned o10 = (unsigned)(T.n_p * nu_pad);
+  const bool cia0 = T.has_cia[0] != 0, cia1 = T.has_cia[1] != 0;
+  const __half* __restrict__ ciab0 = T.cia16;
+  const __half* __restrict__ ciab1 = T.cia16 + (size_t)T.n_T * nu_pad;
+  const LevRec* __restrict__ rec = a.recs + (size_t)i * a.rec_ld;
+  const int L = S.n_lev - 1;
+  const float kLn2f = 0.6931471805599453f;
+  const v2 one = pk(1.f), L2hi = pk(kL2Hi), L2lo = pk(kL2Lo);
+
+  v2 acc[NMU], E[NMU];
+#pragma unroll
+  for (int k = 0; k < NMU; ++k) {
+    acc[k] = pk(0.f);
+    E[k] = one;
+  }
+  v2 chip = pk(0.f), Sp = pk(0.f), S0 = pk(0.f), tau = pk(0.f);
+  float hdp_prev = 0.f;
+  for (int j = 0; j <= L; ++j) {
+    const float4* rp = reinterpret_cast<const float4*>(rec + j);
+    const float4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3);
+    const unsigned rb00 = (unsigned)__float_as_int(r0.x) * (unsigned)nu_pad + (unsigned)col;
+    const unsigned rb10 = rb00 + o10, rb01 = rb00 + (unsigned)nu_pad, rb11 = rb10 + (unsigned)nu_pad;
+    const v2 wT = pk(r0.y), wp = pk(r0.z), wq = pk(r0.w);
+
+    // absorption coefficient: two species per step for independent chains
+    v2 chiA = pk(0.f), chiB = pk(0.f);
+    int s = 0;
+    for (; s + 1 < K; s += 2) {
+      const __half* b = sPtr[s];
+      const __half* c = sPtr[s + 1];
+      const v2 f00 = h2f2(ldh2(b + rb00)), f10 = h2f2(ldh2(b + rb10));
+      const v2 f01 = h2f2(ldh2(b + rb01)), f11 = h2f2(ldh2(b + rb11));
+      const v2 g00 = h2f2(ldh2(c + rb00)), g10 = h2f2(ldh2(c + rb10));
+      const v2 g01 = h2f2(ldh2(c + rb01)), g11 = h2f2(ldh2(c + rb11));
+      const v2 d01 = sub2(f01, f00), e01 = sub2(g01, g00);
+      const v2 d11 = sub2(sub2(f11, f10), d01), e11 = sub2(sub2(g11, g10), e01);
+      const v2 l = fma2(wq, d11, fma2(wp, d01, fma2(wT, sub2(f10, f00), f00)));
+      const v2 m = fma2(wq, e11, fma2(wp, e01, fma2(wT, sub2(g10, g00), g00)));
+      const v2 el = fma2(L2lo, l, fma2(L2hi, l, sA2[s]));
+      const v2 em = fma2(L2lo, m, fma2(L2hi, m, sA2[s + 1]));
+      chiA = fma2(sAc2[s], ex2_2(el), chiA);
+      chiB = fma2(sAc2[s + 1], ex2_2(em), chiB);
+    }
+    if (s < K) {
+      const __half* b = sPtr[s];
+      const v2 f00 = h2f2(ldh2(b + rb00)), f10 = h2f2(ldh2(b + rb10));
+      const v2 f01 = h2f2(ldh2(b + rb01)), f11 = h2f2(ldh2(b + rb11));
+      const v2 d01 = sub2(f01, f00);
+      const v2 d11 = sub2(sub2(f11, f10), d01);
+      const v2 l = fma2(wq, d11, fma2(wp, d01, fma2(wT, sub2(f10, f00), f00)));
+      const v2 el = fma2(L2lo, l, fma2(L2hi, l, sA2[s]));
+      chiA = fma2(sAc2[s], ex2_2(el), chiA);
+    }
+    if (cia0 || cia1) {
+      const unsigned cb = (unsigned)__float_as_int(r2.x) * (unsigned)nu_pad + (unsigned)col;
+      if (cia0) {
+        const v2 c0 = h2f2(ldh2(ciab0 + cb)), c1 = h2f2(ldh2(ciab0 + cb + nu_pad));
+        const v2 l = fma2(wT, sub2(c1, c0), c0);
+        const v2 e = fma2(L2lo, l, fma2(L2hi, l, pk(r1.x)));
+        chiB = fma2(pk(r2.z), ex2_2(e), chiB);
+      }
+      if (cia1) {
+        const v2 c0 = h2f2(ldh2(ciab1 + cb)), c1 = h2f2(ldh2(ciab1 + cb + nu_pad));
+        const v2 l = fma2(wT, sub2(c1, c0), c0);
+        const v2 e = fma2(L2lo, l, fma2(L2hi, l, pk(r1.y)));
+        chiA = fma2(pk(r2.w), ex2_2(e), chiA);
+      }
+    }
+    const v2 chi = add2(chiA, chiB);
+    // Planck source.  t at the lane's first point: the exponent upl * nu to
+    // ~2^-46 (head product, its exact FMA error and the tail cross terms),
+    // t = 2^head (1 + ln2 * tail); the neighbour point is t * e^{-hc dnu/kT}.
+    v2 Sj;
+    {
+      const float upl = r1.z, upl_lo = r2.y;
+      const float p0 = upl * nu0;
+      const float y0 = fmaf(upl, nu0, -p0) + fmaf(upl, nl0, upl_lo * nu0);
+      const float h0 = ex2f(p0);
+      const float t0 = fmaf(h0, y0 * kLn2f, h0);
+      const v2 t = pk(t0, t0 * r3.x);
+      v2 om = sub2(one, t);
+      const float x0 = -p0 * kLn2f;  // hc nu / kT of the lane's first (smaller) point
+      if (__any_sync(0xffffffffu, x0 < 0.0625f)) {
+        // 1 - e^{-x} without cancellation for small x
+        const v2 x = pk(x0, x0 * nu_ratio);
+        const v2 ser = mul2(x, fma2(mul2(x, pk(-0.5f)),
+                                    fma2(mul2(x, pk(-1.f / 3.f)), fma2(pk(-0.25f), x, one), one), one));
+        const float2 xf = up(x), sf = up(ser), of = up(om);
+        om = pk(xf.x < 0.0625f ? sf.x : of.x, xf.y < 0.0625f ? sf.y : of.y);
+      }
+      Sj = mul2(mul2(c1n, t), rcp_2(om));
+    }
+    if (j == 0) {
+      S0 = Sj;
+    } else {
+      // layer j-1 between levels j-1 (top, Sp) and j (bottom, Sj)
+      const v2 dt = mul2(pk(hdp_prev), add2(chi, chip));
+      const v2 rr = rcp_2(dt);
+      const v2 dS = sub2(Sj, Sp);
+      tau = add2(tau, dt);
+      const float2 dtf = up(dt);
+      const bool thin = __any_sync(0xffffffffu, fminf(dtf.x, dtf.y) < thin_dtau);
+#pragma unroll
+      for (int k = 0; k < NMU; ++k) {
+        if (k < nmu) {
+          const v2 En = ex2_2(mul2(tau, sMnl[k]));   // e^{-tau_j / mu}
+          v2 c = mul2(sub2(E[k], En), rr);           // (E_{j-1} - E_j) / dtau
+          if (thin) {
+            // E_{j-1} q(D) / mu with q(D) = (1 - e^{-D}) / D by its series
+            const v2 im = sImu[k];
+            const v2 D = mul2(dt, im);
+            const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
+                                                              pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
+            const v2 cs = mul2(mul2(E[k], qs), im);
+            const float2 Df = up(D), csf = up(cs), cf = up(c);
+            c = pk(Df.x < kThinD ? csf.x : cf.x, Df.y < kThinD ? csf.y : cf.y);
+          }
+          acc[k] = fma2(c, dS, acc[k]);
+          E[k] = En;
+        }
+      }
+    }
+    chip = chi;
+    Sp = Sj;
+    hdp_prev = r1.w;
+  }
+  // I_0(mu_k) = S_0 + mu_k acc_k;  F+ = sum_k 2 pi w_k mu_k I_0(mu_k)
+  float F0 = 0.f, F1 = 0.f;
+  const float2 s0 = up(S0);
+#pragma unroll
+  for (int k = 0; k < NMU; ++k) {
+    if (k < nmu) {
+      const float2 f = up(acc[k]);
+      const float mk = S.mu[k], wk = S.wflux[k];
+      F0 = fmaf(wk, fmaf(mk, f.x, s0.x), F0);
+      F1 = fmaf(wk, fmaf(mk, f.y, s0.y), F1);
+    }
+  }
+  if (in0) out[k0] = F0;
+  if (in1) out[k0 + 1] = F1;
+}
+
+template <int NMU>
+__global__ void __launch_bounds__(512) k_forward32(FwdArgs a) {
+  __shared__ int s_item;
+  __shared__ const __half* sPtr[HR2_MAX_SPECIES];
+  __shared__ v2 sMnl[NMU], sImu[NMU];
+  __shared__ v2 sA2[kMaxWarps][HR2_MAX_SPECIES];
+  __shared__ v2 sAc2[kMaxWarps][HR2_MAX_SPECIES];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const PlanDev* plan = a.plan;
+  const int total = plan->total_items;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (int)atomicAdd(a.counter, 1u);
+    __syncthreads();
+    const int item = s_item;
+    if (item >= total) break;
+    int pos = 0;
+    while (item >= plan->item_start[pos + 1]) ++pos;
+    const int g = plan->order[pos];
+    const int rem = item - plan->item_start[pos];
+    const int nsb = plan->n_sblocks[g];
+    const int tile = rem / nsb;
+    const int sb = rem - tile * nsb;
+    const SetupDev& S = *a.setups[g];
+    const TablesDev& T = *S.tables;
+    if (threadIdx.x < S.n_species)
+      sPtr[threadIdx.x] = T.sig16 + (size_t)S.species[threadIdx.x] * T.n_T * T.n_p * T.nu_pad;
+    if (threadIdx.x < NMU) {
+      const bool on = (int)threadIdx.x < S.n_mu;
+      sMnl[threadIdx.x] = pk(on ? S.mu_nlog2e[threadIdx.x] : 0.f);
+      sImu[threadIdx.x] = pk(on ? S.inv_mu[threadIdx.x] : 0.f);
+    }
+    const int local = sb * a.warps + warp;
+    const bool active = local < plan->count[g];
+    const int i = active ? a.perm[plan->first[g] + local] : 0;
+    if (active && lane < S.n_species) {
+      sA2[warp][lane] = pk(a.samp[i].A[lane]);
+      sAc2[warp][lane] = pk(a.samp[i].Ac[lane]);
+    }
+    __syncthreads();
+    if (active) solve_tile<NMU>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu);
+  }
+}
+
+cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, cudaStream_t s) {
+  const int threads = 32 * a.warps;
+  switch (max_nmu) {
+    case 1: k_forward32<1><<<grid, threads, 0, s>>>(a); break;
+    case 2: k_forward32<2><<<grid, threads, 0, s>>>(a); break;
+    case 3: k_forward32<3><<<grid, threads, 0, s>>>(a); break;
+    case 4: k_forward32<4><<<grid, threads, 0, s>>>(a); break;
+    case 5: k_forward32<5><<<grid, threads, 0, s>>>(a); break;
+    case 6: k_forward32<6><<<grid, threads, 0, s>>>(a); break;
+    case 7: k_forward32<7><<<grid, threads, 0, s>>>(a); break;
+    case 8: k_forward32<8><<<grid, threads, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------- FP64 forward
+// The plain FP64 path: one thread per wavenumber point, one block per
+// (sample, 128-point chunk), FP64 tables, exp/expm1 in double.
+constexpr int kF64Block = 128;
+
+template <int NMU>
+__global__ void __launch_bounds__(kF64Block) k_forward64(FwdArgs a) {
+  __shared__ double sT[HR2_MAX_LEVELS], sN[HR2_MAX_LEVELS], swT[HR2_MAX_LEVELS];
+  __shared__ int sa[HR2_MAX_LEVELS];
+  __shared__ double sx[HR2_MAX_SPECIES];
+  __shared__ double sc[3];
+  const int i = blockIdx.y;
+  const SampleDev& sd = a.samp[i];
+  if (sd.setup < 0) return;
+  const SetupDev& S = *a.setups[sd.setup];
+  const TablesDev& T = *S.tables;
+  if (blockIdx.x * kF64Block >= S.n_nu) return;
+  const int k = blockIdx.x * kF64Block + threadIdx.x;
+  double* out = a.highres64 + (size_t)i * a.highres64_ld;
+  float* uout = a.user_highres ? a.user_highres + (size_t)i * a.highres_ld : nullptr;
+  if (sd.status != 0) {
+    if (k < S.n_nu) {
+      out[k] = __longlong_as_double(0x7ff8000000000000ll);
+      if (uout) uout[k] = __int_as_float(0x7fc00000);
+    }
+    return;
+  }
+  const double* th = a.params + (size_t)i * HR2_NPARAM;
+  if (threadIdx.x < S.n_species) sx[threadIdx.x] = exp10(th[HR2_P_X0 + threadIdx.x]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sumx = 0.0, mabs = 0.0;
+    for (int s = 0; s < S.n_species; ++s) {
+      sumx += sx[s];
+      mabs += sx[s] * S.mass64[s];
+    }
+    const double xh2 = (1.0 - sumx) / (1.0 + S.r_he);
+    const double xhe = S.r_he * xh2;
+    const double mmw = mabs + xh2 * kMassH2 + xhe * kMassHe;
+    sc[0] = 1.0 / (mmw * kAMU * exp10(th[HR2_P_LOGG]));
+    sc[1] = xh2;
+    sc[2] = xhe;
+  }
+  const int L = S.n_lev - 1;
+  for (int j = threadIdx.x; j <= L; j += kF64Block) {
+    const double Tj = fe_temperature(S, th + HR2_P_T0, (double)(L - j) / (double)L);
+    int ac;
+    double w;
+    grid_cell(T.T_grid64, T.n_T, Tj, ac, w);
+    sT[j] = Tj;
+    sa[j] = ac;
+    swT[j] = w;
+    sN[j] = S.levels[j].p_dyn64 / (kKB * Tj);
+  }
+  __syncthreads();
+  if (k >= S.n_nu) return;
+  const double c = sc[0], xh2 = sc[1], xhe = sc[2];
+  const int col = S.nu_first + k;
+  const double nu = T.nu0 + (double)col * T.dnu;
+  const int nu_pad = T.nu_pad, np = T.n_p;
+  double I[NMU];
+  double chip = 0.0, Sp = 0.0;
+  for (int j = L; j >= 0; --j) {
+    const LevelDev& lv = S.levels[j];
+    const double wT = swT[j], wp = lv.wp64;
+    const size_t row = ((size_t)sa[j] * np + lv.pcell) * nu_pad + col;
+    double chi = 0.0;
+    for (int s = 0; s < S.n_species; ++s) {
+      const double* t = T.sig64 + (size_t)S.species[s] * T.n_T * np * nu_pad + row;
+      const double v = (1.0 - wT) * (1.0 - wp) * t[0] + wT * (1.0 - wp) * t[(size_t)np * nu_pad] +
+                       (1.0 - wT) * wp * t[nu_pad] + wT * wp * t[(size_t)(np + 1) * nu_pad];
+      chi += sx[s] * exp10(v);
+    }
+    for (int p = 0; p < 2; ++p) {
+      if (!T.has_cia[p]) continue;
+      const double* t = T.cia64 + (size_t)p * T.n_T * nu_pad + (size_t)sa[j] * nu_pad + col;
+      const double v = (1.0 - wT) * t[0] + wT * t[nu_pad];
+      chi += xh2 * (p == 0 ? xh2 : xhe) * sN[j] * exp10(v);
+    }
+    const double Sj = kC1 * nu * nu * nu / expm1(kC2 * nu / sT[j]);
+    if (j == L) {
+#pragma unroll
+      for (int m = 0; m < NMU; ++m) I[m] = Sj;
+    } else {
+      const double dtau = (chi + chip) * lv.half_dp64 * c;
+#pragma unroll
+      for (int m = 0; m < NMU; ++m) {
+        if (m < S.n_mu) {
+          const double D = dtau / S.mu64[m];
+          const double e = exp(-D);
+          const double q = (D > 0.0) ? -expm1(-D) / D : 1.0;
+          I[m] = I[m] * e + (1.0 - q) * Sj + (q - e) * Sp;
+        }
+      }
+    }
+    chip = chi;
+    Sp = Sj;
+  }
+  double F = 0.0;
+#pragma unroll
+  for (int m = 0; m < NMU; ++m)
+    if (m < S.n_mu) F += S.wmu64[m] * S.mu64[m] * I[m];
+  F *= 2.0 * kPi;
+  out[k] = F;
+  if (uout) uout[k] = (float)F;
+}
+
+cudaError_t launch_forward64(const FwdArgs& a, int max_nmu, int max_nu, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  dim3 grid((max_nu + kF64Block - 1) / kF64Block, a.n);
+  switch (max_nmu) {
+    case 1: k_forward64<1><<<grid, kF64Block, 0, s>>>(a); break;
+    case 2: k_forward64<2><<<grid, kF64Block, 0, s>>>(a); break;
+    case 3: k_forward64<3><<<grid, kF64Block, 0, s>>>(a); break;
+    case 4: k_forward64<4><<<grid, kF64Block, 0, s>>>(a); break;
+    case 5: k_forward64<5><<<grid, kF64Block, 0, s>>>(a); break;
+    case 6: k_forward64<6><<<grid, kF64Block, 0, s>>>(a); break;
+    case 7: k_forward64<7><<<grid, kF64Block, 0, s>>>(a); break;
+    case 8: k_forward64<8><<<grid, kF64Block, 0, s>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ bins
+// D_m,b = f (R_star/d)^2 sum_m W[b][m] F+_m: the instrument profile and the
+// binning as one banded operator (Sects. 2.7-2.8).  One block per sample,
+// one warp per bin, fixed-order butterfly reduction.
+template <bool FP64>
+__global__ void __launch_bounds__(256) k_bins(FwdArgs a, float* bins, int bins_ld) {
+  const int i = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const SampleDev& sd = a.samp[i];
+  float* out = bins + (size_t)i * bins_ld;
+  const float qnan = __int_as_float(0x7fc00000);
+  if (sd.setup < 0) {
+    for (int b = threadIdx.x; b < bins_ld; b += blockDim.x) out[b] = qnan;
+    return;
+  }
+  const SetupDev& S = *a.setups[sd.setup];
+  if (sd.status != 0) {
+    for (int b = threadIdx.x; b < S.n_bins; b += blockDim.x) out[b] = qnan;
+    return;
+  }
+  for (int b = warp; b < S.n_bins; b += nw) {
+    const long long r0 = S.w_rowptr[b], r1 = S.w_rowptr[b + 1];
+    const int c0 = S.w_col0[b];
+    if (FP64) {
+      const double* F = a.highres64 + (size_t)i * a.highres64_ld + c0;
+      double acc = 0.0;
+      for (long long t = r0 + lane; t < r1; t += 32) acc += S.w64[t] * F[t - r0];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) out[b] = (float)(acc * sd.scale);
+    } else {
+      const float* F = a.highres + (size_t)i * a.highres_ld + c0;
+      float acc = 0.f;
+      for (long long t = r0 + lane; t < r1; t += 32) acc = fmaf(S.w32[t], F[t - r0], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) out[b] = (float)((double)acc * sd.scale);
+    }
+  }
+}
+
+cudaError_t launch_bins(const FwdArgs& a, float* bins, int bins_ld, bool fp64, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  if (fp64) k_bins<true><<<a.n, 256, 0, s>>>(a, bins, bins_ld);
+  else k_bins<false><<<a.n, 256, 0, s>>>(a, bins, bins_ld);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ lnL
+// ln L = sum_j -(D_j - D_m,j)^2 / (2 s_j^2) - ln(2 pi s_j^2) / 2, with
+// s_j^2 = sigma_j^2 (+ 10^eps) (Eqs. 19, 22-23).  One warp per sample, FP64,
+// fixed-order butterfly reduction.
+__global__ void __launch_bounds__(256) k_lnl(LnlArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (i >= a.n) return;
+  const int g = a.setup_of_sample[i];
+  if (g < 0 || g >= a.n_setups) {
+    if (lane == 0) a.lnl[i] = -HUGE_VAL;
+    return;
+  }
+  const SetupDev& S = *a.setups[g];
+  const double eps = a.log_eps ? a.log_eps[i] : __longlong_as_double(0x7ff8000000000000ll);
+  const double add = isfinite(eps) ? exp10(eps) : 0.0;
+  const float* m = a.bins + (size_t)i * a.bins_ld;
+  double acc = 0.0;
+  int bad = 0;
+  for (int b = lane; b < S.n_bins; b += 32) {
+    const double dm = (double)m[b];
+    if (!isfinite(dm)) bad = 1;
+    const double sg = S.obs_sigma[b];
+    const double s2 = sg * sg + add;
+    const double r = S.obs_D[b] - dm;
+    acc += -r * r / (2.0 * s2) - 0.5 * log(2.0 * kPi * s2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  bad = __reduce_or_sync(0xffffffffu, bad);
+  if (lane == 0) a.lnl[i] = bad ? -HUGE_VAL : acc;
+}
+
+cudaError_t launch_lnl(const LnlArgs& a, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  k_lnl<<<(a.n + 7) / 8, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace hr2

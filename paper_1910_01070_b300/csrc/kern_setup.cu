@@ -1,0 +1,304 @@
+// kern_setup.cu -- device kernels run once per table or setup creation:
+// table quantisation, level grid, quadrature nodes and the combined
+// instrument-profile + binning operator W.  All in FP64.
+#include "hr2_internal.cuh"
+
+namespace hr2 {
+
+// ---------------------------------------------------------------- tables
+__global__ void k_quantise_fp16(const double* __restrict__ src, __half* __restrict__ dst, long long rows, int n_nu,
+                                int nu_pad, double off) {
+  long long total = rows * (long long)nu_pad;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long r = t / nu_pad;
+    int c = (int)(t - r * nu_pad);
+    // binary16 of (value - offset), round to nearest even
+    dst[t] = (c < n_nu) ? __double2half(src[r * n_nu + c] - off) : __double2half(0.0);
+  }
+}
+
+__global__ void k_copy_pad_fp64(const double* __restrict__ src, double* __restrict__ dst, long long rows, int n_nu,
+                                int nu_pad) {
+  long long total = rows * (long long)nu_pad;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long r = t / nu_pad;
+    int c = (int)(t - r * nu_pad);
+    dst[t] = (c < n_nu) ? src[r * n_nu + c] : 0.0;
+  }
+}
+
+cudaError_t quantise_fp16(const double* d_src, __half* d_dst, long long rows, int n_nu, int nu_pad, double off,
+                          cudaStream_t s) {
+  long long total = rows * (long long)nu_pad;
+  int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  k_quantise_fp16<<<grid, 256, 0, s>>>(d_src, d_dst, rows, n_nu, nu_pad, off);
+  return cudaGetLastError();
+}
+
+cudaError_t copy_pad_fp64(const double* d_src, double* d_dst, long long rows, int n_nu, int nu_pad,
+                          cudaStream_t s) {
+  long long total = rows * (long long)nu_pad;
+  int grid = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  k_copy_pad_fp64<<<grid, 256, 0, s>>>(d_src, d_dst, rows, n_nu, nu_pad);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ quadratures
+// Legendre P_n and P'_n at x by the three-term recurrence.
+__device__ void legendre_pd(int n, double x, double& p, double& dp) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) {
+    p = 1.0;
+    dp = 0.0;
+    return;
+  }
+  for (int k = 2; k <= n; ++k) {
+    double p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  p = p1;
+  dp = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+// out = [mu (n_mu, ascending) | w (n_mu) | gll (n_gll)], all on [0,1].
+// Gauss-Legendre nodes (angle quadrature of Eq. 8) by Newton on P_n;
+// Gauss-Lobatto points of the reference element (Sect. 2.5.1) as the end
+// points plus the roots of P'_{n_gll-1}.
+__global__ void k_quadratures(int n_mu, int n_gll, double* out) {
+  int t = threadIdx.x;
+  if (t < n_mu) {
+    int n = n_mu;
+    int i = t;
+    double x = cos(kPi * (i + 0.75) / (n + 0.5));
+    double p, dp;
+    for (int it = 0; it < 60; ++it) {
+      legendre_pd(n, x, p, dp);
+      double dx = p / dp;
+      x -= dx;
+      if (fabs(dx) < 1e-16) break;
+    }
+    legendre_pd(n, x, p, dp);
+    out[n - 1 - i] = 0.5 * (x + 1.0);
+    out[n_mu + n - 1 - i] = 1.0 / ((1.0 - x * x) * dp * dp);  // = w_x / 2
+  }
+  if (t < n_gll) {
+    int N = n_gll - 1;
+    double v;
+    if (t == 0) {
+      v = 0.0;
+    } else if (t == N) {
+      v = 1.0;
+    } else {
+      double x = -cos(kPi * t / N);
+      for (int it = 0; it < 60; ++it) {
+        double p, dp;
+        legendre_pd(N, x, p, dp);
+        double d2p = (2.0 * x * dp - N * (N + 1.0) * p) / (1.0 - x * x);
+        double dx = dp / d2p;
+        x -= dx;
+        if (fabs(dx) < 1e-16) break;
+      }
+      v = 0.5 * (x + 1.0);
+    }
+    out[2 * n_mu + t] = v;
+  }
+}
+
+cudaError_t build_quadratures(int n_mu, int n_gll, double* d_out, cudaStream_t s) {
+  k_quadratures<<<1, 32, 0, s>>>(n_mu, n_gll, d_out);
+  return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- levels
+// Level j (0 = top) at log10 p_j = lt + (lb - lt) j / L (equidistant in
+// log p, Sect. 2); the p-grid cell of the table that brackets it (clamped to
+// the grid ends) and the half pressure thickness of layer j.
+__device__ double level_log10p(int j, int L, double lt, double lb) { return lt + (lb - lt) * (double)j / (double)L; }
+
+__global__ void k_levels(int n_lev, double lt, double lb, const TablesDev* tab, LevelDev* lev) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_lev) return;
+  int L = n_lev - 1;
+  double lp = level_log10p(j, L, lt, lb);
+  double p = pow(10.0, lp) * kBar;
+  const double* g = tab->log10p_grid64;
+  int np = tab->n_p;
+  int b;
+  double w;
+  if (lp <= g[0]) {
+    b = 0;
+    w = 0.0;
+  } else if (lp >= g[np - 1]) {
+    b = np - 2;
+    w = 1.0;
+  } else {
+    b = 0;
+    while (g[b + 1] < lp) ++b;
+    w = (lp - g[b]) / (g[b + 1] - g[b]);
+  }
+  double half_dp = 0.0;
+  if (j < L) {
+    double pn = pow(10.0, level_log10p(j + 1, L, lt, lb)) * kBar;
+    half_dp = 0.5 * (pn - p);
+  }
+  LevelDev d;
+  d.pcell = b;
+  d.wp = (float)w;
+  d.wp64 = w;
+  d.p_dyn = (float)p;
+  d.p_dyn64 = p;
+  d.half_dp = (float)half_dp;
+  d.half_dp64 = half_dp;
+  lev[j] = d;
+}
+
+cudaError_t build_setup_levels(int n_lev, double p_top, double p_bot, const TablesDev* d_tab, LevelDev* d_levels,
+                               cudaStream_t s) {
+  k_levels<<<(n_lev + 127) / 128, 128, 0, s>>>(n_lev, log10(p_top), log10(p_bot), d_tab, d_levels);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------ instrument profile + bins
+// Gaussian instrument profile (Sect. 2.7): sigma_i = nu_i / (R 2 sqrt(2 ln 2))
+// centred on output point i, kept for |nu_m - nu_i| <= 5 sigma_i and
+// renormalised over the kept points.  Binning (Sect. 2.8): point i belongs to
+// bin b when edge_b <= nu_i < edge_{b+1} (the last bin closed).
+constexpr double kFwhmToSigma = 2.3548200450309493;  // 2 sqrt(2 ln 2)
+
+__device__ double setup_nu(const TablesDev& t, int nu_first, int i) {
+  return __dadd_rn(t.nu0, __dmul_rn((double)(nu_first + i), t.dnu));
+}
+
+__global__ void k_w_points(const TablesDev* tab, int nu_first, int n_nu, double R, int n_bins,
+                           const double* __restrict__ edges, int* lo, int* hi, double* invz, int* bin) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_nu) return;
+  const TablesDev& t = *tab;
+  double nui = setup_nu(t, nu_first, i);
+  if (R > 0.0) {
+    double sig = nui / (R * kFwhmToSigma);
+    double reach = 5.0 * sig;
+    int k = (int)(reach / t.dnu) + 2;
+    int a = max(0, i - k), b = min(n_nu - 1, i + k);
+    while (a < i && fabs(setup_nu(t, nu_first, a) - nui) > reach) ++a;
+    while (b > i && fabs(setup_nu(t, nu_first, b) - nui) > reach) --b;
+    double z = 0.0;
+    for (int m = a; m <= b; ++m) {
+      double dx = setup_nu(t, nu_first, m) - nui;
+      z += exp(-dx * dx / (2.0 * sig * sig));
+    }
+    lo[i] = a;
+    hi[i] = b;
+    invz[i] = 1.0 / z;
+  } else {
+    lo[i] = i;
+    hi[i] = i;
+    invz[i] = 1.0;
+  }
+  // bin index: -1 below the first edge, n_bins above the last one
+  int bb;
+  if (nui < edges[0]) {
+    bb = -1;
+  } else if (nui > edges[n_bins]) {
+    bb = n_bins;
+  } else if (nui == edges[n_bins]) {
+    bb = n_bins - 1;
+  } else {
+    int l = 0, r = n_bins;  // largest b with edges[b] <= nui
+    while (r - l > 1) {
+      int mid = (l + r) / 2;
+      if (edges[mid] <= nui) l = mid;
+      else r = mid;
+    }
+    bb = l;
+  }
+  bin[i] = bb;
+}
+
+// rowinfo[4b..4b+3] = first member point, member count, first column, columns
+__global__ void k_w_rows(int n_nu, int n_bins, const int* __restrict__ bin, const int* __restrict__ lo,
+                         const int* __restrict__ hi, int* rowinfo, int* err) {
+  int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n_bins) return;
+  // members of bin b form a contiguous run of the non-decreasing bin[]
+  int l = 0, r = n_nu;
+  while (l < r) {
+    int m = (l + r) / 2;
+    if (bin[m] < b) l = m + 1;
+    else r = m;
+  }
+  int i0 = l;
+  r = n_nu;
+  while (l < r) {
+    int m = (l + r) / 2;
+    if (bin[m] <= b) l = m + 1;
+    else r = m;
+  }
+  int cnt = l - i0;
+  if (cnt <= 0) {
+    atomicExch(err, 1);
+    rowinfo[4 * b + 0] = 0;
+    rowinfo[4 * b + 1] = 0;
+    rowinfo[4 * b + 2] = 0;
+    rowinfo[4 * b + 3] = 0;
+    return;
+  }
+  int c0 = lo[i0], c1 = hi[i0];
+  for (int i = i0; i < i0 + cnt; ++i) {
+    c0 = min(c0, lo[i]);
+    c1 = max(c1, hi[i]);
+  }
+  rowinfo[4 * b + 0] = i0;
+  rowinfo[4 * b + 1] = cnt;
+  rowinfo[4 * b + 2] = c0;
+  rowinfo[4 * b + 3] = c1 - c0 + 1;
+}
+
+cudaError_t build_w_rows(const TablesDev* d_tab, int nu_first, int n_nu, double R, int n_bins,
+                             const double* d_edges, int* d_lo, int* d_hi, double* d_invz, int* d_bin, int* d_rowinfo,
+                             int* d_err, cudaStream_t s) {
+  k_w_points<<<(n_nu + 127) / 128, 128, 0, s>>>(d_tab, nu_first, n_nu, R, n_bins, d_edges, d_lo, d_hi, d_invz, d_bin);
+  k_w_rows<<<(n_bins + 127) / 128, 128, 0, s>>>(n_nu, n_bins, d_bin, d_lo, d_hi, d_rowinfo, d_err);
+  return cudaGetLastError();
+}
+
+// W[b][m] = (1/n_b) sum over members i of b of g_i(m) / Z_i.
+__global__ void k_w_values(const TablesDev* tab, int nu_first, double R, const int* __restrict__ lo,
+                           const int* __restrict__ hi, const double* __restrict__ invz, const int* __restrict__ rowinfo,
+                           const long long* __restrict__ rowptr, float* w32, double* w64) {
+  int b = blockIdx.x;
+  const TablesDev& t = *tab;
+  int i0 = rowinfo[4 * b], cnt = rowinfo[4 * b + 1], c0 = rowinfo[4 * b + 2], nc = rowinfo[4 * b + 3];
+  long long base = rowptr[b];
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) {
+    int m = c0 + c;
+    double acc = 0.0;
+    if (R > 0.0) {
+      double num = setup_nu(t, nu_first, m);
+      for (int i = i0; i < i0 + cnt; ++i) {
+        if (m < lo[i] || m > hi[i]) continue;
+        double nui = setup_nu(t, nu_first, i);
+        double sig = nui / (R * kFwhmToSigma);
+        double dx = num - nui;
+        acc += exp(-dx * dx / (2.0 * sig * sig)) * invz[i];
+      }
+    } else {
+      acc = (m >= i0 && m < i0 + cnt) ? 1.0 : 0.0;
+    }
+    acc /= (double)cnt;
+    w64[base + c] = acc;
+    w32[base + c] = (float)acc;
+  }
+}
+
+cudaError_t build_w_values(const TablesDev* d_tab, int nu_first, double R, int n_bins, const int* d_lo,
+                               const int* d_hi, const double* d_invz, const int* d_rowinfo, const long long* d_rowptr,
+                               float* d_w32, double* d_w64, cudaStream_t s) {
+  k_w_values<<<n_bins, 256, 0, s>>>(d_tab, nu_first, R, d_lo, d_hi, d_invz, d_rowinfo, d_rowptr, d_w32, d_w64);
+  return cudaGetLastError();
+}
+
+}  // namespace hr2

@@ -1,0 +1,336 @@
+"""ctypes binding of libhr2.so (include/hr2.h).
+
+Argument marshalling only: every step of the forward model and the
+likelihood runs in the library's CUDA kernels.  Functions keep the C names.
+Device buffers are torch CUDA tensors (their ``data_ptr()`` is passed);
+streams default to torch's current stream.  Loading fails loudly if the
+library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhr2.so")
+
+HR2_OK, HR2_EINVAL, HR2_ENOMEM, HR2_ECUDA, HR2_ETIMEDOUT, HR2_EBUSY = 0, -1, -2, -3, -4, -5
+HR2_SAMPLE_BAD_T, HR2_SAMPLE_BAD_ABUND, HR2_SAMPLE_BAD_SCALE, HR2_SAMPLE_BAD_SETUP = 1, 2, 4, 8
+HR2_MAX_TNODES, HR2_MAX_SPECIES, HR2_MAX_MU, HR2_MAX_LEVELS, HR2_MAX_SETUPS = 16, 16, 8, 256, 32
+HR2_P_LOGG, HR2_P_F, HR2_P_DIST, HR2_P_T0, HR2_P_X0, HR2_NPARAM = 0, 1, 2, 3, 19, 35
+HR2_STORE_FP16_OFFSET, HR2_STORE_FP64 = 1, 2
+
+EXPORTED = [
+    "hr2_ctx_create", "hr2_ctx_destroy", "hr2_last_error", "hr2_ctx_memory", "hr2_set_launch_config",
+    "hr2_get_launch_config", "hr2_reserve", "create_opacity_tables", "hr2_tables_upload_species",
+    "hr2_tables_info", "hr2_tables_destroy", "hr2_setup_create", "hr2_setup_set_observation", "hr2_setup_info",
+    "hr2_setup_destroy", "forward_model_batch", "log_likelihood_batch", "hr2_evaluate_host", "hr2_profile_enable",
+    "hr2_profile_read", "hr2_nodes_from_b", "hr2_version",
+]
+
+
+class Hr2Error(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("hr2 error %d: %s" % (code, msg))
+        self.code = code
+
+
+class TableDesc(C.Structure):
+    _fields_ = [("n_species", C.c_int), ("n_T", C.c_int), ("T_grid", C.POINTER(C.c_double)), ("n_p", C.c_int),
+                ("log10p_grid", C.POINTER(C.c_double)), ("nu0", C.c_double), ("dnu", C.c_double), ("n_nu", C.c_int),
+                ("species_mass", C.POINTER(C.c_double)), ("has_cia_h2h2", C.c_int), ("has_cia_h2he", C.c_int)]
+
+
+class SetupDesc(C.Structure):
+    _fields_ = [("nu_first", C.c_int), ("n_nu", C.c_int), ("n_layers", C.c_int), ("p_top", C.c_double),
+                ("p_bot", C.c_double), ("n_species", C.c_int), ("species", C.POINTER(C.c_int)), ("n_mu", C.c_int),
+                ("fe_elements", C.c_int), ("fe_order", C.c_int), ("resolving_power", C.c_double),
+                ("n_bins", C.c_int), ("bin_edges", C.POINTER(C.c_double)), ("obs_flux", C.POINTER(C.c_double)),
+                ("obs_sigma", C.POINTER(C.c_double)), ("r_he", C.c_double), ("radius_cm", C.c_double)]
+
+
+class LaunchCfg(C.Structure):
+    _fields_ = [("warps_per_cta", C.c_int), ("ctas_per_sm", C.c_int)]
+
+
+_LIB = None
+_LOCK = threading.Lock()
+_VP, _DP, _IP, _FP = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_float)
+
+
+def lib():
+    """Load libhr2.so (raises if it is missing: there is no fallback)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libhr2.so not built: run python -m paper_1910_01070_b300.build")
+            L = C.CDLL(LIB_PATH)
+            sig = {
+                "hr2_ctx_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(_VP)]),
+                "hr2_ctx_destroy": (C.c_int, [_VP]),
+                "hr2_last_error": (C.c_char_p, [_VP]),
+                "hr2_ctx_memory": (C.c_int, [_VP, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
+                "hr2_set_launch_config": (C.c_int, [_VP, C.POINTER(LaunchCfg)]),
+                "hr2_get_launch_config": (C.c_int, [_VP, C.POINTER(LaunchCfg)]),
+                "hr2_reserve": (C.c_int, [_VP, _VP, C.c_int, C.c_int]),
+                "create_opacity_tables": (C.c_int, [_VP, C.POINTER(TableDesc), _DP, _DP, _DP, C.c_int,
+                                                    C.POINTER(_VP)]),
+                "hr2_tables_upload_species": (C.c_int, [_VP, _VP, C.c_int, _DP]),
+                "hr2_tables_info": (C.c_int, [_VP, _DP, C.POINTER(C.c_size_t)]),
+                "hr2_tables_destroy": (C.c_int, [_VP, _VP]),
+                "hr2_setup_create": (C.c_int, [_VP, _VP, C.POINTER(SetupDesc), C.POINTER(_VP)]),
+                "hr2_setup_set_observation": (C.c_int, [_VP, _VP, _DP, _DP]),
+                "hr2_setup_info": (C.c_int, [_VP, _IP, _IP, C.POINTER(C.c_longlong)]),
+                "hr2_setup_destroy": (C.c_int, [_VP, _VP]),
+                "forward_model_batch": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), _VP, _VP, C.c_int, _VP, C.c_int,
+                                                  _VP, C.c_int, _VP, _VP]),
+                "log_likelihood_batch": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), _VP, _VP, C.c_int, _VP, C.c_int,
+                                                   _VP, _VP]),
+                "hr2_evaluate_host": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), _VP, _VP, _VP, C.c_int, _VP, _VP,
+                                                C.c_int, _VP]),
+                "hr2_profile_enable": (C.c_int, [_VP, C.c_int]),
+                "hr2_profile_read": (C.c_int, [_VP, C.c_int, _DP, _IP]),
+                "hr2_nodes_from_b": (C.c_int, [C.c_int, C.c_double, _DP, _DP]),
+                "hr2_version": (C.c_char_p, []),
+            }
+            for name, (res, args) in sig.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _LIB = L
+    return _LIB
+
+
+def _check(rc: int, ctx=None):
+    if rc != HR2_OK:
+        raise Hr2Error(rc, lib().hr2_last_error(ctx).decode())
+
+
+def _dptr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(_DP)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _tensor_ptr(t, dtype, name, shape=None):
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape[: len(shape)]) != tuple(shape):
+        raise ValueError("%s has shape %s, expected leading %s" % (name, tuple(t.shape), shape))
+    return t.data_ptr()
+
+
+def _setup_array(setups):
+    arr = (_VP * len(setups))(*[s.handle if hasattr(s, "handle") else s for s in setups])
+    return arr
+
+
+# ------------------------------------------------------------------ raw ABI
+def hr2_version() -> str:
+    return lib().hr2_version().decode()
+
+
+def hr2_ctx_create(device: int = 0, mem_budget_bytes: int = 0):
+    h = _VP()
+    _check(lib().hr2_ctx_create(device, mem_budget_bytes, C.byref(h)))
+    return h
+
+
+def hr2_ctx_destroy(ctx):
+    _check(lib().hr2_ctx_destroy(ctx))
+
+
+def hr2_last_error(ctx=None) -> str:
+    return lib().hr2_last_error(ctx).decode()
+
+
+def hr2_ctx_memory(ctx):
+    u, b = C.c_size_t(), C.c_size_t()
+    _check(lib().hr2_ctx_memory(ctx, C.byref(u), C.byref(b)), ctx)
+    return u.value, b.value
+
+
+def hr2_set_launch_config(ctx, warps_per_cta: int, ctas_per_sm: int):
+    cfg = LaunchCfg(warps_per_cta, ctas_per_sm)
+    _check(lib().hr2_set_launch_config(ctx, C.byref(cfg)), ctx)
+
+
+def hr2_get_launch_config(ctx):
+    cfg = LaunchCfg()
+    _check(lib().hr2_get_launch_config(ctx, C.byref(cfg)), ctx)
+    return cfg.warps_per_cta, cfg.ctas_per_sm
+
+
+def hr2_reserve(ctx, n: int, n_nu_max: int, stream=None):
+    _check(lib().hr2_reserve(ctx, _stream_ptr(stream), n, n_nu_max), ctx)
+
+
+def create_opacity_tables(ctx, T_grid, log10p_grid, nu0, dnu, n_nu, species_mass, log10_sigma=None,
+                          log10_cia_h2h2=None, log10_cia_h2he=None, storage=HR2_STORE_FP16_OFFSET):
+    T_grid, pT = _dptr(T_grid)
+    log10p_grid, pp = _dptr(log10p_grid)
+    mass, pm = _dptr(species_mass)
+    d = TableDesc(len(mass), len(T_grid), pT, len(log10p_grid), pp, float(nu0), float(dnu), int(n_nu), pm,
+                  int(log10_cia_h2h2 is not None), int(log10_cia_h2he is not None))
+    keep = []
+
+    def opt(a, shape):
+        if a is None:
+            return _DP()
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        assert a.shape == shape, (a.shape, shape)
+        keep.append(a)
+        return a.ctypes.data_as(_DP)
+
+    K, nT, nP = len(mass), len(T_grid), len(log10p_grid)
+    ps = opt(log10_sigma, (K, nT, nP, int(n_nu)))
+    c0 = opt(log10_cia_h2h2, (nT, int(n_nu)))
+    c1 = opt(log10_cia_h2he, (nT, int(n_nu)))
+    h = _VP()
+    _check(lib().create_opacity_tables(ctx, C.byref(d), ps, c0, c1, int(storage), C.byref(h)), ctx)
+    return h
+
+
+def hr2_tables_upload_species(ctx, tables, s: int, log10_sigma_s):
+    a, p = _dptr(log10_sigma_s)
+    _check(lib().hr2_tables_upload_species(ctx, tables, int(s), p), ctx)
+
+
+def hr2_tables_info(tables, n_species: int):
+    off = np.zeros(n_species + 2)
+    b = C.c_size_t()
+    _check(lib().hr2_tables_info(tables, off.ctypes.data_as(_DP), C.byref(b)))
+    return off, b.value
+
+
+def hr2_tables_destroy(ctx, tables):
+    _check(lib().hr2_tables_destroy(ctx, tables), ctx)
+
+
+def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_elements, fe_order,
+                     resolving_power, bin_edges, p_top=1e-4, p_bot=100.0, r_he=0.17, radius_cm=7.1492e9,
+                     obs_flux=None, obs_sigma=None):
+    sp = np.ascontiguousarray(np.asarray(species, dtype=np.int32))
+    edges, pe = _dptr(bin_edges)
+    keep = [sp, edges]
+    if obs_flux is not None:
+        of, pf = _dptr(obs_flux)
+        os_, ps = _dptr(obs_sigma)
+        keep += [of, os_]
+    else:
+        pf, ps = _DP(), _DP()
+    d = SetupDesc(int(nu_first), int(n_nu), int(n_layers), float(p_top), float(p_bot), len(sp),
+                  sp.ctypes.data_as(_IP), int(n_mu), int(fe_elements), int(fe_order), float(resolving_power),
+                  len(edges) - 1, pe, pf, ps, float(r_he), float(radius_cm))
+    h = _VP()
+    _check(lib().hr2_setup_create(ctx, tables, C.byref(d), C.byref(h)), ctx)
+    return h
+
+
+def hr2_setup_set_observation(ctx, setup, obs_flux, obs_sigma):
+    f, pf = _dptr(obs_flux)
+    s, ps = _dptr(obs_sigma)
+    _check(lib().hr2_setup_set_observation(ctx, setup, pf, ps), ctx)
+
+
+def hr2_setup_info(setup):
+    nb, nn, nnz = C.c_int(), C.c_int(), C.c_longlong()
+    _check(lib().hr2_setup_info(setup, C.byref(nb), C.byref(nn), C.byref(nnz)))
+    return nb.value, nn.value, nnz.value
+
+
+def hr2_setup_destroy(ctx, setup):
+    _check(lib().hr2_setup_destroy(ctx, setup), ctx)
+
+
+def forward_model_batch(ctx, setups: Sequence, setup_of_sample, params, out_bins, out_highres=None,
+                        out_status=None, stream=None):
+    """Device tensors: setup_of_sample int32 [n], params float64 [n, 35], out_bins float32 [n, ld],
+    out_highres float32 [n, ld2] or None, out_status int32 [n] or None."""
+    import torch
+    n = int(params.shape[0]) if params is not None else 0
+    arr = _setup_array(setups)
+    p_sos = _tensor_ptr(setup_of_sample, torch.int32, "setup_of_sample", (n,))
+    p_par = _tensor_ptr(params, torch.float64, "params", (n, HR2_NPARAM))
+    p_bins = _tensor_ptr(out_bins, torch.float32, "out_bins", (n,))
+    p_hr = _tensor_ptr(out_highres, torch.float32, "out_highres", (n,))
+    p_st = _tensor_ptr(out_status, torch.int32, "out_status", (n,))
+    rc = lib().forward_model_batch(ctx, len(setups), arr, p_sos, p_par, n, p_bins, int(out_bins.shape[1]),
+                                   p_hr, int(out_highres.shape[1]) if out_highres is not None else 0, p_st,
+                                   _stream_ptr(stream))
+    _check(rc, ctx)
+
+
+def log_likelihood_batch(ctx, setups: Sequence, setup_of_sample, model_bins, out_lnL, log_eps=None, stream=None):
+    import torch
+    n = int(model_bins.shape[0])
+    arr = _setup_array(setups)
+    rc = lib().log_likelihood_batch(
+        ctx, len(setups), arr, _tensor_ptr(setup_of_sample, torch.int32, "setup_of_sample", (n,)),
+        _tensor_ptr(model_bins, torch.float32, "model_bins", (n,)), int(model_bins.shape[1]),
+        _tensor_ptr(log_eps, torch.float64, "log_eps", (n,)), n,
+        _tensor_ptr(out_lnL, torch.float64, "out_lnL", (n,)), _stream_ptr(stream))
+    _check(rc, ctx)
+
+
+def hr2_evaluate_host(ctx, setups: Sequence, setup_of_sample, params, out_lnL, log_eps=None, out_bins=None,
+                      stream=None):
+    """Host numpy buffers (pinned torch CPU tensors also accepted): int32 [n], float64 [n, 35],
+    float64 [n] out, optional float64 [n], optional float32 [n, ld] out.  Synchronous."""
+
+    def hp(a, dtype, name):
+        if a is None:
+            return None
+        if hasattr(a, "data_ptr"):  # torch CPU tensor (pinned or not)
+            if a.is_cuda or not a.is_contiguous():
+                raise ValueError("%s must be a contiguous host tensor" % name)
+            return a.data_ptr()
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("%s must be C-contiguous %s" % (name, dtype))
+        return a.ctypes.data
+
+    n = int(params.shape[0])
+    arr = _setup_array(setups)
+    rc = lib().hr2_evaluate_host(ctx, len(setups), arr, hp(setup_of_sample, np.int32, "setup_of_sample"),
+                                 hp(params, np.float64, "params"), hp(log_eps, np.float64, "log_eps"), n,
+                                 hp(out_lnL, np.float64, "out_lnL"), hp(out_bins, np.float32, "out_bins"),
+                                 int(out_bins.shape[1]) if out_bins is not None else 0, _stream_ptr(stream))
+    _check(rc, ctx)
+
+
+def hr2_profile_enable(ctx, on: bool = True):
+    _check(lib().hr2_profile_enable(ctx, int(bool(on))), ctx)
+
+
+def hr2_profile_read(ctx, reset: bool = True):
+    """(summed ms of the main forward kernel, launches) since the last reset."""
+    ms, n = C.c_double(), C.c_int()
+    _check(lib().hr2_profile_read(ctx, int(bool(reset)), C.byref(ms), C.byref(n)), ctx)
+    return ms.value, n.value
+
+
+def hr2_nodes_from_b(T1: float, b) -> np.ndarray:
+    b, pb = _dptr(b)
+    out = np.zeros(len(b) + 1)
+    _check(lib().hr2_nodes_from_b(len(out), float(T1), pb, out.ctypes.data_as(_DP)))
+    return out

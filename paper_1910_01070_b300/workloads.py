@@ -242,8 +242,20 @@ class Workload:
         return theta, sid
 
     def truth(self, g: int = 0) -> np.ndarray:
-        """A fixed "true" parameter vector of setup g for the mock observation."""
-        return draw_params(self.setups[g], 1, self.seed + 7919 + g, self.prior)[0]
+        """The "true" parameter vector of setup g for the mock observation: a
+        late-T-dwarf-like atmosphere as in the paper's test case (Sect. 4:
+        log g = 4.75, f = 1, d = 10 pc), a monotonic profile from 2200 K at the
+        bottom to 500 K at the top, and log10 mixing ratios of -3.5.  A workload
+        whose prior fixes nodes independently draws them from that prior."""
+        st = self.setups[g]
+        if self.prior.free_nodes is not None:
+            return draw_params(st, 1, self.seed + 7919 + g, self.prior)[0]
+        th = np.zeros(NPARAM)
+        th[P_LOGG], th[P_F], th[P_DIST] = 4.75, 1.0, self.prior.dist_pc
+        nt = st.n_tnodes
+        th[P_T0:P_T0 + nt] = 2200.0 * (500.0 / 2200.0) ** (np.arange(nt) / (nt - 1))
+        th[P_X0:P_X0 + len(st.species)] = -3.5
+        return th
 
 
 def _grid_T(n: int) -> np.ndarray:

@@ -1,0 +1,337 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Gates (written here, not derived from the CUDA path):
+  * FP16-offset tables, FP32 solve: max relative flux error per spectrum
+    <= 1e-4 on F+ and on the binned model, against the oracle run on the
+    same dequantised tables (the tables the kernels actually read);
+  * plain FP64 path with FP64 tables: <= 2e-7, the rounding of its FP32
+    outputs (the ABI returns F+ and the bins as float);
+  * log-likelihood: same model bins -> FP64 reduction agrees to 1e-9
+    relative; end to end |delta lnL| < 1e-3 for samples near the data.
+Sizes span several 64-point tiles with ragged heads and tails; the full
+workload sizes run in the launch shape the benchmark times and are checked
+on sampled outputs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_01070_b300 import hr2
+from paper_1910_01070_b300 import workloads as W
+from paper_1910_01070_b300.engine import Engine
+from tests.helpers import FLUX_RTOL, FP64_RTOL, LNL_ATOL, oracle_model, rel_flux_err, tables_as_stored
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_1910_01070_b300 import build
+    build.build()
+    e = Engine(0)
+    yield e
+    e.close()
+
+
+def _dev(a, dtype):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def _run(eng, setups, sid, theta, highres_ld=None):
+    n = len(sid)
+    nb = max(hr2.hr2_setup_info(s)[0] for s in setups)
+    nn = highres_ld or max(hr2.hr2_setup_info(s)[1] for s in setups)
+    bins = torch.full((n, nb), -7.0, dtype=torch.float32, device="cuda")
+    hi = torch.full((n, nn), -7.0, dtype=torch.float32, device="cuda")
+    st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    eng.forward(setups, _dev(sid, torch.int32), _dev(theta, torch.float64), bins, hi, st)
+    torch.cuda.synchronize()
+    return bins.cpu().numpy().astype(np.float64), hi.cpu().numpy().astype(np.float64), st.cpu().numpy()
+
+
+def _compare(om, theta, bins, hi, tol, n_nu):
+    ob, otop, ok = om.forward(theta, want_top=True)
+    assert ok
+    e_hi = rel_flux_err(hi[:n_nu], otop)
+    e_b = rel_flux_err(bins[: om.n_bins], ob)
+    assert e_hi <= tol, e_hi
+    assert e_b <= tol, e_b
+    return e_hi, e_b
+
+
+# ------------------------------------------------------------ tiny grids
+TINY = [
+    # n_nu, L, K, nT, nP, n_mu, R, bins, first_off, fe (Ke, q)
+    (16, 3, 2, 3, 3, 2, 0.0, 4, 0, (2, 1)),
+    (100, 7, 3, 4, 3, 3, 500.0, 5, 0, (3, 2)),
+    (130, 12, 1, 5, 4, 8, 2000.0, 7, 5, (2, 3)),
+    (65, 1, 2, 2, 2, 1, 0.0, 3, 63, (1, 1)),
+    (257, 30, 4, 6, 5, 5, 800.0, 9, 17, (4, 2)),
+]
+
+
+@pytest.mark.parametrize("storage", ["fp16", "fp64"])
+@pytest.mark.parametrize("case", TINY, ids=[f"nu{c[0]}_L{c[1]}_K{c[2]}_mu{c[5]}" for c in TINY])
+def test_tiny_grids_match_oracle(eng, storage, case):
+    n_nu, L, K, nT, nP, nmu, R, nb, off, (Ke, q) = case
+    spec = W.TableSpec(K, np.linspace(300.0, 2500.0, nT), np.linspace(-4.0, 2.0, nP), 5000.0, 1.0,
+                       n_nu + off + 3, seed=hash(case) % 1000)
+    tabs = W.make_tables(spec)
+    setup = W.make_setup(spec, 5000.0 + off, 5000.0 + off + n_nu - 1, L, range(K), nmu, Ke, q, R, nb)
+    t = eng.add_tables(spec, storage, tabs)
+    s = eng.add_setup(t, setup)
+    theta = W.draw_params(setup, 4, 17, W.Prior(T1=(900.0, 2400.0), b=(0.85, 0.99)))
+    bins, hi, st = _run(eng, [s], np.zeros(4, np.int32), theta, highres_ld=n_nu + 64)
+    assert np.all(st == 0)
+    om = oracle_model(tables_as_stored(tabs, storage), setup)
+    tol = FLUX_RTOL if storage == "fp16" else FP64_RTOL
+    for i in range(4):
+        _compare(om, theta[i], bins[i], hi[i], tol, n_nu)
+    assert np.all(hi[:, n_nu:] == -7.0)      # nothing written past the setup's points
+
+
+def test_cia_only_setup(eng):
+    spec = W.TableSpec(2, np.linspace(300.0, 2500.0, 4), np.linspace(-4.0, 2.0, 3), 5000.0, 1.0, 90, seed=3)
+    tabs = W.make_tables(spec)
+    setup = W.make_setup(spec, 5000.0, 5089.0, 9, [], 3, 2, 1, 300.0, 4)
+    t = eng.add_tables(spec, "fp16", tabs)
+    s = eng.add_setup(t, setup)
+    theta = W.draw_params(setup, 2, 5, W.Prior(b=(0.8, 0.95)))
+    bins, hi, st = _run(eng, [s], np.zeros(2, np.int32), theta)
+    om = oracle_model(tables_as_stored(tabs, "fp16"), setup)
+    for i in range(2):
+        _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, 90)
+
+
+# ------------------------------------------------------------ named workloads
+_CACHE = {}
+
+
+def _workload_on(eng, name, storage, n=None):
+    key = (name, storage)
+    if key not in _CACHE:
+        wl = W.WORKLOADS[name]() if storage is None else W.WORKLOADS[name]()
+        tabs = W.make_tables(wl.table)
+        st = storage or wl.storage
+        t = eng.add_tables(wl.table, st, tabs)
+        setups = [eng.add_setup(t, s) for s in wl.setups]
+        _CACHE[key] = (wl, tabs, tables_as_stored(tabs, st), setups, st, t)
+    return _CACHE[key][:5]
+
+
+def _tables_of(name, storage):
+    return _CACHE[(name, storage)][5]
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp16"])
+def test_single_model_50_layers(eng, storage):
+    wl, tabs, stored, setups, st = _workload_on(eng, "single_l50_k1_nu6001", storage)
+    theta, sid = wl.params()
+    bins, hi, status = _run(eng, setups, sid, theta)
+    om = oracle_model(stored, wl.setups[0])
+    tol = FLUX_RTOL if st == "fp16" else FP64_RTOL
+    e = _compare(om, theta[0], bins[0], hi[0], tol, wl.setups[0].n_nu)
+    print("single model", storage, "rel err (F+, bins):", e)
+
+
+def _observation(eng, wl, stored, setups, g=0):
+    om = oracle_model(stored, wl.setups[g])
+    truth = wl.truth(g)
+    tb, ok = om.forward(truth)
+    assert ok
+    D, sig = W.mock_observation(tb, wl.seed + g)
+    eng.set_observation(setups[g], D, sig)
+    return om, truth, D, sig
+
+
+@pytest.mark.parametrize("storage", ["fp16", "fp64"])
+def test_batch_100_layers_reduced_with_lnl(eng, storage):
+    wl, tabs, stored, setups, st = _workload_on(eng, "batch1024_l100_k6_nu8501", storage)
+    om, truth, D, sig = _observation(eng, wl, stored, setups)
+    theta, sid = wl.params(12)
+    # near-truth samples: the truth and small perturbations of it
+    near = np.repeat(truth[None, :], 4, axis=0)
+    near[1:, 0] += np.array([1e-3, -2e-3, 5e-4])
+    near[1:, 3:10] *= 1.0 + np.array([1e-3, -1e-3, 2e-3])[:, None]
+    theta = np.concatenate([theta, near])
+    sid = np.zeros(len(theta), np.int32)
+    bins, hi, status = _run(eng, setups, sid, theta)
+    assert np.all(status == 0)
+    tol = FLUX_RTOL if st == "fp16" else FP64_RTOL
+    worst = 0.0
+    ob_all = []
+    for i in range(len(theta)):
+        e = _compare(om, theta[i], bins[i], hi[i], tol, wl.setups[0].n_nu)
+        worst = max(worst, *e)
+        ob_all.append(om.forward(theta[i])[0])
+    print(storage, "worst rel flux err", worst)
+    # likelihood on the GPU's own bins (FP64 reduction) and end to end
+    bins_t = _dev(bins.astype(np.float32), torch.float32)
+    lnl = eng.lnl(setups, _dev(sid, torch.int32), bins_t).cpu().numpy()
+    for i in range(len(theta)):
+        ref_same = oracle.lnL(D, sig, bins[i])
+        assert abs(lnl[i] - ref_same) <= 1e-9 * abs(ref_same) + 1e-9
+    for i in range(len(theta) - 4, len(theta)):
+        ref = oracle.lnL(D, sig, ob_all[i])
+        d_sig = (bins[i] - ob_all[i]) / sig
+        print("sample %d: dlnL %.3e  max|dDm|/sigma %.3e  max Dm/sigma %.1f  max rel bin err %.2e"
+              % (i, lnl[i] - ref, np.max(np.abs(d_sig)), np.max(ob_all[i] / sig),
+                 np.max(np.abs(bins[i] / ob_all[i] - 1))))
+    for i in range(len(theta) - 4, len(theta)):
+        ref = oracle.lnL(D, sig, ob_all[i])
+        assert abs(lnl[i] - ref) < LNL_ATOL, (i, lnl[i], ref)
+    # error inflation (Eqs. 22-23)
+    eps = np.full(len(theta), np.log10(np.median(sig) ** 2))
+    eps[0] = np.nan
+    lnl_e = eng.lnl(setups, _dev(sid, torch.int32), bins_t, _dev(eps, torch.float64)).cpu().numpy()
+    for i in range(len(theta)):
+        ref = oracle.lnL(D, sig, bins[i], eps[i])
+        assert abs(lnl_e[i] - ref) <= 1e-9 * abs(ref) + 1e-9
+
+
+def test_batch_1024_full_size_sampled(eng):
+    """The benchmark's workload and launch shape; 12 samples checked fully."""
+    wl, tabs, stored, setups, st = _workload_on(eng, "batch1024_l100_k6_nu8501", "fp16")
+    theta, sid = wl.params()
+    assert len(theta) == 1024
+    bins, hi, status = _run(eng, setups, sid, theta)
+    om = oracle_model(stored, wl.setups[0])
+    pick = np.random.default_rng(0).choice(1024, 12, replace=False)
+    for i in pick:
+        _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, wl.setups[0].n_nu)
+    assert np.all(np.isfinite(bins[status == 0]))
+
+
+def test_uneven_three_setups_sampled_and_alone_equals_mix(eng):
+    wl, tabs, stored, setups, st = _workload_on(eng, "uneven2048_3setups", "fp16")
+    theta, sid = wl.params()
+    bins, hi, status = _run(eng, setups, sid, theta, highres_ld=max(s.n_nu for s in wl.setups))
+    rng = np.random.default_rng(1)
+    for g, s in enumerate(wl.setups):
+        om = oracle_model(stored, s)
+        idx = np.nonzero(sid == g)[0]
+        for i in rng.choice(idx, 2, replace=False):
+            _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, s.n_nu)
+    # a sample's result does not depend on the rest of the batch
+    sub = rng.choice(len(theta), 37, replace=False)
+    b2, h2, _ = _run(eng, setups, sid[sub], theta[sub], highres_ld=hi.shape[1])
+    assert np.array_equal(b2, bins[sub])
+    assert np.array_equal(h2, hi[sub])
+
+
+def test_launch_shapes_agree_bitwise(eng):
+    wl, tabs, stored, setups, st = _workload_on(eng, "uneven2048_3setups", "fp16")
+    theta, sid = wl.params(96, seed_offset=3)
+    ref = None
+    old = hr2.hr2_get_launch_config(eng.ctx)
+    try:
+        for w, c in ((1, 1), (4, 2), (8, 3), (16, 1)):
+            eng.set_launch_config(w, c)
+            out = _run(eng, setups, sid, theta, highres_ld=10001)
+            if ref is None:
+                ref = out
+            else:
+                assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1])
+    finally:
+        eng.set_launch_config(*old)
+
+
+def test_invalid_samples_flagged(eng):
+    wl, tabs, stored, setups, st = _workload_on(eng, "batch1024_l100_k6_nu8501", "fp16")
+    om, truth, D, sig = _observation(eng, wl, stored, setups)
+    theta = np.repeat(truth[None], 5, axis=0)
+    theta[1, 1] = -1.0                 # f <= 0
+    theta[2, W.P_X0] = 0.1             # abundances sum above 1
+    theta[3, W.P_T0 + 2] = -50.0       # negative temperature node
+    sid = np.array([0, 0, 0, 0, 3], np.int32)   # last: setup index out of range
+    bins, hi, status = _run(eng, setups, sid, theta)
+    assert status[0] == 0
+    assert status[1] & hr2.HR2_SAMPLE_BAD_SCALE
+    assert status[2] & hr2.HR2_SAMPLE_BAD_ABUND
+    assert status[3] & hr2.HR2_SAMPLE_BAD_T
+    assert status[4] == hr2.HR2_SAMPLE_BAD_SETUP
+    assert np.all(np.isnan(bins[1:]))
+    lnl = eng.lnl(setups, _dev(sid, torch.int32), _dev(bins.astype(np.float32), torch.float32)).cpu().numpy()
+    assert np.isfinite(lnl[0]) and np.all(lnl[1:] == -np.inf)
+
+
+def test_evaluate_host_matches_device_calls(eng):
+    wl, tabs, stored, setups, st = _workload_on(eng, "batch1024_l100_k6_nu8501", "fp16")
+    _observation(eng, wl, stored, setups)
+    theta, sid = wl.params(64, seed_offset=5)
+    out_bins = np.zeros((64, 300), np.float32)
+    lnl_h = eng.evaluate_host(setups, sid, theta, out_bins=out_bins)
+    bins, hi, status = _run(eng, setups, sid, theta)
+    lnl_d = eng.lnl(setups, _dev(sid, torch.int32), _dev(bins.astype(np.float32), torch.float32)).cpu().numpy()
+    assert np.array_equal(out_bins.astype(np.float64), bins)
+    assert np.array_equal(lnl_h, lnl_d)
+
+
+def test_empty_batch_and_argument_errors(eng):
+    wl, tabs, stored, setups, st = _workload_on(eng, "batch1024_l100_k6_nu8501", "fp16")
+    e = torch.empty((0, 300), dtype=torch.float32, device="cuda")
+    hr2.forward_model_batch(eng.ctx, setups, torch.empty(0, dtype=torch.int32, device="cuda"),
+                            torch.empty((0, 35), dtype=torch.float64, device="cuda"), e)
+    theta, sid = wl.params(2)
+    small = torch.empty((2, 10), dtype=torch.float32, device="cuda")
+    with pytest.raises(hr2.Hr2Error) as ei:
+        hr2.forward_model_batch(eng.ctx, setups, _dev(sid, torch.int32), _dev(theta, torch.float64), small)
+    assert ei.value.code == hr2.HR2_EINVAL
+    with pytest.raises(hr2.Hr2Error) as ei:
+        bad = W.make_setup(wl.table, 4000.0, 12500.0, 100, range(6), 4, 3, 2, 300.0, 300)
+        bad.nu_first = wl.table.n_nu - 10
+        eng.add_setup(_tables_of("batch1024_l100_k6_nu8501", "fp16"), bad)
+    assert ei.value.code == hr2.HR2_EINVAL
+    with pytest.raises(hr2.Hr2Error) as ei:      # a bin with no point in it
+        edges = np.array([4000.0, 4000.2, 4000.4, 5000.0])
+        s = W.make_setup(wl.table, 4000.0, 5000.0, 10, [0], 2, 1, 1, 0.0, 3)
+        s.bin_edges = edges
+        eng.add_setup(_tables_of("batch1024_l100_k6_nu8501", "fp16"), s)
+    assert ei.value.code == hr2.HR2_EINVAL
+
+
+def test_memory_budget_admission():
+    e = Engine(0, mem_budget_bytes=1 << 20)
+    try:
+        wl = W.batch1024_l100_k6_nu8501()
+        with pytest.raises(hr2.Hr2Error) as ei:
+            e.add_tables(wl.table, "fp16", W.make_tables(wl.table))
+        assert ei.value.code == hr2.HR2_ENOMEM
+        assert e.memory()[0] <= 1 << 20
+    finally:
+        e.close()
+
+
+@pytest.mark.slow
+def test_large_tables_sampled(eng):
+    """290001-point, 12-absorber FP16 tables (~2 GB), batch 256, 8 nodes, R=1000 -> 2000 bins."""
+    wl = W.large_l100_k12_nu290001_b256()
+    spec = wl.table
+    h2h2, h2he = W.cia_tables(spec)
+    t = hr2.create_opacity_tables(eng.ctx, spec.T_grid, spec.log10p_grid, spec.nu0, spec.dnu, spec.n_nu,
+                                  spec.masses, None, h2h2, h2he, hr2.HR2_STORE_FP16_OFFSET)
+    from tests.helpers import fp16_offset_dequantise
+    stored = np.empty((spec.n_species, len(spec.T_grid), len(spec.log10p_grid), spec.n_nu))
+    for s in range(spec.n_species):
+        v = W.species_table(spec, s)
+        hr2.hr2_tables_upload_species(eng.ctx, t, s, v)
+        stored[s] = fp16_offset_dequantise(v)
+        del v
+    s0 = eng.add_setup(t, wl.setups[0])
+    theta, sid = wl.params()
+    bins, hi, status = _run(eng, [s0], sid, theta)
+    tabs = dict(T_grid=spec.T_grid, log10p_grid=spec.log10p_grid, nu0=spec.nu0, dnu=spec.dnu,
+                log10_sigma=stored, log10_cia_h2h2=fp16_offset_dequantise(h2h2),
+                log10_cia_h2he=fp16_offset_dequantise(h2he), species_mass=spec.masses)
+    om = oracle_model(tabs, wl.setups[0])
+    rng = np.random.default_rng(2)
+    idx = np.sort(rng.choice(spec.n_nu, 1500, replace=False))
+    sel = np.sort(rng.choice(wl.setups[0].n_bins, 10, replace=False))
+    for i in (0, 131):
+        ref, ok = om.top_flux_at(theta[i], idx)
+        assert ok
+        assert rel_flux_err(hi[i][idx], ref) <= FLUX_RTOL
+        refb, _ = om.bins_at(theta[i], sel)
+        assert rel_flux_err(bins[i][sel], refb) <= FLUX_RTOL
