@@ -251,6 +251,37 @@ int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups
                       const int* setup_of_sample, const double* params, const double* log_eps, int n,
                       double* out_lnL, float* out_bins, int bins_ld, void* stream);
 
+/* ------------------------------------------------- allocation-free variant
+ * (No counterpart in the paper.)  forward_model_batch_noalloc computes
+ * exactly what forward_model_batch computes, for FP16-offset tables, but
+ * allocates no device memory at all.  It is for callers that may not let a
+ * library allocate: a host application whose device memory belongs to
+ * another allocator (a framework's caching pool that must account for every
+ * byte), or a latency-critical evaluation loop that cannot accept the
+ * device-wide synchronisation cudaMalloc may imply.
+ *
+ * Its scratch (per-sample and per-level records, the work plan and the work
+ * counter) lives in one statically sized device array of
+ * HR2_NOALLOC_SCRATCH_BYTES, which every GPU that loads the library holds
+ * until the process exits.  The caller passes all inputs and outputs as for
+ * forward_model_batch, except that out_highres is REQUIRED: the F+ buffer is
+ * an output here, not scratch.
+ *   - Limit: the batch must fit the array, roughly n * (L+1) * 64 bytes plus
+ *     n * 148 bytes plus 1 KB (about 1024 samples of 121 levels); larger
+ *     batches, FP64 tables or a NULL out_highres return HR2_EINVAL with a
+ *     message giving the bytes needed.
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     the work counter that must start at zero is cleared on the device by
+ *     each call itself.  Calls whose work overlaps on the GPU (different
+ *     streams, or different host threads) race on the array: serialise them. */
+#define HR2_NOALLOC_SCRATCH_BYTES (8u << 20)
+int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
+                                const int* setup_of_sample, const double* params, int n, float* out_bins,
+                                int bins_ld, float* out_highres, int highres_ld, int* out_status, void* stream);
+
 /* -------------------------------------------------------- instrumentation
  * (No counterpart in the paper.)  While enabled, every forward_model_batch
  * records a pair of CUDA events on its stream around the launch of the main

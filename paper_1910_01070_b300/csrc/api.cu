@@ -887,3 +887,85 @@ extern "C" int hr2_nodes_from_b(int n_nodes, double T1, const double* b, double*
 }
 
 extern "C" const char* hr2_version(void) { return "hr2-b300 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------ allocation-free variant
+// forward_model_batch_noalloc: the FP32 forward path with its scratch in one
+// static device array instead of the context's workspace.  Nothing here calls
+// cudaMalloc, cudaFree or an allocating routine.
+namespace {
+constexpr size_t kNoallocBytes = HR2_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoallocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Device address of the array on the current device (looked up once per device).
+int noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= kNoallocMaxDevices) return fail(HR2_EINVAL, "device %d unsupported", device);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return fail(HR2_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return HR2_OK;
+}
+}  // namespace
+
+extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
+                                           const int* setup_of_sample, const double* params, int n, float* out_bins,
+                                           int bins_ld, float* out_highres, int highres_ld, int* out_status,
+                                           void* stream) {
+  if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
+  if (n < 0) return fail(HR2_EINVAL, "n < 0");
+  BatchShape sh;
+  int rc = check_setups(ctx, n_setups, setups, &sh);
+  if (rc) return rc;
+  if (sh.storage != HR2_STORE_FP16_OFFSET)
+    return fail(HR2_EINVAL, "the allocation-free variant runs FP16-offset tables only");
+  if (n == 0) return HR2_OK;
+  if (!setup_of_sample || !params || !out_bins || !out_highres)
+    return fail(HR2_EINVAL, "setup_of_sample, params, out_bins and out_highres are required");
+  if (bins_ld < sh.max_bins) return fail(HR2_EINVAL, "bins_ld %d < largest n_bins %d", bins_ld, sh.max_bins);
+  if (highres_ld < sh.max_nu) return fail(HR2_EINVAL, "highres_ld %d < largest n_nu %d", highres_ld, sh.max_nu);
+  const size_t off_counter = align256(sizeof(PlanDev));
+  const size_t off_perm = off_counter + 256;
+  const size_t off_samp = off_perm + align256(sizeof(int) * (size_t)n);
+  const size_t off_recs = off_samp + align256(sizeof(SampleDev) * (size_t)n);
+  const size_t need = off_recs + sizeof(LevRec) * (size_t)n * sh.max_lev;
+  if (need > kNoallocBytes)
+    return fail(HR2_EINVAL, "batch of %d samples with %d levels needs %zu bytes of scratch; the allocation-free "
+                "variant holds %zu", n, sh.max_lev, need, kNoallocBytes);
+  HR2_CU(cudaSetDevice(ctx->device));
+  char* base = nullptr;
+  if ((rc = noalloc_scratch(ctx->device, (void**)&base))) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  FwdArgs a{};
+  for (int g = 0; g < n_setups; ++g) a.setups[g] = setups[g]->dev;
+  a.n_setups = n_setups;
+  a.n = n;
+  a.setup_of_sample = setup_of_sample;
+  a.params = params;
+  a.plan = (const PlanDev*)base;
+  a.counter = (unsigned int*)(base + off_counter);
+  a.perm = (const int*)(base + off_perm);
+  a.samp = (SampleDev*)(base + off_samp);
+  a.recs = (LevRec*)(base + off_recs);
+  a.rec_ld = sh.max_lev;
+  a.status = out_status;
+  a.highres = out_highres;
+  a.highres_ld = highres_ld;
+  a.warps = ctx->cfg.warps_per_cta;
+  cudaError_t e;
+  // the planner resets the work counter to zero on the device before the
+  // forward kernel reads it; everything else is overwritten by the kernels
+  if ((e = launch_prep(a, s)) != cudaSuccess || (e = launch_plan(a, (int*)a.perm, (PlanDev*)a.plan, s)) != cudaSuccess ||
+      (e = launch_forward32(a, sh.max_mu, ctx->n_sm * ctx->cfg.ctas_per_sm, s)) != cudaSuccess ||
+      (e = launch_bins(a, out_bins, bins_ld, false, s)) != cudaSuccess)
+    return fail(HR2_ECUDA, "allocation-free launch: %s", cudaGetErrorString(e));
+  return HR2_OK;
+}

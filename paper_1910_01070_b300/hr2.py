@@ -28,7 +28,8 @@ EXPORTED = [
     "hr2_ctx_create", "hr2_ctx_destroy", "hr2_last_error", "hr2_ctx_memory", "hr2_set_launch_config",
     "hr2_get_launch_config", "hr2_reserve", "create_opacity_tables", "hr2_tables_upload_species",
     "hr2_tables_info", "hr2_tables_destroy", "hr2_setup_create", "hr2_setup_set_observation", "hr2_setup_info",
-    "hr2_setup_destroy", "forward_model_batch", "log_likelihood_batch", "hr2_evaluate_host", "hr2_profile_enable",
+    "hr2_setup_destroy", "forward_model_batch", "forward_model_batch_noalloc", "log_likelihood_batch",
+    "hr2_evaluate_host", "hr2_profile_enable",
     "hr2_profile_read", "hr2_nodes_from_b", "hr2_version",
 ]
 
@@ -89,6 +90,8 @@ def lib():
                 "hr2_setup_destroy": (C.c_int, [_VP, _VP]),
                 "forward_model_batch": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), _VP, _VP, C.c_int, _VP, C.c_int,
                                                   _VP, C.c_int, _VP, _VP]),
+                "forward_model_batch_noalloc": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), _VP, _VP, C.c_int, _VP,
+                                                          C.c_int, _VP, C.c_int, _VP, _VP]),
                 "log_likelihood_batch": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), _VP, _VP, C.c_int, _VP, C.c_int,
                                                    _VP, _VP]),
                 "hr2_evaluate_host": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), _VP, _VP, _VP, C.c_int, _VP, _VP,
@@ -278,6 +281,25 @@ def forward_model_batch(ctx, setups: Sequence, setup_of_sample, params, out_bins
     rc = lib().forward_model_batch(ctx, len(setups), arr, p_sos, p_par, n, p_bins, int(out_bins.shape[1]),
                                    p_hr, int(out_highres.shape[1]) if out_highres is not None else 0, p_st,
                                    _stream_ptr(stream))
+    _check(rc, ctx)
+
+
+HR2_NOALLOC_SCRATCH_BYTES = 8 << 20
+
+
+def forward_model_batch_noalloc(ctx, setups: Sequence, setup_of_sample, params, out_bins, out_highres,
+                                out_status=None, stream=None):
+    """forward_model_batch without any device allocation (FP16 tables; out_highres required).
+    Its scratch is one static device array shared by all calls: do not overlap calls on the GPU."""
+    import torch
+    n = int(params.shape[0])
+    arr = _setup_array(setups)
+    rc = lib().forward_model_batch_noalloc(
+        ctx, len(setups), arr, _tensor_ptr(setup_of_sample, torch.int32, "setup_of_sample", (n,)),
+        _tensor_ptr(params, torch.float64, "params", (n, HR2_NPARAM)), n,
+        _tensor_ptr(out_bins, torch.float32, "out_bins", (n,)), int(out_bins.shape[1]),
+        _tensor_ptr(out_highres, torch.float32, "out_highres", (n,)), int(out_highres.shape[1]),
+        _tensor_ptr(out_status, torch.int32, "out_status", (n,)), _stream_ptr(stream))
     _check(rc, ctx)
 
 
