@@ -129,6 +129,15 @@ typedef struct {
   const double* obs_sigma;    /* [n_bins] observational errors sigma_j, or NULL */
   double r_he;                /* n_He / n_H2 of the H2/He filling gas (> 0)     */
   double radius_cm;           /* R_* of the radius-distance relation, cm        */
+  int level_cache;            /* FP16 tables only.  Nonzero: interpolate the
+                                 tables in p onto this setup's levels once, at
+                                 creation (FP64 arithmetic, stored as FP32
+                                 times log2 10, n_species x levels x n_T x
+                                 columns x 4 bytes of device memory), so that
+                                 each sample interpolates in T only.  Zero:
+                                 every evaluation interpolates the FP16 tables
+                                 bilinearly.  One batch call takes setups of a
+                                 single kind.                                    */
 } hr2_setup_desc;
 
 /* Launch shape of the persistent forward kernel (chosen by the autotuner). */
@@ -291,6 +300,12 @@ int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2_setup* con
  * launches, and with reset != 0 forgets them. */
 int hr2_profile_enable(hr2_ctx* ctx, int on);
 int hr2_profile_read(hr2_ctx* ctx, int reset, double* kernel_ms, int* launches);
+
+/* Wait for `stream` and report whether a bounded device-side wait of the
+ * last batch on that stream gave up (HR2_ETIMEDOUT; its outputs are then not
+ * valid).  No counterpart in the paper.  hr2_evaluate_host checks the same
+ * word itself. */
+int hr2_stream_check(hr2_ctx* ctx, void* stream);
 
 /* ------------------------------------------------------------- helpers */
 

@@ -42,7 +42,7 @@ struct Workspace {
   SampleDev* samp = nullptr;
   int* perm = nullptr;
   PlanDev* plan = nullptr;
-  unsigned int* counter = nullptr;
+  unsigned int* counter = nullptr;   // [0] work counter, [1] error word
   float* highres = nullptr;
   double* highres64 = nullptr;
   double* io_params = nullptr;
@@ -57,7 +57,7 @@ struct hr2_ctx {
   int n_sm = 0;
   size_t budget = 0;
   size_t used = 0;
-  hr2_launch_cfg cfg{8, 2};
+  hr2_launch_cfg cfg{4, 4};
   std::mutex mu;
   std::map<void*, size_t> blocks;  // device allocations and their sizes
   std::map<void*, Workspace*> ws;  // per stream
@@ -175,7 +175,7 @@ static int ws_ensure(hr2_ctx* ctx, cudaStream_t stream, int n, int lev, int nu, 
   const size_t nc = (size_t)std::max(nw.n_cap, 1);
   if ((rc = dalloc_t(ctx, &nw.recs, nc * std::max(nw.lev_cap, 1))) ||
       (rc = dalloc_t(ctx, &nw.samp, nc)) || (rc = dalloc_t(ctx, &nw.perm, nc)) ||
-      (rc = dalloc_t(ctx, &nw.plan, 1)) || (rc = dalloc_t(ctx, &nw.counter, 1)))
+      (rc = dalloc_t(ctx, &nw.plan, 1)) || (rc = dalloc_t(ctx, &nw.counter, 2)))
     goto bad;
   if (nw.nu_cap > 0 && (rc = dalloc_t(ctx, &nw.highres, nc * nw.nu_cap))) goto bad;
   if (nw.nu64_cap > 0 && (rc = dalloc_t(ctx, &nw.highres64, nc * nw.nu64_cap))) goto bad;
@@ -185,6 +185,10 @@ static int ws_ensure(hr2_ctx* ctx, cudaStream_t stream, int n, int lev, int nu, 
         (rc = dalloc_t(ctx, &nw.io_logeps, ic)) || (rc = dalloc_t(ctx, &nw.io_lnl, ic)) ||
         (rc = dalloc_t(ctx, &nw.io_bins, ic * std::max(nw.io_bins_cap, 1))))
       goto bad;
+  }
+  if (cudaMemset(nw.counter, 0, 2 * sizeof(unsigned int)) != cudaSuccess) {
+    rc = fail(HR2_ECUDA, "workspace counter initialisation failed");
+    goto bad;
   }
   *w = nw;
   return HR2_OK;
@@ -574,6 +578,16 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
     h.mu_nlog2e[k] = (float)(-kLog2e / mu);
     h.wflux[k] = (float)(2.0 * kPi * w * mu);
   }
+  // nodes beyond n_mu (up to the kernel's compile-time count) are padding:
+  // mu = 1 with zero weight, so they add nothing to F+
+  for (int k = d->n_mu; k < HR2_MAX_MU; ++k) {
+    h.mu64[k] = 1.0;
+    h.wmu64[k] = 0.0;
+    h.mu[k] = 1.f;
+    h.inv_mu[k] = 1.f;
+    h.mu_nlog2e[k] = (float)(-kLog2e);
+    h.wflux[k] = 0.f;
+  }
   for (int i = 0; i <= d->fe_order; ++i) h.gll[i] = quad[2 * d->n_mu + i];
 
   // instrument profile + binning operator
@@ -628,6 +642,22 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
                             d_rowptr, d_w32, d_w64, 0)) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
       rc = fail(HR2_ECUDA, "setup operator values: %s", cudaGetErrorString(e));
+      goto fail_tmp;
+    }
+  }
+  if (d->level_cache && th.storage == HR2_STORE_FP16_OFFSET) {
+    float *d_lvl = nullptr, *d_cia = nullptr;
+    const size_t per_tile = (size_t)h.n_lev * std::max(1, h.n_species) * th.n_T * kTileNu;
+    if ((rc = dalloc_t(ctx, &d_lvl, per_tile * h.n_tiles))) goto fail_tmp;
+    track(d_lvl);
+    if ((rc = dalloc_t(ctx, &d_cia, (size_t)h.n_tiles * 2 * th.n_T * kTileNu))) goto fail_tmp;
+    track(d_cia);
+    h.lvl32 = d_lvl;
+    h.cia32 = d_cia;
+    h.cached = 1;
+    if ((e = build_level_cache(tab->dev, h, d_lvl, d_cia, 0)) != cudaSuccess ||
+        (e = cudaDeviceSynchronize()) != cudaSuccess) {
+      rc = fail(HR2_ECUDA, "setup level-gridded operand: %s", cudaGetErrorString(e));
       goto fail_tmp;
     }
   }
@@ -692,7 +722,7 @@ extern "C" int hr2_setup_destroy(hr2_ctx* ctx, hr2_setup* s) {
 
 // ------------------------------------------------------------ batch calls
 struct BatchShape {
-  int max_lev = 0, max_nu = 0, max_bins = 0, max_mu = 0, storage = 0;
+  int max_lev = 0, max_nu = 0, max_bins = 0, max_mu = 0, max_k = 0, storage = 0, cached = 0;
 };
 
 static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups, BatchShape* sh) {
@@ -706,13 +736,28 @@ static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setu
     if (!t0) t0 = s->tables;
     if (s->tables->host.storage != t0->host.storage)
       return fail(HR2_EINVAL, "setups of one batch must share the table storage type");
+    if (s->host.cached != setups[0]->host.cached)
+      return fail(HR2_EINVAL, "setups of one batch must all use, or all not use, the level-gridded operand");
     sh->max_lev = std::max(sh->max_lev, s->host.n_lev);
     sh->max_nu = std::max(sh->max_nu, s->host.n_nu);
     sh->max_bins = std::max(sh->max_bins, s->host.n_bins);
     sh->max_mu = std::max(sh->max_mu, s->host.n_mu);
+    sh->max_k = std::max(sh->max_k, s->host.n_species);
   }
   sh->storage = t0->host.storage;
+  sh->cached = setups[0]->host.cached;
   return HR2_OK;
+}
+
+// Samples per work item: the configured value, reduced so that the cached
+// path's per-warp double buffers fit in the CTA's shared memory.
+static int warps_for(const hr2_ctx* ctx, const BatchShape& sh) {
+  int w = ctx->cfg.warps_per_cta;
+  if (sh.cached) {
+    const size_t cap = 200u * 1024u;
+    while (w > 1 && forward32_smem_bytes(w, sh.max_k) > cap) --w;
+  }
+  return w;
 }
 
 extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
@@ -748,7 +793,8 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
   a.recs = w->recs;
   a.rec_ld = w->lev_cap;
   a.samp = w->samp;
-  a.warps = ctx->cfg.warps_per_cta;
+  a.warps = warps_for(ctx, sh);
+  a.err = (int*)(w->counter + 1);
   cudaError_t e;
   if ((e = launch_prep(a, s)) != cudaSuccess) return fail(HR2_ECUDA, "prep launch: %s", cudaGetErrorString(e));
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -757,6 +803,7 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
     HR2_CU(cudaEventCreate(&ev.second));
   }
   if (fp64) {
+    HR2_CU(cudaMemsetAsync(a.err, 0, sizeof(int), s));   // the planner clears it on the FP32 path
     if (ev.first) HR2_CU(cudaEventRecord(ev.first, s));
     a.highres64 = w->highres64;
     a.highres64_ld = w->nu64_cap;
@@ -773,7 +820,7 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
       return fail(HR2_ECUDA, "plan launch: %s", cudaGetErrorString(e));
     const int grid = ctx->n_sm * ctx->cfg.ctas_per_sm;
     if (ev.first) HR2_CU(cudaEventRecord(ev.first, s));
-    if ((e = launch_forward32(a, sh.max_mu, grid, s)) != cudaSuccess)
+    if ((e = launch_forward32(a, sh.max_mu, grid, sh.cached != 0, sh.max_k, s)) != cudaSuccess)
       return fail(HR2_ECUDA, "forward32 launch: %s", cudaGetErrorString(e));
     if (ev.second) HR2_CU(cudaEventRecord(ev.second, s));
   }
@@ -814,6 +861,15 @@ extern "C" int log_likelihood_batch(hr2_ctx* ctx, int n_setups, const hr2_setup*
   return HR2_OK;
 }
 
+// Reads the device error word of a workspace (the stream must be idle).
+static int check_device_error(const Workspace* w) {
+  if (!w || !w->counter) return HR2_OK;
+  unsigned int word[2] = {0, 0};
+  HR2_CU(cudaMemcpy(word, w->counter, sizeof(word), cudaMemcpyDeviceToHost));
+  if (word[1] & 1u) return fail(HR2_ETIMEDOUT, "a bounded device-side wait gave up during the last batch");
+  return HR2_OK;
+}
+
 extern "C" int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
                                  const int* setup_of_sample, const double* params, const double* log_eps, int n,
                                  double* out_lnL, float* out_bins, int bins_ld, void* stream) {
@@ -846,7 +902,22 @@ extern "C" int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* co
   if (out_bins)
     HR2_CU(cudaMemcpyAsync(out_bins, w->io_bins, sizeof(float) * (size_t)n * ld, cudaMemcpyDeviceToHost, s));
   HR2_CU(cudaStreamSynchronize(s));
-  return HR2_OK;
+  return check_device_error(w);
+}
+
+extern "C" int hr2_stream_check(hr2_ctx* ctx, void* stream) {
+  if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
+  HR2_CU(cudaSetDevice(ctx->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  HR2_CU(cudaStreamSynchronize(s));
+  Workspace* w = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    auto it = ctx->ws.find((void*)s);
+    if (it == ctx->ws.end()) return HR2_OK;
+    w = it->second;
+  }
+  return check_device_error(w);
 }
 
 // ------------------------------------------------------------ instrumentation
@@ -952,6 +1023,7 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
   a.params = params;
   a.plan = (const PlanDev*)base;
   a.counter = (unsigned int*)(base + off_counter);
+  a.err = (int*)(base + off_counter + sizeof(unsigned int));
   a.perm = (const int*)(base + off_perm);
   a.samp = (SampleDev*)(base + off_samp);
   a.recs = (LevRec*)(base + off_recs);
@@ -959,12 +1031,12 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
   a.status = out_status;
   a.highres = out_highres;
   a.highres_ld = highres_ld;
-  a.warps = ctx->cfg.warps_per_cta;
+  a.warps = warps_for(ctx, sh);
   cudaError_t e;
   // the planner resets the work counter to zero on the device before the
   // forward kernel reads it; everything else is overwritten by the kernels
   if ((e = launch_prep(a, s)) != cudaSuccess || (e = launch_plan(a, (int*)a.perm, (PlanDev*)a.plan, s)) != cudaSuccess ||
-      (e = launch_forward32(a, sh.max_mu, ctx->n_sm * ctx->cfg.ctas_per_sm, s)) != cudaSuccess ||
+      (e = launch_forward32(a, sh.max_mu, ctx->n_sm * ctx->cfg.ctas_per_sm, sh.cached != 0, sh.max_k, s)) != cudaSuccess ||
       (e = launch_bins(a, out_bins, bins_ld, false, s)) != cudaSuccess)
     return fail(HR2_ECUDA, "allocation-free launch: %s", cudaGetErrorString(e));
   return HR2_OK;

@@ -89,6 +89,11 @@ struct SetupDev {
   const double* obs_sigma;       // [n_bins] or null
   float cost;                    // relative cost of one work item (scheduling)
   const TablesDev* tables;       // device copy
+  // level-gridded operand (level_cache): the tables interpolated in p onto
+  // the levels, times log2(10), FP32, columns local to the setup's tiles
+  int cached;
+  const float* lvl32;            // [n_tiles][n_lev][n_T][n_species][64]
+  const float* cia32;            // [n_tiles][n_T][2][64]
 };
 
 // Per-(sample, level) inputs of the FP32 forward kernel, written by the
@@ -113,13 +118,16 @@ struct __align__(16) LevRec {
   float ch2h2;       // 1 + ln2 * (tail of bh2h2)
   float ch2he;       // 1 + ln2 * (tail of bh2he)
   float rdnu;        // e^{-h c dnu / (k T_j)}: Planck factor between neighbouring points
-  float pad0, pad1, pad2;
+  float wh2h2;       // 2^(bh2h2 exactly): the H2-H2 factor as a weight
+  float wh2he;       // 2^(bh2he exactly)
+  float pad0;
 };
 
 // Per-sample scalars written by the prep kernel.
 struct SampleDev {
   float A[HR2_MAX_SPECIES];   // head of log2(x_s c) + off_s log2(10) - shift, c = 1/(mmw m_u g)
   float Ac[HR2_MAX_SPECIES];  // 1 + ln2 * (its tail)
+  float W[HR2_MAX_SPECIES];   // 2^(log2(x_s c) + off_s log2(10) - shift): the same factor as a weight
   double scale;               // f (R_* / d)^2
   int status;                 // HR2_SAMPLE_* bits
   int setup;                  // setup index, -1 if invalid
@@ -155,12 +163,14 @@ struct FwdArgs {
   int rec_ld;
   SampleDev* samp;          // [n]
   int warps;                // samples per work item
+  int* err;                 // device error word (bit 0: a bounded wait gave up), or null
 };
 
 // Launchers (kern_*.cu).
 cudaError_t launch_prep(const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_plan(const FwdArgs& a, int* perm, PlanDev* plan, cudaStream_t s);
-cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, cudaStream_t s);
+cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, int max_k, cudaStream_t s);
+size_t forward32_smem_bytes(int warps, int max_k);
 cudaError_t launch_forward64(const FwdArgs& a, int max_nmu, int max_nu, cudaStream_t s);
 cudaError_t launch_bins(const FwdArgs& a, float* bins, int bins_ld, bool fp64, cudaStream_t s);
 struct LnlArgs {
@@ -185,6 +195,8 @@ cudaError_t build_w_rows(const TablesDev* d_tab, int nu_first, int n_nu, double 
 cudaError_t build_w_values(const TablesDev* d_tab, int nu_first, double R, int n_bins, const int* d_lo,
                            const int* d_hi, const double* d_invz, const int* d_rowinfo, const long long* d_rowptr,
                            float* d_w32, double* d_w64, cudaStream_t s);
+cudaError_t build_level_cache(const TablesDev* d_tab, const SetupDev& h, float* d_lvl, float* d_cia,
+                              cudaStream_t s);
 cudaError_t quantise_fp16(const double* d_src, __half* d_dst, long long rows, int n_nu, int nu_pad, double off,
                           cudaStream_t s);
 cudaError_t copy_pad_fp64(const double* d_src, double* d_dst, long long rows, int n_nu, int nu_pad,

@@ -121,6 +121,7 @@ __global__ void k_prep(FwdArgs a) {
     const float hi = (float)A;
     sd->A[lane] = hi;
     sd->Ac[lane] = (float)(1.0 + kLn2 * (A - (double)hi));
+    sd->W[lane] = (float)exp2(A);
   }
 
   const int L = S.n_lev - 1;
@@ -152,7 +153,9 @@ __global__ void k_prep(FwdArgs a) {
     r.upl_lo = (float)(upl - (double)r.upl);
     r.half_dp = (float)ldexp(lv.half_dp64, (int)shift);
     r.rdnu = (float)exp(-kC2 * T.dnu / Tj);
-    r.pad0 = r.pad1 = r.pad2 = 0.f;
+    r.wh2h2 = (float)exp2(b0);
+    r.wh2he = (float)exp2(b1);
+    r.pad0 = 0.f;
     rec[j] = r;
   }
   status = __reduce_or_sync(0xffffffffu, status);
@@ -215,6 +218,7 @@ __global__ void k_plan(FwdArgs a, int* perm, PlanDev* plan) {
     plan->total_items = items;
     plan->n_setups = a.n_setups;
     *a.counter = 0u;
+    if (a.err) *a.err = 0;
   }
   __syncthreads();
   if (tid < 32) {
@@ -321,10 +325,185 @@ constexpr float kThinD = 0.25f;
 // For optically thin layers (D < kThinD) the difference is taken as
 //   E_l - E_{l+1} = E_l D q(D),  q = 1 - D/2 + D^2/6 - ... (no cancellation).
 //   F+ = 2 pi sum_k w_k mu_k I_0(mu_k)                             (Eq. 8)
+__device__ __forceinline__ v2 ldf2(const float* p) {
+  return __ldg(reinterpret_cast<const unsigned long long*>(p));
+}
+__device__ __forceinline__ v2 lds2f(const float* p) { return *reinterpret_cast<const unsigned long long*>(p); }
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// ---- per-warp bulk-copy pipeline (Blackwell bulk async copies + mbarrier)
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait on a phase: gives up after ~1 s of SM clock and reports it.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > 2000000000ll) return false;
+  return true;
+}
+// bytes (multiple of 16) from global src to shared dst (both 16-byte aligned),
+// completion counted on bar
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+// Per-warp shared-memory layout of the cached path:
+//   rows[2][2 K + 4][64] floats, per stage (double-buffered by level
+//     parity): the rows of T cells a and a+1 of every absorber ([a][s],
+//     [a+1][s]), then the CIA rows [a][pair], [a+1][pair];
+//   recs[3][16]: the level records, three levels deep;
+//   bar[2]: one mbarrier per stage.
+struct WarpPipe {
+  float* rows;
+  float* recs;
+  unsigned long long* bar;
+};
+__host__ __device__ __forceinline__ size_t warp_rows_floats(int max_k) { return (size_t)2 * (2 * max_k + 4) * kTileNu; }
+__host__ __device__ __forceinline__ size_t warp_pipe_bytes(int max_k) {
+  return warp_rows_floats(max_k) * sizeof(float) + 3 * sizeof(LevRec) + 2 * sizeof(unsigned long long);
+}
+__device__ __forceinline__ WarpPipe warp_pipe(unsigned char* base, int max_k) {
+  WarpPipe w;
+  w.rows = reinterpret_cast<float*>(base);
+  w.recs = reinterpret_cast<float*>(base + warp_rows_floats(max_k) * sizeof(float));
+  w.bar = reinterpret_cast<unsigned long long*>(base + warp_rows_floats(max_k) * sizeof(float) + 3 * sizeof(LevRec));
+  return w;
+}
+
+// Issue stage st: one bulk copy of the absorber rows of one level (T cells
+// acell and acell+1, 2 K x 256 bytes), one of the CIA rows (1 KB, if any CIA
+// table) and up to two level records (rec_a -> record slot slot_a, rec_b ->
+// slot_b; NULL to skip), all counted on the stage's barrier.  One lane
+// issues everything.
+__device__ __forceinline__ void issue_stage(const WarpPipe& w, int st, int K, const float* lvl_level,
+                                            const float* cia_tile, int acell, bool has_cia, const LevRec* rec_a,
+                                            int slot_a, const LevRec* rec_b, int slot_b, int lane) {
+  if (lane == 0) {
+    const unsigned rows_bytes = (unsigned)(2 * K * kTileNu * sizeof(float));
+    const unsigned cia_bytes = has_cia ? (unsigned)(4 * kTileNu * sizeof(float)) : 0u;
+    const unsigned bytes = rows_bytes + cia_bytes + (rec_a ? (unsigned)sizeof(LevRec) : 0u) +
+                           (rec_b ? (unsigned)sizeof(LevRec) : 0u);
+    unsigned long long* bar = w.bar + st;
+    mbar_expect_tx(bar, bytes);
+    float* dst = w.rows + (size_t)st * (2 * K + 4) * kTileNu;
+    if (rows_bytes) bulk_copy(dst, lvl_level + (size_t)acell * K * kTileNu, rows_bytes, bar);
+    if (has_cia) bulk_copy(dst + (size_t)2 * K * kTileNu, cia_tile + (size_t)acell * 2 * kTileNu, cia_bytes, bar);
+    if (rec_a) bulk_copy(w.recs + (size_t)slot_a * 16, rec_a, (unsigned)sizeof(LevRec), bar);
+    if (rec_b) bulk_copy(w.recs + (size_t)slot_b * 16, rec_b, (unsigned)sizeof(LevRec), bar);
+  }
+}
+
+// Physics of one level for the lane's two wavenumbers, given chi_j: the
+// Planck source, and for j > 0 the layer above it added to the telescoped sum.
+struct LevelState {
+  v2 chip, Sp, S0, tau;
+  float hdp_prev;
+};
+
 template <int NMU>
+__device__ __forceinline__ void level_physics(int j, const v2 chi, const float upl, const float upl_lo, const float rdnu,
+                                              const float half_dp, const float nu0, const float nl0,
+                                              const float nu_ratio, const v2 c1n, const float thin_dtau,
+                                              const float thin_all, const v2* sMnl, const v2* sImu, v2* acc, v2* E,
+                                              LevelState& st) {
+  const float kLn2f = 0.6931471805599453f;
+  const v2 one = pk(1.f);
+  // Planck source.  t at the lane's first point: the exponent upl * nu to
+  // ~2^-46 (head product, its exact FMA error and the tail cross terms),
+  // t = 2^head (1 + ln2 * tail); the neighbour point is t * e^{-hc dnu/kT}.
+  v2 Sj;
+  {
+    const float p0 = upl * nu0;
+    const float y0 = fmaf(upl, nu0, -p0) + fmaf(upl, nl0, upl_lo * nu0);
+    const float h0 = ex2f(p0);
+    const float t0 = fmaf(h0, y0 * kLn2f, h0);
+    const v2 t = pk(t0, t0 * rdnu);
+    v2 om = sub2(one, t);
+    const float x0 = -p0 * kLn2f;  // hc nu / kT of the lane's first (smaller) point
+    if (__any_sync(0xffffffffu, x0 < 0.0625f)) {
+      // 1 - e^{-x} without cancellation for small x
+      const v2 x = pk(x0, x0 * nu_ratio);
+      const v2 ser = mul2(x, fma2(mul2(x, pk(-0.5f)),
+                                  fma2(mul2(x, pk(-1.f / 3.f)), fma2(pk(-0.25f), x, one), one), one));
+      const float2 xf = up(x), sf = up(ser), of = up(om);
+      om = pk(xf.x < 0.0625f ? sf.x : of.x, xf.y < 0.0625f ? sf.y : of.y);
+    }
+    Sj = mul2(mul2(c1n, t), rcp_2(om));
+  }
+  if (j == 0) {
+    st.S0 = Sj;
+  } else {
+    // layer j-1 between levels j-1 (top, Sp) and j (bottom, Sj)
+    const v2 dt = mul2(pk(st.hdp_prev), add2(chi, st.chip));
+    const v2 rr = rcp_2(dt);
+    const v2 dS = sub2(Sj, st.Sp);
+    st.tau = add2(st.tau, dt);
+    const float2 dtf = up(dt);
+    const bool thin = __any_sync(0xffffffffu, fminf(dtf.x, dtf.y) < thin_dtau);
+    // every lane's layer is optically thin for every node: series only
+    const bool allthin = thin && __all_sync(0xffffffffu, fmaxf(dtf.x, dtf.y) < thin_all);
+#pragma unroll
+    for (int k = 0; k < NMU; ++k) {
+      // nodes beyond the setup's count are padded with mu = 1 and zero weight
+      const v2 mk = sMnl[k];
+      const v2 En = ex2_2(mul2(st.tau, mk));   // e^{-tau_j / mu}
+      v2 c;
+      if (allthin) {
+        const v2 im = sImu[k];
+        const v2 D = mul2(dt, im);
+        const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
+                                                          pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
+        c = mul2(mul2(E[k], qs), im);
+      } else {
+        c = mul2(sub2(E[k], En), rr);           // (E_{j-1} - E_j) / dtau
+        if (thin) {
+          // E_{j-1} q(D) / mu with q(D) = (1 - e^{-D}) / D by its series
+          const v2 im = sImu[k];
+          const v2 D = mul2(dt, im);
+          const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
+                                                            pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
+          const v2 cs = mul2(mul2(E[k], qs), im);
+          const float2 Df = up(D), csf = up(cs), cf = up(c);
+          c = pk(Df.x < kThinD ? csf.x : cf.x, Df.y < kThinD ? csf.y : cf.y);
+        }
+      }
+      acc[k] = fma2(c, dS, acc[k]);
+      E[k] = En;
+    }
+  }
+  st.chip = chi;
+  st.Sp = Sj;
+  st.hdp_prev = half_dp;
+}
+
+// One warp computes one sample on one 64-point wavenumber tile (two points
+// per lane), sweeping the levels from the top (j = 0) to the bottom (j = L).
+// CACHED: absorber rows come from the setup's level-gridded operand through
+// the warp's bulk-copy pipeline (rows of level j+1 and the record of level
+// j+2 land while level j is computed).  Otherwise the FP16 tables are read
+// and interpolated bilinearly in place.
+template <int NMU, bool CACHED>
 __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
-                                           const v2* sA2, const v2* sAc2, const __half* const* sPtr,
-                                           const v2* sMnl, const v2* sImu) {
+                                           const v2* sA2, const v2* sAc2, const void* const* sPtr,
+                                           const v2* sMnl, const v2* sImu, const WarpPipe& wp_, unsigned& phase_base) {
   const int lane = threadIdx.x & 31;
   const SampleDev& sd = a.samp[i];
   float* out = a.highres + (size_t)i * a.highres_ld;
@@ -342,160 +521,192 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
   const float nl0 = (float)(nu0d - (double)nu0);       // tail
   const float nu_ratio = (float)(nu1d / nu0d);
   const v2 c1n = pk((float)(kC1 * nu0d * nu0d * nu0d), (float)(kC1 * nu1d * nu1d * nu1d));
-  const int nmu = S.n_mu;
-  const float thin_dtau = kThinD * S.mu[nmu - 1];   // dtau below which some node is thin
+  // dtau below which some node is thin (largest mu, padded nodes included),
+  // and below which every node is (smallest mu)
+  const float thin_dtau = kThinD * S.mu[NMU - 1];
+  const float thin_all = kThinD * S.mu[0];
   const int K = S.n_species;
-  const int nu_pad = T.nu_pad;
-  const unsigned o10 = (unsigned)(T.n_p * nu_pad);
-  const bool cia0 = T.has_cia[0] != 0, cia1 = T.has_cia[1] != 0;
-  const __half* __restrict__ ciab0 = T.cia16;
-  const __half* __restrict__ ciab1 = T.cia16 + (size_t)T.n_T * nu_pad;
-  const LevRec* __restrict__ rec = a.recs + (size_t)i * a.rec_ld;
   const int L = S.n_lev - 1;
-  const float kLn2f = 0.6931471805599453f;
-  const v2 one = pk(1.f), L2hi = pk(kL2Hi), L2lo = pk(kL2Lo);
+  const int nT = T.n_T;
+  const bool cia0 = T.has_cia[0] != 0, cia1 = T.has_cia[1] != 0;
+  const LevRec* __restrict__ rec = a.recs + (size_t)i * a.rec_ld;
 
   v2 acc[NMU], E[NMU];
 #pragma unroll
   for (int k = 0; k < NMU; ++k) {
     acc[k] = pk(0.f);
-    E[k] = one;
+    E[k] = pk(1.f);
   }
-  v2 chip = pk(0.f), Sp = pk(0.f), S0 = pk(0.f), tau = pk(0.f);
-  float hdp_prev = 0.f;
-  for (int j = 0; j <= L; ++j) {
-    const float4* rp = reinterpret_cast<const float4*>(rec + j);
-    const float4 r0 = __ldg(rp), r1 = __ldg(rp + 1), r2 = __ldg(rp + 2), r3 = __ldg(rp + 3);
-    const unsigned rb00 = (unsigned)__float_as_int(r0.x) * (unsigned)nu_pad + (unsigned)col;
-    const unsigned rb10 = rb00 + o10, rb01 = rb00 + (unsigned)nu_pad, rb11 = rb10 + (unsigned)nu_pad;
-    const v2 wT = pk(r0.y), wp = pk(r0.z), wq = pk(r0.w);
+  LevelState st;
+  st.chip = st.Sp = st.S0 = st.tau = pk(0.f);
+  st.hdp_prev = 0.f;
 
-    // absorption coefficient: two species per step for independent chains
-    v2 chiA = pk(0.f), chiB = pk(0.f);
-    int s = 0;
-    for (; s + 1 < K; s += 2) {
-      const __half* b = sPtr[s];
-      const __half* c = sPtr[s + 1];
-      const v2 f00 = h2f2(ldh2(b + rb00)), f10 = h2f2(ldh2(b + rb10));
-      const v2 f01 = h2f2(ldh2(b + rb01)), f11 = h2f2(ldh2(b + rb11));
-      const v2 g00 = h2f2(ldh2(c + rb00)), g10 = h2f2(ldh2(c + rb10));
-      const v2 g01 = h2f2(ldh2(c + rb01)), g11 = h2f2(ldh2(c + rb11));
-      const v2 d01 = sub2(f01, f00), e01 = sub2(g01, g00);
-      const v2 d11 = sub2(sub2(f11, f10), d01), e11 = sub2(sub2(g11, g10), e01);
-      const v2 l = fma2(wq, d11, fma2(wp, d01, fma2(wT, sub2(f10, f00), f00)));
-      const v2 m = fma2(wq, e11, fma2(wp, e01, fma2(wT, sub2(g10, g00), g00)));
-      const v2 el = fma2(L2lo, l, fma2(L2hi, l, sA2[s]));
-      const v2 em = fma2(L2lo, m, fma2(L2hi, m, sA2[s + 1]));
-      chiA = fma2(sAc2[s], ex2_2(el), chiA);
-      chiB = fma2(sAc2[s + 1], ex2_2(em), chiB);
-    }
-    if (s < K) {
-      const __half* b = sPtr[s];
-      const v2 f00 = h2f2(ldh2(b + rb00)), f10 = h2f2(ldh2(b + rb10));
-      const v2 f01 = h2f2(ldh2(b + rb01)), f11 = h2f2(ldh2(b + rb11));
-      const v2 d01 = sub2(f01, f00);
-      const v2 d11 = sub2(sub2(f11, f10), d01);
-      const v2 l = fma2(wq, d11, fma2(wp, d01, fma2(wT, sub2(f10, f00), f00)));
-      const v2 el = fma2(L2lo, l, fma2(L2hi, l, sA2[s]));
-      chiA = fma2(sAc2[s], ex2_2(el), chiA);
-    }
-    if (cia0 || cia1) {
-      const unsigned cb = (unsigned)__float_as_int(r2.x) * (unsigned)nu_pad + (unsigned)col;
+  if constexpr (CACHED) {
+    const v2* sW2 = sA2;   // cached path: per-sample absorber weights
+    // Pipeline over the levels (g = phase_base + j counts this warp's levels
+    // across items; level g uses stage g & 1, whose barrier completes phase
+    // (g >> 1) & 1).  Record of level j sits in record slot j % 3.
+    //   before the loop: stage of level 0 <- rows(0), records 0 and 1
+    //   level j:         wait stage(j)   -> rows(j) and record j+1 present
+    //                    issue stage(j+1) <- rows(j+1) (cell from record
+    //                                        j+1), record j+2
+    //                    compute level j
+    if (phase_base == 0xffffffffu) return;       // this warp's pipeline failed earlier
+    const float* lvl_tile = S.lvl32 + (size_t)tile * (L + 1) * nT * K * kTileNu;
+    const float* cia_tile = S.cia32 + (size_t)tile * nT * 2 * kTileNu;
+    const size_t lvl_step = (size_t)nT * K * kTileNu;
+    const bool has_cia = cia0 || cia1;
+    const unsigned ph = phase_base;
+    issue_stage(wp_, (int)(ph & 1u), K, lvl_tile, cia_tile, __ldg(&rec[0].acell), has_cia, rec, 0,
+                L >= 1 ? rec + 1 : nullptr, 1, lane);
+    for (int j = 0; j <= L; ++j) {
+      const unsigned g = ph + (unsigned)j;
+      const int stg = (int)(g & 1u);
+      if (!mbar_wait(wp_.bar + stg, (g >> 1) & 1u)) {
+        // the stage never completed: report, drain it (bounded) and stop using
+        // this warp's pipeline
+        if (lane == 0 && a.err) atomicOr(a.err, 1);
+        mbar_wait(wp_.bar + stg, (g >> 1) & 1u);
+        phase_base = 0xffffffffu;
+        return;
+      }
+      __syncwarp();
+      if (j < L) {
+        const int acell_n = __float_as_int(wp_.recs[(size_t)((j + 1) % 3) * 16 + 8]);
+        issue_stage(wp_, (int)((g + 1u) & 1u), K, lvl_tile + (size_t)(j + 1) * lvl_step, cia_tile, acell_n,
+                    has_cia, (j + 2 <= L) ? rec + (j + 2) : nullptr, (j + 2) % 3, nullptr, 0, lane);
+      }
+      const float* rj = wp_.recs + (size_t)(j % 3) * 16;
+      const float4 r0 = *reinterpret_cast<const float4*>(rj);
+      const float4 r1 = *reinterpret_cast<const float4*>(rj + 4);
+      const float4 r2 = *reinterpret_cast<const float4*>(rj + 8);
+      const float4 r3 = *reinterpret_cast<const float4*>(rj + 12);
+      const float r3x = r3.x;
+      const v2 wT = pk(r0.y);
+      const float* rowa = wp_.rows + (size_t)stg * (2 * K + 4) * kTileNu + 2 * lane;   // [a][s]
+      const float* rowb = rowa + (size_t)K * kTileNu;                                   // [a+1][s]
+      // chi = sum_s W_s 2^(log2 10 * log10 sigma_s), W_s = x_s c 10^off_s 2^-shift
+      v2 chiA = pk(0.f), chiB = pk(0.f);
+      int s = 0;
+      for (; s + 1 < K; s += 2) {
+        const v2 p0 = lds2f(rowa + s * kTileNu), p1 = lds2f(rowb + s * kTileNu);
+        const v2 q0 = lds2f(rowa + (s + 1) * kTileNu), q1 = lds2f(rowb + (s + 1) * kTileNu);
+        chiA = fma2(sW2[s], ex2_2(fma2(wT, sub2(p1, p0), p0)), chiA);
+        chiB = fma2(sW2[s + 1], ex2_2(fma2(wT, sub2(q1, q0), q0)), chiB);
+      }
+      if (s < K) {
+        const v2 p0 = lds2f(rowa + s * kTileNu), p1 = lds2f(rowb + s * kTileNu);
+        chiA = fma2(sW2[s], ex2_2(fma2(wT, sub2(p1, p0), p0)), chiA);
+      }
+      const float* ca = rowa + (size_t)2 * K * kTileNu;   // [a][pair], then [a+1][pair]
       if (cia0) {
-        const v2 c0 = h2f2(ldh2(ciab0 + cb)), c1 = h2f2(ldh2(ciab0 + cb + nu_pad));
-        const v2 l = fma2(wT, sub2(c1, c0), c0);
-        const v2 e = fma2(L2lo, l, fma2(L2hi, l, pk(r1.x)));
-        chiB = fma2(pk(r2.z), ex2_2(e), chiB);
+        const v2 c0 = lds2f(ca), c1 = lds2f(ca + 2 * kTileNu);
+        chiB = fma2(pk(r3.y), ex2_2(fma2(wT, sub2(c1, c0), c0)), chiB);
       }
       if (cia1) {
-        const v2 c0 = h2f2(ldh2(ciab1 + cb)), c1 = h2f2(ldh2(ciab1 + cb + nu_pad));
-        const v2 l = fma2(wT, sub2(c1, c0), c0);
-        const v2 e = fma2(L2lo, l, fma2(L2hi, l, pk(r1.y)));
-        chiA = fma2(pk(r2.w), ex2_2(e), chiA);
+        const v2 c0 = lds2f(ca + kTileNu), c1 = lds2f(ca + 3 * kTileNu);
+        chiA = fma2(pk(r3.z), ex2_2(fma2(wT, sub2(c1, c0), c0)), chiA);
       }
+      level_physics<NMU>(j, add2(chiA, chiB), r1.z, r2.y, r3x, r1.w, nu0, nl0, nu_ratio, c1n, thin_dtau, thin_all,
+                         sMnl, sImu, acc, E, st);
+      __syncwarp();  // every lane is done with stage stg and record j before they are refilled
     }
-    const v2 chi = add2(chiA, chiB);
-    // Planck source.  t at the lane's first point: the exponent upl * nu to
-    // ~2^-46 (head product, its exact FMA error and the tail cross terms),
-    // t = 2^head (1 + ln2 * tail); the neighbour point is t * e^{-hc dnu/kT}.
-    v2 Sj;
-    {
-      const float upl = r1.z, upl_lo = r2.y;
-      const float p0 = upl * nu0;
-      const float y0 = fmaf(upl, nu0, -p0) + fmaf(upl, nl0, upl_lo * nu0);
-      const float h0 = ex2f(p0);
-      const float t0 = fmaf(h0, y0 * kLn2f, h0);
-      const v2 t = pk(t0, t0 * r3.x);
-      v2 om = sub2(one, t);
-      const float x0 = -p0 * kLn2f;  // hc nu / kT of the lane's first (smaller) point
-      if (__any_sync(0xffffffffu, x0 < 0.0625f)) {
-        // 1 - e^{-x} without cancellation for small x
-        const v2 x = pk(x0, x0 * nu_ratio);
-        const v2 ser = mul2(x, fma2(mul2(x, pk(-0.5f)),
-                                    fma2(mul2(x, pk(-1.f / 3.f)), fma2(pk(-0.25f), x, one), one), one));
-        const float2 xf = up(x), sf = up(ser), of = up(om);
-        om = pk(xf.x < 0.0625f ? sf.x : of.x, xf.y < 0.0625f ? sf.y : of.y);
+    phase_base = ph + (unsigned)(L + 1);
+  } else {
+    const int nu_pad = T.nu_pad;
+    const unsigned o10 = (unsigned)(T.n_p * nu_pad);
+    const __half* __restrict__ ciab0 = T.cia16;
+    const __half* __restrict__ ciab1 = T.cia16 + (size_t)T.n_T * nu_pad;
+    const v2 L2hi = pk(kL2Hi), L2lo = pk(kL2Lo);
+    const float4* rp = reinterpret_cast<const float4*>(rec);
+    for (int j = 0; j <= L; ++j) {
+      const float4* q = rp + 4 * j;
+      const float4 r0 = __ldg(q), r1 = __ldg(q + 1), r2 = __ldg(q + 2), r3 = __ldg(q + 3);
+      const v2 wT = pk(r0.y);
+      const unsigned rb00 = (unsigned)__float_as_int(r0.x) * (unsigned)nu_pad + (unsigned)col;
+      const unsigned rb10 = rb00 + o10, rb01 = rb00 + (unsigned)nu_pad, rb11 = rb10 + (unsigned)nu_pad;
+      const v2 wp = pk(r0.z), wq = pk(r0.w);
+      v2 chiA = pk(0.f), chiB = pk(0.f);
+      // log10 sigma: bilinear in (T, log10 p) written as corner 00 plus weighted
+      // differences (exact partition of unity); two species per step
+      int s = 0;
+      for (; s + 1 < K; s += 2) {
+        const __half* b = static_cast<const __half*>(sPtr[s]);
+        const __half* c = static_cast<const __half*>(sPtr[s + 1]);
+        const v2 f00 = h2f2(ldh2(b + rb00)), f10 = h2f2(ldh2(b + rb10));
+        const v2 f01 = h2f2(ldh2(b + rb01)), f11 = h2f2(ldh2(b + rb11));
+        const v2 g00 = h2f2(ldh2(c + rb00)), g10 = h2f2(ldh2(c + rb10));
+        const v2 g01 = h2f2(ldh2(c + rb01)), g11 = h2f2(ldh2(c + rb11));
+        const v2 d01 = sub2(f01, f00), e01 = sub2(g01, g00);
+        const v2 d11 = sub2(sub2(f11, f10), d01), e11 = sub2(sub2(g11, g10), e01);
+        const v2 l = fma2(wq, d11, fma2(wp, d01, fma2(wT, sub2(f10, f00), f00)));
+        const v2 m = fma2(wq, e11, fma2(wp, e01, fma2(wT, sub2(g10, g00), g00)));
+        const v2 el = fma2(L2lo, l, fma2(L2hi, l, sA2[s]));
+        const v2 em = fma2(L2lo, m, fma2(L2hi, m, sA2[s + 1]));
+        chiA = fma2(sAc2[s], ex2_2(el), chiA);
+        chiB = fma2(sAc2[s + 1], ex2_2(em), chiB);
       }
-      Sj = mul2(mul2(c1n, t), rcp_2(om));
-    }
-    if (j == 0) {
-      S0 = Sj;
-    } else {
-      // layer j-1 between levels j-1 (top, Sp) and j (bottom, Sj)
-      const v2 dt = mul2(pk(hdp_prev), add2(chi, chip));
-      const v2 rr = rcp_2(dt);
-      const v2 dS = sub2(Sj, Sp);
-      tau = add2(tau, dt);
-      const float2 dtf = up(dt);
-      const bool thin = __any_sync(0xffffffffu, fminf(dtf.x, dtf.y) < thin_dtau);
-#pragma unroll
-      for (int k = 0; k < NMU; ++k) {
-        if (k < nmu) {
-          const v2 En = ex2_2(mul2(tau, sMnl[k]));   // e^{-tau_j / mu}
-          v2 c = mul2(sub2(E[k], En), rr);           // (E_{j-1} - E_j) / dtau
-          if (thin) {
-            // E_{j-1} q(D) / mu with q(D) = (1 - e^{-D}) / D by its series
-            const v2 im = sImu[k];
-            const v2 D = mul2(dt, im);
-            const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
-                                                              pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
-            const v2 cs = mul2(mul2(E[k], qs), im);
-            const float2 Df = up(D), csf = up(cs), cf = up(c);
-            c = pk(Df.x < kThinD ? csf.x : cf.x, Df.y < kThinD ? csf.y : cf.y);
-          }
-          acc[k] = fma2(c, dS, acc[k]);
-          E[k] = En;
+      if (s < K) {
+        const __half* b = static_cast<const __half*>(sPtr[s]);
+        const v2 f00 = h2f2(ldh2(b + rb00)), f10 = h2f2(ldh2(b + rb10));
+        const v2 f01 = h2f2(ldh2(b + rb01)), f11 = h2f2(ldh2(b + rb11));
+        const v2 d01 = sub2(f01, f00);
+        const v2 d11 = sub2(sub2(f11, f10), d01);
+        const v2 l = fma2(wq, d11, fma2(wp, d01, fma2(wT, sub2(f10, f00), f00)));
+        const v2 el = fma2(L2lo, l, fma2(L2hi, l, sA2[s]));
+        chiA = fma2(sAc2[s], ex2_2(el), chiA);
+      }
+      if (cia0 || cia1) {
+        const unsigned cb = (unsigned)__float_as_int(r2.x) * (unsigned)nu_pad + (unsigned)col;
+        if (cia0) {
+          const v2 c0 = h2f2(ldh2(ciab0 + cb)), c1 = h2f2(ldh2(ciab0 + cb + nu_pad));
+          const v2 l = fma2(wT, sub2(c1, c0), c0);
+          chiB = fma2(pk(r2.z), ex2_2(fma2(L2lo, l, fma2(L2hi, l, pk(r1.x)))), chiB);
+        }
+        if (cia1) {
+          const v2 c0 = h2f2(ldh2(ciab1 + cb)), c1 = h2f2(ldh2(ciab1 + cb + nu_pad));
+          const v2 l = fma2(wT, sub2(c1, c0), c0);
+          chiA = fma2(pk(r2.w), ex2_2(fma2(L2lo, l, fma2(L2hi, l, pk(r1.y)))), chiA);
         }
       }
+      level_physics<NMU>(j, add2(chiA, chiB), r1.z, r2.y, r3.x, r1.w, nu0, nl0, nu_ratio, c1n, thin_dtau, thin_all,
+                         sMnl, sImu, acc, E, st);
     }
-    chip = chi;
-    Sp = Sj;
-    hdp_prev = r1.w;
   }
   // I_0(mu_k) = S_0 + mu_k acc_k;  F+ = sum_k 2 pi w_k mu_k I_0(mu_k)
   float F0 = 0.f, F1 = 0.f;
-  const float2 s0 = up(S0);
+  const float2 s0 = up(st.S0);
 #pragma unroll
   for (int k = 0; k < NMU; ++k) {
-    if (k < nmu) {
-      const float2 f = up(acc[k]);
-      const float mk = S.mu[k], wk = S.wflux[k];
-      F0 = fmaf(wk, fmaf(mk, f.x, s0.x), F0);
-      F1 = fmaf(wk, fmaf(mk, f.y, s0.y), F1);
-    }
+    const float2 f = up(acc[k]);
+    const float mk = S.mu[k], wk = S.wflux[k];
+    F0 = fmaf(wk, fmaf(mk, f.x, s0.x), F0);
+    F1 = fmaf(wk, fmaf(mk, f.y, s0.y), F1);
   }
   if (in0) out[k0] = F0;
   if (in1) out[k0 + 1] = F1;
 }
 
-template <int NMU>
-__global__ void __launch_bounds__(512) k_forward32(FwdArgs a) {
+template <int NMU, bool CACHED>
+__global__ void __launch_bounds__(512) k_forward32(FwdArgs a, int max_k) {
+  extern __shared__ __align__(16) unsigned char dyn_smem[];   // cached path: per-warp pipelines
   __shared__ int s_item;
-  __shared__ const __half* sPtr[HR2_MAX_SPECIES];
+  __shared__ const void* sPtr[HR2_MAX_SPECIES];
   __shared__ v2 sMnl[NMU], sImu[NMU];
   __shared__ v2 sA2[kMaxWarps][HR2_MAX_SPECIES];
   __shared__ v2 sAc2[kMaxWarps][HR2_MAX_SPECIES];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpPipe wp_{};
+  unsigned phase_base = 0;
+  if (CACHED) {
+    wp_ = warp_pipe(dyn_smem + (size_t)warp * warp_pipe_bytes(max_k), max_k);
+    if (lane == 0) {
+      mbar_init(wp_.bar, 1);
+      mbar_init(wp_.bar + 1, 1);
+      mbar_fence_init();
+    }
+    __syncwarp();
+  }
   const PlanDev* plan = a.plan;
   const int total = plan->total_items;
   for (;;) {
@@ -513,39 +724,61 @@ __global__ void __launch_bounds__(512) k_forward32(FwdArgs a) {
     const int sb = rem - tile * nsb;
     const SetupDev& S = *a.setups[g];
     const TablesDev& T = *S.tables;
-    if (threadIdx.x < S.n_species)
+    if (!CACHED && threadIdx.x < S.n_species)
       sPtr[threadIdx.x] = T.sig16 + (size_t)S.species[threadIdx.x] * T.n_T * T.n_p * T.nu_pad;
     if (threadIdx.x < NMU) {
-      const bool on = (int)threadIdx.x < S.n_mu;
-      sMnl[threadIdx.x] = pk(on ? S.mu_nlog2e[threadIdx.x] : 0.f);
-      sImu[threadIdx.x] = pk(on ? S.inv_mu[threadIdx.x] : 0.f);
+      sMnl[threadIdx.x] = pk(S.mu_nlog2e[threadIdx.x]);
+      sImu[threadIdx.x] = pk(S.inv_mu[threadIdx.x]);
     }
     const int local = sb * a.warps + warp;
     const bool active = local < plan->count[g];
     const int i = active ? a.perm[plan->first[g] + local] : 0;
     if (active && lane < S.n_species) {
-      sA2[warp][lane] = pk(a.samp[i].A[lane]);
-      sAc2[warp][lane] = pk(a.samp[i].Ac[lane]);
+      if (CACHED) {
+        sA2[warp][lane] = pk(a.samp[i].W[lane]);
+      } else {
+        sA2[warp][lane] = pk(a.samp[i].A[lane]);
+        sAc2[warp][lane] = pk(a.samp[i].Ac[lane]);
+      }
     }
     __syncthreads();
-    if (active) solve_tile<NMU>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu);
+    if (active)
+      solve_tile<NMU, CACHED>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, wp_, phase_base);
   }
 }
 
-cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, cudaStream_t s) {
-  const int threads = 32 * a.warps;
+size_t forward32_smem_bytes(int warps, int max_k) { return (size_t)warps * warp_pipe_bytes(max_k); }
+
+template <int NMU, bool CACHED>
+static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_t s) {
+  const size_t smem = CACHED ? forward32_smem_bytes(a.warps, max_k) : 0;
+  if (CACHED) {
+    cudaError_t e = cudaFuncSetAttribute(k_forward32<NMU, CACHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_forward32<NMU, CACHED><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
+  return cudaGetLastError();
+}
+
+template <bool CACHED>
+static cudaError_t launch_forward32_t(const FwdArgs& a, int max_nmu, int grid, int max_k, cudaStream_t s) {
   switch (max_nmu) {
-    case 1: k_forward32<1><<<grid, threads, 0, s>>>(a); break;
-    case 2: k_forward32<2><<<grid, threads, 0, s>>>(a); break;
-    case 3: k_forward32<3><<<grid, threads, 0, s>>>(a); break;
-    case 4: k_forward32<4><<<grid, threads, 0, s>>>(a); break;
-    case 5: k_forward32<5><<<grid, threads, 0, s>>>(a); break;
-    case 6: k_forward32<6><<<grid, threads, 0, s>>>(a); break;
-    case 7: k_forward32<7><<<grid, threads, 0, s>>>(a); break;
-    case 8: k_forward32<8><<<grid, threads, 0, s>>>(a); break;
+    case 1: return launch_one<1, CACHED>(a, grid, max_k, s);
+    case 2: return launch_one<2, CACHED>(a, grid, max_k, s);
+    case 3: return launch_one<3, CACHED>(a, grid, max_k, s);
+    case 4: return launch_one<4, CACHED>(a, grid, max_k, s);
+    case 5: return launch_one<5, CACHED>(a, grid, max_k, s);
+    case 6: return launch_one<6, CACHED>(a, grid, max_k, s);
+    case 7: return launch_one<7, CACHED>(a, grid, max_k, s);
+    case 8: return launch_one<8, CACHED>(a, grid, max_k, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+}
+
+cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, int max_k, cudaStream_t s) {
+  return cached ? launch_forward32_t<true>(a, max_nmu, grid, max_k, s)
+                : launch_forward32_t<false>(a, max_nmu, grid, max_k, s);
 }
 
 // ---------------------------------------------------------- FP64 forward

@@ -301,4 +301,67 @@ cudaError_t build_w_values(const TablesDev* d_tab, int nu_first, double R, int n
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------- level-gridded operand
+// lvl[t][j][a][s][c] = log2(10) * ((1 - w_p) v[sp][a][b_j][col] + w_p v[sp][a][b_j+1][col])
+// for the setup's 64-point tiles t, levels j (p cell b_j, weight w_p), T rows
+// a, absorbers s (table species sp = species[s]) and columns c < 64 (table
+// column (tile0 + t)*64 + c): the p part of the bilinear interpolation
+// (Sect. 2.8), done once per setup in FP64.  The rows of T cells a and a+1
+// of every absorber at one level form one contiguous block of 2 K x 256
+// bytes, fetched with a single bulk copy.
+struct SpeciesList {
+  int sp[HR2_MAX_SPECIES];
+};
+
+__global__ void k_level_cache(const TablesDev* tab, const LevelDev* lev, int n_species, SpeciesList list, int n_lev,
+                              int tile0, int n_tiles, float* out) {
+  const TablesDev& t = *tab;
+  const long long total = (long long)n_tiles * n_lev * t.n_T * n_species * kTileNu;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long r = idx;
+    const int c = (int)(r % kTileNu);
+    r /= kTileNu;
+    const int s = (int)(r % n_species);
+    r /= n_species;
+    const int a = (int)(r % t.n_T);
+    r /= t.n_T;
+    const int j = (int)(r % n_lev);
+    const int tt = (int)(r / n_lev);
+    const LevelDev lv = lev[j];
+    const size_t row0 = (((size_t)list.sp[s] * t.n_T + a) * t.n_p + lv.pcell) * t.nu_pad + (size_t)(tile0 + tt) * kTileNu + c;
+    const double v0 = (double)__half2float(t.sig16[row0]);
+    const double v1 = (double)__half2float(t.sig16[row0 + t.nu_pad]);
+    out[idx] = (float)(kLog2_10 * ((1.0 - lv.wp64) * v0 + lv.wp64 * v1));
+  }
+}
+
+// cia[t][a][p][c] = log2(10) * v_cia[p][a][(tile0 + t)*64 + c] (0 for an absent pair)
+__global__ void k_cia_cache(const TablesDev* tab, int tile0, int n_tiles, float* out) {
+  const TablesDev& t = *tab;
+  const long long total = (long long)n_tiles * t.n_T * 2 * kTileNu;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long r = idx;
+    const int c = (int)(r % kTileNu);
+    r /= kTileNu;
+    const int p = (int)(r % 2);
+    r /= 2;
+    const int a = (int)(r % t.n_T);
+    const int tt = (int)(r / t.n_T);
+    out[idx] = t.has_cia[p] ? (float)(kLog2_10 * (double)__half2float(
+                                  t.cia16[((size_t)p * t.n_T + a) * t.nu_pad + (size_t)(tile0 + tt) * kTileNu + c]))
+                            : 0.f;
+  }
+}
+
+cudaError_t build_level_cache(const TablesDev* d_tab, const SetupDev& h, float* d_lvl, float* d_cia, cudaStream_t s) {
+  SpeciesList list{};
+  for (int i = 0; i < h.n_species; ++i) list.sp[i] = h.species[i];
+  if (h.n_species > 0)
+    k_level_cache<<<4096, 256, 0, s>>>(d_tab, h.levels, h.n_species, list, h.n_lev, h.tile0, h.n_tiles, d_lvl);
+  k_cia_cache<<<1024, 256, 0, s>>>(d_tab, h.tile0, h.n_tiles, d_cia);
+  return cudaGetLastError();
+}
+
 }  // namespace hr2

@@ -30,7 +30,7 @@ EXPORTED = [
     "hr2_tables_info", "hr2_tables_destroy", "hr2_setup_create", "hr2_setup_set_observation", "hr2_setup_info",
     "hr2_setup_destroy", "forward_model_batch", "forward_model_batch_noalloc", "log_likelihood_batch",
     "hr2_evaluate_host", "hr2_profile_enable",
-    "hr2_profile_read", "hr2_nodes_from_b", "hr2_version",
+    "hr2_profile_read", "hr2_stream_check", "hr2_nodes_from_b", "hr2_version",
 ]
 
 
@@ -51,7 +51,8 @@ class SetupDesc(C.Structure):
                 ("p_bot", C.c_double), ("n_species", C.c_int), ("species", C.POINTER(C.c_int)), ("n_mu", C.c_int),
                 ("fe_elements", C.c_int), ("fe_order", C.c_int), ("resolving_power", C.c_double),
                 ("n_bins", C.c_int), ("bin_edges", C.POINTER(C.c_double)), ("obs_flux", C.POINTER(C.c_double)),
-                ("obs_sigma", C.POINTER(C.c_double)), ("r_he", C.c_double), ("radius_cm", C.c_double)]
+                ("obs_sigma", C.POINTER(C.c_double)), ("r_he", C.c_double), ("radius_cm", C.c_double),
+                ("level_cache", C.c_int)]
 
 
 class LaunchCfg(C.Structure):
@@ -98,6 +99,7 @@ def lib():
                                                 C.c_int, _VP]),
                 "hr2_profile_enable": (C.c_int, [_VP, C.c_int]),
                 "hr2_profile_read": (C.c_int, [_VP, C.c_int, _DP, _IP]),
+                "hr2_stream_check": (C.c_int, [_VP, _VP]),
                 "hr2_nodes_from_b": (C.c_int, [C.c_int, C.c_double, _DP, _DP]),
                 "hr2_version": (C.c_char_p, []),
             }
@@ -232,7 +234,7 @@ def hr2_tables_destroy(ctx, tables):
 
 def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_elements, fe_order,
                      resolving_power, bin_edges, p_top=1e-4, p_bot=100.0, r_he=0.17, radius_cm=7.1492e9,
-                     obs_flux=None, obs_sigma=None):
+                     obs_flux=None, obs_sigma=None, level_cache=True):
     sp = np.ascontiguousarray(np.asarray(species, dtype=np.int32))
     edges, pe = _dptr(bin_edges)
     keep = [sp, edges]
@@ -244,7 +246,7 @@ def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_el
         pf, ps = _DP(), _DP()
     d = SetupDesc(int(nu_first), int(n_nu), int(n_layers), float(p_top), float(p_bot), len(sp),
                   sp.ctypes.data_as(_IP), int(n_mu), int(fe_elements), int(fe_order), float(resolving_power),
-                  len(edges) - 1, pe, pf, ps, float(r_he), float(radius_cm))
+                  len(edges) - 1, pe, pf, ps, float(r_he), float(radius_cm), int(bool(level_cache)))
     h = _VP()
     _check(lib().hr2_setup_create(ctx, tables, C.byref(d), C.byref(h)), ctx)
     return h
@@ -349,6 +351,11 @@ def hr2_profile_read(ctx, reset: bool = True):
     ms, n = C.c_double(), C.c_int()
     _check(lib().hr2_profile_read(ctx, int(bool(reset)), C.byref(ms), C.byref(n)), ctx)
     return ms.value, n.value
+
+
+def hr2_stream_check(ctx, stream=None):
+    """Synchronise the stream; raises Hr2Error(HR2_ETIMEDOUT) if a bounded device wait gave up."""
+    _check(lib().hr2_stream_check(ctx, _stream_ptr(stream)), ctx)
 
 
 def hr2_nodes_from_b(T1: float, b) -> np.ndarray:

@@ -47,6 +47,7 @@ def _run(eng, setups, sid, theta, highres_ld=None):
     hi = torch.full((n, nn), -7.0, dtype=torch.float32, device="cuda")
     st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
     eng.forward(setups, _dev(sid, torch.int32), _dev(theta, torch.float64), bins, hi, st)
+    hr2.hr2_stream_check(eng.ctx)             # no bounded device wait gave up
     torch.cuda.synchronize()
     return bins.cpu().numpy().astype(np.float64), hi.cpu().numpy().astype(np.float64), st.cpu().numpy()
 
