@@ -39,7 +39,7 @@ PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=30)
+    p.add_argument("--steps", type=int, default=300)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="hr2", choices=["hr2", "reference"])
     p.add_argument("--workload", default=WORKLOAD)
@@ -66,7 +66,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except OSError:
@@ -279,6 +279,12 @@ def run_hr2(args, world, rank, local):
                 "kernel": "k_forward32", "kernel_ms": kernel_ms,
                 "note": "exponentials required by the method per launch / event-timed kernel time; peak = "
                         "SMs x 32 ex2/clk/SM (measured) x 2032 MHz"}
+    hbm_peak, hbm_src = _hbm_peak()
+    hbm = None
+    if traffic:
+        gbs = traffic / (kernel_ms / 1e3) / 1e9
+        hbm = {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak, "peak_source": hbm_src,
+               "traffic_bytes_per_launch": traffic}
 
     # end to end through the host-buffer entry point (pinned buffers)
     h_par = [torch.as_tensor(p[0].cpu().numpy()).pin_memory() for p in pool]
@@ -325,12 +331,22 @@ def run_hr2(args, world, rank, local):
                            "l2": "flushed between timed steps (256 MB write outside the events)",
                            "launch": list(hr2.hr2_get_launch_config(eng.ctx))},
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-                "fp64_path": fp64, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+                "fp64_path": fp64, "e2e": e2e, "roofline": roofline, "hbm": hbm, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": 5 * args.steps}
         if fp64:
             line["speedup_vs_fp64_path"] = value / fp64["value"]
         print(json.dumps(line), flush=True)
     eng.close()
+
+
+def _hbm_peak():
+    """Measured copy bandwidth of this machine's B300 (GB/s), else the recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
 
 
 def _kernel_hash() -> str:
