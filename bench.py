@@ -166,7 +166,9 @@ def run_reference(args, world, rank):
     oracle.build()
     tabs = W.make_tables(wl.table)
     om = oracle.Model(tabs, wl.setups[0].as_dict())
-    per_step = max(1, args.cpu_samples // 4)
+    # one sample per host core per step: each step is about one model's worth
+    # of CPU time, so --steps K ends within a few minutes for K of a few hundred
+    per_step = max(1, os.cpu_count() or 1)
     times = []
     for k in range(args.warmup + args.steps):
         theta, _ = wl.params(per_step, seed_offset=1000 + k)

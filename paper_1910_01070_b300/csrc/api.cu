@@ -754,8 +754,7 @@ static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setu
 static int warps_for(const hr2_ctx* ctx, const BatchShape& sh) {
   int w = ctx->cfg.warps_per_cta;
   if (sh.cached) {
-    const size_t cap = 200u * 1024u;
-    while (w > 1 && forward32_smem_bytes(w, sh.max_k) > cap) --w;
+    while (w > 1 && forward32_smem_bytes(w, sh.max_k) > kForwardSmemCap) --w;
   }
   return w;
 }

@@ -12,6 +12,8 @@ namespace hr2 {
 // Wavenumber tile of one work item: 32 lanes x 2 consecutive points.
 constexpr int kTileNu = 64;
 constexpr int kMaxWarps = 16;
+// dynamic shared memory the cached forward kernel may use per CTA
+constexpr size_t kForwardSmemCap = 200u * 1024u;
 constexpr int kCiaH2H2 = HR2_MAX_SPECIES;      // offset slot of the H2-H2 CIA table
 constexpr int kCiaH2He = HR2_MAX_SPECIES + 1;  // offset slot of the H2-He CIA table
 

@@ -753,9 +753,21 @@ template <int NMU, bool CACHED>
 static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_t s) {
   const size_t smem = CACHED ? forward32_smem_bytes(a.warps, max_k) : 0;
   if (CACHED) {
-    cudaError_t e = cudaFuncSetAttribute(k_forward32<NMU, CACHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    // raise the kernel's dynamic shared-memory limit once (to the largest the
+    // library ever asks for), so that later launches, also under stream
+    // capture, make no attribute call
+    static unsigned long long raised = 0;   // one bit per device
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (!(raised & bit)) {
+      e = cudaFuncSetAttribute(k_forward32<NMU, CACHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kForwardSmemCap);
+      if (e != cudaSuccess) return e;
+      raised |= bit;
+    }
+    if (smem > kForwardSmemCap) return cudaErrorInvalidValue;
   }
   k_forward32<NMU, CACHED><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
   return cudaGetLastError();
