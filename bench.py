@@ -46,6 +46,11 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU comparison")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-samples", type=int, default=64)
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the uneven three-setup batch and the serving-loop measurements")
+    p.add_argument("--serving-seconds", type=float, default=4.0)
+    p.add_argument("--sweep-large", action="store_true",
+                   help="instead of the main line: batch sweep on the 290001-point, 12-absorber tables")
     return p.parse_args()
 
 
@@ -322,6 +327,10 @@ def run_hr2(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(wl, args.cpu_samples)
 
+    extras = None
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = run_extras(args, local, flush)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "models/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -335,10 +344,157 @@ def run_hr2(args, world, rank, local):
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
                 "fp64_path": fp64, "e2e": e2e, "roofline": roofline, "hbm": hbm, "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": 5 * args.steps}
+        if extras:
+            line.update(extras)
         if fp64:
             line["speedup_vs_fp64_path"] = value / fp64["value"]
         print(json.dumps(line), flush=True)
     eng.close()
+
+
+def _gpu_workload(wl, eng, dev, seed_offset=0):
+    """Tables and setups of a workload on the engine with a mock observation per setup
+    (the GPU model of the setup's true sample plus seeded noise)."""
+    import torch
+    from paper_1910_01070_b300 import workloads as W
+    t = eng.add_tables(wl.table, "fp16", W.make_tables(wl.table))
+    setups = [eng.add_setup(t, s) for s in wl.setups]
+    for g, (h, s) in enumerate(zip(setups, wl.setups)):
+        tb = eng.forward(setups, torch.full((1,), g, dtype=torch.int32, device=dev),
+                         torch.as_tensor(wl.truth(g)[None, :], device=dev))
+        D, sig = W.mock_observation(tb.double().cpu().numpy()[0, : s.n_bins], wl.seed + g)
+        eng.set_observation(h, D, sig)
+    return setups
+
+
+def run_extras(args, local, flush):
+    """The uneven three-setup batch (one persistent launch over 2048 samples of 12 setup
+    variants) and the continuous-batching serving loop on those setups."""
+    import torch
+
+    from paper_1910_01070_b300 import hr2, serving
+    from paper_1910_01070_b300 import workloads as W
+    from paper_1910_01070_b300.engine import Engine
+
+    dev = torch.device("cuda", local)
+    wl = W.uneven2048_3setups()
+    out = {}
+    with Engine(local) as eng:
+        setups = _gpu_workload(wl, eng, dev)
+        n = wl.n_samples
+        nb = max(s.n_bins for s in wl.setups)
+        pool = []
+        for p in range(3):
+            th, sid = wl.params(n, seed_offset=31 + p)
+            pool.append((torch.as_tensor(th, device=dev), torch.as_tensor(sid, device=dev), sid))
+        bins = torch.empty((n, nb), dtype=torch.float32, device=dev)
+        lnl = torch.empty(n, dtype=torch.float64, device=dev)
+        stream = torch.cuda.current_stream()
+        for k in range(3):
+            hr2.forward_model_batch(eng.ctx, setups, pool[k][1], pool[k][0], bins, None, None, stream)
+        torch.cuda.synchronize()
+        steps = max(3, min(args.steps, 40))
+        evs = []
+        hr2.hr2_profile_read(eng.ctx, True)
+        hr2.hr2_profile_enable(eng.ctx, True)
+        for k in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            th, sd, _ = pool[k % 3]
+            e0.record(stream)
+            hr2.forward_model_batch(eng.ctx, setups, sd, th, bins, None, None, stream)
+            hr2.log_likelihood_batch(eng.ctx, setups, sd, bins, lnl, None, stream)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        hr2.hr2_profile_enable(eng.ctx, False)
+        kms, nl = hr2.hr2_profile_read(eng.ctx, True)
+        times = [a.elapsed_time(b) for a, b in evs]
+        cap = n * steps / (sum(times) / 1e3)
+        ops = 0.0
+        for p in range(3):
+            for g, s in enumerate(wl.setups):
+                ops += float(np.sum(pool[p][2] == g)) * mufu_ops_per_model(s, 2)
+        ops /= 3
+        props = torch.cuda.get_device_properties(local)
+        peak = props.multi_processor_count * 32 * 2032e6 / 1e12
+        out["uneven_batch"] = {"workload": wl.name, "samples": n, "setups": len(wl.setups),
+                               "value": cap, "unit": "models/s", "ms_per_step": float(np.mean(times)),
+                               "p99_ms": float(np.percentile(times, 99)),
+                               "kernel_ms": kms / max(nl, 1),
+                               "alu_frac": ops / (kms / max(nl, 1) / 1e3) / 1e12 / peak,
+                               "launch": list(hr2.hr2_get_launch_config(eng.ctx))}
+        # serving: 16 nested-sampling-like streams over the 12 setups, Poisson arrivals
+        shapes = [(s.n_bins, s.n_nu, s.n_layers + 1) for s in wl.setups]
+        res = []
+        for load in (0.5, 0.8, 1.2):
+            srv = serving.Server(eng.ctx, setups, shapes, device=local, slots=3, max_batch=2048,
+                                 mem_budget=4 << 30)
+            streams, templates = [], []
+            for k in range(16):
+                g = k % len(wl.setups)
+                t = wl.truth(g)
+                lo, hi = t.copy(), t.copy()
+                lo[0], hi[0] = 4.0, 5.5
+                lo[1], hi[1] = 0.5, 2.0
+                nt = wl.setups[g].n_tnodes
+                lo[3:3 + nt], hi[3:3 + nt] = 0.7 * t[3:3 + nt], 1.3 * t[3:3 + nt]
+                nsp = len(wl.setups[g].species)
+                lo[19:19 + nsp], hi[19:19 + nsp] = -8.0, -2.0
+                rate = load * cap / (16 * 272.0)
+                streams.append(serving.RetrievalStream(k, g, lo, hi, rate=rate, seed=100 + k))
+                templates.append(t)
+            st = serving.run_open_loop(srv, streams, templates, duration=args.serving_seconds)
+            st["offered_load"] = load
+            st["offered_models_per_s"] = load * cap
+            res.append(st)
+        out["serving"] = {"streams": 16, "request_sizes": "32-512", "capacity_models_per_s": cap,
+                          "latency": "arrival to lnL on the host", "loads": res}
+    return out
+
+
+def run_sweep_large(args, local):
+    """Batch sweep on the 290001-point, 12-absorber FP16 tables (2.09 GB), direct FP16
+    interpolation and the level-gridded operand: kernel ms, models/s and the table bytes a
+    model's rows span, to show where HBM binds (small batches) and where the ALU does."""
+    import torch
+
+    from paper_1910_01070_b300 import hr2
+    from paper_1910_01070_b300 import workloads as W
+    from paper_1910_01070_b300.build import build
+    from paper_1910_01070_b300.engine import Engine
+
+    build()
+    dev = torch.device("cuda", local)
+    wl = W.large_l100_k12_nu290001_b256()
+    s = wl.setups[0]
+    res = []
+    with Engine(local) as eng:
+        t = eng.add_tables(wl.table, "fp16")
+        setups = {"direct": eng.add_setup(t, s, level_cache=False), "cached": eng.add_setup(t, s, level_cache=True)}
+        th_all, _ = wl.params(256)
+        per_model_bytes = (s.n_layers + 1) * 4 * s.n_nu * (len(s.species) + 1) * 2
+        for mode, h in setups.items():
+            for b in (1, 2, 4, 8, 16, 32, 64, 128, 256):
+                th = torch.as_tensor(th_all[:b], device=dev)
+                sd = torch.zeros(b, dtype=torch.int32, device=dev)
+                bins = torch.empty((b, s.n_bins), dtype=torch.float32, device=dev)
+                eng.forward([h], sd, th, bins)
+                torch.cuda.synchronize()
+                hr2.hr2_profile_read(eng.ctx, True)
+                hr2.hr2_profile_enable(eng.ctx, True)
+                reps = 3
+                for _ in range(reps):
+                    eng.forward([h], sd, th, bins)
+                torch.cuda.synchronize()
+                hr2.hr2_profile_enable(eng.ctx, False)
+                ms, n = hr2.hr2_profile_read(eng.ctx, True)
+                ms /= max(n, 1)
+                res.append({"mode": mode, "batch": b, "kernel_ms": ms, "models_per_s": b / (ms / 1e3),
+                            "table_row_bytes_per_model": per_model_bytes,
+                            "row_bytes_per_s_gbs": b * per_model_bytes / (ms / 1e3) / 1e9})
+                print(json.dumps(res[-1]), flush=True)
+    return res
 
 
 def _hbm_peak():
@@ -365,6 +521,9 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.sweep_large:
+        if rank == 0:
+            run_sweep_large(args, local)
     else:
         run_hr2(args, world, rank, local)
     if world > 1:
