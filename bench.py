@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--serving-seconds", type=float, default=4.0)
     p.add_argument("--sweep-large", action="store_true",
                    help="instead of the main line: batch sweep on the 290001-point, 12-absorber tables")
+    p.add_argument("--sweep-nu", type=int, default=290001, help="wavenumber points of the swept tables")
+    p.add_argument("--sweep-modes", default="direct,cached")
+    p.add_argument("--sweep-batches", default="1,2,4,8,16,32,64,128,256")
     return p.parse_args()
 
 
@@ -466,16 +469,18 @@ def run_sweep_large(args, local):
 
     build()
     dev = torch.device("cuda", local)
-    wl = W.large_l100_k12_nu290001_b256()
+    wl = W.large_l100_k12_nu290001_b256(args.sweep_nu)
     s = wl.setups[0]
     res = []
+    modes = [m for m in args.sweep_modes.split(",") if m]
+    batches = [int(b) for b in args.sweep_batches.split(",") if b]
     with Engine(local) as eng:
         t = eng.add_tables(wl.table, "fp16")
-        setups = {"direct": eng.add_setup(t, s, level_cache=False), "cached": eng.add_setup(t, s, level_cache=True)}
+        setups = {m: eng.add_setup(t, s, level_cache=(m == "cached")) for m in modes}
         th_all, _ = wl.params(256)
         per_model_bytes = (s.n_layers + 1) * 4 * s.n_nu * (len(s.species) + 1) * 2
         for mode, h in setups.items():
-            for b in (1, 2, 4, 8, 16, 32, 64, 128, 256):
+            for b in batches:
                 th = torch.as_tensor(th_all[:b], device=dev)
                 sd = torch.zeros(b, dtype=torch.int32, device=dev)
                 bins = torch.empty((b, s.n_bins), dtype=torch.float32, device=dev)
@@ -490,7 +495,8 @@ def run_sweep_large(args, local):
                 hr2.hr2_profile_enable(eng.ctx, False)
                 ms, n = hr2.hr2_profile_read(eng.ctx, True)
                 ms /= max(n, 1)
-                res.append({"mode": mode, "batch": b, "kernel_ms": ms, "models_per_s": b / (ms / 1e3),
+                res.append({"workload": wl.name, "mode": mode, "batch": b, "kernel_ms": ms,
+                            "models_per_s": b / (ms / 1e3),
                             "table_row_bytes_per_model": per_model_bytes,
                             "row_bytes_per_s_gbs": b * per_model_bytes / (ms / 1e3) / 1e9})
                 print(json.dumps(res[-1]), flush=True)

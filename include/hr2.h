@@ -142,8 +142,10 @@ typedef struct {
 
 /* Launch shape of the persistent forward kernel (chosen by the autotuner). */
 typedef struct {
-  int warps_per_cta;          /* samples processed together per work item: 1..16 */
-  int ctas_per_sm;            /* persistent CTAs per SM: 1..8                     */
+  int warps_per_cta;          /* samples processed together per work item: 1..16;
+                                 a batch with fewer samples uses fewer, with
+                                 proportionally more CTAs per SM               */
+  int ctas_per_sm;            /* persistent CTAs per SM: 1..32                    */
 } hr2_launch_cfg;
 
 /* ------------------------------------------------------------- contexts */

@@ -255,8 +255,8 @@ extern "C" int hr2_ctx_memory(const hr2_ctx* ctx, size_t* used, size_t* budget) 
 
 extern "C" int hr2_set_launch_config(hr2_ctx* ctx, const hr2_launch_cfg* cfg) {
   if (!ctx || !cfg) return fail(HR2_EINVAL, "NULL argument");
-  if (cfg->warps_per_cta < 1 || cfg->warps_per_cta > kMaxWarps || cfg->ctas_per_sm < 1 || cfg->ctas_per_sm > 8)
-    return fail(HR2_EINVAL, "launch config out of range (warps 1..%d, ctas_per_sm 1..8)", kMaxWarps);
+  if (cfg->warps_per_cta < 1 || cfg->warps_per_cta > kMaxWarps || cfg->ctas_per_sm < 1 || cfg->ctas_per_sm > 32)
+    return fail(HR2_EINVAL, "launch config out of range (warps 1..%d, ctas_per_sm 1..32)", kMaxWarps);
   ctx->cfg = *cfg;
   return HR2_OK;
 }
@@ -749,14 +749,22 @@ static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setu
   return HR2_OK;
 }
 
-// Samples per work item: the configured value, reduced so that the cached
-// path's per-warp double buffers fit in the CTA's shared memory.
-static int warps_for(const hr2_ctx* ctx, const BatchShape& sh) {
-  int w = ctx->cfg.warps_per_cta;
+// Launch shape of one batch: the configured samples per work item, reduced
+// for batches smaller than that (a work item's warps would idle otherwise)
+// and so that the cached path's per-warp pipelines fit the CTA's shared
+// memory; the persistent CTAs per SM are raised to keep the configured
+// number of warps per SM.
+struct LaunchShape {
+  int warps, ctas_per_sm;
+};
+static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {
+  int w = std::min(std::min(ctx->cfg.warps_per_cta, kForwardMaxThreads / 32), std::max(1, n));
   if (sh.cached) {
     while (w > 1 && forward32_smem_bytes(w, sh.max_k) > kForwardSmemCap) --w;
   }
-  return w;
+  const int target = ctx->cfg.warps_per_cta * ctx->cfg.ctas_per_sm;
+  const int ctas = std::max(1, std::min(32, (target + w - 1) / w));
+  return {w, ctas};
 }
 
 extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
@@ -792,7 +800,8 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
   a.recs = w->recs;
   a.rec_ld = w->lev_cap;
   a.samp = w->samp;
-  a.warps = warps_for(ctx, sh);
+  const LaunchShape ls = shape_for(ctx, sh, n);
+  a.warps = ls.warps;
   a.err = (int*)(w->counter + 1);
   cudaError_t e;
   if ((e = launch_prep(a, s)) != cudaSuccess) return fail(HR2_ECUDA, "prep launch: %s", cudaGetErrorString(e));
@@ -817,7 +826,7 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
     a.highres_ld = out_highres ? highres_ld : w->nu_cap;
     if ((e = launch_plan(a, w->perm, w->plan, s)) != cudaSuccess)
       return fail(HR2_ECUDA, "plan launch: %s", cudaGetErrorString(e));
-    const int grid = ctx->n_sm * ctx->cfg.ctas_per_sm;
+    const int grid = ctx->n_sm * ls.ctas_per_sm;
     if (ev.first) HR2_CU(cudaEventRecord(ev.first, s));
     if ((e = launch_forward32(a, sh.max_mu, grid, sh.cached != 0, sh.max_k, s)) != cudaSuccess)
       return fail(HR2_ECUDA, "forward32 launch: %s", cudaGetErrorString(e));
@@ -1030,12 +1039,13 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
   a.status = out_status;
   a.highres = out_highres;
   a.highres_ld = highres_ld;
-  a.warps = warps_for(ctx, sh);
+  const LaunchShape ls = shape_for(ctx, sh, n);
+  a.warps = ls.warps;
   cudaError_t e;
   // the planner resets the work counter to zero on the device before the
   // forward kernel reads it; everything else is overwritten by the kernels
   if ((e = launch_prep(a, s)) != cudaSuccess || (e = launch_plan(a, (int*)a.perm, (PlanDev*)a.plan, s)) != cudaSuccess ||
-      (e = launch_forward32(a, sh.max_mu, ctx->n_sm * ctx->cfg.ctas_per_sm, sh.cached != 0, sh.max_k, s)) != cudaSuccess ||
+      (e = launch_forward32(a, sh.max_mu, ctx->n_sm * ls.ctas_per_sm, sh.cached != 0, sh.max_k, s)) != cudaSuccess ||
       (e = launch_bins(a, out_bins, bins_ld, false, s)) != cudaSuccess)
     return fail(HR2_ECUDA, "allocation-free launch: %s", cudaGetErrorString(e));
   return HR2_OK;

@@ -12,6 +12,11 @@ namespace hr2 {
 // Wavenumber tile of one work item: 32 lanes x 2 consecutive points.
 constexpr int kTileNu = 64;
 constexpr int kMaxWarps = 16;
+// launch bounds of the FP32 forward kernel: at most 4 warps (samples) per
+// CTA, registers budgeted for 4 resident CTAs (16 warps) per SM (measured
+// faster than 24 warps at 80 registers)
+constexpr int kForwardMaxThreads = 128;
+constexpr int kForwardMinBlocks = 4;
 // dynamic shared memory the cached forward kernel may use per CTA
 constexpr size_t kForwardSmemCap = 200u * 1024u;
 constexpr int kCiaH2H2 = HR2_MAX_SPECIES;      // offset slot of the H2-H2 CIA table

@@ -688,7 +688,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
 }
 
 template <int NMU, bool CACHED>
-__global__ void __launch_bounds__(512) k_forward32(FwdArgs a, int max_k) {
+__global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forward32(FwdArgs a, int max_k) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];   // cached path: per-warp pipelines
   __shared__ int s_item;
   __shared__ const void* sPtr[HR2_MAX_SPECIES];

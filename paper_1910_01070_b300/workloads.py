@@ -300,13 +300,15 @@ def uneven2048_3setups() -> Workload:
     return Workload("uneven2048_3setups", t, setups, 2048, Prior(), seed)
 
 
-def large_l100_k12_nu290001_b256() -> Workload:
+def large_l100_k12_nu290001_b256(n_nu: int = 290001) -> Workload:
     """256 samples on 0.1 cm^-1 tables over 1000-30000 cm^-1 (290001 points), 12 absorbers,
-    100 layers, 8 nodes, R=1000, 2000 bins."""
+    100 layers, 8 nodes, R=1000, 2000 bins.  A smaller n_nu keeps the same grid from
+    1000 cm^-1 up (for captures that must hold only a few GB)."""
     seed = BASE_SEED + 4
-    t = TableSpec(12, _grid_T(20), _grid_logp(15), 1000.0, 0.1, 290001, seed)
-    s = make_setup(t, 1000.0, 30000.0, 100, range(12), 8, 3, 2, 1000.0, 2000)
-    return Workload("large_l100_k12_nu290001_b256", t, [s], 256, Prior(), seed)
+    t = TableSpec(12, _grid_T(20), _grid_logp(15), 1000.0, 0.1, n_nu, seed)
+    s = make_setup(t, 1000.0, 1000.0 + 0.1 * (n_nu - 1), 100, range(12), 8, 3, 2, 1000.0, 2000)
+    name = "large_l100_k12_nu%d_b256" % n_nu
+    return Workload(name, t, [s], 256, Prior(), seed)
 
 
 def tiny(n_nu: int = 16, n_layers: int = 3, n_species: int = 2, n_T: int = 3, n_p: int = 3,

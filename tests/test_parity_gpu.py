@@ -73,7 +73,7 @@ TINY = [
 ]
 
 
-@pytest.mark.parametrize("storage", ["fp16", "fp64"])
+@pytest.mark.parametrize("storage", ["fp16-level-gridded", "fp16-direct", "fp64"])
 @pytest.mark.parametrize("case", TINY, ids=[f"nu{c[0]}_L{c[1]}_K{c[2]}_mu{c[5]}" for c in TINY])
 def test_tiny_grids_match_oracle(eng, storage, case):
     n_nu, L, K, nT, nP, nmu, R, nb, off, (Ke, q) = case
@@ -81,8 +81,9 @@ def test_tiny_grids_match_oracle(eng, storage, case):
                        n_nu + off + 3, seed=hash(case) % 1000)
     tabs = W.make_tables(spec)
     setup = W.make_setup(spec, 5000.0 + off, 5000.0 + off + n_nu - 1, L, range(K), nmu, Ke, q, R, nb)
-    t = eng.add_tables(spec, storage, tabs)
-    s = eng.add_setup(t, setup)
+    t = eng.add_tables(spec, storage[:4], tabs)
+    s = eng.add_setup(t, setup, level_cache=(storage == "fp16-level-gridded"))
+    storage = storage[:4]
     theta = W.draw_params(setup, 4, 17, W.Prior(T1=(900.0, 2400.0), b=(0.85, 0.99)))
     bins, hi, st = _run(eng, [s], np.zeros(4, np.int32), theta, highres_ld=n_nu + 64)
     assert np.all(st == 0)
@@ -220,6 +221,31 @@ def test_uneven_three_setups_sampled_and_alone_equals_mix(eng):
     b2, h2, _ = _run(eng, setups, sid[sub], theta[sub], highres_ld=hi.shape[1])
     assert np.array_equal(b2, bins[sub])
     assert np.array_equal(h2, hi[sub])
+
+
+def test_direct_fp16_path_on_uneven_setups(eng):
+    """The bilinear-in-place FP16 path (no level-gridded operand) on mixed setups."""
+    wl, tabs, stored, setups, st = _workload_on(eng, "uneven2048_3setups", "fp16")
+    t = _tables_of("uneven2048_3setups", "fp16")
+    direct = [eng.add_setup(t, s, level_cache=False) for s in wl.setups]
+    theta, sid = wl.params(60, seed_offset=9)
+    bins, hi, status = _run(eng, direct, sid, theta, highres_ld=max(s.n_nu for s in wl.setups))
+    for g, s in enumerate(wl.setups):
+        om = oracle_model(stored, s)
+        for i in np.nonzero(sid == g)[0][:1]:
+            _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, s.n_nu)
+    with pytest.raises(hr2.Hr2Error):             # one batch takes setups of one kind
+        _run(eng, [setups[0], direct[1]], np.zeros(2, np.int32), theta[:2])
+
+
+def test_small_batches_use_every_warp(eng):
+    """Batches smaller than a work item (1, 2, 3 samples) give the same results as inside a large batch."""
+    wl, tabs, stored, setups, st = _workload_on(eng, "batch1024_l100_k6_nu8501", "fp16")
+    theta, sid = wl.params(8, seed_offset=21)
+    ref = _run(eng, setups, sid, theta)
+    for m in (1, 2, 3):
+        got = _run(eng, setups, sid[:m], theta[:m])
+        assert np.array_equal(got[0], ref[0][:m]) and np.array_equal(got[1], ref[1][:m])
 
 
 def test_launch_shapes_agree_bitwise(eng):
