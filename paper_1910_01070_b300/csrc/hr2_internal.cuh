@@ -9,14 +9,15 @@
 
 namespace hr2 {
 
-// Wavenumber tile of one work item: 32 lanes x 2 consecutive points.
-constexpr int kTileNu = 64;
+// Wavenumber tile of one work item: 32 lanes x 2 packed pairs of
+// consecutive points (lane l holds columns 2l, 2l+1, 64+2l, 65+2l).
+constexpr int kTileNu = 128;
 constexpr int kMaxWarps = 16;
 // launch bounds of the FP32 forward kernel: at most 4 warps (samples) per
-// CTA, registers budgeted for 4 resident CTAs (16 warps) per SM (measured
-// faster than 24 warps at 80 registers)
+// CTA, registers budgeted for 3 resident CTAs (12 warps) per SM; with two
+// packed pairs per lane each warp has enough independent work per level
 constexpr int kForwardMaxThreads = 128;
-constexpr int kForwardMinBlocks = 4;
+constexpr int kForwardMinBlocks = 3;
 // dynamic shared memory the cached forward kernel may use per CTA
 constexpr size_t kForwardSmemCap = 200u * 1024u;
 constexpr int kCiaH2H2 = HR2_MAX_SPECIES;      // offset slot of the H2-H2 CIA table

@@ -411,95 +411,127 @@ __device__ __forceinline__ void issue_stage(const WarpPipe& w, int st, int K, co
   }
 }
 
-// Physics of one level for the lane's two wavenumbers, given chi_j: the
-// Planck source, and for j > 0 the layer above it added to the telescoped sum.
-struct LevelState {
-  v2 chip, Sp, S0, tau;
-  float hdp_prev;
+// Each lane carries kPairs packed pairs of neighbouring wavenumbers: pair p
+// holds tile columns 64 p + 2 lane and 64 p + 2 lane + 1, so that a warp's
+// shared-memory row reads stay contiguous and every per-level cost that does
+// not depend on the wavenumber (records, weights, copies, votes, loop
+// control) is paid once for all of them.
+constexpr int kPairs = kTileNu / 64;
+
+// Per-lane constants of the wavenumber grid, one set per pair.
+struct NuConst {
+  float nu0[kPairs], nl0[kPairs], ratio[kPairs];  // first point (head, tail), nu_1 / nu_0
+  v2 c1n[kPairs];                                 // c1 nu^3 of both points
 };
 
+// Level sweep state of one pair: chi and S of the level above, S_0 and the
+// cumulative optical depth tau_j.
+struct LevelState {
+  v2 chip, Sp, S0, tau;
+};
+
+// Physics of one level for the lane's wavenumbers, given chi_j: the Planck
+// source, and for j > 0 the layer above it added to the telescoped sum.
 template <int NMU>
-__device__ __forceinline__ void level_physics(int j, const v2 chi, const float upl, const float upl_lo, const float rdnu,
-                                              const float half_dp, const float nu0, const float nl0,
-                                              const float nu_ratio, const v2 c1n, const float thin_dtau,
-                                              const float thin_all, const v2* sMnl, const v2* sImu, v2* acc, v2* E,
-                                              LevelState& st) {
+__device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], const float upl, const float upl_lo,
+                                              const float rdnu, const float half_dp, float& hdp_prev,
+                                              const NuConst& nc, const float thin_dtau, const float thin_all,
+                                              const v2* sMnl, const v2* sImu, v2 (&acc)[kPairs][NMU],
+                                              v2 (&E)[kPairs][NMU], LevelState (&st)[kPairs]) {
   const float kLn2f = 0.6931471805599453f;
   const v2 one = pk(1.f);
-  // Planck source.  t at the lane's first point: the exponent upl * nu to
+  // Planck source.  t at a pair's first point: the exponent upl * nu to
   // ~2^-46 (head product, its exact FMA error and the tail cross terms),
   // t = 2^head (1 + ln2 * tail); the neighbour point is t * e^{-hc dnu/kT}.
-  v2 Sj;
-  {
-    const float p0 = upl * nu0;
-    const float y0 = fmaf(upl, nu0, -p0) + fmaf(upl, nl0, upl_lo * nu0);
+  // hc nu / kT is smallest at pair 0's first point, which decides whether
+  // the small-x form is needed anywhere in the warp.
+  v2 Sj[kPairs];
+  const bool small_x = __any_sync(0xffffffffu, -(upl * nc.nu0[0]) * kLn2f < 0.0625f);
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    const float p0 = upl * nc.nu0[p];
+    const float y0 = fmaf(upl, nc.nu0[p], -p0) + fmaf(upl, nc.nl0[p], upl_lo * nc.nu0[p]);
     const float h0 = ex2f(p0);
     const float t0 = fmaf(h0, y0 * kLn2f, h0);
     const v2 t = pk(t0, t0 * rdnu);
     v2 om = sub2(one, t);
-    const float x0 = -p0 * kLn2f;  // hc nu / kT of the lane's first (smaller) point
-    if (__any_sync(0xffffffffu, x0 < 0.0625f)) {
+    if (small_x) {
       // 1 - e^{-x} without cancellation for small x
-      const v2 x = pk(x0, x0 * nu_ratio);
+      const float x0 = -p0 * kLn2f;
+      const v2 x = pk(x0, x0 * nc.ratio[p]);
       const v2 ser = mul2(x, fma2(mul2(x, pk(-0.5f)),
                                   fma2(mul2(x, pk(-1.f / 3.f)), fma2(pk(-0.25f), x, one), one), one));
       const float2 xf = up(x), sf = up(ser), of = up(om);
       om = pk(xf.x < 0.0625f ? sf.x : of.x, xf.y < 0.0625f ? sf.y : of.y);
     }
-    Sj = mul2(mul2(c1n, t), rcp_2(om));
+    Sj[p] = mul2(mul2(nc.c1n[p], t), rcp_2(om));
   }
   if (j == 0) {
-    st.S0 = Sj;
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) st[p].S0 = Sj[p];
   } else {
     // layer j-1 between levels j-1 (top, Sp) and j (bottom, Sj)
-    const v2 dt = mul2(pk(st.hdp_prev), add2(chi, st.chip));
-    const v2 rr = rcp_2(dt);
-    const v2 dS = sub2(Sj, st.Sp);
-    st.tau = add2(st.tau, dt);
-    const float2 dtf = up(dt);
-    const bool thin = __any_sync(0xffffffffu, fminf(dtf.x, dtf.y) < thin_dtau);
+    v2 dt[kPairs], rr[kPairs], dS[kPairs];
+    float dmin = 3.0e38f, dmax = 0.f;
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+      dt[p] = mul2(pk(hdp_prev), add2(chi[p], st[p].chip));
+      rr[p] = rcp_2(dt[p]);
+      dS[p] = sub2(Sj[p], st[p].Sp);
+      st[p].tau = add2(st[p].tau, dt[p]);
+      const float2 dtf = up(dt[p]);
+      dmin = fminf(dmin, fminf(dtf.x, dtf.y));
+      dmax = fmaxf(dmax, fmaxf(dtf.x, dtf.y));
+    }
+    const bool thin = __any_sync(0xffffffffu, dmin < thin_dtau);
     // every lane's layer is optically thin for every node: series only
-    const bool allthin = thin && __all_sync(0xffffffffu, fmaxf(dtf.x, dtf.y) < thin_all);
+    const bool allthin = thin && __all_sync(0xffffffffu, dmax < thin_all);
 #pragma unroll
     for (int k = 0; k < NMU; ++k) {
       // nodes beyond the setup's count are padded with mu = 1 and zero weight
       const v2 mk = sMnl[k];
-      const v2 En = ex2_2(mul2(st.tau, mk));   // e^{-tau_j / mu}
-      v2 c;
-      if (allthin) {
-        const v2 im = sImu[k];
-        const v2 D = mul2(dt, im);
-        const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
-                                                          pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
-        c = mul2(mul2(E[k], qs), im);
-      } else {
-        c = mul2(sub2(E[k], En), rr);           // (E_{j-1} - E_j) / dtau
-        if (thin) {
-          // E_{j-1} q(D) / mu with q(D) = (1 - e^{-D}) / D by its series
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) {
+        const v2 En = ex2_2(mul2(st[p].tau, mk));   // e^{-tau_j / mu}
+        v2 c;
+        if (allthin) {
           const v2 im = sImu[k];
-          const v2 D = mul2(dt, im);
+          const v2 D = mul2(dt[p], im);
           const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
                                                             pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
-          const v2 cs = mul2(mul2(E[k], qs), im);
-          const float2 Df = up(D), csf = up(cs), cf = up(c);
-          c = pk(Df.x < kThinD ? csf.x : cf.x, Df.y < kThinD ? csf.y : cf.y);
+          c = mul2(mul2(E[p][k], qs), im);
+        } else {
+          c = mul2(sub2(E[p][k], En), rr[p]);           // (E_{j-1} - E_j) / dtau
+          if (thin) {
+            // E_{j-1} q(D) / mu with q(D) = (1 - e^{-D}) / D by its series
+            const v2 im = sImu[k];
+            const v2 D = mul2(dt[p], im);
+            const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
+                                                              pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
+            const v2 cs = mul2(mul2(E[p][k], qs), im);
+            const float2 Df = up(D), csf = up(cs), cf = up(c);
+            c = pk(Df.x < kThinD ? csf.x : cf.x, Df.y < kThinD ? csf.y : cf.y);
+          }
         }
+        acc[p][k] = fma2(c, dS[p], acc[p][k]);
+        E[p][k] = En;
       }
-      acc[k] = fma2(c, dS, acc[k]);
-      E[k] = En;
     }
   }
-  st.chip = chi;
-  st.Sp = Sj;
-  st.hdp_prev = half_dp;
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    st[p].chip = chi[p];
+    st[p].Sp = Sj[p];
+  }
+  hdp_prev = half_dp;
 }
 
-// One warp computes one sample on one 64-point wavenumber tile (two points
-// per lane), sweeping the levels from the top (j = 0) to the bottom (j = L).
-// CACHED: absorber rows come from the setup's level-gridded operand through
-// the warp's bulk-copy pipeline (rows of level j+1 and the record of level
-// j+2 land while level j is computed).  Otherwise the FP16 tables are read
-// and interpolated bilinearly in place.
+// One warp computes one sample on one kTileNu-point wavenumber tile
+// (kPairs packed pairs per lane), sweeping the levels from the top (j = 0)
+// to the bottom (j = L).  CACHED: absorber rows come from the setup's
+// level-gridded operand through the warp's bulk-copy pipeline (rows of level
+// j+1 and the record of level j+2 land while level j is computed).
+// Otherwise the FP16 tables are read and interpolated bilinearly in place.
 template <int NMU, bool CACHED>
 __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
                                            const v2* sA2, const v2* sAc2, const void* const* sPtr,
@@ -507,20 +539,32 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
   const int lane = threadIdx.x & 31;
   const SampleDev& sd = a.samp[i];
   float* out = a.highres + (size_t)i * a.highres_ld;
-  const int col = (S.tile0 + tile) * kTileNu + 2 * lane;  // table column of point 0
-  const int k0 = col - S.nu_first;
-  const bool in0 = k0 >= 0 && k0 < S.n_nu;
-  const bool in1 = k0 + 1 >= 0 && k0 + 1 < S.n_nu;
+  const int col = (S.tile0 + tile) * kTileNu + 2 * lane;  // table column of pair 0's first point
+  int kout[kPairs];
+  bool in0[kPairs], in1[kPairs];
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    kout[p] = col + 64 * p - S.nu_first;
+    in0[p] = kout[p] >= 0 && kout[p] < S.n_nu;
+    in1[p] = kout[p] + 1 >= 0 && kout[p] + 1 < S.n_nu;
+  }
   if (sd.status != 0) {
-    if (in0) out[k0] = __int_as_float(0x7fc00000);
-    if (in1) out[k0 + 1] = __int_as_float(0x7fc00000);
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+      if (in0[p]) out[kout[p]] = __int_as_float(0x7fc00000);
+      if (in1[p]) out[kout[p] + 1] = __int_as_float(0x7fc00000);
+    }
     return;
   }
-  const double nu0d = T.nu0 + (double)col * T.dnu, nu1d = T.nu0 + (double)(col + 1) * T.dnu;
-  const float nu0 = (float)nu0d;                       // head
-  const float nl0 = (float)(nu0d - (double)nu0);       // tail
-  const float nu_ratio = (float)(nu1d / nu0d);
-  const v2 c1n = pk((float)(kC1 * nu0d * nu0d * nu0d), (float)(kC1 * nu1d * nu1d * nu1d));
+  NuConst nc;
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) {
+    const double nu0d = T.nu0 + (double)(col + 64 * p) * T.dnu, nu1d = nu0d + T.dnu;
+    nc.nu0[p] = (float)nu0d;                               // head
+    nc.nl0[p] = (float)(nu0d - (double)nc.nu0[p]);         // tail
+    nc.ratio[p] = (float)(nu1d / nu0d);
+    nc.c1n[p] = pk((float)(kC1 * nu0d * nu0d * nu0d), (float)(kC1 * nu1d * nu1d * nu1d));
+  }
   // dtau below which some node is thin (largest mu, padded nodes included),
   // and below which every node is (smallest mu)
   const float thin_dtau = kThinD * S.mu[NMU - 1];
@@ -531,15 +575,18 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
   const bool cia0 = T.has_cia[0] != 0, cia1 = T.has_cia[1] != 0;
   const LevRec* __restrict__ rec = a.recs + (size_t)i * a.rec_ld;
 
-  v2 acc[NMU], E[NMU];
+  v2 acc[kPairs][NMU], E[kPairs][NMU];
 #pragma unroll
-  for (int k = 0; k < NMU; ++k) {
-    acc[k] = pk(0.f);
-    E[k] = pk(1.f);
-  }
-  LevelState st;
-  st.chip = st.Sp = st.S0 = st.tau = pk(0.f);
-  st.hdp_prev = 0.f;
+  for (int p = 0; p < kPairs; ++p)
+#pragma unroll
+    for (int k = 0; k < NMU; ++k) {
+      acc[p][k] = pk(0.f);
+      E[p][k] = pk(1.f);
+    }
+  LevelState st[kPairs];
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) st[p].chip = st[p].Sp = st[p].S0 = st[p].tau = pk(0.f);
+  float hdp_prev = 0.f;
 
   if constexpr (CACHED) {
     const v2* sW2 = sA2;   // cached path: per-sample absorber weights
@@ -581,34 +628,55 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       const float4 r1 = *reinterpret_cast<const float4*>(rj + 4);
       const float4 r2 = *reinterpret_cast<const float4*>(rj + 8);
       const float4 r3 = *reinterpret_cast<const float4*>(rj + 12);
-      const float r3x = r3.x;
       const v2 wT = pk(r0.y);
       const float* rowa = wp_.rows + (size_t)stg * (2 * K + 4) * kTileNu + 2 * lane;   // [a][s]
       const float* rowb = rowa + (size_t)K * kTileNu;                                   // [a+1][s]
       // chi = sum_s W_s 2^(log2 10 * log10 sigma_s), W_s = x_s c 10^off_s 2^-shift
-      v2 chiA = pk(0.f), chiB = pk(0.f);
+      v2 chA[kPairs], chB[kPairs];
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) chA[p] = chB[p] = pk(0.f);
       int s = 0;
       for (; s + 1 < K; s += 2) {
-        const v2 p0 = lds2f(rowa + s * kTileNu), p1 = lds2f(rowb + s * kTileNu);
-        const v2 q0 = lds2f(rowa + (s + 1) * kTileNu), q1 = lds2f(rowb + (s + 1) * kTileNu);
-        chiA = fma2(sW2[s], ex2_2(fma2(wT, sub2(p1, p0), p0)), chiA);
-        chiB = fma2(sW2[s + 1], ex2_2(fma2(wT, sub2(q1, q0), q0)), chiB);
+        const v2 w0 = sW2[s], w1 = sW2[s + 1];
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          const int o = s * kTileNu + 64 * p;
+          const v2 p0 = lds2f(rowa + o), p1 = lds2f(rowb + o);
+          const v2 q0 = lds2f(rowa + o + kTileNu), q1 = lds2f(rowb + o + kTileNu);
+          chA[p] = fma2(w0, ex2_2(fma2(wT, sub2(p1, p0), p0)), chA[p]);
+          chB[p] = fma2(w1, ex2_2(fma2(wT, sub2(q1, q0), q0)), chB[p]);
+        }
       }
       if (s < K) {
-        const v2 p0 = lds2f(rowa + s * kTileNu), p1 = lds2f(rowb + s * kTileNu);
-        chiA = fma2(sW2[s], ex2_2(fma2(wT, sub2(p1, p0), p0)), chiA);
+        const v2 w0 = sW2[s];
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          const int o = s * kTileNu + 64 * p;
+          const v2 p0 = lds2f(rowa + o), p1 = lds2f(rowb + o);
+          chA[p] = fma2(w0, ex2_2(fma2(wT, sub2(p1, p0), p0)), chA[p]);
+        }
       }
       const float* ca = rowa + (size_t)2 * K * kTileNu;   // [a][pair], then [a+1][pair]
       if (cia0) {
-        const v2 c0 = lds2f(ca), c1 = lds2f(ca + 2 * kTileNu);
-        chiB = fma2(pk(r3.y), ex2_2(fma2(wT, sub2(c1, c0), c0)), chiB);
+        const v2 w = pk(r3.y);
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          const v2 c0 = lds2f(ca + 64 * p), c1 = lds2f(ca + 2 * kTileNu + 64 * p);
+          chB[p] = fma2(w, ex2_2(fma2(wT, sub2(c1, c0), c0)), chB[p]);
+        }
       }
       if (cia1) {
-        const v2 c0 = lds2f(ca + kTileNu), c1 = lds2f(ca + 3 * kTileNu);
-        chiA = fma2(pk(r3.z), ex2_2(fma2(wT, sub2(c1, c0), c0)), chiA);
+        const v2 w = pk(r3.z);
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          const v2 c0 = lds2f(ca + kTileNu + 64 * p), c1 = lds2f(ca + 3 * kTileNu + 64 * p);
+          chA[p] = fma2(w, ex2_2(fma2(wT, sub2(c1, c0), c0)), chA[p]);
+        }
       }
-      level_physics<NMU>(j, add2(chiA, chiB), r1.z, r2.y, r3x, r1.w, nu0, nl0, nu_ratio, c1n, thin_dtau, thin_all,
-                         sMnl, sImu, acc, E, st);
+      v2 chi[kPairs];
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
+      level_physics<NMU>(j, chi, r1.z, r2.y, r3.x, r1.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu, acc, E, st);
       __syncwarp();  // every lane is done with stage stg and record j before they are refilled
     }
     phase_base = ph + (unsigned)(L + 1);
@@ -626,65 +694,74 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       const unsigned rb00 = (unsigned)__float_as_int(r0.x) * (unsigned)nu_pad + (unsigned)col;
       const unsigned rb10 = rb00 + o10, rb01 = rb00 + (unsigned)nu_pad, rb11 = rb10 + (unsigned)nu_pad;
       const v2 wp = pk(r0.z), wq = pk(r0.w);
-      v2 chiA = pk(0.f), chiB = pk(0.f);
+      v2 chA[kPairs], chB[kPairs];
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) chA[p] = chB[p] = pk(0.f);
       // log10 sigma: bilinear in (T, log10 p) written as corner 00 plus weighted
-      // differences (exact partition of unity); two species per step
+      // differences (exact partition of unity); two species per step, the
+      // pairs of the lane in parallel
       int s = 0;
-      for (; s + 1 < K; s += 2) {
+      for (; s < K; s += 2) {
+        const bool two = s + 1 < K;
         const __half* b = static_cast<const __half*>(sPtr[s]);
-        const __half* c = static_cast<const __half*>(sPtr[s + 1]);
-        const v2 f00 = h2f2(ldh2(b + rb00)), f10 = h2f2(ldh2(b + rb10));
-        const v2 f01 = h2f2(ldh2(b + rb01)), f11 = h2f2(ldh2(b + rb11));
-        const v2 g00 = h2f2(ldh2(c + rb00)), g10 = h2f2(ldh2(c + rb10));
-        const v2 g01 = h2f2(ldh2(c + rb01)), g11 = h2f2(ldh2(c + rb11));
-        const v2 d01 = sub2(f01, f00), e01 = sub2(g01, g00);
-        const v2 d11 = sub2(sub2(f11, f10), d01), e11 = sub2(sub2(g11, g10), e01);
-        const v2 l = fma2(wq, d11, fma2(wp, d01, fma2(wT, sub2(f10, f00), f00)));
-        const v2 m = fma2(wq, e11, fma2(wp, e01, fma2(wT, sub2(g10, g00), g00)));
-        const v2 el = fma2(L2lo, l, fma2(L2hi, l, sA2[s]));
-        const v2 em = fma2(L2lo, m, fma2(L2hi, m, sA2[s + 1]));
-        chiA = fma2(sAc2[s], ex2_2(el), chiA);
-        chiB = fma2(sAc2[s + 1], ex2_2(em), chiB);
-      }
-      if (s < K) {
-        const __half* b = static_cast<const __half*>(sPtr[s]);
-        const v2 f00 = h2f2(ldh2(b + rb00)), f10 = h2f2(ldh2(b + rb10));
-        const v2 f01 = h2f2(ldh2(b + rb01)), f11 = h2f2(ldh2(b + rb11));
-        const v2 d01 = sub2(f01, f00);
-        const v2 d11 = sub2(sub2(f11, f10), d01);
-        const v2 l = fma2(wq, d11, fma2(wp, d01, fma2(wT, sub2(f10, f00), f00)));
-        const v2 el = fma2(L2lo, l, fma2(L2hi, l, sA2[s]));
-        chiA = fma2(sAc2[s], ex2_2(el), chiA);
+        const __half* c = static_cast<const __half*>(sPtr[two ? s + 1 : s]);
+        const v2 A0 = sA2[s], Ac0 = sAc2[s];
+        const v2 A1 = sA2[two ? s + 1 : s], Ac1 = two ? sAc2[s + 1] : pk(0.f);
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          const unsigned o = 64u * (unsigned)p;
+          const v2 f00 = h2f2(ldh2(b + rb00 + o)), f10 = h2f2(ldh2(b + rb10 + o));
+          const v2 f01 = h2f2(ldh2(b + rb01 + o)), f11 = h2f2(ldh2(b + rb11 + o));
+          const v2 g00 = h2f2(ldh2(c + rb00 + o)), g10 = h2f2(ldh2(c + rb10 + o));
+          const v2 g01 = h2f2(ldh2(c + rb01 + o)), g11 = h2f2(ldh2(c + rb11 + o));
+          const v2 d01 = sub2(f01, f00), e01 = sub2(g01, g00);
+          const v2 d11 = sub2(sub2(f11, f10), d01), e11 = sub2(sub2(g11, g10), e01);
+          const v2 l = fma2(wq, d11, fma2(wp, d01, fma2(wT, sub2(f10, f00), f00)));
+          const v2 m = fma2(wq, e11, fma2(wp, e01, fma2(wT, sub2(g10, g00), g00)));
+          const v2 el = fma2(L2lo, l, fma2(L2hi, l, A0));
+          const v2 em = fma2(L2lo, m, fma2(L2hi, m, A1));
+          chA[p] = fma2(Ac0, ex2_2(el), chA[p]);
+          chB[p] = fma2(Ac1, ex2_2(em), chB[p]);   // zero weight when K is odd and s = K - 1
+        }
       }
       if (cia0 || cia1) {
         const unsigned cb = (unsigned)__float_as_int(r2.x) * (unsigned)nu_pad + (unsigned)col;
-        if (cia0) {
-          const v2 c0 = h2f2(ldh2(ciab0 + cb)), c1 = h2f2(ldh2(ciab0 + cb + nu_pad));
-          const v2 l = fma2(wT, sub2(c1, c0), c0);
-          chiB = fma2(pk(r2.z), ex2_2(fma2(L2lo, l, fma2(L2hi, l, pk(r1.x)))), chiB);
-        }
-        if (cia1) {
-          const v2 c0 = h2f2(ldh2(ciab1 + cb)), c1 = h2f2(ldh2(ciab1 + cb + nu_pad));
-          const v2 l = fma2(wT, sub2(c1, c0), c0);
-          chiA = fma2(pk(r2.w), ex2_2(fma2(L2lo, l, fma2(L2hi, l, pk(r1.y)))), chiA);
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          const unsigned o = 64u * (unsigned)p;
+          if (cia0) {
+            const v2 c0 = h2f2(ldh2(ciab0 + cb + o)), c1 = h2f2(ldh2(ciab0 + cb + nu_pad + o));
+            const v2 l = fma2(wT, sub2(c1, c0), c0);
+            chB[p] = fma2(pk(r2.z), ex2_2(fma2(L2lo, l, fma2(L2hi, l, pk(r1.x)))), chB[p]);
+          }
+          if (cia1) {
+            const v2 c0 = h2f2(ldh2(ciab1 + cb + o)), c1 = h2f2(ldh2(ciab1 + cb + nu_pad + o));
+            const v2 l = fma2(wT, sub2(c1, c0), c0);
+            chA[p] = fma2(pk(r2.w), ex2_2(fma2(L2lo, l, fma2(L2hi, l, pk(r1.y)))), chA[p]);
+          }
         }
       }
-      level_physics<NMU>(j, add2(chiA, chiB), r1.z, r2.y, r3.x, r1.w, nu0, nl0, nu_ratio, c1n, thin_dtau, thin_all,
-                         sMnl, sImu, acc, E, st);
+      v2 chi[kPairs];
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
+      level_physics<NMU>(j, chi, r1.z, r2.y, r3.x, r1.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu, acc, E, st);
     }
   }
   // I_0(mu_k) = S_0 + mu_k acc_k;  F+ = sum_k 2 pi w_k mu_k I_0(mu_k)
-  float F0 = 0.f, F1 = 0.f;
-  const float2 s0 = up(st.S0);
 #pragma unroll
-  for (int k = 0; k < NMU; ++k) {
-    const float2 f = up(acc[k]);
-    const float mk = S.mu[k], wk = S.wflux[k];
-    F0 = fmaf(wk, fmaf(mk, f.x, s0.x), F0);
-    F1 = fmaf(wk, fmaf(mk, f.y, s0.y), F1);
+  for (int p = 0; p < kPairs; ++p) {
+    float F0 = 0.f, F1 = 0.f;
+    const float2 s0 = up(st[p].S0);
+#pragma unroll
+    for (int k = 0; k < NMU; ++k) {
+      const float2 f = up(acc[p][k]);
+      const float mk = S.mu[k], wk = S.wflux[k];
+      F0 = fmaf(wk, fmaf(mk, f.x, s0.x), F0);
+      F1 = fmaf(wk, fmaf(mk, f.y, s0.y), F1);
+    }
+    if (in0[p]) out[kout[p]] = F0;
+    if (in1[p]) out[kout[p] + 1] = F1;
   }
-  if (in0) out[k0] = F0;
-  if (in1) out[k0 + 1] = F1;
 }
 
 template <int NMU, bool CACHED>
