@@ -484,37 +484,55 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
       dmax = fmaxf(dmax, fmaxf(dtf.x, dtf.y));
     }
     const bool thin = __any_sync(0xffffffffu, dmin < thin_dtau);
-    // every lane's layer is optically thin for every node: series only
     const bool allthin = thin && __all_sync(0xffffffffu, dmax < thin_all);
+    // The three regimes are separate loops so that the decision is taken once
+    // per level.  Nodes beyond the setup's count are padded with mu = 1 and
+    // zero weight.
+    if (allthin) {
+      // every lane's layer is optically thin for every node: series only,
+      // (E_{j-1} - E_j) / dtau = E_{j-1} q(D) / mu
 #pragma unroll
-    for (int k = 0; k < NMU; ++k) {
-      // nodes beyond the setup's count are padded with mu = 1 and zero weight
-      const v2 mk = sMnl[k];
+      for (int k = 0; k < NMU; ++k) {
+        const v2 mk = sMnl[k], im = sImu[k];
 #pragma unroll
-      for (int p = 0; p < kPairs; ++p) {
-        const v2 En = ex2_2(mul2(st[p].tau, mk));   // e^{-tau_j / mu}
-        v2 c;
-        if (allthin) {
-          const v2 im = sImu[k];
+        for (int p = 0; p < kPairs; ++p) {
+          const v2 En = ex2_2(mul2(st[p].tau, mk));   // e^{-tau_j / mu}
           const v2 D = mul2(dt[p], im);
           const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
                                                             pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
-          c = mul2(mul2(E[p][k], qs), im);
-        } else {
-          c = mul2(sub2(E[p][k], En), rr[p]);           // (E_{j-1} - E_j) / dtau
-          if (thin) {
-            // E_{j-1} q(D) / mu with q(D) = (1 - e^{-D}) / D by its series
-            const v2 im = sImu[k];
-            const v2 D = mul2(dt[p], im);
-            const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
-                                                              pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
-            const v2 cs = mul2(mul2(E[p][k], qs), im);
-            const float2 Df = up(D), csf = up(cs), cf = up(c);
-            c = pk(Df.x < kThinD ? csf.x : cf.x, Df.y < kThinD ? csf.y : cf.y);
-          }
+          acc[p][k] = fma2(mul2(mul2(E[p][k], qs), im), dS[p], acc[p][k]);
+          E[p][k] = En;
         }
-        acc[p][k] = fma2(c, dS[p], acc[p][k]);
-        E[p][k] = En;
+      }
+    } else if (thin) {
+      // some are thin: the series where D < kThinD, the difference elsewhere
+#pragma unroll
+      for (int k = 0; k < NMU; ++k) {
+        const v2 mk = sMnl[k], im = sImu[k];
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          const v2 En = ex2_2(mul2(st[p].tau, mk));
+          const v2 c = mul2(sub2(E[p][k], En), rr[p]);
+          const v2 D = mul2(dt[p], im);
+          const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
+                                                            pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
+          const v2 cs = mul2(mul2(E[p][k], qs), im);
+          const float2 Df = up(D), csf = up(cs), cf = up(c);
+          const v2 cc = pk(Df.x < kThinD ? csf.x : cf.x, Df.y < kThinD ? csf.y : cf.y);
+          acc[p][k] = fma2(cc, dS[p], acc[p][k]);
+          E[p][k] = En;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < NMU; ++k) {
+        const v2 mk = sMnl[k];
+#pragma unroll
+        for (int p = 0; p < kPairs; ++p) {
+          const v2 En = ex2_2(mul2(st[p].tau, mk));
+          acc[p][k] = fma2(mul2(sub2(E[p][k], En), rr[p]), dS[p], acc[p][k]);   // (E_{j-1} - E_j) / dtau
+          E[p][k] = En;
+        }
       }
     }
   }
