@@ -722,7 +722,7 @@ extern "C" int hr2_setup_destroy(hr2_ctx* ctx, hr2_setup* s) {
 
 // ------------------------------------------------------------ batch calls
 struct BatchShape {
-  int max_lev = 0, max_nu = 0, max_bins = 0, max_mu = 0, max_k = 0, storage = 0, cached = 0;
+  int max_lev = 0, max_nu = 0, max_bins = 0, max_mu = 0, max_k = 0, min_k = 1 << 30, storage = 0, cached = 0;
 };
 
 static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups, BatchShape* sh) {
@@ -743,6 +743,7 @@ static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setu
     sh->max_bins = std::max(sh->max_bins, s->host.n_bins);
     sh->max_mu = std::max(sh->max_mu, s->host.n_mu);
     sh->max_k = std::max(sh->max_k, s->host.n_species);
+    sh->min_k = std::min(sh->min_k, s->host.n_species);
   }
   sh->storage = t0->host.storage;
   sh->cached = setups[0]->host.cached;
@@ -757,6 +758,15 @@ static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setu
 struct LaunchShape {
   int warps, ctas_per_sm;
 };
+// Compile-time absorber bound of the cached forward kernel: the batch's
+// absorber count rounded up to even when every setup has that count or one
+// less (the padded absorber gets weight 0), else 0 (runtime count).
+static int absorber_bound(const BatchShape& sh) {
+  if (!sh.cached || sh.max_k < 1) return 0;
+  const int kt = (sh.max_k + 1) & ~1;
+  return (sh.min_k >= kt - 1 && kt <= HR2_MAX_SPECIES) ? kt : 0;
+}
+
 static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {
   int w = std::min(std::min(ctx->cfg.warps_per_cta, kForwardMaxThreads / 32), std::max(1, n));
   if (sh.cached) {
@@ -828,7 +838,7 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
       return fail(HR2_ECUDA, "plan launch: %s", cudaGetErrorString(e));
     const int grid = ctx->n_sm * ls.ctas_per_sm;
     if (ev.first) HR2_CU(cudaEventRecord(ev.first, s));
-    if ((e = launch_forward32(a, sh.max_mu, grid, sh.cached != 0, sh.max_k, s)) != cudaSuccess)
+    if ((e = launch_forward32(a, sh.max_mu, grid, sh.cached != 0, sh.max_k, absorber_bound(sh), s)) != cudaSuccess)
       return fail(HR2_ECUDA, "forward32 launch: %s", cudaGetErrorString(e));
     if (ev.second) HR2_CU(cudaEventRecord(ev.second, s));
   }
@@ -1045,7 +1055,8 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
   // the planner resets the work counter to zero on the device before the
   // forward kernel reads it; everything else is overwritten by the kernels
   if ((e = launch_prep(a, s)) != cudaSuccess || (e = launch_plan(a, (int*)a.perm, (PlanDev*)a.plan, s)) != cudaSuccess ||
-      (e = launch_forward32(a, sh.max_mu, ctx->n_sm * ls.ctas_per_sm, sh.cached != 0, sh.max_k, s)) != cudaSuccess ||
+      (e = launch_forward32(a, sh.max_mu, ctx->n_sm * ls.ctas_per_sm, sh.cached != 0, sh.max_k, absorber_bound(sh),
+                        s)) != cudaSuccess ||
       (e = launch_bins(a, out_bins, bins_ld, false, s)) != cudaSuccess)
     return fail(HR2_ECUDA, "allocation-free launch: %s", cudaGetErrorString(e));
   return HR2_OK;

@@ -177,7 +177,10 @@ struct FwdArgs {
 // Launchers (kern_*.cu).
 cudaError_t launch_prep(const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_plan(const FwdArgs& a, int* perm, PlanDev* plan, cudaStream_t s);
-cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, int max_k, cudaStream_t s);
+// kt: 0, or an even bound on the absorber count of the cached path with
+// every setup of the batch at kt or kt - 1 absorbers (see absorber_bound)
+cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, int max_k, int kt,
+                             cudaStream_t s);
 size_t forward32_smem_bytes(int warps, int max_k);
 cudaError_t launch_forward64(const FwdArgs& a, int max_nmu, int max_nu, cudaStream_t s);
 cudaError_t launch_bins(const FwdArgs& a, float* bins, int bins_ld, bool fp64, cudaStream_t s);

@@ -550,7 +550,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
 // level-gridded operand through the warp's bulk-copy pipeline (rows of level
 // j+1 and the record of level j+2 land while level j is computed).
 // Otherwise the FP16 tables are read and interpolated bilinearly in place.
-template <int NMU, bool CACHED>
+template <int NMU, bool CACHED, int KT>
 __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
                                            const v2* sA2, const v2* sAc2, const void* const* sPtr,
                                            const v2* sMnl, const v2* sImu, const WarpPipe& wp_, unsigned& phase_base) {
@@ -653,6 +653,22 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       v2 chA[kPairs], chB[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chA[p] = chB[p] = pk(0.f);
+      if constexpr (KT > 0) {
+        // every setup of the batch has K = KT or KT - 1 absorbers; a padded
+        // absorber has weight 0 and reads finite rows of the stage
+#pragma unroll
+        for (int s = 0; s < KT; s += 2) {
+          const v2 w0 = sW2[s], w1 = sW2[s + 1];
+#pragma unroll
+          for (int p = 0; p < kPairs; ++p) {
+            const int o = s * kTileNu + 64 * p;
+            const v2 p0 = lds2f(rowa + o), p1 = lds2f(rowb + o);
+            const v2 q0 = lds2f(rowa + o + kTileNu), q1 = lds2f(rowb + o + kTileNu);
+            chA[p] = fma2(w0, ex2_2(fma2(wT, sub2(p1, p0), p0)), chA[p]);
+            chB[p] = fma2(w1, ex2_2(fma2(wT, sub2(q1, q0), q0)), chB[p]);
+          }
+        }
+      } else {
       int s = 0;
       for (; s + 1 < K; s += 2) {
         const v2 w0 = sW2[s], w1 = sW2[s + 1];
@@ -673,6 +689,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
           const v2 p0 = lds2f(rowa + o), p1 = lds2f(rowb + o);
           chA[p] = fma2(w0, ex2_2(fma2(wT, sub2(p1, p0), p0)), chA[p]);
         }
+      }
       }
       const float* ca = rowa + (size_t)2 * K * kTileNu;   // [a][pair], then [a+1][pair]
       if (cia0) {
@@ -782,7 +799,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
   }
 }
 
-template <int NMU, bool CACHED>
+template <int NMU, bool CACHED, int KT>
 __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forward32(FwdArgs a, int max_k) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];   // cached path: per-warp pipelines
   __shared__ int s_item;
@@ -795,6 +812,13 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
   unsigned phase_base = 0;
   if (CACHED) {
     wp_ = warp_pipe(dyn_smem + (size_t)warp * warp_pipe_bytes(max_k), max_k);
+    // zero the stage rows once, so that rows a padded absorber may read are
+    // finite before any copy has written them; then order these generic
+    // writes before the bulk copies that will overwrite them
+    const int nrow = (int)warp_rows_floats(max_k);
+    for (int q = lane; q < nrow; q += 32) wp_.rows[q] = 0.f;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
     if (lane == 0) {
       mbar_init(wp_.bar, 1);
       mbar_init(wp_.bar + 1, 1);
@@ -828,23 +852,23 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
     const int local = sb * a.warps + warp;
     const bool active = local < plan->count[g];
     const int i = active ? a.perm[plan->first[g] + local] : 0;
-    if (active && lane < S.n_species) {
-      if (CACHED) {
-        sA2[warp][lane] = pk(a.samp[i].W[lane]);
-      } else {
+    if (CACHED) {
+      if (lane < HR2_MAX_SPECIES) sA2[warp][lane] = (active && lane < S.n_species) ? pk(a.samp[i].W[lane]) : pk(0.f);
+    } else if (active && lane < S.n_species) {
+      {
         sA2[warp][lane] = pk(a.samp[i].A[lane]);
         sAc2[warp][lane] = pk(a.samp[i].Ac[lane]);
       }
     }
     __syncthreads();
     if (active)
-      solve_tile<NMU, CACHED>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, wp_, phase_base);
+      solve_tile<NMU, CACHED, KT>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, wp_, phase_base);
   }
 }
 
 size_t forward32_smem_bytes(int warps, int max_k) { return (size_t)warps * warp_pipe_bytes(max_k); }
 
-template <int NMU, bool CACHED>
+template <int NMU, bool CACHED, int KT>
 static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_t s) {
   const size_t smem = CACHED ? forward32_smem_bytes(a.warps, max_k) : 0;
   if (CACHED) {
@@ -857,35 +881,53 @@ static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(raised & bit)) {
-      e = cudaFuncSetAttribute(k_forward32<NMU, CACHED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_forward32<NMU, CACHED, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kForwardSmemCap);
       if (e != cudaSuccess) return e;
       raised |= bit;
     }
     if (smem > kForwardSmemCap) return cudaErrorInvalidValue;
   }
-  k_forward32<NMU, CACHED><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
+  k_forward32<NMU, CACHED, KT><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
   return cudaGetLastError();
 }
 
-template <bool CACHED>
-static cudaError_t launch_forward32_t(const FwdArgs& a, int max_nmu, int grid, int max_k, cudaStream_t s) {
-  switch (max_nmu) {
-    case 1: return launch_one<1, CACHED>(a, grid, max_k, s);
-    case 2: return launch_one<2, CACHED>(a, grid, max_k, s);
-    case 3: return launch_one<3, CACHED>(a, grid, max_k, s);
-    case 4: return launch_one<4, CACHED>(a, grid, max_k, s);
-    case 5: return launch_one<5, CACHED>(a, grid, max_k, s);
-    case 6: return launch_one<6, CACHED>(a, grid, max_k, s);
-    case 7: return launch_one<7, CACHED>(a, grid, max_k, s);
-    case 8: return launch_one<8, CACHED>(a, grid, max_k, s);
+// cached path: absorber bound kt (0 = any mix of absorber counts, else an
+// even bound with every setup at kt or kt - 1)
+template <int NMU>
+static cudaError_t launch_cached(const FwdArgs& a, int grid, int max_k, int kt, cudaStream_t s) {
+  switch (kt) {
+    case 0: return launch_one<NMU, true, 0>(a, grid, max_k, s);
+    case 2: return launch_one<NMU, true, 2>(a, grid, max_k, s);
+    case 4: return launch_one<NMU, true, 4>(a, grid, max_k, s);
+    case 6: return launch_one<NMU, true, 6>(a, grid, max_k, s);
+    case 8: return launch_one<NMU, true, 8>(a, grid, max_k, s);
+    case 10: return launch_one<NMU, true, 10>(a, grid, max_k, s);
+    case 12: return launch_one<NMU, true, 12>(a, grid, max_k, s);
+    case 14: return launch_one<NMU, true, 14>(a, grid, max_k, s);
+    case 16: return launch_one<NMU, true, 16>(a, grid, max_k, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, int max_k, cudaStream_t s) {
-  return cached ? launch_forward32_t<true>(a, max_nmu, grid, max_k, s)
-                : launch_forward32_t<false>(a, max_nmu, grid, max_k, s);
+template <int NMU>
+static cudaError_t launch_nmu(const FwdArgs& a, int grid, bool cached, int max_k, int kt, cudaStream_t s) {
+  return cached ? launch_cached<NMU>(a, grid, max_k, kt, s) : launch_one<NMU, false, 0>(a, grid, max_k, s);
+}
+
+cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, int max_k, int kt,
+                             cudaStream_t s) {
+  switch (max_nmu) {
+    case 1: return launch_nmu<1>(a, grid, cached, max_k, kt, s);
+    case 2: return launch_nmu<2>(a, grid, cached, max_k, kt, s);
+    case 3: return launch_nmu<3>(a, grid, cached, max_k, kt, s);
+    case 4: return launch_nmu<4>(a, grid, cached, max_k, kt, s);
+    case 5: return launch_nmu<5>(a, grid, cached, max_k, kt, s);
+    case 6: return launch_nmu<6>(a, grid, cached, max_k, kt, s);
+    case 7: return launch_nmu<7>(a, grid, cached, max_k, kt, s);
+    case 8: return launch_nmu<8>(a, grid, cached, max_k, kt, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 // ---------------------------------------------------------- FP64 forward

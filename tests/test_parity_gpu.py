@@ -107,6 +107,52 @@ def test_cia_only_setup(eng):
         _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, 90)
 
 
+def _absorber_spec(K, seed, with_cia=True):
+    spec = W.TableSpec(K, np.linspace(300.0, 2500.0, 5), np.linspace(-4.0, 2.0, 4), 5000.0, 1.0, 300, seed=seed)
+    tabs = W.make_tables(spec)
+    if not with_cia:
+        tabs = dict(tabs, log10_cia_h2h2=None, log10_cia_h2he=None)
+    return spec, tabs
+
+
+@pytest.mark.parametrize("K,with_cia", [(3, False), (5, False), (5, True), (6, False)])
+def test_absorber_counts_level_gridded(eng, K, with_cia):
+    """The level-gridded kernel is compiled for an even absorber bound; an odd
+    count runs with one zero-weight absorber, whose shared-memory rows are the
+    stage's neighbouring rows (CIA rows, or never-copied zeroed rows without CIA)."""
+    spec, tabs = _absorber_spec(K, 40 + K, with_cia)
+    setup = W.make_setup(spec, 5000.0, 5299.0, 20, range(K), 4, 2, 2, 300.0, 6)
+    t = eng.add_tables(spec, "fp16", tabs)
+    s = eng.add_setup(t, setup)
+    theta = W.draw_params(setup, 8, 23, W.Prior(b=(0.8, 0.97)))
+    bins, hi, st = _run(eng, [s], np.zeros(8, np.int32), theta)
+    assert np.all(st == 0)
+    om = oracle_model(tables_as_stored(tabs, "fp16"), setup)
+    for i in range(8):
+        _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, 300)
+
+
+@pytest.mark.parametrize("ks", [(5, 6), (4, 6), (6, 3, 5)])
+def test_mixed_absorber_counts_in_one_batch(eng, ks):
+    """Setups with different absorber counts in one batch: counts K and K-1
+    share the even bound (zero-weight padding), wider mixes take the
+    runtime-count kernel.  Every sample matches the oracle of its setup."""
+    spec, tabs = _absorber_spec(max(ks), 77)
+    t = eng.add_tables(spec, "fp16", tabs)
+    specs = [W.make_setup(spec, 5000.0 + 7 * g, 5250.0 + 11 * g, 16 + 3 * g, range(k), 3, 2, 2, 300.0, 5)
+             for g, k in enumerate(ks)]
+    setups = [eng.add_setup(t, sp) for sp in specs]
+    sid = np.arange(12, dtype=np.int32) % len(ks)
+    theta = np.concatenate([W.draw_params(specs[g], 1, 100 + i, W.Prior(b=(0.8, 0.97))) for i, g in enumerate(sid)])
+    bins, hi, st = _run(eng, setups, sid, theta)
+    assert np.all(st == 0)
+    stored = tables_as_stored(tabs, "fp16")
+    for g, sp in enumerate(specs):
+        om = oracle_model(stored, sp)
+        for i in np.nonzero(sid == g)[0]:
+            _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, sp.n_nu)
+
+
 # ------------------------------------------------------------ named workloads
 _CACHE = {}
 
