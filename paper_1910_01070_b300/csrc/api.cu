@@ -57,7 +57,7 @@ struct hr2_ctx {
   int n_sm = 0;
   size_t budget = 0;
   size_t used = 0;
-  hr2_launch_cfg cfg{4, 3};
+  hr2_launch_cfg cfg{2, 6};
   std::mutex mu;
   std::map<void*, size_t> blocks;  // device allocations and their sizes
   std::map<void*, Workspace*> ws;  // per stream

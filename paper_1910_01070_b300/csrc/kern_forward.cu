@@ -369,7 +369,7 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
 //   rows[2][2 K + 4][64] floats, per stage (double-buffered by level
 //     parity): the rows of T cells a and a+1 of every absorber ([a][s],
 //     [a+1][s]), then the CIA rows [a][pair], [a+1][pair];
-//   recs[3][16]: the level records, three levels deep;
+//   recs[4][16]: the level records, a ring of four (level j in slot j & 3);
 //   bar[2]: one mbarrier per stage.
 struct WarpPipe {
   float* rows;
@@ -378,25 +378,26 @@ struct WarpPipe {
 };
 __host__ __device__ __forceinline__ size_t warp_rows_floats(int max_k) { return (size_t)2 * (2 * max_k + 4) * kTileNu; }
 __host__ __device__ __forceinline__ size_t warp_pipe_bytes(int max_k) {
-  return warp_rows_floats(max_k) * sizeof(float) + 3 * sizeof(LevRec) + 2 * sizeof(unsigned long long);
+  return warp_rows_floats(max_k) * sizeof(float) + 4 * sizeof(LevRec) + 2 * sizeof(unsigned long long);
 }
 __device__ __forceinline__ WarpPipe warp_pipe(unsigned char* base, int max_k) {
   WarpPipe w;
   w.rows = reinterpret_cast<float*>(base);
   w.recs = reinterpret_cast<float*>(base + warp_rows_floats(max_k) * sizeof(float));
-  w.bar = reinterpret_cast<unsigned long long*>(base + warp_rows_floats(max_k) * sizeof(float) + 3 * sizeof(LevRec));
+  w.bar = reinterpret_cast<unsigned long long*>(base + warp_rows_floats(max_k) * sizeof(float) + 4 * sizeof(LevRec));
   return w;
 }
 
 // Issue stage st: one bulk copy of the absorber rows of one level (T cells
-// acell and acell+1, 2 K x 256 bytes), one of the CIA rows (1 KB, if any CIA
-// table) and up to two level records (rec_a -> record slot slot_a, rec_b ->
-// slot_b; NULL to skip), all counted on the stage's barrier.  One lane
-// issues everything.
+// acell and acell+1, 2 K x kTileNu floats), one of the CIA rows (4 x kTileNu
+// floats, when copy_cia: the stage does not hold those of acell yet) and up
+// to two level records (rec_a -> record slot slot_a, rec_b -> slot_b; NULL to
+// skip), all counted on the stage's barrier.  One lane issues everything.
 __device__ __forceinline__ void issue_stage(const WarpPipe& w, int st, int K, const float* lvl_level,
-                                            const float* cia_tile, int acell, bool has_cia, const LevRec* rec_a,
+                                            const float* cia_tile, int acell, bool copy_cia, const LevRec* rec_a,
                                             int slot_a, const LevRec* rec_b, int slot_b, int lane) {
   if (lane == 0) {
+    const bool has_cia = copy_cia;
     const unsigned rows_bytes = (unsigned)(2 * K * kTileNu * sizeof(float));
     const unsigned cia_bytes = has_cia ? (unsigned)(4 * kTileNu * sizeof(float)) : 0u;
     const unsigned bytes = rows_bytes + cia_bytes + (rec_a ? (unsigned)sizeof(LevRec) : 0u) +
@@ -610,7 +611,8 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     const v2* sW2 = sA2;   // cached path: per-sample absorber weights
     // Pipeline over the levels (g = phase_base + j counts this warp's levels
     // across items; level g uses stage g & 1, whose barrier completes phase
-    // (g >> 1) & 1).  Record of level j sits in record slot j % 3.
+    // (g >> 1) & 1).  Record of level j sits in record slot j & 3.  A stage
+    // keeps its CIA rows until a level with another T cell lands in it.
     //   before the loop: stage of level 0 <- rows(0), records 0 and 1
     //   level j:         wait stage(j)   -> rows(j) and record j+1 present
     //                    issue stage(j+1) <- rows(j+1) (cell from record
@@ -622,8 +624,11 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     const size_t lvl_step = (size_t)nT * K * kTileNu;
     const bool has_cia = cia0 || cia1;
     const unsigned ph = phase_base;
-    issue_stage(wp_, (int)(ph & 1u), K, lvl_tile, cia_tile, __ldg(&rec[0].acell), has_cia, rec, 0,
-                L >= 1 ? rec + 1 : nullptr, 1, lane);
+    const int acell0 = __ldg(&rec[0].acell);
+    int cia_cell0 = -1, cia_cell1 = -1;   // T cell whose CIA rows stage 0 / 1 holds
+    if (ph & 1u) cia_cell1 = acell0; else cia_cell0 = acell0;
+    issue_stage(wp_, (int)(ph & 1u), K, lvl_tile, cia_tile, acell0, has_cia, rec, 0, L >= 1 ? rec + 1 : nullptr, 1,
+                lane);
     for (int j = 0; j <= L; ++j) {
       const unsigned g = ph + (unsigned)j;
       const int stg = (int)(g & 1u);
@@ -637,11 +642,14 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       }
       __syncwarp();
       if (j < L) {
-        const int acell_n = __float_as_int(wp_.recs[(size_t)((j + 1) % 3) * 16 + 8]);
-        issue_stage(wp_, (int)((g + 1u) & 1u), K, lvl_tile + (size_t)(j + 1) * lvl_step, cia_tile, acell_n,
-                    has_cia, (j + 2 <= L) ? rec + (j + 2) : nullptr, (j + 2) % 3, nullptr, 0, lane);
+        const int acell_n = __float_as_int(wp_.recs[((j + 1) & 3) * 16 + 8]);
+        const int sn = (int)((g + 1u) & 1u);
+        const bool copy_cia = has_cia && (sn ? cia_cell1 : cia_cell0) != acell_n;
+        if (sn) cia_cell1 = acell_n; else cia_cell0 = acell_n;
+        issue_stage(wp_, sn, K, lvl_tile + (size_t)(j + 1) * lvl_step, cia_tile, acell_n, copy_cia,
+                    (j + 2 <= L) ? rec + (j + 2) : nullptr, (j + 2) & 3, nullptr, 0, lane);
       }
-      const float* rj = wp_.recs + (size_t)(j % 3) * 16;
+      const float* rj = wp_.recs + (j & 3) * 16;
       const float4 r0 = *reinterpret_cast<const float4*>(rj);
       const float4 r1 = *reinterpret_cast<const float4*>(rj + 4);
       const float4 r2 = *reinterpret_cast<const float4*>(rj + 8);
