@@ -53,8 +53,11 @@ class _Model(C.Structure):
         ("n_used", C.c_int), ("species", C.POINTER(C.c_int)),
         ("n_mu", C.c_int), ("fe_elements", C.c_int), ("fe_order", C.c_int),
         ("resolving_power", C.c_double), ("n_bins", C.c_int), ("bin_edges", C.POINTER(C.c_double)),
-        ("r_he", C.c_double), ("radius_cm", C.c_double),
+        ("r_he", C.c_double), ("radius_cm", C.c_double), ("interp", C.c_int),
     ]
+
+# interpolation space of the opacity tables (a setup option)
+INTERP = {"log10": 0, "linear": 1}
 
 
 _DP = C.POINTER(C.c_double)
@@ -77,6 +80,8 @@ def _lib():
                 "or_sc_intensity": (C.c_double, [C.c_int, _DP, _DP, C.c_double, C.c_double]),
                 "or_sc_flux": (C.c_double, [C.c_int, _DP, _DP, C.c_double, C.c_int]),
                 "or_log10_sigma": (C.c_double, [M, C.c_int, C.c_double, C.c_double, C.c_int]),
+                "or_sigma": (C.c_double, [M, C.c_int, C.c_double, C.c_double, C.c_int]),
+                "or_cia_coeff": (C.c_double, [M, _DP, C.c_double, C.c_int]),
                 "or_convolve": (None, [M, _DP, _DP]),
                 "or_bin": (C.c_int, [M, _DP, _DP]),
                 "or_forward": (C.c_int, [M, _DP, _DP, _DP]),
@@ -176,7 +181,8 @@ class Model:
     [K][nT][np][nnu] (float64, already the values the CUDA path stores),
     optional log10_cia_h2h2 / log10_cia_h2he [nT][nnu], species_mass [K].
     ``setup`` is a dict with nu_first, n_nu, n_layers, p_top, p_bot, species,
-    n_mu, fe_elements, fe_order, resolving_power, bin_edges, r_he, radius_cm.
+    n_mu, fe_elements, fe_order, resolving_power, bin_edges, r_he, radius_cm,
+    and optionally interp ("log10", the default, or "linear").
     """
 
     def __init__(self, tables: dict, setup: dict):
@@ -221,7 +227,9 @@ class Model:
         m.bin_edges = keepd(edges)
         m.r_he = float(setup["r_he"])
         m.radius_cm = float(setup["radius_cm"])
+        m.interp = INTERP[setup.get("interp", "log10")]
         self.m = m
+        self._cia = {key: m_ptr for key, m_ptr in (("h2h2", m.log10_cia_h2h2), ("h2he", m.log10_cia_h2he))}
         self.ref = C.byref(m)
         self.n_bins = m.n_bins
         self.n_nu = m.n_nu
@@ -280,6 +288,14 @@ class Model:
 
     def log10_sigma(self, s: int, T: float, log10p: float, inu: int) -> float:
         return _lib().or_log10_sigma(self.ref, int(s), float(T), float(log10p), int(inu))
+
+    def sigma(self, s: int, T: float, log10p: float, inu: int) -> float:
+        """Cross-section in the setup's interpolation space."""
+        return _lib().or_sigma(self.ref, int(s), float(T), float(log10p), int(inu))
+
+    def cia_coeff(self, pair: str, T: float, inu: int) -> float:
+        """CIA coefficient (pair "h2h2" or "h2he") in the setup's interpolation space."""
+        return _lib().or_cia_coeff(self.ref, self._cia[pair], float(T), int(inu))
 
     def convolve(self, F):
         F, pF = _d(F)

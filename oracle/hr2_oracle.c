@@ -75,7 +75,16 @@ typedef struct {
   const double* bin_edges;      /* [n_bins+1] cm^-1, ascending                */
   double r_he;                  /* n_He / n_H2 of the filling gas             */
   double radius_cm;             /* R_star in the radius-distance relation        */
+  int interp;                   /* OR_INTERP_LOG10 or OR_INTERP_LINEAR        */
 } or_model;
+
+/* Interpolation space of the opacity tables (Sect. 2.8 says the tables are
+ * interpolated but not in which quantity).  OR_INTERP_LOG10 (reading R3, the
+ * default) interpolates log10 sigma and exponentiates the result;
+ * OR_INTERP_LINEAR interpolates the cross-sections (and CIA coefficients)
+ * themselves, with the same cells and weights. */
+#define OR_INTERP_LOG10  0
+#define OR_INTERP_LINEAR 1
 
 /* ======================================================================
  * Quadratures
@@ -263,6 +272,34 @@ double or_log10_cia(const or_model* m, const double* cia, double T, int inu) {
   return (1.0 - wT) * cia[(size_t)a * m->n_nu_tab + inu] + wT * cia[(size_t)(a + 1) * m->n_nu_tab + inu];
 }
 
+/* Cross-section (cm^2) of table species s at (T, log10 p), table index inu,
+ * in the setup's interpolation space: 10^(bilinear log10 sigma), or the
+ * bilinear combination of the four corner cross-sections 10^(log10 sigma). */
+double or_sigma(const or_model* m, int s, double T, double log10p, int inu) {
+  if (m->interp != OR_INTERP_LINEAR) return pow(10.0, or_log10_sigma(m, s, T, log10p, inu));
+  int a, b;
+  double wT, wp;
+  or_cell(m->T_grid, m->n_T, T, &a, &wT);
+  or_cell(m->log10p_grid, m->n_p, log10p, &b, &wp);
+  const double* tab = m->log10_sigma + (size_t)s * m->n_T * m->n_p * m->n_nu_tab;
+#define OR_SIG(ia, ib) pow(10.0, tab[((size_t)(ia) * m->n_p + (ib)) * m->n_nu_tab + inu])
+  double v = (1.0 - wT) * (1.0 - wp) * OR_SIG(a, b) + wT * (1.0 - wp) * OR_SIG(a + 1, b) +
+             (1.0 - wT) * wp * OR_SIG(a, b + 1) + wT * wp * OR_SIG(a + 1, b + 1);
+#undef OR_SIG
+  return v;
+}
+
+/* Collision-induced absorption coefficient (cm^5) at T, table index inu, in
+ * the setup's interpolation space (linear in T either way). */
+double or_cia_coeff(const or_model* m, const double* cia, double T, int inu) {
+  if (m->interp != OR_INTERP_LINEAR) return pow(10.0, or_log10_cia(m, cia, T, inu));
+  int a;
+  double wT;
+  or_cell(m->T_grid, m->n_T, T, &a, &wT);
+  return (1.0 - wT) * pow(10.0, cia[(size_t)a * m->n_nu_tab + inu]) +
+         wT * pow(10.0, cia[(size_t)(a + 1) * m->n_nu_tab + inu]);
+}
+
 /* ======================================================================
  * Per-sample state
  * ====================================================================== */
@@ -331,12 +368,12 @@ int or_prepare(const or_model* m, const double* theta, or_state* st) {
 double or_chi(const or_model* m, const or_state* st, int j, int inu) {
   double chi = 0.0;
   for (int s = 0; s < m->n_used; ++s)
-    chi += st->x[s] * pow(10.0, or_log10_sigma(m, m->species[s], st->T[j], st->log10p_bar[j], inu));
+    chi += st->x[s] * or_sigma(m, m->species[s], st->T[j], st->log10p_bar[j], inu);
   double n_tot = st->p[j] / (OR_KB * st->T[j]);
   if (m->log10_cia_h2h2)
-    chi += st->x_h2 * st->x_h2 * n_tot * pow(10.0, or_log10_cia(m, m->log10_cia_h2h2, st->T[j], inu));
+    chi += st->x_h2 * st->x_h2 * n_tot * or_cia_coeff(m, m->log10_cia_h2h2, st->T[j], inu);
   if (m->log10_cia_h2he)
-    chi += st->x_h2 * st->x_he * n_tot * pow(10.0, or_log10_cia(m, m->log10_cia_h2he, st->T[j], inu));
+    chi += st->x_h2 * st->x_he * n_tot * or_cia_coeff(m, m->log10_cia_h2he, st->T[j], inu);
   return chi;
 }
 

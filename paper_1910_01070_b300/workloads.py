@@ -78,6 +78,7 @@ class SetupSpec:
     p_bot: float = 100.0        # bar
     r_he: float = 0.17          # n_He / n_H2
     radius_cm: float = R_JUPITER_CM
+    interp: str = "log10"       # opacity interpolation space: "log10" or "linear"
 
     @property
     def n_bins(self) -> int:

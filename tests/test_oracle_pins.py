@@ -509,3 +509,84 @@ def test_convolution_truncates_at_five_sigma(oracle_lib):
     reach = np.abs(nu[c] - nu) <= 5 * sig
     assert np.all(out[reach] > 0) and np.all(out[~reach] == 0)
     assert reach.sum() < len(nu)
+
+
+# ------------------------------------------------------------ linear-sigma interpolation option
+def _linear_model(fill=None, cia=True, cia_fill=None, species=(0, 1), n_layers=4):
+    spec = W.TableSpec(2, np.linspace(400.0, 2400.0, 4), np.linspace(-4.0, 2.0, 3), 6000.0, 1.0, 24, seed=99,
+                       cia=cia)
+    tabs = W.make_tables(spec)
+    if fill is not None:
+        tabs["log10_sigma"] = fill(tabs)
+    if cia_fill is not None:
+        tabs["log10_cia_h2h2"] = cia_fill(tabs)
+    setup = W.make_setup(spec, 6000.0, 6023.0, n_layers, list(species), 3, 2, 1, 0.0, 4)
+    setup.interp = "linear"
+    return oracle.Model(tabs, setup.as_dict()), tabs, setup
+
+
+def test_linear_interpolation_exact_at_nodes_and_for_bilinear_cross_sections(oracle_lib):
+    """With the linear option the cross-section itself is interpolated: exact
+    at the grid nodes and for any sigma bilinear in (T, log10 p); the log10
+    option is not exact for such a field (it interpolates geometrically)."""
+    m, tabs, setup = _linear_model()
+    T, lp, sig = tabs["T_grid"], tabs["log10p_grid"], tabs["log10_sigma"]
+    for a in range(len(T)):
+        for b in range(len(lp)):
+            assert m.sigma(1, T[a], lp[b], 5) == pytest.approx(10 ** sig[1, a, b, 5], rel=1e-13)
+    c = [2.0e-22, 3.0e-25, 4.0e-23, 1.0e-25]
+    field = lambda t, p: c[0] + c[1] * t + c[2] * (p + 4.0) + c[3] * t * (p + 4.0)
+    fill = lambda tb: np.broadcast_to(np.log10(field(tb["T_grid"][:, None], tb["log10p_grid"][None, :]))[None, :, :, None],
+                                      tb["log10_sigma"].shape).copy()
+    m2, t2, s2 = _linear_model(fill=fill)
+    mlog = oracle.Model(t2, dict(s2.as_dict(), interp="log10"))
+    rng = np.random.default_rng(8)
+    worst_log = 0.0
+    for _ in range(20):
+        t, p = rng.uniform(T[0], T[-1]), rng.uniform(lp[0], lp[-1])
+        assert m2.sigma(0, t, p, 3) == pytest.approx(field(t, p), rel=1e-12)
+        worst_log = max(worst_log, abs(mlog.sigma(0, t, p, 3) / field(t, p) - 1.0))
+    assert worst_log > 1e-3
+    assert m2.sigma(0, 50.0, -9.0, 3) == pytest.approx(field(T[0], lp[0]), rel=1e-12)   # clamped
+
+
+def test_linear_interpolation_bounds_the_log_interpolation(oracle_lib):
+    """Weighted AM-GM: sum w_i 10^l_i >= 10^(sum w_i l_i), equal where the
+    corners agree; so the linear option never gives less than the log10 one."""
+    m, tabs, setup = _linear_model()
+    mlog = oracle.Model(tabs, dict(setup.as_dict(), interp="log10"))
+    rng = np.random.default_rng(9)
+    T, lp = tabs["T_grid"], tabs["log10p_grid"]
+    for _ in range(50):
+        t, p, inu = rng.uniform(T[0], T[-1]), rng.uniform(lp[0], lp[-1]), int(rng.integers(0, 24))
+        assert m.sigma(1, t, p, inu) >= mlog.sigma(1, t, p, inu) * (1 - 1e-14)
+    flat = lambda tb: np.full(tb["log10_sigma"].shape, -22.5)
+    m3, t3, s3 = _linear_model(fill=flat)
+    assert m3.sigma(0, 1234.0, -1.3, 2) == pytest.approx(10 ** -22.5, rel=1e-13)
+
+
+def test_linear_option_cia_and_optical_depth_closed_form(oracle_lib):
+    """CIA coefficient linear in T is reproduced exactly between nodes, and on
+    an isothermal atmosphere the layer optical depth is the trapezoid of
+    x sigma(T) + x_H2^2 n k(T) with those exact values."""
+    sa, sb = 1.0e-22, 2.0e-25          # sigma(T) = sa + sb (T - 400), constant in p
+    ka, kb = 1.0e-45, 3.0e-48          # k_H2H2(T) = ka + kb (T - 400)
+    fill = lambda tb: np.broadcast_to(np.log10(sa + sb * (tb["T_grid"] - 400.0))[None, :, None, None],
+                                      tb["log10_sigma"].shape).copy()
+    cia_fill = lambda tb: np.broadcast_to(np.log10(ka + kb * (tb["T_grid"] - 400.0))[:, None],
+                                          (len(tb["T_grid"]), 24)).copy()
+    m, tabs, setup = _linear_model(fill=fill, cia_fill=cia_fill, species=(0,), n_layers=5)
+    tabs["log10_cia_h2he"] = None
+    m = oracle.Model(dict(tabs, log10_cia_h2he=None), setup.as_dict())
+    Tiso = 1111.0
+    assert m.cia_coeff("h2h2", Tiso, 4) == pytest.approx(ka + kb * (Tiso - 400.0), rel=1e-12)
+    x = 2e-4
+    th = _theta([Tiso, Tiso, Tiso], logx=(math.log10(x),))
+    dtau, ok = m.layer_dtau(th, 4)
+    assert ok
+    xh2 = (1 - x) / 1.17
+    mmw = x * tabs["species_mass"][0] + xh2 * 2.01588 + 0.17 * xh2 * 4.002602
+    p = 10 ** np.linspace(-4.0, 2.0, 6) * 1e6
+    chi = x * (sa + sb * (Tiso - 400.0)) + xh2 * xh2 * (p / (KB * Tiso)) * (ka + kb * (Tiso - 400.0))
+    expect = 0.5 * (chi[:-1] + chi[1:]) * np.diff(p) / (mmw * AMU * 10 ** 4.75)
+    assert np.allclose(dtau, expect, rtol=1e-8)
