@@ -453,7 +453,59 @@ def run_extras(args, local, flush):
             res.append(st)
         out["serving"] = {"streams": 16, "request_sizes": "32-512", "capacity_models_per_s": cap,
                           "latency": "arrival to lnL on the host", "loads": res}
+    out["linear_sigma_option"] = run_linear_option(args, local, flush)
     return out
+
+
+def run_linear_option(args, local, flush):
+    """The benchmark workload with the opacity tables interpolated in sigma instead of
+    log10 sigma (a setup option; a different model, so not the headline): forward +
+    lnL per step, same batch, same L2 flush."""
+    import dataclasses
+
+    import torch
+
+    from paper_1910_01070_b300 import hr2
+    from paper_1910_01070_b300 import workloads as W
+    from paper_1910_01070_b300.engine import Engine
+
+    dev = torch.device("cuda", local)
+    wl = W.WORKLOADS[args.workload]()
+    spec = dataclasses.replace(wl.setups[0], interp="linear")
+    with Engine(local) as eng:
+        t = eng.add_tables(wl.table, "fp16", W.make_tables(wl.table))
+        s = eng.add_setup(t, spec)
+        tb = eng.forward([s], torch.zeros(1, dtype=torch.int32, device=dev),
+                         torch.as_tensor(wl.truth(0)[None, :], device=dev))
+        D, sig = W.mock_observation(tb.double().cpu().numpy()[0, : spec.n_bins], wl.seed)
+        eng.set_observation(s, D, sig)
+        n = wl.n_samples
+        th, sid = wl.params(n, seed_offset=7)
+        th, sid = torch.as_tensor(th, device=dev), torch.as_tensor(sid, device=dev)
+        bins = torch.empty((n, spec.n_bins), dtype=torch.float32, device=dev)
+        lnl = torch.empty(n, dtype=torch.float64, device=dev)
+        stream = torch.cuda.current_stream()
+        for _ in range(3):
+            hr2.forward_model_batch(eng.ctx, [s], sid, th, bins, None, None, stream)
+        torch.cuda.synchronize()
+        steps = max(3, min(args.steps, 40))
+        evs = []
+        hr2.hr2_profile_read(eng.ctx, True)
+        hr2.hr2_profile_enable(eng.ctx, True)
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hr2.forward_model_batch(eng.ctx, [s], sid, th, bins, None, None, stream)
+            hr2.log_likelihood_batch(eng.ctx, [s], sid, bins, lnl, None, stream)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        hr2.hr2_profile_enable(eng.ctx, False)
+        kms, nl = hr2.hr2_profile_read(eng.ctx, True)
+        times = [a.elapsed_time(b) for a, b in evs]
+        return {"workload": wl.name, "interp": "linear", "samples": n, "value": n * steps / (sum(times) / 1e3),
+                "unit": "models/s", "ms_per_step": float(np.mean(times)), "kernel_ms": kms / max(nl, 1)}
 
 
 def run_sweep_large(args, local):

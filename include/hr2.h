@@ -87,6 +87,11 @@ typedef enum {
 #define HR2_STORE_FP16_OFFSET 1  /* FP16 of (log10 sigma - off_s), off_s integer */
 #define HR2_STORE_FP64        2  /* FP64 log10 sigma (the plain FP64 path)       */
 
+/* Interpolation space of the opacity tables (Sect. 2.8 names the
+ * interpolation of the tables but not the quantity interpolated). */
+#define HR2_INTERP_LOG10  0  /* bilinear in log10 sigma, then 10^x (default)     */
+#define HR2_INTERP_LINEAR 1  /* bilinear in sigma itself (CIA: linear in T)      */
+
 typedef struct hr2_ctx hr2_ctx;
 typedef struct hr2_tables hr2_tables;
 typedef struct hr2_setup hr2_setup;
@@ -138,6 +143,13 @@ typedef struct {
                                  every evaluation interpolates the FP16 tables
                                  bilinearly.  One batch call takes setups of a
                                  single kind.                                    */
+  int interp;                 /* HR2_INTERP_LOG10 or HR2_INTERP_LINEAR.  With
+                                 FP16 tables the linear option needs
+                                 level_cache (the operand then holds the
+                                 p-interpolated cross-sections, so each sample
+                                 interpolates in T with FMAs only); FP64
+                                 tables take either.  One batch call takes
+                                 setups of a single option.                      */
 } hr2_setup_desc;
 
 /* Launch shape of the persistent forward kernel (chosen by the autotuner). */

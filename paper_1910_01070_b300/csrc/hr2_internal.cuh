@@ -98,10 +98,14 @@ struct SetupDev {
   float cost;                    // relative cost of one work item (scheduling)
   const TablesDev* tables;       // device copy
   // level-gridded operand (level_cache): the tables interpolated in p onto
-  // the levels, times log2(10), FP32, columns local to the setup's tiles
+  // the levels, FP32, columns local to the setup's tiles
   int cached;
-  const float* lvl32;            // [n_tiles][n_lev][n_T][n_species][64]
-  const float* cia32;            // [n_tiles][n_T][2][64]
+  const float* lvl32;            // [n_tiles][n_lev][n_T][n_species][kTileNu]
+  const float* cia32;            // [n_tiles][n_T][2][kTileNu]
+  // interpolation space (HR2_INTERP_*): with HR2_INTERP_LINEAR the operand
+  // holds 10^(stored log10 sigma) interpolated linearly in log10 p (and the
+  // CIA operand 10^(stored value)), and the kernels interpolate linearly in T
+  int interp;
 };
 
 // Per-(sample, level) inputs of the FP32 forward kernel, written by the
@@ -179,7 +183,7 @@ cudaError_t launch_prep(const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_plan(const FwdArgs& a, int* perm, PlanDev* plan, cudaStream_t s);
 // kt: 0, or an even bound on the absorber count of the cached path with
 // every setup of the batch at kt or kt - 1 absorbers (see absorber_bound)
-cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, int max_k, int kt,
+cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, int max_k, int kt,
                              cudaStream_t s);
 size_t forward32_smem_bytes(int warps, int max_k);
 cudaError_t launch_forward64(const FwdArgs& a, int max_nmu, int max_nu, cudaStream_t s);

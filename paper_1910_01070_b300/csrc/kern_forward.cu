@@ -412,6 +412,15 @@ __device__ __forceinline__ void issue_stage(const WarpPipe& w, int st, int K, co
   }
 }
 
+// Absorption per molecule from a T-interpolated operand value: 2^x on the
+// log10 option (the operand holds log2 of the offset cross-section), x
+// itself on the linear option (the operand holds the cross-section).
+template <bool LIN>
+__device__ __forceinline__ v2 row_value(v2 x) {
+  if constexpr (LIN) return x;
+  else return ex2_2(x);
+}
+
 // Each lane carries kPairs packed pairs of neighbouring wavenumbers: pair p
 // holds tile columns 64 p + 2 lane and 64 p + 2 lane + 1, so that a warp's
 // shared-memory row reads stay contiguous and every per-level cost that does
@@ -551,7 +560,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
 // level-gridded operand through the warp's bulk-copy pipeline (rows of level
 // j+1 and the record of level j+2 land while level j is computed).
 // Otherwise the FP16 tables are read and interpolated bilinearly in place.
-template <int NMU, bool CACHED, int KT>
+template <int NMU, bool CACHED, int KT, bool LIN>
 __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
                                            const v2* sA2, const v2* sAc2, const void* const* sPtr,
                                            const v2* sMnl, const v2* sImu, const WarpPipe& wp_, unsigned& phase_base) {
@@ -672,8 +681,8 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
             const int o = s * kTileNu + 64 * p;
             const v2 p0 = lds2f(rowa + o), p1 = lds2f(rowb + o);
             const v2 q0 = lds2f(rowa + o + kTileNu), q1 = lds2f(rowb + o + kTileNu);
-            chA[p] = fma2(w0, ex2_2(fma2(wT, sub2(p1, p0), p0)), chA[p]);
-            chB[p] = fma2(w1, ex2_2(fma2(wT, sub2(q1, q0), q0)), chB[p]);
+            chA[p] = fma2(w0, row_value<LIN>(fma2(wT, sub2(p1, p0), p0)), chA[p]);
+            chB[p] = fma2(w1, row_value<LIN>(fma2(wT, sub2(q1, q0), q0)), chB[p]);
           }
         }
       } else {
@@ -685,8 +694,8 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
           const int o = s * kTileNu + 64 * p;
           const v2 p0 = lds2f(rowa + o), p1 = lds2f(rowb + o);
           const v2 q0 = lds2f(rowa + o + kTileNu), q1 = lds2f(rowb + o + kTileNu);
-          chA[p] = fma2(w0, ex2_2(fma2(wT, sub2(p1, p0), p0)), chA[p]);
-          chB[p] = fma2(w1, ex2_2(fma2(wT, sub2(q1, q0), q0)), chB[p]);
+          chA[p] = fma2(w0, row_value<LIN>(fma2(wT, sub2(p1, p0), p0)), chA[p]);
+          chB[p] = fma2(w1, row_value<LIN>(fma2(wT, sub2(q1, q0), q0)), chB[p]);
         }
       }
       if (s < K) {
@@ -695,7 +704,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
         for (int p = 0; p < kPairs; ++p) {
           const int o = s * kTileNu + 64 * p;
           const v2 p0 = lds2f(rowa + o), p1 = lds2f(rowb + o);
-          chA[p] = fma2(w0, ex2_2(fma2(wT, sub2(p1, p0), p0)), chA[p]);
+          chA[p] = fma2(w0, row_value<LIN>(fma2(wT, sub2(p1, p0), p0)), chA[p]);
         }
       }
       }
@@ -705,7 +714,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {
           const v2 c0 = lds2f(ca + 64 * p), c1 = lds2f(ca + 2 * kTileNu + 64 * p);
-          chB[p] = fma2(w, ex2_2(fma2(wT, sub2(c1, c0), c0)), chB[p]);
+          chB[p] = fma2(w, row_value<LIN>(fma2(wT, sub2(c1, c0), c0)), chB[p]);
         }
       }
       if (cia1) {
@@ -713,7 +722,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {
           const v2 c0 = lds2f(ca + kTileNu + 64 * p), c1 = lds2f(ca + 3 * kTileNu + 64 * p);
-          chA[p] = fma2(w, ex2_2(fma2(wT, sub2(c1, c0), c0)), chA[p]);
+          chA[p] = fma2(w, row_value<LIN>(fma2(wT, sub2(c1, c0), c0)), chA[p]);
         }
       }
       v2 chi[kPairs];
@@ -807,7 +816,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
   }
 }
 
-template <int NMU, bool CACHED, int KT>
+template <int NMU, bool CACHED, int KT, bool LIN>
 __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forward32(FwdArgs a, int max_k) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];   // cached path: per-warp pipelines
   __shared__ int s_item;
@@ -870,13 +879,13 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
     }
     __syncthreads();
     if (active)
-      solve_tile<NMU, CACHED, KT>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, wp_, phase_base);
+      solve_tile<NMU, CACHED, KT, LIN>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, wp_, phase_base);
   }
 }
 
 size_t forward32_smem_bytes(int warps, int max_k) { return (size_t)warps * warp_pipe_bytes(max_k); }
 
-template <int NMU, bool CACHED, int KT>
+template <int NMU, bool CACHED, int KT, bool LIN>
 static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_t s) {
   const size_t smem = CACHED ? forward32_smem_bytes(a.warps, max_k) : 0;
   if (CACHED) {
@@ -889,51 +898,53 @@ static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(raised & bit)) {
-      e = cudaFuncSetAttribute(k_forward32<NMU, CACHED, KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_forward32<NMU, CACHED, KT, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kForwardSmemCap);
       if (e != cudaSuccess) return e;
       raised |= bit;
     }
     if (smem > kForwardSmemCap) return cudaErrorInvalidValue;
   }
-  k_forward32<NMU, CACHED, KT><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
+  k_forward32<NMU, CACHED, KT, LIN><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
   return cudaGetLastError();
 }
 
 // cached path: absorber bound kt (0 = any mix of absorber counts, else an
 // even bound with every setup at kt or kt - 1)
-template <int NMU>
+template <int NMU, bool LIN>
 static cudaError_t launch_cached(const FwdArgs& a, int grid, int max_k, int kt, cudaStream_t s) {
   switch (kt) {
-    case 0: return launch_one<NMU, true, 0>(a, grid, max_k, s);
-    case 2: return launch_one<NMU, true, 2>(a, grid, max_k, s);
-    case 4: return launch_one<NMU, true, 4>(a, grid, max_k, s);
-    case 6: return launch_one<NMU, true, 6>(a, grid, max_k, s);
-    case 8: return launch_one<NMU, true, 8>(a, grid, max_k, s);
-    case 10: return launch_one<NMU, true, 10>(a, grid, max_k, s);
-    case 12: return launch_one<NMU, true, 12>(a, grid, max_k, s);
-    case 14: return launch_one<NMU, true, 14>(a, grid, max_k, s);
-    case 16: return launch_one<NMU, true, 16>(a, grid, max_k, s);
+    case 0: return launch_one<NMU, true, 0, LIN>(a, grid, max_k, s);
+    case 2: return launch_one<NMU, true, 2, LIN>(a, grid, max_k, s);
+    case 4: return launch_one<NMU, true, 4, LIN>(a, grid, max_k, s);
+    case 6: return launch_one<NMU, true, 6, LIN>(a, grid, max_k, s);
+    case 8: return launch_one<NMU, true, 8, LIN>(a, grid, max_k, s);
+    case 10: return launch_one<NMU, true, 10, LIN>(a, grid, max_k, s);
+    case 12: return launch_one<NMU, true, 12, LIN>(a, grid, max_k, s);
+    case 14: return launch_one<NMU, true, 14, LIN>(a, grid, max_k, s);
+    case 16: return launch_one<NMU, true, 16, LIN>(a, grid, max_k, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 template <int NMU>
-static cudaError_t launch_nmu(const FwdArgs& a, int grid, bool cached, int max_k, int kt, cudaStream_t s) {
-  return cached ? launch_cached<NMU>(a, grid, max_k, kt, s) : launch_one<NMU, false, 0>(a, grid, max_k, s);
+static cudaError_t launch_nmu(const FwdArgs& a, int grid, bool cached, bool linear, int max_k, int kt,
+                              cudaStream_t s) {
+  if (!cached) return linear ? cudaErrorInvalidValue : launch_one<NMU, false, 0, false>(a, grid, max_k, s);
+  return linear ? launch_cached<NMU, true>(a, grid, max_k, kt, s) : launch_cached<NMU, false>(a, grid, max_k, kt, s);
 }
 
-cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, int max_k, int kt,
+cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, int max_k, int kt,
                              cudaStream_t s) {
   switch (max_nmu) {
-    case 1: return launch_nmu<1>(a, grid, cached, max_k, kt, s);
-    case 2: return launch_nmu<2>(a, grid, cached, max_k, kt, s);
-    case 3: return launch_nmu<3>(a, grid, cached, max_k, kt, s);
-    case 4: return launch_nmu<4>(a, grid, cached, max_k, kt, s);
-    case 5: return launch_nmu<5>(a, grid, cached, max_k, kt, s);
-    case 6: return launch_nmu<6>(a, grid, cached, max_k, kt, s);
-    case 7: return launch_nmu<7>(a, grid, cached, max_k, kt, s);
-    case 8: return launch_nmu<8>(a, grid, cached, max_k, kt, s);
+    case 1: return launch_nmu<1>(a, grid, cached, linear, max_k, kt, s);
+    case 2: return launch_nmu<2>(a, grid, cached, linear, max_k, kt, s);
+    case 3: return launch_nmu<3>(a, grid, cached, linear, max_k, kt, s);
+    case 4: return launch_nmu<4>(a, grid, cached, linear, max_k, kt, s);
+    case 5: return launch_nmu<5>(a, grid, cached, linear, max_k, kt, s);
+    case 6: return launch_nmu<6>(a, grid, cached, linear, max_k, kt, s);
+    case 7: return launch_nmu<7>(a, grid, cached, linear, max_k, kt, s);
+    case 8: return launch_nmu<8>(a, grid, cached, linear, max_k, kt, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -998,6 +1009,7 @@ __global__ void __launch_bounds__(kF64Block) k_forward64(FwdArgs a) {
   const int col = S.nu_first + k;
   const double nu = T.nu0 + (double)col * T.dnu;
   const int nu_pad = T.nu_pad, np = T.n_p;
+  const bool lin = S.interp == HR2_INTERP_LINEAR;   // interpolation space of the tables
   double I[NMU];
   double chip = 0.0, Sp = 0.0;
   for (int j = L; j >= 0; --j) {
@@ -1007,15 +1019,19 @@ __global__ void __launch_bounds__(kF64Block) k_forward64(FwdArgs a) {
     double chi = 0.0;
     for (int s = 0; s < S.n_species; ++s) {
       const double* t = T.sig64 + (size_t)S.species[s] * T.n_T * np * nu_pad + row;
-      const double v = (1.0 - wT) * (1.0 - wp) * t[0] + wT * (1.0 - wp) * t[(size_t)np * nu_pad] +
-                       (1.0 - wT) * wp * t[nu_pad] + wT * wp * t[(size_t)(np + 1) * nu_pad];
-      chi += sx[s] * exp10(v);
+      const double* t10 = t + (size_t)np * nu_pad;
+      const double sig = lin ? (1.0 - wT) * (1.0 - wp) * exp10(t[0]) + wT * (1.0 - wp) * exp10(t10[0]) +
+                                   (1.0 - wT) * wp * exp10(t[nu_pad]) + wT * wp * exp10(t10[nu_pad])
+                             : exp10((1.0 - wT) * (1.0 - wp) * t[0] + wT * (1.0 - wp) * t10[0] +
+                                     (1.0 - wT) * wp * t[nu_pad] + wT * wp * t10[nu_pad]);
+      chi += sx[s] * sig;
     }
     for (int p = 0; p < 2; ++p) {
       if (!T.has_cia[p]) continue;
       const double* t = T.cia64 + (size_t)p * T.n_T * nu_pad + (size_t)sa[j] * nu_pad + col;
-      const double v = (1.0 - wT) * t[0] + wT * t[nu_pad];
-      chi += xh2 * (p == 0 ? xh2 : xhe) * sN[j] * exp10(v);
+      const double kcia =
+          lin ? (1.0 - wT) * exp10(t[0]) + wT * exp10(t[nu_pad]) : exp10((1.0 - wT) * t[0] + wT * t[nu_pad]);
+      chi += xh2 * (p == 0 ? xh2 : xhe) * sN[j] * kcia;
     }
     const double Sj = kC1 * nu * nu * nu / expm1(kC2 * nu / sT[j]);
     if (j == L) {

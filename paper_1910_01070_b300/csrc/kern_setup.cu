@@ -303,18 +303,20 @@ cudaError_t build_w_values(const TablesDev* d_tab, int nu_first, double R, int n
 
 // ------------------------------------------------------- level-gridded operand
 // lvl[t][j][a][s][c] = log2(10) * ((1 - w_p) v[sp][a][b_j][col] + w_p v[sp][a][b_j+1][col])
-// for the setup's 64-point tiles t, levels j (p cell b_j, weight w_p), T rows
-// a, absorbers s (table species sp = species[s]) and columns c < 64 (table
-// column (tile0 + t)*64 + c): the p part of the bilinear interpolation
+// (log10 option) or (1 - w_p) 10^v[sp][a][b_j][col] + w_p 10^v[sp][a][b_j+1][col]
+// (linear option), v the stored FP16 value log10 sigma - off_s, for the
+// setup's kTileNu-point tiles t, levels j (p cell b_j, weight w_p), T rows a,
+// absorbers s (table species sp = species[s]) and columns c < kTileNu (table
+// column (tile0 + t)*kTileNu + c): the p part of the bilinear interpolation
 // (Sect. 2.8), done once per setup in FP64.  The rows of T cells a and a+1
-// of every absorber at one level form one contiguous block of 2 K x 256
-// bytes, fetched with a single bulk copy.
+// of every absorber at one level form one contiguous block of 2 K x kTileNu
+// floats, fetched with a single bulk copy.
 struct SpeciesList {
   int sp[HR2_MAX_SPECIES];
 };
 
 __global__ void k_level_cache(const TablesDev* tab, const LevelDev* lev, int n_species, SpeciesList list, int n_lev,
-                              int tile0, int n_tiles, float* out) {
+                              int tile0, int n_tiles, int linear, float* out) {
   const TablesDev& t = *tab;
   const long long total = (long long)n_tiles * n_lev * t.n_T * n_species * kTileNu;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -332,12 +334,14 @@ __global__ void k_level_cache(const TablesDev* tab, const LevelDev* lev, int n_s
     const size_t row0 = (((size_t)list.sp[s] * t.n_T + a) * t.n_p + lv.pcell) * t.nu_pad + (size_t)(tile0 + tt) * kTileNu + c;
     const double v0 = (double)__half2float(t.sig16[row0]);
     const double v1 = (double)__half2float(t.sig16[row0 + t.nu_pad]);
-    out[idx] = (float)(kLog2_10 * ((1.0 - lv.wp64) * v0 + lv.wp64 * v1));
+    out[idx] = linear ? (float)((1.0 - lv.wp64) * exp10(v0) + lv.wp64 * exp10(v1))
+                      : (float)(kLog2_10 * ((1.0 - lv.wp64) * v0 + lv.wp64 * v1));
   }
 }
 
-// cia[t][a][p][c] = log2(10) * v_cia[p][a][(tile0 + t)*64 + c] (0 for an absent pair)
-__global__ void k_cia_cache(const TablesDev* tab, int tile0, int n_tiles, float* out) {
+// cia[t][a][p][c] = log2(10) * v_cia[p][a][(tile0 + t)*kTileNu + c] (log10
+// option) or 10^v_cia[...] (linear option); 0 for an absent pair
+__global__ void k_cia_cache(const TablesDev* tab, int tile0, int n_tiles, int linear, float* out) {
   const TablesDev& t = *tab;
   const long long total = (long long)n_tiles * t.n_T * 2 * kTileNu;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
@@ -349,9 +353,10 @@ __global__ void k_cia_cache(const TablesDev* tab, int tile0, int n_tiles, float*
     r /= 2;
     const int a = (int)(r % t.n_T);
     const int tt = (int)(r / t.n_T);
-    out[idx] = t.has_cia[p] ? (float)(kLog2_10 * (double)__half2float(
-                                  t.cia16[((size_t)p * t.n_T + a) * t.nu_pad + (size_t)(tile0 + tt) * kTileNu + c]))
-                            : 0.f;
+    const double v = t.has_cia[p] ? (double)__half2float(
+                                        t.cia16[((size_t)p * t.n_T + a) * t.nu_pad + (size_t)(tile0 + tt) * kTileNu + c])
+                                  : 0.0;
+    out[idx] = !t.has_cia[p] ? 0.f : (linear ? (float)exp10(v) : (float)(kLog2_10 * v));
   }
 }
 
@@ -359,8 +364,9 @@ cudaError_t build_level_cache(const TablesDev* d_tab, const SetupDev& h, float* 
   SpeciesList list{};
   for (int i = 0; i < h.n_species; ++i) list.sp[i] = h.species[i];
   if (h.n_species > 0)
-    k_level_cache<<<4096, 256, 0, s>>>(d_tab, h.levels, h.n_species, list, h.n_lev, h.tile0, h.n_tiles, d_lvl);
-  k_cia_cache<<<1024, 256, 0, s>>>(d_tab, h.tile0, h.n_tiles, d_cia);
+    k_level_cache<<<4096, 256, 0, s>>>(d_tab, h.levels, h.n_species, list, h.n_lev, h.tile0, h.n_tiles,
+                                       h.interp == HR2_INTERP_LINEAR, d_lvl);
+  k_cia_cache<<<1024, 256, 0, s>>>(d_tab, h.tile0, h.n_tiles, h.interp == HR2_INTERP_LINEAR, d_cia);
   return cudaGetLastError();
 }
 

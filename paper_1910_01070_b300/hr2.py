@@ -23,6 +23,8 @@ HR2_SAMPLE_BAD_T, HR2_SAMPLE_BAD_ABUND, HR2_SAMPLE_BAD_SCALE, HR2_SAMPLE_BAD_SET
 HR2_MAX_TNODES, HR2_MAX_SPECIES, HR2_MAX_MU, HR2_MAX_LEVELS, HR2_MAX_SETUPS = 16, 16, 8, 256, 32
 HR2_P_LOGG, HR2_P_F, HR2_P_DIST, HR2_P_T0, HR2_P_X0, HR2_NPARAM = 0, 1, 2, 3, 19, 35
 HR2_STORE_FP16_OFFSET, HR2_STORE_FP64 = 1, 2
+HR2_INTERP_LOG10, HR2_INTERP_LINEAR = 0, 1
+INTERP = {"log10": HR2_INTERP_LOG10, "linear": HR2_INTERP_LINEAR}
 
 EXPORTED = [
     "hr2_ctx_create", "hr2_ctx_destroy", "hr2_last_error", "hr2_ctx_memory", "hr2_set_launch_config",
@@ -52,7 +54,7 @@ class SetupDesc(C.Structure):
                 ("fe_elements", C.c_int), ("fe_order", C.c_int), ("resolving_power", C.c_double),
                 ("n_bins", C.c_int), ("bin_edges", C.POINTER(C.c_double)), ("obs_flux", C.POINTER(C.c_double)),
                 ("obs_sigma", C.POINTER(C.c_double)), ("r_he", C.c_double), ("radius_cm", C.c_double),
-                ("level_cache", C.c_int)]
+                ("level_cache", C.c_int), ("interp", C.c_int)]
 
 
 class LaunchCfg(C.Structure):
@@ -234,7 +236,8 @@ def hr2_tables_destroy(ctx, tables):
 
 def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_elements, fe_order,
                      resolving_power, bin_edges, p_top=1e-4, p_bot=100.0, r_he=0.17, radius_cm=7.1492e9,
-                     obs_flux=None, obs_sigma=None, level_cache=True):
+                     obs_flux=None, obs_sigma=None, level_cache=True, interp="log10"):
+    """interp: "log10" (HR2_INTERP_LOG10) or "linear" (HR2_INTERP_LINEAR)."""
     sp = np.ascontiguousarray(np.asarray(species, dtype=np.int32))
     edges, pe = _dptr(bin_edges)
     keep = [sp, edges]
@@ -246,7 +249,8 @@ def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_el
         pf, ps = _DP(), _DP()
     d = SetupDesc(int(nu_first), int(n_nu), int(n_layers), float(p_top), float(p_bot), len(sp),
                   sp.ctypes.data_as(_IP), int(n_mu), int(fe_elements), int(fe_order), float(resolving_power),
-                  len(edges) - 1, pe, pf, ps, float(r_he), float(radius_cm), int(bool(level_cache)))
+                  len(edges) - 1, pe, pf, ps, float(r_he), float(radius_cm), int(bool(level_cache)),
+                  INTERP[interp])
     h = _VP()
     _check(lib().hr2_setup_create(ctx, tables, C.byref(d), C.byref(h)), ctx)
     return h

@@ -72,3 +72,21 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(hr2, "_LIB", None)
     with pytest.raises(RuntimeError):
         hr2.lib()
+
+
+def _struct_fields(src, name):
+    body = re.search(r"typedef struct \{((?:(?!typedef struct).)*?)\}\s*" + name + ";", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            fields += re.findall(r"(\w+)\s*(?:,|$)", decl)     # "double p_top, p_bot" declares two
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("hr2_setup_desc", "SetupDesc"), ("hr2_table_desc", "TableDesc"),
+                                          ("hr2_launch_cfg", "LaunchCfg")])
+def test_binding_structs_follow_the_header(cname, pyname):
+    """The ctypes mirrors list the header's fields in the header's order."""
+    assert [f[0] for f in getattr(hr2, pyname)._fields_] == _struct_fields(_header(), cname)

@@ -8,10 +8,12 @@ Gates (written here, not derived from the CUDA path):
     outputs (the ABI returns F+ and the bins as float);
   * log-likelihood: same model bins -> FP64 reduction agrees to 1e-9
     relative; end to end |delta lnL| < 1e-3 for samples near the data.
-Sizes span several 64-point tiles with ragged heads and tails; the full
+Sizes span several 128-point tiles with ragged heads and tails; the full
 workload sizes run in the launch shape the benchmark times and are checked
 on sampled outputs.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -151,6 +153,77 @@ def test_mixed_absorber_counts_in_one_batch(eng, ks):
         om = oracle_model(stored, sp)
         for i in np.nonzero(sid == g)[0]:
             _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, sp.n_nu)
+
+
+# ------------------------------------------------------------ linear-sigma interpolation option
+@pytest.mark.parametrize("storage", ["fp16-level-gridded", "fp64"])
+@pytest.mark.parametrize("case", TINY[1:], ids=[f"nu{c[0]}_L{c[1]}_K{c[2]}_mu{c[5]}" for c in TINY[1:]])
+def test_linear_option_tiny_grids_match_oracle(eng, storage, case):
+    n_nu, L, K, nT, nP, nmu, R, nb, off, (Ke, q) = case
+    spec = W.TableSpec(K, np.linspace(300.0, 2500.0, nT), np.linspace(-4.0, 2.0, nP), 5000.0, 1.0,
+                       n_nu + off + 3, seed=hash(case) % 1000 + 1)
+    tabs = W.make_tables(spec)
+    setup = W.make_setup(spec, 5000.0 + off, 5000.0 + off + n_nu - 1, L, range(K), nmu, Ke, q, R, nb)
+    setup.interp = "linear"
+    t = eng.add_tables(spec, storage[:4], tabs)
+    s = eng.add_setup(t, setup, level_cache=(storage == "fp16-level-gridded"))
+    theta = W.draw_params(setup, 4, 19, W.Prior(T1=(900.0, 2400.0), b=(0.85, 0.99)))
+    bins, hi, st = _run(eng, [s], np.zeros(4, np.int32), theta, highres_ld=n_nu + 64)
+    assert np.all(st == 0)
+    om = oracle_model(tables_as_stored(tabs, storage[:4]), setup)
+    tol = FLUX_RTOL if storage[:4] == "fp16" else FP64_RTOL
+    for i in range(4):
+        _compare(om, theta[i], bins[i], hi[i], tol, n_nu)
+
+
+@pytest.mark.parametrize("storage", ["fp16", "fp64"])
+def test_linear_option_on_the_batch_workload_with_lnl(eng, storage):
+    """The 100-layer, 6-absorber setup with the linear option: spectra against
+    the oracle run with the same option, and lnL near the data-generating
+    sample.  Both options give different spectra (the option is not a no-op)."""
+    wl = W.batch1024_l100_k6_nu8501()
+    tabs = W.make_tables(wl.table)
+    stored = tables_as_stored(tabs, storage)
+    spec = dataclasses.replace(wl.setups[0], interp="linear")
+    t = eng.add_tables(wl.table, storage, tabs)
+    s = eng.add_setup(t, spec)
+    om = oracle_model(stored, spec)
+    truth = wl.truth(0)
+    tb, ok = om.forward(truth)
+    assert ok
+    D, sig = W.mock_observation(tb, wl.seed + 5)
+    eng.set_observation(s, D, sig)
+    theta, _ = wl.params(8, seed_offset=31)
+    near = np.repeat(truth[None, :], 3, axis=0)
+    near[1:, 0] += np.array([1e-3, -1e-3])
+    theta = np.concatenate([theta, near])
+    sid = np.zeros(len(theta), np.int32)
+    bins, hi, status = _run(eng, [s], sid, theta)
+    assert np.all(status == 0)
+    tol = FLUX_RTOL if storage == "fp16" else FP64_RTOL
+    for i in range(len(theta)):
+        _compare(om, theta[i], bins[i], hi[i], tol, spec.n_nu)
+    om_log = oracle_model(stored, wl.setups[0])
+    assert np.max(np.abs(om_log.forward(theta[0])[0] / bins[0] - 1.0)) > 1e-3
+    lnl = eng.lnl([s], _dev(sid, torch.int32), _dev(bins.astype(np.float32), torch.float32)).cpu().numpy()
+    for i in range(len(theta) - 3, len(theta)):
+        ref = oracle.lnL(D, sig, om.forward(theta[i])[0])
+        assert abs(lnl[i] - ref) < LNL_ATOL, (i, lnl[i], ref)
+
+
+def test_linear_option_argument_errors(eng):
+    spec, tabs = _absorber_spec(2, 5)
+    t = eng.add_tables(spec, "fp16", tabs)
+    setup = W.make_setup(spec, 5000.0, 5199.0, 8, range(2), 2, 1, 1, 0.0, 3)
+    setup.interp = "linear"
+    with pytest.raises(hr2.Hr2Error) as ei:                 # FP16 tables need the level-gridded operand
+        eng.add_setup(t, setup, level_cache=False)
+    assert ei.value.code == hr2.HR2_EINVAL
+    lin = eng.add_setup(t, setup)
+    log = eng.add_setup(t, dataclasses.replace(setup, interp="log10"))
+    theta = W.draw_params(setup, 2, 3, W.Prior(b=(0.8, 0.95)))
+    with pytest.raises(hr2.Hr2Error):                        # one option per batch
+        _run(eng, [lin, log], np.array([0, 1], np.int32), theta)
 
 
 # ------------------------------------------------------------ named workloads
