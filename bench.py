@@ -454,7 +454,44 @@ def run_extras(args, local, flush):
         out["serving"] = {"streams": 16, "request_sizes": "32-512", "capacity_models_per_s": cap,
                           "latency": "arrival to lnL on the host", "loads": res}
     out["linear_sigma_option"] = run_linear_option(args, local, flush)
+    out["nested_sampling"] = run_nested(args, local)
     return out
+
+
+def run_nested(args, local):
+    """A bounded nested-sampling run on the benchmark setup and its mock observation:
+    the driver's loop (host proposals, forward + lnL batch, device-side absorb) timed
+    end to end; likelihood evaluations per second is the figure."""
+    import torch
+
+    from paper_1910_01070_b300 import hr2
+    from paper_1910_01070_b300 import workloads as W
+    from paper_1910_01070_b300.engine import Engine
+    from paper_1910_01070_b300.nested import GpuBackend, NestedSampler
+
+    dev = torch.device("cuda", local)
+    wl = W.WORKLOADS[args.workload]()
+    spec = wl.setups[0]
+    with Engine(local) as eng:
+        t = eng.add_tables(wl.table, "fp16", W.make_tables(wl.table))
+        s = eng.add_setup(t, spec)
+        truth = wl.truth(0)
+        tb = eng.forward([s], torch.zeros(1, dtype=torch.int32, device=dev), torch.as_tensor(truth[None, :], device=dev))
+        D, sig = W.mock_observation(tb.double().cpu().numpy()[0, : spec.n_bins], wl.seed)
+        eng.set_observation(s, D, sig)
+        lo, hi = truth.copy(), truth.copy()
+        lo[0], hi[0] = 4.0, 5.5
+        lo[1], hi[1] = 0.5, 2.0
+        nt = spec.n_tnodes
+        lo[3:3 + nt], hi[3:3 + nt] = 300.0, 3000.0
+        nsp = len(spec.species)
+        lo[19:19 + nsp], hi[19:19 + nsp] = -8.0, -2.0
+        n_live, batch = 1024, 4096
+        be = GpuBackend(eng.ctx, [s], 0, n_live=n_live)
+        res = NestedSampler(be, lo, hi, batch=batch, seed=1).run(dlogz=0.5, max_rounds=10)
+        res.update({"workload": wl.name, "n_live": n_live, "batch": batch, "free_parameters": int(np.sum(hi > lo)),
+                    "note": "bounded run (10 rounds): throughput of the sampling loop, not a converged evidence"})
+        return res
 
 
 def run_linear_option(args, local, flush):

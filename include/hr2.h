@@ -321,6 +321,56 @@ int hr2_profile_read(hr2_ctx* ctx, int reset, double* kernel_ms, int* launches);
  * word itself. */
 int hr2_stream_check(hr2_ctx* ctx, void* stream);
 
+/* ------------------------------------------------------ nested sampling
+ * Evidence bookkeeping of nested sampling (Sect. 3.2, after Skilling 2004),
+ * kept on the device so that a sampler can run propose -> forward_model_batch
+ * -> log_likelihood_batch -> hr2_ns_absorb on one stream without a host
+ * round trip per replacement.  With N live points the i-th point to leave
+ * the live set (the lowest likelihood, L*_i) has prior mass X_i = exp(-i/N)
+ * inside its contour and shell weight w_i = X_{i-1} - X_i (X_0 = 1);
+ * ln Z = ln sum_i L*_i w_i and the information H = sum_i p_i ln(L*_i / Z),
+ * p_i = L*_i w_i / Z, accumulate in FP64 log-sum-exp, one dead point at a
+ * time in order.  The sampler itself (MultiNest in the paper) is the
+ * caller's; this is the part that runs per likelihood batch. */
+typedef struct {
+  long long n_dead;   /* dead points so far (i of the last one)              */
+  long long n_seen;   /* candidates examined so far                          */
+  double log_z;       /* ln Z over the dead points; -inf before the first    */
+  double info;        /* H over the dead points, nats                        */
+  double log_x;       /* ln X of the last dead point, -n_dead / N            */
+  double lnl_min;     /* smallest live lnL after the call                    */
+  double lnl_max;     /* largest live lnL after the call                     */
+  double reserved;
+} hr2_ns_state;
+
+/* hr2_ns_state_init: a fresh state (n_dead 0, log_z -inf, H 0) in the DEVICE
+ * struct `state`, asynchronously on `stream`. */
+int hr2_ns_state_init(hr2_ctx* ctx, hr2_ns_state* state, void* stream);
+
+/* hr2_ns_absorb: use n_cand scored candidates in order (Sect. 3.2): a
+ * candidate with lnL strictly above the live minimum (ties: lowest index; a
+ * NaN counts as +inf) replaces that live point, which becomes dead point i =
+ * n_dead + 1 with ln w_i = -(i-1)/N + ln(1 - e^(-1/N)); other candidates are
+ * skipped.  Stops when dead_cap dead points exist (the rest are not
+ * examined; state->n_seen tells how far it got).  All pointers are DEVICE:
+ *   live_lnl     double [n_live], live_theta double [n_live][HR2_NPARAM]
+ *                (updated in place)
+ *   cand_lnl     double [n_cand], cand_theta double [n_cand][HR2_NPARAM]
+ *   state        hr2_ns_state (updated; lnl_min / lnl_max refreshed)
+ *   dead_lnl, dead_logw  double [dead_cap], dead_theta double
+ *                [dead_cap][HR2_NPARAM]: dead point k at index k (absolute)
+ * Asynchronous on `stream`; one CTA.  Returns HR2_EINVAL for n_live < 1,
+ * n_cand < 0 or NULL pointers. */
+int hr2_ns_absorb(hr2_ctx* ctx, int n_live, double* live_lnl, double* live_theta, int n_cand, const double* cand_lnl,
+                  const double* cand_theta, hr2_ns_state* state, double* dead_lnl, double* dead_logw,
+                  double* dead_theta, long long dead_cap, void* stream);
+
+/* hr2_ns_finalize: ln Z and H with the live points added, each with weight
+ * X_n / N, in index order: out (DEVICE double [2]) = {ln Z, H}.  The state
+ * is not modified.  Asynchronous on `stream`. */
+int hr2_ns_finalize(hr2_ctx* ctx, int n_live, const double* live_lnl, const hr2_ns_state* state, double* out,
+                    void* stream);
+
 /* ------------------------------------------------------------- helpers */
 
 /* Nodal temperatures from the retrieved bottom temperature T_1 and the

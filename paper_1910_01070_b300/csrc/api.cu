@@ -947,6 +947,40 @@ extern "C" int hr2_stream_check(hr2_ctx* ctx, void* stream) {
   return check_device_error(w);
 }
 
+// ------------------------------------------------------------ nested sampling
+extern "C" int hr2_ns_state_init(hr2_ctx* ctx, hr2_ns_state* state, void* stream) {
+  if (!ctx || !state) return fail(HR2_EINVAL, "NULL argument");
+  HR2_CU(cudaSetDevice(ctx->device));
+  cudaError_t e = launch_ns_init(state, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(HR2_ECUDA, "ns init launch: %s", cudaGetErrorString(e));
+  return HR2_OK;
+}
+
+extern "C" int hr2_ns_absorb(hr2_ctx* ctx, int n_live, double* live_lnl, double* live_theta, int n_cand,
+                             const double* cand_lnl, const double* cand_theta, hr2_ns_state* state, double* dead_lnl,
+                             double* dead_logw, double* dead_theta, long long dead_cap, void* stream) {
+  if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
+  if (n_live < 1 || n_cand < 0 || dead_cap < 0) return fail(HR2_EINVAL, "need n_live >= 1, n_cand >= 0, dead_cap >= 0");
+  if (!live_lnl || !live_theta || !state || (n_cand && (!cand_lnl || !cand_theta)) ||
+      (dead_cap && (!dead_lnl || !dead_logw || !dead_theta)))
+    return fail(HR2_EINVAL, "NULL argument");
+  HR2_CU(cudaSetDevice(ctx->device));
+  cudaError_t e = launch_ns_absorb(n_live, live_lnl, live_theta, n_cand, cand_lnl, cand_theta, state, dead_lnl,
+                                   dead_logw, dead_theta, dead_cap, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(HR2_ECUDA, "ns absorb launch: %s", cudaGetErrorString(e));
+  return HR2_OK;
+}
+
+extern "C" int hr2_ns_finalize(hr2_ctx* ctx, int n_live, const double* live_lnl, const hr2_ns_state* state,
+                               double* out, void* stream) {
+  if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
+  if (n_live < 1 || !live_lnl || !state || !out) return fail(HR2_EINVAL, "need n_live >= 1 and non-NULL pointers");
+  HR2_CU(cudaSetDevice(ctx->device));
+  cudaError_t e = launch_ns_finalize(n_live, live_lnl, state, out, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(HR2_ECUDA, "ns finalize launch: %s", cudaGetErrorString(e));
+  return HR2_OK;
+}
+
 // ------------------------------------------------------------ instrumentation
 extern "C" int hr2_profile_enable(hr2_ctx* ctx, int on) {
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");

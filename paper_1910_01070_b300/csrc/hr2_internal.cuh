@@ -199,6 +199,13 @@ struct LnlArgs {
   double* lnl;
 };
 cudaError_t launch_lnl(const LnlArgs& a, cudaStream_t s);
+// nested-sampling evidence bookkeeping (kern_nested.cu)
+cudaError_t launch_ns_init(hr2_ns_state* st, cudaStream_t s);
+cudaError_t launch_ns_absorb(int n_live, double* live_lnl, double* live_theta, int n_cand, const double* cand_lnl,
+                             const double* cand_theta, hr2_ns_state* st, double* dead_lnl, double* dead_logw,
+                             double* dead_theta, long long dead_cap, cudaStream_t s);
+cudaError_t launch_ns_finalize(int n_live, const double* live_lnl, const hr2_ns_state* st, double* out,
+                               cudaStream_t s);
 
 // Setup construction kernels (kern_setup.cu); asynchronous on s.
 cudaError_t build_setup_levels(int n_lev, double p_top, double p_bot, const TablesDev* d_tab, LevelDev* d_levels,

@@ -33,6 +33,7 @@ EXPORTED = [
     "hr2_setup_destroy", "forward_model_batch", "forward_model_batch_noalloc", "log_likelihood_batch",
     "hr2_evaluate_host", "hr2_profile_enable",
     "hr2_profile_read", "hr2_stream_check", "hr2_nodes_from_b", "hr2_version",
+    "hr2_ns_state_init", "hr2_ns_absorb", "hr2_ns_finalize",
 ]
 
 
@@ -59,6 +60,12 @@ class SetupDesc(C.Structure):
 
 class LaunchCfg(C.Structure):
     _fields_ = [("warps_per_cta", C.c_int), ("ctas_per_sm", C.c_int)]
+
+
+class NsState(C.Structure):
+    _fields_ = [("n_dead", C.c_longlong), ("n_seen", C.c_longlong), ("log_z", C.c_double), ("info", C.c_double),
+                ("log_x", C.c_double), ("lnl_min", C.c_double), ("lnl_max", C.c_double),
+                ("reserved", C.c_double)]
 
 
 _LIB = None
@@ -104,6 +111,10 @@ def lib():
                 "hr2_stream_check": (C.c_int, [_VP, _VP]),
                 "hr2_nodes_from_b": (C.c_int, [C.c_int, C.c_double, _DP, _DP]),
                 "hr2_version": (C.c_char_p, []),
+                "hr2_ns_state_init": (C.c_int, [_VP, _VP, _VP]),
+                "hr2_ns_absorb": (C.c_int, [_VP, C.c_int, _VP, _VP, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP,
+                                            C.c_longlong, _VP]),
+                "hr2_ns_finalize": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, _VP]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -355,6 +366,49 @@ def hr2_profile_read(ctx, reset: bool = True):
     ms, n = C.c_double(), C.c_int()
     _check(lib().hr2_profile_read(ctx, int(bool(reset)), C.byref(ms), C.byref(n)), ctx)
     return ms.value, n.value
+
+
+# ------------------------------------------------------------ nested sampling
+NS_STATE_DOUBLES = C.sizeof(NsState) // 8
+
+
+def hr2_ns_state_init(ctx, state, stream=None):
+    """state: CUDA float64 tensor of NS_STATE_DOUBLES elements holding an hr2_ns_state."""
+    import torch
+    _check(lib().hr2_ns_state_init(ctx, _tensor_ptr(state, torch.float64, "state", (NS_STATE_DOUBLES,)),
+                                   _stream_ptr(stream)), ctx)
+
+
+def hr2_ns_absorb(ctx, live_lnl, live_theta, cand_lnl, cand_theta, state, dead_lnl, dead_logw, dead_theta,
+                  stream=None):
+    """CUDA float64 tensors: live [N], [N, 35] (updated), candidates [m], [m, 35], the state,
+    dead [cap], [cap], [cap, 35] (dead point k at row k)."""
+    import torch
+    n, m, cap = int(live_lnl.shape[0]), int(cand_lnl.shape[0]), int(dead_lnl.shape[0])
+    f = torch.float64
+    rc = lib().hr2_ns_absorb(
+        ctx, n, _tensor_ptr(live_lnl, f, "live_lnl"), _tensor_ptr(live_theta, f, "live_theta", (n, HR2_NPARAM)), m,
+        _tensor_ptr(cand_lnl, f, "cand_lnl"), _tensor_ptr(cand_theta, f, "cand_theta", (m, HR2_NPARAM)),
+        _tensor_ptr(state, f, "state", (NS_STATE_DOUBLES,)), _tensor_ptr(dead_lnl, f, "dead_lnl"),
+        _tensor_ptr(dead_logw, f, "dead_logw", (cap,)), _tensor_ptr(dead_theta, f, "dead_theta", (cap, HR2_NPARAM)),
+        cap, _stream_ptr(stream))
+    _check(rc, ctx)
+
+
+def hr2_ns_finalize(ctx, live_lnl, state, out, stream=None):
+    """out: CUDA float64 tensor [2] <- (ln Z, H) with the live points added."""
+    import torch
+    f = torch.float64
+    _check(lib().hr2_ns_finalize(ctx, int(live_lnl.shape[0]), _tensor_ptr(live_lnl, f, "live_lnl"),
+                                 _tensor_ptr(state, f, "state", (NS_STATE_DOUBLES,)), _tensor_ptr(out, f, "out", (2,)),
+                                 _stream_ptr(stream)), ctx)
+
+
+def ns_state_read(state) -> dict:
+    """The hr2_ns_state in a (device) float64 tensor, as a dict (synchronises)."""
+    raw = state.detach().cpu().numpy().tobytes()
+    st = NsState.from_buffer_copy(raw)
+    return {name: getattr(st, name) for name, _ in NsState._fields_ if name != "reserved"}
 
 
 def hr2_stream_check(ctx, stream=None):
