@@ -54,7 +54,12 @@ class _Model(C.Structure):
         ("n_mu", C.c_int), ("fe_elements", C.c_int), ("fe_order", C.c_int),
         ("resolving_power", C.c_double), ("n_bins", C.c_int), ("bin_edges", C.POINTER(C.c_double)),
         ("r_he", C.c_double), ("radius_cm", C.c_double), ("interp", C.c_int),
+        ("profile", C.c_int), ("n_hopf", C.c_int), ("hopf_tau", C.POINTER(C.c_double)),
+        ("hopf_q", C.POINTER(C.c_double)),
     ]
+
+# temperature profile of the setup (Sect. 2.5)
+PROFILE = {"fe": 0, "milne": 1}
 
 # interpolation space of the opacity tables (a setup option)
 INTERP = {"log10": 0, "linear": 1}
@@ -82,6 +87,8 @@ def _lib():
                 "or_log10_sigma": (C.c_double, [M, C.c_int, C.c_double, C.c_double, C.c_int]),
                 "or_sigma": (C.c_double, [M, C.c_int, C.c_double, C.c_double, C.c_int]),
                 "or_cia_coeff": (C.c_double, [M, _DP, C.c_double, C.c_int]),
+                "or_hopf": (C.c_double, [M, C.c_double]),
+                "or_effective_temperature": (C.c_double, [M, _DP]),
                 "or_convolve": (None, [M, _DP, _DP]),
                 "or_bin": (C.c_int, [M, _DP, _DP]),
                 "or_forward": (C.c_int, [M, _DP, _DP, _DP]),
@@ -182,7 +189,8 @@ class Model:
     optional log10_cia_h2h2 / log10_cia_h2he [nT][nnu], species_mass [K].
     ``setup`` is a dict with nu_first, n_nu, n_layers, p_top, p_bot, species,
     n_mu, fe_elements, fe_order, resolving_power, bin_edges, r_he, radius_cm,
-    and optionally interp ("log10", the default, or "linear").
+    and optionally interp ("log10", the default, or "linear") and profile ("fe", the
+    default, or "milne": parameters 3 and 4 are Tbar_eff and log10 kappa_R).
     """
 
     def __init__(self, tables: dict, setup: dict):
@@ -228,6 +236,13 @@ class Model:
         m.r_he = float(setup["r_he"])
         m.radius_cm = float(setup["radius_cm"])
         m.interp = INTERP[setup.get("interp", "log10")]
+        m.profile = PROFILE[setup.get("profile", "fe")]
+        if m.profile == PROFILE["milne"]:
+            from . import hopf
+            ht, hq = hopf.hopf_table()
+            m.n_hopf = len(ht)
+            m.hopf_tau = keepd(ht)
+            m.hopf_q = keepd(hq)
         self.m = m
         self._cia = {key: m_ptr for key, m_ptr in (("h2h2", m.log10_cia_h2h2), ("h2he", m.log10_cia_h2he))}
         self.ref = C.byref(m)
@@ -288,6 +303,17 @@ class Model:
 
     def log10_sigma(self, s: int, T: float, log10p: float, inu: int) -> float:
         return _lib().or_log10_sigma(self.ref, int(s), float(T), float(log10p), int(inu))
+
+    def hopf(self, tau: float) -> float:
+        """q(tau) as the Milne profile uses it (Milne setups only)."""
+        assert self.m.profile == PROFILE["milne"]
+        return _lib().or_hopf(self.ref, float(tau))
+
+    def effective_temperature(self, theta) -> float:
+        """T_eff from F+ integrated over the setup's wavenumbers (Sect. 2.6)."""
+        _, top, ok = self.forward(theta, want_top=True)
+        top, pt = _d(top)
+        return _lib().or_effective_temperature(self.ref, pt) if ok else float("nan")
 
     def sigma(self, s: int, T: float, log10p: float, inu: int) -> float:
         """Cross-section in the setup's interpolation space."""

@@ -76,7 +76,21 @@ typedef struct {
   double r_he;                  /* n_He / n_H2 of the filling gas             */
   double radius_cm;             /* R_star in the radius-distance relation        */
   int interp;                   /* OR_INTERP_LOG10 or OR_INTERP_LINEAR        */
+  int profile;                  /* OR_PROFILE_FE or OR_PROFILE_MILNE          */
+  int n_hopf;                   /* Hopf function table (Milne profile only):  */
+  const double* hopf_tau;       /*   [n_hopf] ascending optical depths         */
+  const double* hopf_q;         /*   [n_hopf] q(tau) at those depths            */
 } or_model;
+
+/* Temperature profile (Sect. 2.5): OR_PROFILE_FE, the finite-element profile
+ * of Sect. 2.5.1 (parameters 3.. are the nodal temperatures), or
+ * OR_PROFILE_MILNE, Milne's gray radiative-equilibrium profile
+ * T^4 = 3/4 Tbar^4 [tau_R + q(tau_R)] with the exact Hopf function q
+ * (parameter 3 is Tbar_eff in K, parameter 4 is log10 of the Rosseland
+ * opacity kappa_R in cm^2 g^-1; reading R15: tau_R = kappa_R p / g, the
+ * hydrostatic optical depth of a constant opacity). */
+#define OR_PROFILE_FE    0
+#define OR_PROFILE_MILNE 1
 
 /* Interpolation space of the opacity tables (Sect. 2.8 says the tables are
  * interpolated but not in which quantity).  OR_INTERP_LOG10 (reading R3, the
@@ -186,6 +200,27 @@ double or_fe_temperature(int Ke, int q, const double* Tnodes, double x) {
 void or_nodes_from_b(int n_nodes, double T1, const double* b, double* Tnodes) {
   Tnodes[0] = T1;
   for (int i = 1; i < n_nodes; ++i) Tnodes[i] = b[i - 1] * Tnodes[i - 1];
+}
+
+/* Hopf function q(tau) from the model's table: linear interpolation,
+ * constant beyond the table's ends. */
+double or_hopf(const or_model* m, double tau) {
+  const double* t = m->hopf_tau;
+  const double* q = m->hopf_q;
+  int n = m->n_hopf;
+  if (tau <= t[0]) return q[0];
+  if (tau >= t[n - 1]) return q[n - 1];
+  int k = 0;
+  while (t[k + 1] < tau) ++k;
+  double w = (tau - t[k]) / (t[k + 1] - t[k]);
+  return (1.0 - w) * q[k] + w * q[k + 1];
+}
+
+/* Milne's profile (Sect. 2.5): T^4 = 3/4 Tbar^4 [tau_R + q(tau_R)] with
+ * tau_R = kappa_R p / g (reading R15), p in dyn cm^-2, g in cm s^-2. */
+double or_milne_temperature(const or_model* m, double Tbar, double log10_kappa, double p, double g) {
+  double tau = pow(10.0, log10_kappa) * p / g;
+  return pow(0.75 * pow(Tbar, 4.0) * (tau + or_hopf(m, tau)), 0.25);
 }
 
 /* ======================================================================
@@ -332,12 +367,16 @@ int or_prepare(const or_model* m, const double* theta, or_state* st) {
   double lt = log10(m->p_top), lb = log10(m->p_bot);
   int Ke = m->fe_elements, q = m->fe_order;
   int ok = 1;
+  double grav = pow(10.0, theta[OR_P_LOGG]);
   for (int j = 0; j <= L; ++j) {
     double lp = lt + (lb - lt) * (double)j / (double)L;
     st->log10p_bar[j] = lp;
     st->p[j] = pow(10.0, lp) * OR_BAR;
-    double xpos = (double)(L - j) / (double)L;
-    double T = or_fe_temperature(Ke, q, theta + OR_P_T0, xpos);
+    double T;
+    if (m->profile == OR_PROFILE_MILNE)
+      T = or_milne_temperature(m, theta[OR_P_T0], theta[OR_P_T0 + 1], st->p[j], grav);
+    else
+      T = or_fe_temperature(Ke, q, theta + OR_P_T0, (double)(L - j) / (double)L);
     st->T[j] = T;
     if (!(T > 0.0) || !isfinite(T)) ok = 0;
   }
@@ -467,6 +506,17 @@ int or_forward(const or_model* m, const double* theta, double* bins, double* Fto
   }
   free(Fc); free(F); free(st);
   return ok;
+}
+
+/* Effective temperature (Sect. 2.6): the outgoing flux F+ at the top of the
+ * atmosphere (before the distance dilution of Eq. 9), integrated over the
+ * setup's wavenumbers by the trapezoid rule, converted with the
+ * Stefan-Boltzmann law F = sigma T_eff^4, sigma = 2 pi^5 k^4 / (15 h^3 c^2). */
+double or_effective_temperature(const or_model* m, const double* Ftop) {
+  double F = 0.0;
+  for (int k = 0; k + 1 < m->n_nu; ++k) F += 0.5 * (Ftop[k] + Ftop[k + 1]) * m->dnu;
+  double sigma = 2.0 * pow(M_PI, 5) * pow(OR_KB, 4) / (15.0 * pow(OR_H, 3) * OR_C * OR_C);
+  return pow(F / sigma, 0.25);
 }
 
 /* F+ (unscaled) at a chosen list of setup indices: the same per-point

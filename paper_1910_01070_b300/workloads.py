@@ -79,6 +79,7 @@ class SetupSpec:
     r_he: float = 0.17          # n_He / n_H2
     radius_cm: float = R_JUPITER_CM
     interp: str = "log10"       # opacity interpolation space: "log10" or "linear"
+    profile: str = "fe"         # temperature profile: "fe" (finite elements) or "milne"
 
     @property
     def n_bins(self) -> int:
@@ -86,7 +87,8 @@ class SetupSpec:
 
     @property
     def n_tnodes(self) -> int:
-        return self.fe_elements * self.fe_order + 1
+        """Temperature parameters: the FE nodes, or (Tbar_eff, log10 kappa_R) for Milne's profile."""
+        return 2 if self.profile == "milne" else self.fe_elements * self.fe_order + 1
 
     def as_dict(self) -> Dict:
         return dataclasses.asdict(self)
@@ -174,6 +176,8 @@ class Prior:
     b: tuple = (0.3, 0.95)
     dist_pc: float = 10.0
     free_nodes: Optional[tuple] = None   # (Tmin, Tmax): independent control points instead of (T1, b)
+    t_bar: tuple = (400.0, 2000.0)       # Milne profile: Tbar_eff, K
+    log_kappa: tuple = (-4.0, 0.0)       # Milne profile: log10 kappa_R, cm^2 g^-1
 
 
 def draw_params(setup: SetupSpec, n: int, seed: int, prior: Prior = Prior()) -> np.ndarray:
@@ -184,7 +188,10 @@ def draw_params(setup: SetupSpec, n: int, seed: int, prior: Prior = Prior()) -> 
     th[:, P_F] = rng.uniform(*prior.f, n)
     th[:, P_DIST] = prior.dist_pc
     nt = setup.n_tnodes
-    if prior.free_nodes is not None:
+    if setup.profile == "milne":
+        th[:, P_T0] = rng.uniform(*prior.t_bar, n)
+        th[:, P_T0 + 1] = rng.uniform(*prior.log_kappa, n)
+    elif prior.free_nodes is not None:
         th[:, P_T0:P_T0 + nt] = rng.uniform(*prior.free_nodes, (n, nt))
     else:
         T1 = rng.uniform(*prior.T1, n)
