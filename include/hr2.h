@@ -74,6 +74,9 @@ typedef enum {
  *                     bottom of the atmosphere (T_1 of Sect. 2.5.1); the setup
  *                     uses fe_elements*fe_order+1 of them
  *   [HR2_P_X0 + s]    log10 volume mixing ratio of the setup's absorber s
+ * With Milne's profile (HR2_PROFILE_MILNE) the temperature entries are
+ *   [HR2_P_T0]        Tbar_eff in K (the gray-atmosphere parameter, Sect. 2.5)
+ *   [HR2_P_T0 + 1]    log10 kappa_R, the Rosseland opacity in cm^2 g^-1
  * Unused entries are ignored.  hr2_nodes_from_b() converts (T_1, b_i) to
  * nodal temperatures. */
 #define HR2_P_LOGG  0
@@ -91,6 +94,13 @@ typedef enum {
  * interpolation of the tables but not the quantity interpolated). */
 #define HR2_INTERP_LOG10  0  /* bilinear in log10 sigma, then 10^x (default)     */
 #define HR2_INTERP_LINEAR 1  /* bilinear in sigma itself (CIA: linear in T)      */
+
+/* Temperature profile (Sect. 2.5). */
+#define HR2_PROFILE_FE    0  /* finite elements on Gauss-Lobatto nodes (Sect.
+                                2.5.1; the default)                              */
+#define HR2_PROFILE_MILNE 1  /* Milne's gray radiative-equilibrium profile
+                                T^4 = 3/4 Tbar^4 [tau_R + q(tau_R)] with the
+                                exact Hopf function q; tau_R = kappa_R p / g     */
 
 typedef struct hr2_ctx hr2_ctx;
 typedef struct hr2_tables hr2_tables;
@@ -150,6 +160,11 @@ typedef struct {
                                  interpolates in T with FMAs only); FP64
                                  tables take either.  One batch call takes
                                  setups of a single option.                      */
+  int profile;                /* HR2_PROFILE_FE or HR2_PROFILE_MILNE.  Milne's
+                                 profile tabulates q(tau) once at creation
+                                 (Chandrasekhar's H-function representation,
+                                 FP64; 32 KB of device memory); a batch may mix
+                                 profiles.                                       */
 } hr2_setup_desc;
 
 /* Launch shape of the persistent forward kernel (chosen by the autotuner). */
@@ -320,6 +335,18 @@ int hr2_profile_read(hr2_ctx* ctx, int reset, double* kernel_ms, int* launches);
  * valid).  No counterpart in the paper.  hr2_evaluate_host checks the same
  * word itself. */
 int hr2_stream_check(hr2_ctx* ctx, void* stream);
+
+/* hr2_effective_temperature: T_eff of each sample (Sect. 2.6): its F+ (the
+ * high-resolution output of forward_model_batch, before the distance
+ * dilution of Eq. 9) integrated over its setup's wavenumber grid by the
+ * trapezoid rule in FP64, converted by the Stefan-Boltzmann law F = sigma
+ * T_eff^4.  Meaningful for a setup spanning the emitted spectrum (the paper
+ * integrates 1-20 micron).  DEVICE pointers: setup_of_sample int [n],
+ * highres float [n][highres_ld] (as forward_model_batch wrote it), out_teff
+ * double [n] (NaN for a sample with an invalid setup index or NaN flux).
+ * Asynchronous on `stream`. */
+int hr2_effective_temperature(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups, const int* setup_of_sample,
+                              const float* highres, int highres_ld, int n, double* out_teff, void* stream);
 
 /* ------------------------------------------------------ nested sampling
  * Evidence bookkeeping of nested sampling (Sect. 3.2, after Skilling 2004),

@@ -519,6 +519,8 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
     return fail(HR2_EINVAL, "interp %d is neither HR2_INTERP_LOG10 nor HR2_INTERP_LINEAR", d->interp);
   if (d->interp == HR2_INTERP_LINEAR && th.storage == HR2_STORE_FP16_OFFSET && !d->level_cache)
     return fail(HR2_EINVAL, "the linear interpolation option on FP16 tables needs level_cache");
+  if (d->profile != HR2_PROFILE_FE && d->profile != HR2_PROFILE_MILNE)
+    return fail(HR2_EINVAL, "profile %d is neither HR2_PROFILE_FE nor HR2_PROFILE_MILNE", d->profile);
   HR2_CU(cudaSetDevice(ctx->device));
 
   hr2_setup* st = new hr2_setup();
@@ -544,6 +546,7 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
   h.r_he = d->r_he;
   h.radius_cm = d->radius_cm;
   h.interp = d->interp;
+  h.profile = d->profile;
   h.n_bins = d->n_bins;
   h.tables = tab->dev;
   const int n_cia = th.has_cia[0] + th.has_cia[1];
@@ -647,6 +650,16 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
                             d_rowptr, d_w32, d_w64, 0)) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
       rc = fail(HR2_ECUDA, "setup operator values: %s", cudaGetErrorString(e));
+      goto fail_tmp;
+    }
+  }
+  if (d->profile == HR2_PROFILE_MILNE) {
+    double* d_hopf = nullptr;
+    if ((rc = dalloc_t(ctx, &d_hopf, (size_t)kHopfN))) goto fail_tmp;
+    track(d_hopf);
+    h.hopf_q = d_hopf;
+    if ((e = build_hopf_table(d_hopf, 0)) != cudaSuccess || (e = cudaDeviceSynchronize()) != cudaSuccess) {
+      rc = fail(HR2_ECUDA, "setup Hopf function: %s", cudaGetErrorString(e));
       goto fail_tmp;
     }
   }
@@ -945,6 +958,29 @@ extern "C" int hr2_stream_check(hr2_ctx* ctx, void* stream) {
     w = it->second;
   }
   return check_device_error(w);
+}
+
+// ------------------------------------------------------------ effective temperature
+extern "C" int hr2_effective_temperature(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
+                                         const int* setup_of_sample, const float* highres, int highres_ld, int n,
+                                         double* out_teff, void* stream) {
+  if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
+  if (n < 0) return fail(HR2_EINVAL, "n < 0");
+  BatchShape sh;
+  int rc = check_setups(ctx, n_setups, setups, &sh);
+  if (rc) return rc;
+  if (n == 0) return HR2_OK;
+  if (!setup_of_sample || !highres || !out_teff) return fail(HR2_EINVAL, "setup_of_sample, highres, out_teff required");
+  if (highres_ld < sh.max_nu) return fail(HR2_EINVAL, "highres_ld %d < largest n_nu %d", highres_ld, sh.max_nu);
+  HR2_CU(cudaSetDevice(ctx->device));
+  FwdArgs a{};
+  for (int g = 0; g < n_setups; ++g) a.setups[g] = setups[g]->dev;
+  a.n_setups = n_setups;
+  a.n = n;
+  a.setup_of_sample = setup_of_sample;
+  cudaError_t e = launch_teff(a, highres, highres_ld, out_teff, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(HR2_ECUDA, "effective temperature launch: %s", cudaGetErrorString(e));
+  return HR2_OK;
 }
 
 // ------------------------------------------------------------ nested sampling

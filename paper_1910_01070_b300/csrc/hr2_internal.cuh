@@ -39,6 +39,15 @@ constexpr double kLn2 = 0.6931471805599453;       // ln(2)
 // second radiation constant h c / k_B (cm K) and 2 h c^2 (erg cm^2 s^-1)
 constexpr double kC2 = kH * kC / kKB;
 constexpr double kC1 = 2.0 * kH * kC * kC;
+// Stefan-Boltzmann constant 2 pi^5 k^4 / (15 h^3 c^2), erg s^-1 cm^-2 K^-4
+constexpr double kSigmaSB = 2.0 * kPi * kPi * kPi * kPi * kPi * kKB * kKB * kKB * kKB / (15.0 * kH * kH * kH * kC * kC);
+
+// Hopf function table of Milne's profile: q at ln tau uniform on
+// [ln kHopfTau0, ln kHopfTau1] (kHopfN points); q(0) below, q(kHopfTau1)
+// above (q approaches q(inf) within e^-60 there)
+constexpr int kHopfN = 4096;
+constexpr double kHopfTau0 = 1e-9;
+constexpr double kHopfTau1 = 60.0;
 
 // Device copy of one opacity table set.
 struct TablesDev {
@@ -102,6 +111,10 @@ struct SetupDev {
   int cached;
   const float* lvl32;            // [n_tiles][n_lev][n_T][n_species][kTileNu]
   const float* cia32;            // [n_tiles][n_T][2][kTileNu]
+  // temperature profile (HR2_PROFILE_*); Milne's profile reads its Hopf
+  // function from hopf_q [kHopfN] (built at setup creation)
+  int profile;
+  const double* hopf_q;
   // interpolation space (HR2_INTERP_*): with HR2_INTERP_LINEAR the operand
   // holds 10^(stored log10 sigma) interpolated linearly in log10 p (and the
   // CIA operand 10^(stored value)), and the kernels interpolate linearly in T
@@ -199,6 +212,9 @@ struct LnlArgs {
   double* lnl;
 };
 cudaError_t launch_lnl(const LnlArgs& a, cudaStream_t s);
+// Hopf function table (kern_setup.cu) and effective temperatures (kern_forward.cu)
+cudaError_t build_hopf_table(double* d_q, cudaStream_t s);
+cudaError_t launch_teff(const FwdArgs& a, const float* highres, int highres_ld, double* out, cudaStream_t s);
 // nested-sampling evidence bookkeeping (kern_nested.cu)
 cudaError_t launch_ns_init(hr2_ns_state* st, cudaStream_t s);
 cudaError_t launch_ns_absorb(int n_live, double* live_lnl, double* live_theta, int n_cand, const double* cand_lnl,

@@ -45,6 +45,29 @@ __device__ double fe_temperature(const SetupDev& S, const double* nodes, double 
   return T;
 }
 
+// Hopf function q(tau) from the setup's table (linear in ln tau).
+__device__ double hopf_q(const double* tab, double tau) {
+  if (!(tau > kHopfTau0)) return tab[0];
+  const double u = (log(tau) - log(kHopfTau0)) * ((kHopfN - 1) / (log(kHopfTau1) - log(kHopfTau0)));
+  if (!(u < kHopfN - 1)) return tab[kHopfN - 1];
+  const int k = (int)u;
+  const double w = u - (double)k;
+  return (1.0 - w) * tab[k] + w * tab[k + 1];
+}
+
+// Temperature of level j (0 = top) of sample parameters th (Sect. 2.5): the
+// finite-element profile, or Milne's T^4 = 3/4 Tbar^4 (tau_R + q(tau_R)) with
+// tau_R = kappa_R p_j / g (th[3] = Tbar in K, th[4] = log10 kappa_R in cm^2/g).
+__device__ double level_temperature(const SetupDev& S, const double* th, int j, double grav) {
+  const int L = S.n_lev - 1;
+  if (S.profile == HR2_PROFILE_MILNE) {
+    const double tau = exp10(th[HR2_P_T0 + 1]) * S.levels[j].p_dyn64 / grav;
+    const double tb = th[HR2_P_T0];
+    return pow(0.75 * tb * tb * tb * tb * (tau + hopf_q(S.hopf_q, tau)), 0.25);
+  }
+  return fe_temperature(S, th + HR2_P_T0, (double)(L - j) / (double)L);
+}
+
 // Cell a with grid[a] <= v <= grid[a+1] and the weight of grid[a+1],
 // clamped to the grid ends (no extrapolation).
 __device__ void grid_cell(const double* grid, int n, double v, int& a, double& w) {
@@ -127,8 +150,7 @@ __global__ void k_prep(FwdArgs a) {
   const int L = S.n_lev - 1;
   LevRec* rec = a.recs + (size_t)i * a.rec_ld;
   for (int j = lane; j <= L; j += 32) {
-    const double x = (double)(L - j) / (double)L;
-    const double Tj = fe_temperature(S, th + HR2_P_T0, x);
+    const double Tj = level_temperature(S, th, j, grav);
     if (!(Tj > 0.0) || !isfinite(Tj)) status |= HR2_SAMPLE_BAD_T;
     int acell;
     double wT;
@@ -949,6 +971,38 @@ cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cache
   }
 }
 
+// ---------------------------------------------------- effective temperature
+// T_eff per sample (Sect. 2.6): F+ (the library's high-resolution output,
+// before the distance dilution) integrated over the sample's setup grid by
+// the trapezoid rule in FP64 (lane-strided sums, fixed-order butterfly), then
+// F = sigma T_eff^4.  One warp per sample.
+__global__ void k_teff(FwdArgs a, const float* __restrict__ highres, int ld, double* out) {
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= a.n) return;
+  const int g = a.setup_of_sample[i];
+  if (g < 0 || g >= a.n_setups) {
+    if (lane == 0) out[i] = __longlong_as_double(0x7ff8000000000000ll);
+    return;
+  }
+  const SetupDev& S = *a.setups[g];
+  const float* F = highres + (size_t)i * ld;
+  const int n = S.n_nu;
+  double acc = 0.0;
+  for (int k = lane; k < n; k += 32) acc += (double)F[k];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) {
+    const double trap = S.tables->dnu * (acc - 0.5 * ((double)F[0] + (double)F[n - 1]));
+    out[i] = pow(trap / kSigmaSB, 0.25);
+  }
+}
+
+cudaError_t launch_teff(const FwdArgs& a, const float* highres, int highres_ld, double* out, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  k_teff<<<(a.n + 7) / 8, 256, 0, s>>>(a, highres, highres_ld, out);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------- FP64 forward
 // The plain FP64 path: one thread per wavenumber point, one block per
 // (sample, 128-point chunk), FP64 tables, exp/expm1 in double.
@@ -993,8 +1047,9 @@ __global__ void __launch_bounds__(kF64Block) k_forward64(FwdArgs a) {
     sc[2] = xhe;
   }
   const int L = S.n_lev - 1;
+  const double grav = exp10(th[HR2_P_LOGG]);
   for (int j = threadIdx.x; j <= L; j += kF64Block) {
-    const double Tj = fe_temperature(S, th + HR2_P_T0, (double)(L - j) / (double)L);
+    const double Tj = level_temperature(S, th, j, grav);
     int ac;
     double w;
     grid_cell(T.T_grid64, T.n_T, Tj, ac, w);

@@ -112,6 +112,98 @@ cudaError_t build_quadratures(int n_mu, int n_gll, double* d_out, cudaStream_t s
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------- Hopf function
+// q(tau) of Milne's problem (Sect. 2.5) from Chandrasekhar's closed form
+//   q(tau) = 1/sqrt(3) + (1/(2 sqrt 3)) int_0^1 g(mu) (1 - e^{-tau/mu}) dmu,
+//   g(mu) = 1 / (H(mu) [(1 - (mu/2) ln((1+mu)/(1-mu)))^2 + (pi mu / 2)^2]),
+//   ln H(mu) = -(mu/pi) int_0^{pi/2} ln(1 - th cot th) / (cos^2 th + mu^2 sin^2 th) dth,
+// H the H-function of conservative isotropic scattering.  Quadratures
+// (Gauss-Legendre): theta = (pi/2) s^2 (128 nodes; removes the log
+// singularity at theta = 0); mu in [1/2, 1) as mu = 1 - (1-s)^3 / 2 (32
+// nodes; clusters at the log singularity of g at mu = 1) and mu in (0, 1/2]
+// as mu = e^{-v} / 2, v in [0, 30] (64 nodes; resolves e^{-tau/mu} down to
+// tau ~ 1e-9).  One CTA, FP64, once per setup.
+constexpr int kHopfTheta = 128, kHopfMuA = 32, kHopfMuB = 64;
+
+// node i of the n-point Gauss-Legendre rule on [-1, 1] and its weight
+__device__ void gauss_legendre_node(int n, int i, double& x, double& w) {
+  double p, dp;
+  x = cos(kPi * (i + 0.75) / (n + 0.5));
+  for (int it = 0; it < 60; ++it) {
+    legendre_pd(n, x, p, dp);
+    const double dx = p / dp;
+    x -= dx;
+    if (fabs(dx) < 1e-16) break;
+  }
+  legendre_pd(n, x, p, dp);
+  w = 2.0 / ((1.0 - x * x) * dp * dp);
+}
+
+// ln(1 - th cot th), by its series th^2/3 (1 + th^2/15 + 2 th^4/315) for small th
+__device__ double ln_one_minus_th_cot(double th) {
+  const double t2 = th * th;
+  if (th < 0.05) return log(t2 / 3.0) + log1p(t2 / 15.0 + 2.0 * t2 * t2 / 315.0);
+  return log(1.0 - th / tan(th));
+}
+
+__global__ void __launch_bounds__(256) k_hopf_table(double* q_out) {
+  __shared__ double s_th[kHopfTheta], s_wth[kHopfTheta];
+  __shared__ double s_mu[kHopfMuA + kHopfMuB], s_wg[kHopfMuA + kHopfMuB];
+  __shared__ double s_tail0;
+  const int t = threadIdx.x;
+  if (t < kHopfTheta) {
+    double x, w;
+    gauss_legendre_node(kHopfTheta, t, x, w);
+    const double sn = 0.5 * (x + 1.0);
+    s_th[t] = 0.5 * kPi * sn * sn;
+    s_wth[t] = 0.5 * w * kPi * sn;               // ds/2 times dtheta/ds
+  }
+  __syncthreads();
+  if (t < kHopfMuA + kHopfMuB) {
+    double x, w, mu, wmu;
+    if (t < kHopfMuA) {
+      gauss_legendre_node(kHopfMuA, t, x, w);
+      const double sn = 0.5 * (x + 1.0), om = 1.0 - sn;
+      mu = 1.0 - 0.5 * om * om * om;
+      wmu = 0.5 * w * 1.5 * om * om;
+    } else {
+      gauss_legendre_node(kHopfMuB, t - kHopfMuA, x, w);
+      const double v = 15.0 * (x + 1.0);
+      mu = 0.5 * exp(-v);
+      wmu = 15.0 * w * mu;
+    }
+    double acc = 0.0;
+    for (int k = 0; k < kHopfTheta; ++k) {
+      const double th = s_th[k], c = cos(th), sn = sin(th);
+      acc += s_wth[k] * ln_one_minus_th_cot(th) / (c * c + mu * mu * sn * sn);
+    }
+    const double H = exp(-mu / kPi * acc);
+    const double a = 1.0 - 0.5 * mu * log((1.0 + mu) / (1.0 - mu));
+    s_mu[t] = mu;
+    s_wg[t] = wmu / (H * (a * a + 0.25 * kPi * kPi * mu * mu));
+  }
+  __syncthreads();
+  if (t == 0) {
+    double z = 0.0;
+    for (int k = 0; k < kHopfMuA + kHopfMuB; ++k) z += s_wg[k];
+    s_tail0 = z;
+  }
+  __syncthreads();
+  const double lt0 = log(kHopfTau0), du = (log(kHopfTau1) - lt0) / (kHopfN - 1);
+  const double c0 = 1.0 / sqrt(3.0), c1 = 0.5 / sqrt(3.0);
+  for (int i = t; i < kHopfN; i += blockDim.x) {
+    const double tau = exp(lt0 + du * i);
+    double tail = 0.0;
+    for (int k = 0; k < kHopfMuA + kHopfMuB; ++k) tail += s_wg[k] * exp(-tau / s_mu[k]);
+    q_out[i] = c0 + c1 * (s_tail0 - tail);
+  }
+}
+
+cudaError_t build_hopf_table(double* d_q, cudaStream_t s) {
+  k_hopf_table<<<1, 256, 0, s>>>(d_q);
+  return cudaGetLastError();
+}
+
 // --------------------------------------------------------------- levels
 // Level j (0 = top) at log10 p_j = lt + (lb - lt) j / L (equidistant in
 // log p, Sect. 2); the p-grid cell of the table that brackets it (clamped to

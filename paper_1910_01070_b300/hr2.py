@@ -25,6 +25,8 @@ HR2_P_LOGG, HR2_P_F, HR2_P_DIST, HR2_P_T0, HR2_P_X0, HR2_NPARAM = 0, 1, 2, 3, 19
 HR2_STORE_FP16_OFFSET, HR2_STORE_FP64 = 1, 2
 HR2_INTERP_LOG10, HR2_INTERP_LINEAR = 0, 1
 INTERP = {"log10": HR2_INTERP_LOG10, "linear": HR2_INTERP_LINEAR}
+HR2_PROFILE_FE, HR2_PROFILE_MILNE = 0, 1
+PROFILE = {"fe": HR2_PROFILE_FE, "milne": HR2_PROFILE_MILNE}
 
 EXPORTED = [
     "hr2_ctx_create", "hr2_ctx_destroy", "hr2_last_error", "hr2_ctx_memory", "hr2_set_launch_config",
@@ -33,7 +35,7 @@ EXPORTED = [
     "hr2_setup_destroy", "forward_model_batch", "forward_model_batch_noalloc", "log_likelihood_batch",
     "hr2_evaluate_host", "hr2_profile_enable",
     "hr2_profile_read", "hr2_stream_check", "hr2_nodes_from_b", "hr2_version",
-    "hr2_ns_state_init", "hr2_ns_absorb", "hr2_ns_finalize",
+    "hr2_ns_state_init", "hr2_ns_absorb", "hr2_ns_finalize", "hr2_effective_temperature",
 ]
 
 
@@ -55,7 +57,7 @@ class SetupDesc(C.Structure):
                 ("fe_elements", C.c_int), ("fe_order", C.c_int), ("resolving_power", C.c_double),
                 ("n_bins", C.c_int), ("bin_edges", C.POINTER(C.c_double)), ("obs_flux", C.POINTER(C.c_double)),
                 ("obs_sigma", C.POINTER(C.c_double)), ("r_he", C.c_double), ("radius_cm", C.c_double),
-                ("level_cache", C.c_int), ("interp", C.c_int)]
+                ("level_cache", C.c_int), ("interp", C.c_int), ("profile", C.c_int)]
 
 
 class LaunchCfg(C.Structure):
@@ -112,6 +114,8 @@ def lib():
                 "hr2_nodes_from_b": (C.c_int, [C.c_int, C.c_double, _DP, _DP]),
                 "hr2_version": (C.c_char_p, []),
                 "hr2_ns_state_init": (C.c_int, [_VP, _VP, _VP]),
+                "hr2_effective_temperature": (C.c_int, [_VP, C.c_int, C.POINTER(_VP), _VP, _VP, C.c_int, C.c_int,
+                                                        _VP, _VP]),
                 "hr2_ns_absorb": (C.c_int, [_VP, C.c_int, _VP, _VP, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP,
                                             C.c_longlong, _VP]),
                 "hr2_ns_finalize": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, _VP]),
@@ -247,8 +251,9 @@ def hr2_tables_destroy(ctx, tables):
 
 def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_elements, fe_order,
                      resolving_power, bin_edges, p_top=1e-4, p_bot=100.0, r_he=0.17, radius_cm=7.1492e9,
-                     obs_flux=None, obs_sigma=None, level_cache=True, interp="log10"):
-    """interp: "log10" (HR2_INTERP_LOG10) or "linear" (HR2_INTERP_LINEAR)."""
+                     obs_flux=None, obs_sigma=None, level_cache=True, interp="log10", profile="fe"):
+    """interp: "log10" (HR2_INTERP_LOG10) or "linear" (HR2_INTERP_LINEAR);
+    profile: "fe" (HR2_PROFILE_FE) or "milne" (HR2_PROFILE_MILNE)."""
     sp = np.ascontiguousarray(np.asarray(species, dtype=np.int32))
     edges, pe = _dptr(bin_edges)
     keep = [sp, edges]
@@ -261,7 +266,7 @@ def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_el
     d = SetupDesc(int(nu_first), int(n_nu), int(n_layers), float(p_top), float(p_bot), len(sp),
                   sp.ctypes.data_as(_IP), int(n_mu), int(fe_elements), int(fe_order), float(resolving_power),
                   len(edges) - 1, pe, pf, ps, float(r_he), float(radius_cm), int(bool(level_cache)),
-                  INTERP[interp])
+                  INTERP[interp], PROFILE[profile])
     h = _VP()
     _check(lib().hr2_setup_create(ctx, tables, C.byref(d), C.byref(h)), ctx)
     return h
@@ -366,6 +371,17 @@ def hr2_profile_read(ctx, reset: bool = True):
     ms, n = C.c_double(), C.c_int()
     _check(lib().hr2_profile_read(ctx, int(bool(reset)), C.byref(ms), C.byref(n)), ctx)
     return ms.value, n.value
+
+
+def hr2_effective_temperature(ctx, setups: Sequence, setup_of_sample, highres, out_teff, stream=None):
+    """CUDA tensors: int32 [n], float32 [n, ld] (F+ from forward_model_batch), float64 [n] out."""
+    import torch
+    n = int(highres.shape[0])
+    rc = lib().hr2_effective_temperature(
+        ctx, len(setups), _setup_array(setups), _tensor_ptr(setup_of_sample, torch.int32, "setup_of_sample", (n,)),
+        _tensor_ptr(highres, torch.float32, "highres", (n,)), int(highres.shape[1]), n,
+        _tensor_ptr(out_teff, torch.float64, "out_teff", (n,)), _stream_ptr(stream))
+    _check(rc, ctx)
 
 
 # ------------------------------------------------------------ nested sampling
