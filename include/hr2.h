@@ -54,6 +54,7 @@ typedef enum {
 #define HR2_SAMPLE_BAD_ABUND  2  /* mixing ratios sum to >= 1 or are not finite */
 #define HR2_SAMPLE_BAD_SCALE  4  /* f, d or g not positive / finite            */
 #define HR2_SAMPLE_BAD_SETUP  8  /* setup index outside [0, n_setups)          */
+#define HR2_SAMPLE_BAD_CLOUD 16  /* cloud parameters not finite or f_c > 1     */
 
 /* ---------------------------------------------------------------- limits */
 #define HR2_MAX_TNODES   16   /* finite-element temperature nodes, K_e q + 1  */
@@ -74,6 +75,12 @@ typedef enum {
  *                     bottom of the atmosphere (T_1 of Sect. 2.5.1); the setup
  *                     uses fe_elements*fe_order+1 of them
  *   [HR2_P_X0 + s]    log10 volume mixing ratio of the setup's absorber s
+ *   [HR2_P_CLOUD]     gray cloud layer (setups with cloud != 0; Appendix,
+ *                     "Impact of a gray cloud layer"): log10 of its optical
+ *                     depth tau_c,
+ *   [HR2_P_CLOUD + 1] log10 of its top pressure in bar,
+ *   [HR2_P_CLOUD + 2] log10 f_c, 0 < f_c <= 1: the layer spans p_top to
+ *                     p_top / f_c, tau_c spread evenly in pressure over it
  * With Milne's profile (HR2_PROFILE_MILNE) the temperature entries are
  *   [HR2_P_T0]        Tbar_eff in K (the gray-atmosphere parameter, Sect. 2.5)
  *   [HR2_P_T0 + 1]    log10 kappa_R, the Rosseland opacity in cm^2 g^-1
@@ -84,7 +91,8 @@ typedef enum {
 #define HR2_P_DIST  2
 #define HR2_P_T0    3
 #define HR2_P_X0   19
-#define HR2_NPARAM 35
+#define HR2_P_CLOUD 35
+#define HR2_NPARAM 38
 
 /* ---------------------------------------------------------------- storage */
 #define HR2_STORE_FP16_OFFSET 1  /* FP16 of (log10 sigma - off_s), off_s integer */
@@ -165,6 +173,10 @@ typedef struct {
                                  (Chandrasekhar's H-function representation,
                                  FP64; 32 KB of device memory); a batch may mix
                                  profiles.                                       */
+  int cloud;                  /* nonzero: add the gray cloud layer of
+                                 parameters HR2_P_CLOUD.. (its optical depth is
+                                 the same at every wavenumber and adds to the
+                                 layers' absorption optical depths)              */
 } hr2_setup_desc;
 
 /* Launch shape of the persistent forward kernel (chosen by the autotuner). */

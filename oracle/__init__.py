@@ -25,7 +25,7 @@ _SO = os.path.join(_HERE, "liboracle.so")
 _LOCK = threading.Lock()
 _LIB = None
 
-NPARAM = 35
+NPARAM = 38
 P_LOGG, P_F, P_DIST, P_T0, P_X0 = 0, 1, 2, 3, 19
 
 
@@ -55,7 +55,7 @@ class _Model(C.Structure):
         ("resolving_power", C.c_double), ("n_bins", C.c_int), ("bin_edges", C.POINTER(C.c_double)),
         ("r_he", C.c_double), ("radius_cm", C.c_double), ("interp", C.c_int),
         ("profile", C.c_int), ("n_hopf", C.c_int), ("hopf_tau", C.POINTER(C.c_double)),
-        ("hopf_q", C.POINTER(C.c_double)),
+        ("hopf_q", C.POINTER(C.c_double)), ("cloud", C.c_int),
     ]
 
 # temperature profile of the setup (Sect. 2.5)
@@ -189,8 +189,9 @@ class Model:
     optional log10_cia_h2h2 / log10_cia_h2he [nT][nnu], species_mass [K].
     ``setup`` is a dict with nu_first, n_nu, n_layers, p_top, p_bot, species,
     n_mu, fe_elements, fe_order, resolving_power, bin_edges, r_he, radius_cm,
-    and optionally interp ("log10", the default, or "linear") and profile ("fe", the
-    default, or "milne": parameters 3 and 4 are Tbar_eff and log10 kappa_R).
+    and optionally interp ("log10", the default, or "linear"), profile ("fe", the
+    default, or "milne": parameters 3 and 4 are Tbar_eff and log10 kappa_R) and
+    cloud (True: a gray cloud layer from parameters 35..37).
     """
 
     def __init__(self, tables: dict, setup: dict):
@@ -237,6 +238,7 @@ class Model:
         m.radius_cm = float(setup["radius_cm"])
         m.interp = INTERP[setup.get("interp", "log10")]
         m.profile = PROFILE[setup.get("profile", "fe")]
+        m.cloud = int(bool(setup.get("cloud", False)))
         if m.profile == PROFILE["milne"]:
             from . import hopf
             ht, hq = hopf.hopf_table()

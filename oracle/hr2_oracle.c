@@ -41,13 +41,17 @@
 /* ---- parameter vector layout (one row per sample) ----
  * 0 log10 g (cgs), 1 calibration factor f, 2 distance d in parsec,
  * 3..18 finite-element nodal temperatures, bottom node first (Sect. 2.5.1),
- * 19..34 log10 volume mixing ratios of the setup's absorbers (Sect. 2.4). */
+ * 19..34 log10 volume mixing ratios of the setup's absorbers (Sect. 2.4),
+ * 35..37 gray cloud layer (Appendix, "Impact of a gray cloud layer"):
+ * log10 of its optical depth, log10 of its top pressure in bar, log10 of
+ * the fraction f_c (reading R16: the layer spans p_top .. p_top / f_c). */
 #define OR_P_LOGG  0
 #define OR_P_F     1
 #define OR_P_DIST  2
 #define OR_P_T0    3
 #define OR_P_X0    19
-#define OR_NPARAM  35
+#define OR_P_CLOUD 35
+#define OR_NPARAM  38
 #define OR_MAX_T   16
 #define OR_MAX_SP  16
 #define OR_MAX_MU  16
@@ -80,6 +84,7 @@ typedef struct {
   int n_hopf;                   /* Hopf function table (Milne profile only):  */
   const double* hopf_tau;       /*   [n_hopf] ascending optical depths         */
   const double* hopf_q;         /*   [n_hopf] q(tau) at those depths            */
+  int cloud;                    /* 1: gray cloud layer from parameters 35..37 */
 } or_model;
 
 /* Temperature profile (Sect. 2.5): OR_PROFILE_FE, the finite-element profile
@@ -350,6 +355,7 @@ typedef struct {
   double mmw;              /* mean molecular weight, u                      */
   double g;                /* surface gravity, cm s^-2                      */
   double scale;            /* f (R_star / d)^2, Eq. (9)                        */
+  double tau_cloud[1024];  /* gray cloud optical depth of each layer          */
 } or_state;
 
 #define OR_MAX_LEVELS 1024
@@ -397,6 +403,24 @@ int or_prepare(const or_model* m, const double* theta, or_state* st) {
   double f = theta[OR_P_F], d = theta[OR_P_DIST] * OR_PARSEC;
   if (!(f > 0.0) || !(d > 0.0) || !isfinite(f) || !isfinite(d) || !isfinite(st->g)) ok = 0;
   st->scale = f * (m->radius_cm / d) * (m->radius_cm / d);
+  /* Gray cloud (reading R17): optical depth tau_c spread evenly in pressure
+   * over [p_top, p_top / f_c] (a constant gray extinction per unit mass in
+   * hydrostatic equilibrium); a layer gets tau_c times the fraction of that
+   * pressure range it covers. */
+  for (int l = 0; l < L; ++l) st->tau_cloud[l] = 0.0;
+  if (m->cloud) {
+    double tc = pow(10.0, theta[OR_P_CLOUD]);
+    double pt = pow(10.0, theta[OR_P_CLOUD + 1]) * OR_BAR;
+    double fc = pow(10.0, theta[OR_P_CLOUD + 2]);
+    if (!isfinite(tc) || !(tc >= 0.0) || !(pt > 0.0) || !isfinite(pt) || !(fc > 0.0) || !(fc <= 1.0)) ok = 0;
+    double pb = pt / fc;
+    if (ok && pb > pt) {
+      for (int l = 0; l < L; ++l) {
+        double lo = fmax(st->p[l], pt), hi = fmin(st->p[l + 1], pb);
+        if (hi > lo) st->tau_cloud[l] = tc * (hi - lo) / (pb - pt);
+      }
+    }
+  }
   st->valid = ok;
   return ok;
 }
@@ -431,7 +455,8 @@ double or_top_flux(const or_model* m, const or_state* st, int k) {
     S[j] = or_planck(nu, st->T[j]);
   }
   double colfac = 1.0 / (st->mmw * OR_AMU * st->g);
-  for (int l = 0; l < L; ++l) dtau[l] = 0.5 * (chi[l] + chi[l + 1]) * (st->p[l + 1] - st->p[l]) * colfac;
+  for (int l = 0; l < L; ++l)
+    dtau[l] = 0.5 * (chi[l] + chi[l + 1]) * (st->p[l + 1] - st->p[l]) * colfac + st->tau_cloud[l];
   return or_sc_flux(L, dtau, S, S[L], m->n_mu);
 }
 
@@ -645,7 +670,7 @@ int or_layer_dtau(const or_model* m, const double* theta, int k, double* dtau) {
   double prev = or_chi(m, st, 0, inu);
   for (int l = 0; l < L; ++l) {
     double next = or_chi(m, st, l + 1, inu);
-    dtau[l] = 0.5 * (prev + next) * (st->p[l + 1] - st->p[l]) * colfac;
+    dtau[l] = 0.5 * (prev + next) * (st->p[l + 1] - st->p[l]) * colfac + st->tau_cloud[l];
     prev = next;
   }
   free(st);

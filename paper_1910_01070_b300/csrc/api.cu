@@ -547,6 +547,7 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
   h.radius_cm = d->radius_cm;
   h.interp = d->interp;
   h.profile = d->profile;
+  h.cloud = d->cloud != 0;
   h.n_bins = d->n_bins;
   h.tables = tab->dev;
   const int n_cia = th.has_cia[0] + th.has_cia[1];

@@ -115,6 +115,7 @@ struct SetupDev {
   // function from hopf_q [kHopfN] (built at setup creation)
   int profile;
   const double* hopf_q;
+  int cloud;                     // gray cloud layer from parameters HR2_P_CLOUD..
   // interpolation space (HR2_INTERP_*): with HR2_INTERP_LINEAR the operand
   // holds 10^(stored log10 sigma) interpolated linearly in log10 p (and the
   // CIA operand 10^(stored value)), and the kernels interpolate linearly in T
@@ -145,7 +146,7 @@ struct __align__(16) LevRec {
   float rdnu;        // e^{-h c dnu / (k T_j)}: Planck factor between neighbouring points
   float wh2h2;       // 2^(bh2h2 exactly): the H2-H2 factor as a weight
   float wh2he;       // 2^(bh2he exactly)
-  float pad0;
+  float dtau_cloud;  // gray cloud optical depth of layer j-1 (between levels j-1 and j)
 };
 
 // Per-sample scalars written by the prep kernel.

@@ -147,6 +147,17 @@ __global__ void k_prep(FwdArgs a) {
     sd->W[lane] = (float)exp2(A);
   }
 
+  // gray cloud layer: tau_c spread evenly in pressure over [pct, pcb]
+  double tau_c = 0.0, pct = 0.0, pcb = 0.0;
+  if (S.cloud) {
+    tau_c = exp10(th[HR2_P_CLOUD]);
+    pct = exp10(th[HR2_P_CLOUD + 1]) * kBar;
+    const double fc = exp10(th[HR2_P_CLOUD + 2]);
+    if (!isfinite(tau_c) || !(tau_c >= 0.0) || !(pct > 0.0) || !isfinite(pct) || !(fc > 0.0) || !(fc <= 1.0))
+      status |= HR2_SAMPLE_BAD_CLOUD;
+    pcb = pct / fc;
+  }
+
   const int L = S.n_lev - 1;
   LevRec* rec = a.recs + (size_t)i * a.rec_ld;
   for (int j = lane; j <= L; j += 32) {
@@ -177,7 +188,11 @@ __global__ void k_prep(FwdArgs a) {
     r.rdnu = (float)exp(-kC2 * T.dnu / Tj);
     r.wh2h2 = (float)exp2(b0);
     r.wh2he = (float)exp2(b1);
-    r.pad0 = 0.f;
+    r.dtau_cloud = 0.f;
+    if (S.cloud && j > 0 && pcb > pct) {   // layer j-1 between levels j-1 and j
+      const double lo = fmax(S.levels[j - 1].p_dyn64, pct), hi = fmin(lv.p_dyn64, pcb);
+      if (hi > lo) r.dtau_cloud = (float)(tau_c * (hi - lo) / (pcb - pct));
+    }
     rec[j] = r;
   }
   status = __reduce_or_sync(0xffffffffu, status);
@@ -466,7 +481,8 @@ struct LevelState {
 // source, and for j > 0 the layer above it added to the telescoped sum.
 template <int NMU>
 __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], const float upl, const float upl_lo,
-                                              const float rdnu, const float half_dp, float& hdp_prev,
+                                              const float rdnu, const float half_dp, const float dtau_cloud,
+                                              float& hdp_prev,
                                               const NuConst& nc, const float thin_dtau, const float thin_all,
                                               const v2* sMnl, const v2* sImu, v2 (&acc)[kPairs][NMU],
                                               v2 (&E)[kPairs][NMU], LevelState (&st)[kPairs]) {
@@ -507,7 +523,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
     float dmin = 3.0e38f, dmax = 0.f;
 #pragma unroll
     for (int p = 0; p < kPairs; ++p) {
-      dt[p] = mul2(pk(hdp_prev), add2(chi[p], st[p].chip));
+      dt[p] = fma2(pk(hdp_prev), add2(chi[p], st[p].chip), pk(dtau_cloud));   // gas trapezoid + gray cloud
       rr[p] = rcp_2(dt[p]);
       dS[p] = sub2(Sj[p], st[p].Sp);
       st[p].tau = add2(st[p].tau, dt[p]);
@@ -750,7 +766,8 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       v2 chi[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
-      level_physics<NMU>(j, chi, r1.z, r2.y, r3.x, r1.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu, acc, E, st);
+      level_physics<NMU>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu, acc, E,
+                         st);
       __syncwarp();  // every lane is done with stage stg and record j before they are refilled
     }
     phase_base = ph + (unsigned)(L + 1);
@@ -818,7 +835,8 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       v2 chi[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
-      level_physics<NMU>(j, chi, r1.z, r2.y, r3.x, r1.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu, acc, E, st);
+      level_physics<NMU>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu, acc, E,
+                         st);
     }
   }
   // I_0(mu_k) = S_0 + mu_k acc_k;  F+ = sum_k 2 pi w_k mu_k I_0(mu_k)
@@ -1013,7 +1031,7 @@ __global__ void __launch_bounds__(kF64Block) k_forward64(FwdArgs a) {
   __shared__ double sT[HR2_MAX_LEVELS], sN[HR2_MAX_LEVELS], swT[HR2_MAX_LEVELS];
   __shared__ int sa[HR2_MAX_LEVELS];
   __shared__ double sx[HR2_MAX_SPECIES];
-  __shared__ double sc[3];
+  __shared__ double sc[6];
   const int i = blockIdx.y;
   const SampleDev& sd = a.samp[i];
   if (sd.setup < 0) return;
@@ -1045,6 +1063,12 @@ __global__ void __launch_bounds__(kF64Block) k_forward64(FwdArgs a) {
     sc[0] = 1.0 / (mmw * kAMU * exp10(th[HR2_P_LOGG]));
     sc[1] = xh2;
     sc[2] = xhe;
+    sc[3] = sc[4] = sc[5] = 0.0;   // gray cloud: tau_c, top and bottom pressure
+    if (S.cloud) {
+      sc[3] = exp10(th[HR2_P_CLOUD]);
+      sc[4] = exp10(th[HR2_P_CLOUD + 1]) * kBar;
+      sc[5] = sc[4] / exp10(th[HR2_P_CLOUD + 2]);
+    }
   }
   const int L = S.n_lev - 1;
   const double grav = exp10(th[HR2_P_LOGG]);
@@ -1093,7 +1117,11 @@ __global__ void __launch_bounds__(kF64Block) k_forward64(FwdArgs a) {
 #pragma unroll
       for (int m = 0; m < NMU; ++m) I[m] = Sj;
     } else {
-      const double dtau = (chi + chip) * lv.half_dp64 * c;
+      double dtau = (chi + chip) * lv.half_dp64 * c;
+      if (sc[5] > sc[4]) {   // gray cloud share of layer j (levels j, j+1)
+        const double lo = fmax(lv.p_dyn64, sc[4]), hi = fmin(S.levels[j + 1].p_dyn64, sc[5]);
+        if (hi > lo) dtau += sc[3] * (hi - lo) / (sc[5] - sc[4]);
+      }
 #pragma unroll
       for (int m = 0; m < NMU; ++m) {
         if (m < S.n_mu) {

@@ -50,7 +50,7 @@ class CapturedBatch:
         hr2.log_likelihood_batch(self.ctx, self.setups, self.sid, self.bins, self.lnl, None, self.stream)
 
     def run(self, params, setup_of_sample, sync: bool = True):
-        """Evaluate up to n samples: params [m, 35], setup_of_sample [m] (torch tensors, any device,
+        """Evaluate up to n samples: params [m, HR2_NPARAM], setup_of_sample [m] (torch tensors, any device,
         or numpy).  Returns (lnL [m], bins [m, n_bins_max]) views of the static buffers."""
         import torch
         m = int(params.shape[0])

@@ -20,8 +20,9 @@ LIB_PATH = os.path.join(_HERE, "libhr2.so")
 
 HR2_OK, HR2_EINVAL, HR2_ENOMEM, HR2_ECUDA, HR2_ETIMEDOUT, HR2_EBUSY = 0, -1, -2, -3, -4, -5
 HR2_SAMPLE_BAD_T, HR2_SAMPLE_BAD_ABUND, HR2_SAMPLE_BAD_SCALE, HR2_SAMPLE_BAD_SETUP = 1, 2, 4, 8
+HR2_SAMPLE_BAD_CLOUD = 16
 HR2_MAX_TNODES, HR2_MAX_SPECIES, HR2_MAX_MU, HR2_MAX_LEVELS, HR2_MAX_SETUPS = 16, 16, 8, 256, 32
-HR2_P_LOGG, HR2_P_F, HR2_P_DIST, HR2_P_T0, HR2_P_X0, HR2_NPARAM = 0, 1, 2, 3, 19, 35
+HR2_P_LOGG, HR2_P_F, HR2_P_DIST, HR2_P_T0, HR2_P_X0, HR2_P_CLOUD, HR2_NPARAM = 0, 1, 2, 3, 19, 35, 38
 HR2_STORE_FP16_OFFSET, HR2_STORE_FP64 = 1, 2
 HR2_INTERP_LOG10, HR2_INTERP_LINEAR = 0, 1
 INTERP = {"log10": HR2_INTERP_LOG10, "linear": HR2_INTERP_LINEAR}
@@ -57,7 +58,7 @@ class SetupDesc(C.Structure):
                 ("fe_elements", C.c_int), ("fe_order", C.c_int), ("resolving_power", C.c_double),
                 ("n_bins", C.c_int), ("bin_edges", C.POINTER(C.c_double)), ("obs_flux", C.POINTER(C.c_double)),
                 ("obs_sigma", C.POINTER(C.c_double)), ("r_he", C.c_double), ("radius_cm", C.c_double),
-                ("level_cache", C.c_int), ("interp", C.c_int), ("profile", C.c_int)]
+                ("level_cache", C.c_int), ("interp", C.c_int), ("profile", C.c_int), ("cloud", C.c_int)]
 
 
 class LaunchCfg(C.Structure):
@@ -251,9 +252,10 @@ def hr2_tables_destroy(ctx, tables):
 
 def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_elements, fe_order,
                      resolving_power, bin_edges, p_top=1e-4, p_bot=100.0, r_he=0.17, radius_cm=7.1492e9,
-                     obs_flux=None, obs_sigma=None, level_cache=True, interp="log10", profile="fe"):
+                     obs_flux=None, obs_sigma=None, level_cache=True, interp="log10", profile="fe", cloud=False):
     """interp: "log10" (HR2_INTERP_LOG10) or "linear" (HR2_INTERP_LINEAR);
-    profile: "fe" (HR2_PROFILE_FE) or "milne" (HR2_PROFILE_MILNE)."""
+    profile: "fe" (HR2_PROFILE_FE) or "milne" (HR2_PROFILE_MILNE);
+    cloud: add the gray cloud layer of parameters HR2_P_CLOUD..."""
     sp = np.ascontiguousarray(np.asarray(species, dtype=np.int32))
     edges, pe = _dptr(bin_edges)
     keep = [sp, edges]
@@ -266,7 +268,7 @@ def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_el
     d = SetupDesc(int(nu_first), int(n_nu), int(n_layers), float(p_top), float(p_bot), len(sp),
                   sp.ctypes.data_as(_IP), int(n_mu), int(fe_elements), int(fe_order), float(resolving_power),
                   len(edges) - 1, pe, pf, ps, float(r_he), float(radius_cm), int(bool(level_cache)),
-                  INTERP[interp], PROFILE[profile])
+                  INTERP[interp], PROFILE[profile], int(bool(cloud)))
     h = _VP()
     _check(lib().hr2_setup_create(ctx, tables, C.byref(d), C.byref(h)), ctx)
     return h
@@ -290,7 +292,7 @@ def hr2_setup_destroy(ctx, setup):
 
 def forward_model_batch(ctx, setups: Sequence, setup_of_sample, params, out_bins, out_highres=None,
                         out_status=None, stream=None):
-    """Device tensors: setup_of_sample int32 [n], params float64 [n, 35], out_bins float32 [n, ld],
+    """Device tensors: setup_of_sample int32 [n], params float64 [n, HR2_NPARAM], out_bins float32 [n, ld],
     out_highres float32 [n, ld2] or None, out_status int32 [n] or None."""
     import torch
     n = int(params.shape[0]) if params is not None else 0
@@ -339,7 +341,7 @@ def log_likelihood_batch(ctx, setups: Sequence, setup_of_sample, model_bins, out
 
 def hr2_evaluate_host(ctx, setups: Sequence, setup_of_sample, params, out_lnL, log_eps=None, out_bins=None,
                       stream=None):
-    """Host numpy buffers (pinned torch CPU tensors also accepted): int32 [n], float64 [n, 35],
+    """Host numpy buffers (pinned torch CPU tensors also accepted): int32 [n], float64 [n, HR2_NPARAM],
     float64 [n] out, optional float64 [n], optional float32 [n, ld] out.  Synchronous."""
 
     def hp(a, dtype, name):
@@ -397,8 +399,8 @@ def hr2_ns_state_init(ctx, state, stream=None):
 
 def hr2_ns_absorb(ctx, live_lnl, live_theta, cand_lnl, cand_theta, state, dead_lnl, dead_logw, dead_theta,
                   stream=None):
-    """CUDA float64 tensors: live [N], [N, 35] (updated), candidates [m], [m, 35], the state,
-    dead [cap], [cap], [cap, 35] (dead point k at row k)."""
+    """CUDA float64 tensors: live [N], [N, HR2_NPARAM] (updated), candidates [m], [m, HR2_NPARAM], the state,
+    dead [cap], [cap], [cap, HR2_NPARAM] (dead point k at row k)."""
     import torch
     n, m, cap = int(live_lnl.shape[0]), int(cand_lnl.shape[0]), int(dead_lnl.shape[0])
     f = torch.float64

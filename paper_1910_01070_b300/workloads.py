@@ -30,8 +30,8 @@ from typing import Dict, List, Optional
 
 import numpy as np
 
-NPARAM = 35
-P_LOGG, P_F, P_DIST, P_T0, P_X0 = 0, 1, 2, 3, 19
+NPARAM = 38
+P_LOGG, P_F, P_DIST, P_T0, P_X0, P_CLOUD = 0, 1, 2, 3, 19, 35
 MAX_TNODES = 16
 MAX_SPECIES = 16
 
@@ -80,6 +80,7 @@ class SetupSpec:
     radius_cm: float = R_JUPITER_CM
     interp: str = "log10"       # opacity interpolation space: "log10" or "linear"
     profile: str = "fe"         # temperature profile: "fe" (finite elements) or "milne"
+    cloud: bool = False         # gray cloud layer from parameters 35..37
 
     @property
     def n_bins(self) -> int:
@@ -178,6 +179,9 @@ class Prior:
     free_nodes: Optional[tuple] = None   # (Tmin, Tmax): independent control points instead of (T1, b)
     t_bar: tuple = (400.0, 2000.0)       # Milne profile: Tbar_eff, K
     log_kappa: tuple = (-4.0, 0.0)       # Milne profile: log10 kappa_R, cm^2 g^-1
+    log_tau_cloud: tuple = (-2.0, 1.0)   # gray cloud: log10 optical depth
+    log_p_cloud: tuple = (-3.0, 1.0)     # gray cloud: log10 top pressure, bar
+    log_f_cloud: tuple = (-1.5, 0.0)     # gray cloud: log10 (top / bottom pressure)
 
 
 def draw_params(setup: SetupSpec, n: int, seed: int, prior: Prior = Prior()) -> np.ndarray:
@@ -203,6 +207,10 @@ def draw_params(setup: SetupSpec, n: int, seed: int, prior: Prior = Prior()) -> 
         th[:, P_T0:P_T0 + nt] = nodes
     k = len(setup.species)
     th[:, P_X0:P_X0 + k] = rng.uniform(*prior.log_x, (n, k))
+    if setup.cloud:
+        th[:, P_CLOUD] = rng.uniform(*prior.log_tau_cloud, n)
+        th[:, P_CLOUD + 1] = rng.uniform(*prior.log_p_cloud, n)
+        th[:, P_CLOUD + 2] = rng.uniform(*prior.log_f_cloud, n)
     return th
 
 

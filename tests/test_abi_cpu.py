@@ -90,3 +90,17 @@ def _struct_fields(src, name):
 def test_binding_structs_follow_the_header(cname, pyname):
     """The ctypes mirrors list the header's fields in the header's order."""
     assert [f[0] for f in getattr(hr2, pyname)._fields_] == _struct_fields(_header(), cname)
+
+
+def test_oracle_binding_struct_follows_the_c_source():
+    """The oracle's ctypes model mirrors or_model field by field (test infrastructure
+    has the same failure mode as the library binding)."""
+    import oracle
+    src = open(os.path.join(os.path.dirname(oracle.__file__), "hr2_oracle.c")).read()
+    body = re.search(r"typedef struct \{((?:(?!typedef struct).)*?)\}\s*or_model;", src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = []
+    for decl in body.split(";"):
+        if decl.strip():
+            fields += re.findall(r"(\w+)\s*(?:,|$)", decl.strip())
+    assert [f[0] for f in oracle._Model._fields_] == fields

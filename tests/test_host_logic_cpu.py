@@ -9,10 +9,11 @@ import pytest
 
 from paper_1910_01070_b300 import autotune
 from paper_1910_01070_b300 import serving
+from paper_1910_01070_b300 import workloads as W
 
 
 def _req(rid, n, setup=0):
-    return serving.Request(rid=rid, stream=0, setup=setup, params=np.zeros((n, 35)))
+    return serving.Request(rid=rid, stream=0, setup=setup, params=np.zeros((n, W.NPARAM)))
 
 
 def test_admission_is_fifo_and_respects_budget():
@@ -43,12 +44,12 @@ def test_packing_takes_whole_requests_in_order():
 
 
 def test_retrieval_stream_is_seeded_and_contracts():
-    lo = np.zeros(35)
-    hi = np.zeros(35)
+    lo = np.zeros(W.NPARAM)
+    hi = np.zeros(W.NPARAM)
     lo[0], hi[0] = 4.0, 5.5
     s1 = serving.RetrievalStream(0, 0, lo, hi, rate=10.0, seed=5)
     s2 = serving.RetrievalStream(0, 0, lo, hi, rate=10.0, seed=5)
-    t = np.zeros(35)
+    t = np.zeros(W.NPARAM)
     r1, r2 = s1.make_request(0, t), s2.make_request(0, t)
     assert np.array_equal(r1.params, r2.params) and 32 <= r1.n <= 512
     assert np.all((r1.params[:, 0] >= 4.0) & (r1.params[:, 0] <= 5.5))

@@ -419,7 +419,7 @@ def test_empty_batch_and_argument_errors(eng):
     wl, tabs, stored, setups, st = _workload_on(eng, "batch1024_l100_k6_nu8501", "fp16")
     e = torch.empty((0, 300), dtype=torch.float32, device="cuda")
     hr2.forward_model_batch(eng.ctx, setups, torch.empty(0, dtype=torch.int32, device="cuda"),
-                            torch.empty((0, 35), dtype=torch.float64, device="cuda"), e)
+                            torch.empty((0, hr2.HR2_NPARAM), dtype=torch.float64, device="cuda"), e)
     theta, sid = wl.params(2)
     small = torch.empty((2, 10), dtype=torch.float32, device="cuda")
     with pytest.raises(hr2.Hr2Error) as ei:

@@ -92,8 +92,8 @@ def test_open_loop_serving_reports_latency(uneven):
     wl, eng, setups = uneven
     shapes = [(s.n_bins, s.n_nu, s.n_layers + 1) for s in wl.setups]
     srv = serving.Server(eng.ctx, setups, shapes, slots=3, max_batch=2048, mem_budget=2 << 30)
-    lo = np.zeros(35)
-    hi = np.zeros(35)
+    lo = np.zeros(hr2.HR2_NPARAM)
+    hi = np.zeros(hr2.HR2_NPARAM)
     streams, templates = [], []
     for k in range(16):
         g = k % len(wl.setups)
