@@ -55,8 +55,11 @@ class _Model(C.Structure):
         ("resolving_power", C.c_double), ("n_bins", C.c_int), ("bin_edges", C.POINTER(C.c_double)),
         ("r_he", C.c_double), ("radius_cm", C.c_double), ("interp", C.c_int),
         ("profile", C.c_int), ("n_hopf", C.c_int), ("hopf_tau", C.POINTER(C.c_double)),
-        ("hopf_q", C.POINTER(C.c_double)), ("cloud", C.c_int),
+        ("hopf_q", C.POINTER(C.c_double)), ("cloud", C.c_int), ("sc_order", C.c_int),
     ]
+
+# short-characteristics source interpolation (Sect. 2.1)
+SC_ORDER = {"linear": 1, "parabolic": 2}
 
 # temperature profile of the setup (Sect. 2.5)
 PROFILE = {"fe": 0, "milne": 1}
@@ -84,6 +87,7 @@ def _lib():
                 "or_planck": (C.c_double, [C.c_double, C.c_double]),
                 "or_sc_intensity": (C.c_double, [C.c_int, _DP, _DP, C.c_double, C.c_double]),
                 "or_sc_flux": (C.c_double, [C.c_int, _DP, _DP, C.c_double, C.c_int]),
+                "or_sc_intensity_parabolic": (C.c_double, [C.c_int, _DP, _DP, C.c_double, C.c_double]),
                 "or_log10_sigma": (C.c_double, [M, C.c_int, C.c_double, C.c_double, C.c_int]),
                 "or_sigma": (C.c_double, [M, C.c_int, C.c_double, C.c_double, C.c_int]),
                 "or_cia_coeff": (C.c_double, [M, _DP, C.c_double, C.c_int]),
@@ -166,6 +170,13 @@ def sc_intensity(dtau, S, I_bottom: float, mu: float) -> float:
     return _lib().or_sc_intensity(len(dtau), pd, ps, float(I_bottom), float(mu))
 
 
+def sc_intensity_parabolic(dtau, S, I_bottom: float, mu: float) -> float:
+    dtau, pd = _d(dtau)
+    S, ps = _d(S)
+    assert len(S) == len(dtau) + 1
+    return _lib().or_sc_intensity_parabolic(len(dtau), pd, ps, float(I_bottom), float(mu))
+
+
 def sc_flux(dtau, S, I_bottom: float, n_mu: int) -> float:
     dtau, pd = _d(dtau)
     S, ps = _d(S)
@@ -191,7 +202,8 @@ class Model:
     n_mu, fe_elements, fe_order, resolving_power, bin_edges, r_he, radius_cm,
     and optionally interp ("log10", the default, or "linear"), profile ("fe", the
     default, or "milne": parameters 3 and 4 are Tbar_eff and log10 kappa_R) and
-    cloud (True: a gray cloud layer from parameters 35..37).
+    cloud (True: a gray cloud layer from parameters 35..37) and sc ("linear", the
+    default, or "parabolic" source interpolation in the short characteristics).
     """
 
     def __init__(self, tables: dict, setup: dict):
@@ -239,6 +251,7 @@ class Model:
         m.interp = INTERP[setup.get("interp", "log10")]
         m.profile = PROFILE[setup.get("profile", "fe")]
         m.cloud = int(bool(setup.get("cloud", False)))
+        m.sc_order = SC_ORDER[setup.get("sc", "linear")]
         if m.profile == PROFILE["milne"]:
             from . import hopf
             ht, hq = hopf.hopf_table()

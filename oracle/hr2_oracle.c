@@ -85,6 +85,7 @@ typedef struct {
   const double* hopf_tau;       /*   [n_hopf] ascending optical depths         */
   const double* hopf_q;         /*   [n_hopf] q(tau) at those depths            */
   int cloud;                    /* 1: gray cloud layer from parameters 35..37 */
+  int sc_order;                 /* 1 linear (default), 2 parabolic source      */
 } or_model;
 
 /* Temperature profile (Sect. 2.5): OR_PROFILE_FE, the finite-element profile
@@ -265,12 +266,75 @@ double or_sc_intensity(int L, const double* dtau, const double* S, double I_bott
   return I;
 }
 
+/* M_k(D) = int_0^D t^k e^{-t} dt, k = 0, 1, 2: by the power series
+ * sum_n (-1)^n D^{k+n+1} / (n! (k+n+1)) for D < 1/2 (no cancellation for thin
+ * layers), else by the closed forms M_0 = 1 - e^{-D}, M_1 = M_0 - D e^{-D},
+ * M_2 = 2 M_1 - D^2 e^{-D}. */
+static void or_moments(double D, double* M0, double* M1, double* M2) {
+  if (D < 0.5) {
+    double s[3] = {0.0, 0.0, 0.0};
+    double term = D;                            /* (-1)^n D^{n+1} / n! */
+    for (int n = 0; n < 60; ++n) {
+      for (int k = 0; k < 3; ++k) s[k] += term * pow(D, k) / (double)(k + n + 1);
+      term *= -D / (double)(n + 1);
+      if (fabs(term) < 1e-30) break;
+    }
+    *M0 = s[0]; *M1 = s[1]; *M2 = s[2];
+  } else {
+    double e = exp(-D);
+    *M0 = -expm1(-D);
+    *M1 = *M0 - D * e;
+    *M2 = 2.0 * *M1 - D * D * e;
+  }
+}
+
+/* Parabolic short characteristics (Sect. 2.1: higher-order interpolants of
+ * the source, after Olson & Kunasz 1987), written here from the definition:
+ * along the ray, t is the optical depth below point l; over layer l (t from 0
+ * to D_u) the source is the parabola through S_{l-1} (t = -D_d), S_l (t = 0)
+ * and S_{l+1} (t = D_u), and I_l = I_{l+1} e^{-D_u} + int_0^{D_u} S(t) e^{-t} dt.
+ * In Taylor form at t = 0, S(t) = S_l + c1 t + c2 t^2 with the divided
+ * differences d_u = (S_{l+1} - S_l)/D_u, d_d = (S_l - S_{l-1})/D_d,
+ * c2 = (d_u - d_d)/(D_u + D_d), c1 = d_u - c2 D_u, so that
+ *   int_0^{D_u} S e^{-t} dt = S_l M_0 + c1 M_1 + c2 M_2.
+ * (The same integral as the Lagrange-weight form, without its cancellation
+ * when D_d << D_u.)  The top layer (no point above) and a layer under a
+ * zero-thickness layer use the linear source (c2 = 0, c1 = d_u). */
+double or_sc_intensity_parabolic(int L, const double* dtau, const double* S, double I_bottom, double mu) {
+  double I = I_bottom;
+  for (int l = L - 1; l >= 0; --l) {
+    double Du = dtau[l] / mu;
+    if (!(Du > 0.0)) continue;                  /* a transparent layer changes nothing */
+    double Dd = (l > 0) ? dtau[l - 1] / mu : 0.0;
+    double M0, M1, M2;
+    or_moments(Du, &M0, &M1, &M2);
+    double du = (S[l + 1] - S[l]) / Du;
+    double c2 = 0.0, c1 = du;
+    if (Dd > 0.0) {
+      double dd = (S[l] - S[l - 1]) / Dd;
+      c2 = (du - dd) / (Du + Dd);
+      c1 = du - c2 * Du;
+    }
+    I = I * exp(-Du) + S[l] * M0 + c1 * M1 + c2 * M2;
+  }
+  return I;
+}
+
 /* Outgoing flux F+ = 2 pi int_0^1 I mu dmu by Gauss-Legendre, Eq. (8). */
 double or_sc_flux(int L, const double* dtau, const double* S, double I_bottom, int n_mu) {
   double mu[OR_MAX_MU], w[OR_MAX_MU];
   or_gauss_legendre01(n_mu, mu, w);
   double F = 0.0;
   for (int k = 0; k < n_mu; ++k) F += w[k] * mu[k] * or_sc_intensity(L, dtau, S, I_bottom, mu[k]);
+  return 2.0 * M_PI * F;
+}
+
+/* The same with the parabolic scheme. */
+double or_sc_flux_parabolic(int L, const double* dtau, const double* S, double I_bottom, int n_mu) {
+  double mu[OR_MAX_MU], w[OR_MAX_MU];
+  or_gauss_legendre01(n_mu, mu, w);
+  double F = 0.0;
+  for (int k = 0; k < n_mu; ++k) F += w[k] * mu[k] * or_sc_intensity_parabolic(L, dtau, S, I_bottom, mu[k]);
   return 2.0 * M_PI * F;
 }
 
@@ -457,6 +521,7 @@ double or_top_flux(const or_model* m, const or_state* st, int k) {
   double colfac = 1.0 / (st->mmw * OR_AMU * st->g);
   for (int l = 0; l < L; ++l)
     dtau[l] = 0.5 * (chi[l] + chi[l + 1]) * (st->p[l + 1] - st->p[l]) * colfac + st->tau_cloud[l];
+  if (m->sc_order == 2) return or_sc_flux_parabolic(L, dtau, S, S[L], m->n_mu);
   return or_sc_flux(L, dtau, S, S[L], m->n_mu);
 }
 

@@ -81,6 +81,7 @@ class SetupSpec:
     interp: str = "log10"       # opacity interpolation space: "log10" or "linear"
     profile: str = "fe"         # temperature profile: "fe" (finite elements) or "milne"
     cloud: bool = False         # gray cloud layer from parameters 35..37
+    sc: str = "linear"          # short characteristics: "linear" or "parabolic" source
 
     @property
     def n_bins(self) -> int:
