@@ -110,6 +110,12 @@ typedef enum {
                                 T^4 = 3/4 Tbar^4 [tau_R + q(tau_R)] with the
                                 exact Hopf function q; tau_R = kappa_R p / g     */
 
+/* Source-function interpolation of the short characteristics (Sect. 2.1). */
+#define HR2_SC_LINEAR    0   /* linear between levels (Eqs. 4-7; the default)   */
+#define HR2_SC_PARABOLIC 1   /* parabola through the level above, the level and
+                                the level below (the top layer stays linear);
+                                about twice the work per layer                  */
+
 typedef struct hr2_ctx hr2_ctx;
 typedef struct hr2_tables hr2_tables;
 typedef struct hr2_setup hr2_setup;
@@ -177,6 +183,8 @@ typedef struct {
                                  parameters HR2_P_CLOUD.. (its optical depth is
                                  the same at every wavenumber and adds to the
                                  layers' absorption optical depths)              */
+  int sc;                     /* HR2_SC_LINEAR or HR2_SC_PARABOLIC.  One batch
+                                 call takes setups of a single kind.             */
 } hr2_setup_desc;
 
 /* Launch shape of the persistent forward kernel (chosen by the autotuner). */

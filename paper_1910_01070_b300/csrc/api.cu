@@ -521,6 +521,8 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
     return fail(HR2_EINVAL, "the linear interpolation option on FP16 tables needs level_cache");
   if (d->profile != HR2_PROFILE_FE && d->profile != HR2_PROFILE_MILNE)
     return fail(HR2_EINVAL, "profile %d is neither HR2_PROFILE_FE nor HR2_PROFILE_MILNE", d->profile);
+  if (d->sc != HR2_SC_LINEAR && d->sc != HR2_SC_PARABOLIC)
+    return fail(HR2_EINVAL, "sc %d is neither HR2_SC_LINEAR nor HR2_SC_PARABOLIC", d->sc);
   HR2_CU(cudaSetDevice(ctx->device));
 
   hr2_setup* st = new hr2_setup();
@@ -548,6 +550,7 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
   h.interp = d->interp;
   h.profile = d->profile;
   h.cloud = d->cloud != 0;
+  h.sc = d->sc;
   h.n_bins = d->n_bins;
   h.tables = tab->dev;
   const int n_cia = th.has_cia[0] + th.has_cia[1];
@@ -742,7 +745,7 @@ extern "C" int hr2_setup_destroy(hr2_ctx* ctx, hr2_setup* s) {
 // ------------------------------------------------------------ batch calls
 struct BatchShape {
   int max_lev = 0, max_nu = 0, max_bins = 0, max_mu = 0, max_k = 0, min_k = 1 << 30, storage = 0, cached = 0;
-  int linear = 0;
+  int linear = 0, para = 0;
 };
 
 static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups, BatchShape* sh) {
@@ -760,6 +763,8 @@ static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setu
       return fail(HR2_EINVAL, "setups of one batch must all use, or all not use, the level-gridded operand");
     if (s->host.interp != setups[0]->host.interp)
       return fail(HR2_EINVAL, "setups of one batch must share the interpolation option");
+    if (s->host.sc != setups[0]->host.sc)
+      return fail(HR2_EINVAL, "setups of one batch must share the source interpolation (linear or parabolic)");
     sh->max_lev = std::max(sh->max_lev, s->host.n_lev);
     sh->max_nu = std::max(sh->max_nu, s->host.n_nu);
     sh->max_bins = std::max(sh->max_bins, s->host.n_bins);
@@ -770,6 +775,7 @@ static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setu
   sh->storage = t0->host.storage;
   sh->cached = setups[0]->host.cached;
   sh->linear = setups[0]->host.interp == HR2_INTERP_LINEAR;
+  sh->para = setups[0]->host.sc == HR2_SC_PARABOLIC;
   return HR2_OK;
 }
 
@@ -861,7 +867,8 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
       return fail(HR2_ECUDA, "plan launch: %s", cudaGetErrorString(e));
     const int grid = ctx->n_sm * ls.ctas_per_sm;
     if (ev.first) HR2_CU(cudaEventRecord(ev.first, s));
-    if ((e = launch_forward32(a, sh.max_mu, grid, sh.cached != 0, sh.linear != 0, sh.max_k, absorber_bound(sh), s)) != cudaSuccess)
+    if ((e = launch_forward32(a, sh.max_mu, grid, sh.cached != 0, sh.linear != 0, sh.para != 0, sh.max_k, absorber_bound(sh),
+                              s)) != cudaSuccess)
       return fail(HR2_ECUDA, "forward32 launch: %s", cudaGetErrorString(e));
     if (ev.second) HR2_CU(cudaEventRecord(ev.second, s));
   }
@@ -1135,8 +1142,8 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
   // the planner resets the work counter to zero on the device before the
   // forward kernel reads it; everything else is overwritten by the kernels
   if ((e = launch_prep(a, s)) != cudaSuccess || (e = launch_plan(a, (int*)a.perm, (PlanDev*)a.plan, s)) != cudaSuccess ||
-      (e = launch_forward32(a, sh.max_mu, ctx->n_sm * ls.ctas_per_sm, sh.cached != 0, sh.linear != 0, sh.max_k,
-                        absorber_bound(sh), s)) != cudaSuccess ||
+      (e = launch_forward32(a, sh.max_mu, ctx->n_sm * ls.ctas_per_sm, sh.cached != 0, sh.linear != 0, sh.para != 0,
+                        sh.max_k, absorber_bound(sh), s)) != cudaSuccess ||
       (e = launch_bins(a, out_bins, bins_ld, false, s)) != cudaSuccess)
     return fail(HR2_ECUDA, "allocation-free launch: %s", cudaGetErrorString(e));
   return HR2_OK;

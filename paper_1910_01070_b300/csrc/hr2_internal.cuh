@@ -116,6 +116,7 @@ struct SetupDev {
   int profile;
   const double* hopf_q;
   int cloud;                     // gray cloud layer from parameters HR2_P_CLOUD..
+  int sc;                        // HR2_SC_LINEAR or HR2_SC_PARABOLIC source interpolation
   // interpolation space (HR2_INTERP_*): with HR2_INTERP_LINEAR the operand
   // holds 10^(stored log10 sigma) interpolated linearly in log10 p (and the
   // CIA operand 10^(stored value)), and the kernels interpolate linearly in T
@@ -197,8 +198,8 @@ cudaError_t launch_prep(const FwdArgs& a, cudaStream_t s);
 cudaError_t launch_plan(const FwdArgs& a, int* perm, PlanDev* plan, cudaStream_t s);
 // kt: 0, or an even bound on the absorber count of the cached path with
 // every setup of the batch at kt or kt - 1 absorbers (see absorber_bound)
-cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, int max_k, int kt,
-                             cudaStream_t s);
+cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, bool para, int max_k,
+                             int kt, cudaStream_t s);
 size_t forward32_smem_bytes(int warps, int max_k);
 cudaError_t launch_forward64(const FwdArgs& a, int max_nmu, int max_nu, cudaStream_t s);
 cudaError_t launch_bins(const FwdArgs& a, float* bins, int bins_ld, bool fp64, cudaStream_t s);

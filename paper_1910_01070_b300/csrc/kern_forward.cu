@@ -472,19 +472,20 @@ struct NuConst {
 };
 
 // Level sweep state of one pair: chi and S of the level above, S_0 and the
-// cumulative optical depth tau_j.
+// cumulative optical depth tau_j; for the parabolic source also the slope
+// dS/dtau and the optical depth of the layer above.
 struct LevelState {
-  v2 chip, Sp, S0, tau;
+  v2 chip, Sp, S0, tau, dup, dtp;
 };
 
 // Physics of one level for the lane's wavenumbers, given chi_j: the Planck
 // source, and for j > 0 the layer above it added to the telescoped sum.
-template <int NMU>
+template <int NMU, bool PARA>
 __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], const float upl, const float upl_lo,
                                               const float rdnu, const float half_dp, const float dtau_cloud,
                                               float& hdp_prev,
                                               const NuConst& nc, const float thin_dtau, const float thin_all,
-                                              const v2* sMnl, const v2* sImu, v2 (&acc)[kPairs][NMU],
+                                              const v2* sMnl, const v2* sImu, const v2* sMu, v2 (&acc)[kPairs][NMU],
                                               v2 (&E)[kPairs][NMU], LevelState (&st)[kPairs]) {
   const float kLn2f = 0.6931471805599453f;
   const v2 one = pk(1.f);
@@ -532,6 +533,59 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
       dmax = fmaxf(dmax, fmaxf(dtf.x, dtf.y));
     }
     const bool thin = __any_sync(0xffffffffu, dmin < thin_dtau);
+    if constexpr (PARA) {
+      // Parabolic source (Sect. 2.1, higher-order interpolant): over layer
+      // j-1 the source is the parabola through levels j-2, j-1, j; in
+      // vertical optical depth below level j-1 it is S_{j-1} + c1 t + c2 t^2
+      // (divided differences; the top layer keeps c2 = 0), along the ray
+      // t -> mu t.  The layer adds E_{j-1} [S_{j-1} M0 + mu c1 M1 + mu^2 c2 M2]
+      // with M_k = int_0^D t^k e^{-t} dt, D = dtau / mu, taken from
+      //   E M0 = E_{j-1} - E_j, E M1 = E M0 - D E_j, E M2 = 2 E M1 - D^2 E_j,
+      // or, where D < kThinD, from the power series of M_k times E_{j-1}.
+      // I_0 = sum of the layers + E_L S_L (added after the sweep).
+      (void)dmax;
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) {
+        const v2 du = mul2(dS[p], rr[p]);
+        v2 c1 = du, c2 = pk(0.f);
+        if (j >= 2) {
+          c2 = mul2(sub2(du, st[p].dup), rcp_2(add2(dt[p], st[p].dtp)));
+          c1 = sub2(du, mul2(c2, dt[p]));
+        }
+        st[p].dup = du;
+        st[p].dtp = dt[p];
+#pragma unroll
+        for (int k = 0; k < NMU; ++k) {
+          const v2 mk = sMnl[k], im = sImu[k], mu = sMu[k];
+          const v2 En = ex2_2(mul2(st[p].tau, mk));
+          const v2 D = mul2(dt[p], im);
+          const v2 D2 = mul2(D, D);
+          v2 m0 = sub2(E[p][k], En);
+          v2 m1 = sub2(m0, mul2(D, En));
+          v2 m2 = sub2(add2(m1, m1), mul2(D2, En));
+          if (thin) {
+            const v2 Ek = E[p][k];
+            const v2 q0 = mul2(D, fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
+                                                                  pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), pk(1.f)));
+            const v2 q1 = mul2(D2, fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 840.f), pk(1.f / 144.f)),
+                                                                   pk(-1.f / 30.f)), pk(1.f / 8.f)), pk(-1.f / 3.f)), pk(0.5f)));
+            const v2 q2 = mul2(mul2(D2, D), fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 960.f), pk(1.f / 168.f)),
+                                                                            pk(-1.f / 36.f)), pk(0.1f)), pk(-0.25f)),
+                                                 pk(1.f / 3.f)));
+            const v2 s0 = mul2(Ek, q0), s1 = mul2(Ek, q1), s2 = mul2(Ek, q2);
+            const float2 Df = up(D), a0 = up(m0), a1 = up(m1), a2 = up(m2), b0 = up(s0), b1 = up(s1), b2 = up(s2);
+            const bool tx = Df.x < kThinD, ty = Df.y < kThinD;
+            m0 = pk(tx ? b0.x : a0.x, ty ? b0.y : a0.y);
+            m1 = pk(tx ? b1.x : a1.x, ty ? b1.y : a1.y);
+            m2 = pk(tx ? b2.x : a2.x, ty ? b2.y : a2.y);
+          }
+          v2 a = fma2(st[p].Sp, m0, acc[p][k]);
+          a = fma2(mul2(mu, c1), m1, a);
+          acc[p][k] = fma2(mul2(mul2(mu, mu), c2), m2, a);
+          E[p][k] = En;
+        }
+      }
+    } else {
     const bool allthin = thin && __all_sync(0xffffffffu, dmax < thin_all);
     // The three regimes are separate loops so that the decision is taken once
     // per level.  Nodes beyond the setup's count are padded with mu = 1 and
@@ -583,6 +637,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
         }
       }
     }
+    }
   }
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
@@ -598,10 +653,11 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
 // level-gridded operand through the warp's bulk-copy pipeline (rows of level
 // j+1 and the record of level j+2 land while level j is computed).
 // Otherwise the FP16 tables are read and interpolated bilinearly in place.
-template <int NMU, bool CACHED, int KT, bool LIN>
+template <int NMU, bool CACHED, int KT, bool LIN, bool PARA>
 __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
                                            const v2* sA2, const v2* sAc2, const void* const* sPtr,
-                                           const v2* sMnl, const v2* sImu, const WarpPipe& wp_, unsigned& phase_base) {
+                                           const v2* sMnl, const v2* sImu, const v2* sMu, const WarpPipe& wp_,
+                                           unsigned& phase_base) {
   const int lane = threadIdx.x & 31;
   const SampleDev& sd = a.samp[i];
   float* out = a.highres + (size_t)i * a.highres_ld;
@@ -651,7 +707,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     }
   LevelState st[kPairs];
 #pragma unroll
-  for (int p = 0; p < kPairs; ++p) st[p].chip = st[p].Sp = st[p].S0 = st[p].tau = pk(0.f);
+  for (int p = 0; p < kPairs; ++p) st[p].chip = st[p].Sp = st[p].S0 = st[p].tau = st[p].dup = st[p].dtp = pk(0.f);
   float hdp_prev = 0.f;
 
   if constexpr (CACHED) {
@@ -766,7 +822,8 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       v2 chi[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
-      level_physics<NMU>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu, acc, E,
+      level_physics<NMU, PARA>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
+                               sMu, acc, E,
                          st);
       __syncwarp();  // every lane is done with stage stg and record j before they are refilled
     }
@@ -835,33 +892,41 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       v2 chi[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
-      level_physics<NMU>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu, acc, E,
+      level_physics<NMU, PARA>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
+                               sMu, acc, E,
                          st);
     }
   }
-  // I_0(mu_k) = S_0 + mu_k acc_k;  F+ = sum_k 2 pi w_k mu_k I_0(mu_k)
+  // I_0(mu_k) = S_0 + mu_k acc_k (telescoped linear source) or
+  // acc_k + E_L S_L (parabolic source);  F+ = sum_k 2 pi w_k mu_k I_0(mu_k)
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
     float F0 = 0.f, F1 = 0.f;
-    const float2 s0 = up(st[p].S0);
+    const float2 s0 = up(st[p].S0), sL = up(st[p].Sp);
 #pragma unroll
     for (int k = 0; k < NMU; ++k) {
       const float2 f = up(acc[p][k]);
       const float mk = S.mu[k], wk = S.wflux[k];
-      F0 = fmaf(wk, fmaf(mk, f.x, s0.x), F0);
-      F1 = fmaf(wk, fmaf(mk, f.y, s0.y), F1);
+      if constexpr (PARA) {
+        const float2 e = up(E[p][k]);
+        F0 = fmaf(wk, fmaf(e.x, sL.x, f.x), F0);
+        F1 = fmaf(wk, fmaf(e.y, sL.y, f.y), F1);
+      } else {
+        F0 = fmaf(wk, fmaf(mk, f.x, s0.x), F0);
+        F1 = fmaf(wk, fmaf(mk, f.y, s0.y), F1);
+      }
     }
     if (in0[p]) out[kout[p]] = F0;
     if (in1[p]) out[kout[p] + 1] = F1;
   }
 }
 
-template <int NMU, bool CACHED, int KT, bool LIN>
+template <int NMU, bool CACHED, int KT, bool LIN, bool PARA>
 __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forward32(FwdArgs a, int max_k) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];   // cached path: per-warp pipelines
   __shared__ int s_item;
   __shared__ const void* sPtr[HR2_MAX_SPECIES];
-  __shared__ v2 sMnl[NMU], sImu[NMU];
+  __shared__ v2 sMnl[NMU], sImu[NMU], sMu[NMU];
   __shared__ v2 sA2[kMaxWarps][HR2_MAX_SPECIES];
   __shared__ v2 sAc2[kMaxWarps][HR2_MAX_SPECIES];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -905,6 +970,7 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
     if (threadIdx.x < NMU) {
       sMnl[threadIdx.x] = pk(S.mu_nlog2e[threadIdx.x]);
       sImu[threadIdx.x] = pk(S.inv_mu[threadIdx.x]);
+      sMu[threadIdx.x] = pk(S.mu[threadIdx.x]);
     }
     const int local = sb * a.warps + warp;
     const bool active = local < plan->count[g];
@@ -919,13 +985,14 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
     }
     __syncthreads();
     if (active)
-      solve_tile<NMU, CACHED, KT, LIN>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, wp_, phase_base);
+      solve_tile<NMU, CACHED, KT, LIN, PARA>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu, wp_,
+                                             phase_base);
   }
 }
 
 size_t forward32_smem_bytes(int warps, int max_k) { return (size_t)warps * warp_pipe_bytes(max_k); }
 
-template <int NMU, bool CACHED, int KT, bool LIN>
+template <int NMU, bool CACHED, int KT, bool LIN, bool PARA = false>
 static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_t s) {
   const size_t smem = CACHED ? forward32_smem_bytes(a.warps, max_k) : 0;
   if (CACHED) {
@@ -938,14 +1005,14 @@ static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(raised & bit)) {
-      e = cudaFuncSetAttribute(k_forward32<NMU, CACHED, KT, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_forward32<NMU, CACHED, KT, LIN, PARA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kForwardSmemCap);
       if (e != cudaSuccess) return e;
       raised |= bit;
     }
     if (smem > kForwardSmemCap) return cudaErrorInvalidValue;
   }
-  k_forward32<NMU, CACHED, KT, LIN><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
+  k_forward32<NMU, CACHED, KT, LIN, PARA><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
   return cudaGetLastError();
 }
 
@@ -967,24 +1034,30 @@ static cudaError_t launch_cached(const FwdArgs& a, int grid, int max_k, int kt, 
   }
 }
 
+// parabolic source: runtime absorber count only (an option, not the fast path)
 template <int NMU>
-static cudaError_t launch_nmu(const FwdArgs& a, int grid, bool cached, bool linear, int max_k, int kt,
+static cudaError_t launch_nmu(const FwdArgs& a, int grid, bool cached, bool linear, bool para, int max_k, int kt,
                               cudaStream_t s) {
+  if (para) {
+    if (!cached) return linear ? cudaErrorInvalidValue : launch_one<NMU, false, 0, false, true>(a, grid, max_k, s);
+    return linear ? launch_one<NMU, true, 0, true, true>(a, grid, max_k, s)
+                  : launch_one<NMU, true, 0, false, true>(a, grid, max_k, s);
+  }
   if (!cached) return linear ? cudaErrorInvalidValue : launch_one<NMU, false, 0, false>(a, grid, max_k, s);
   return linear ? launch_cached<NMU, true>(a, grid, max_k, kt, s) : launch_cached<NMU, false>(a, grid, max_k, kt, s);
 }
 
-cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, int max_k, int kt,
-                             cudaStream_t s) {
+cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, bool para, int max_k,
+                             int kt, cudaStream_t s) {
   switch (max_nmu) {
-    case 1: return launch_nmu<1>(a, grid, cached, linear, max_k, kt, s);
-    case 2: return launch_nmu<2>(a, grid, cached, linear, max_k, kt, s);
-    case 3: return launch_nmu<3>(a, grid, cached, linear, max_k, kt, s);
-    case 4: return launch_nmu<4>(a, grid, cached, linear, max_k, kt, s);
-    case 5: return launch_nmu<5>(a, grid, cached, linear, max_k, kt, s);
-    case 6: return launch_nmu<6>(a, grid, cached, linear, max_k, kt, s);
-    case 7: return launch_nmu<7>(a, grid, cached, linear, max_k, kt, s);
-    case 8: return launch_nmu<8>(a, grid, cached, linear, max_k, kt, s);
+    case 1: return launch_nmu<1>(a, grid, cached, linear, para, max_k, kt, s);
+    case 2: return launch_nmu<2>(a, grid, cached, linear, para, max_k, kt, s);
+    case 3: return launch_nmu<3>(a, grid, cached, linear, para, max_k, kt, s);
+    case 4: return launch_nmu<4>(a, grid, cached, linear, para, max_k, kt, s);
+    case 5: return launch_nmu<5>(a, grid, cached, linear, para, max_k, kt, s);
+    case 6: return launch_nmu<6>(a, grid, cached, linear, para, max_k, kt, s);
+    case 7: return launch_nmu<7>(a, grid, cached, linear, para, max_k, kt, s);
+    case 8: return launch_nmu<8>(a, grid, cached, linear, para, max_k, kt, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1022,6 +1095,30 @@ cudaError_t launch_teff(const FwdArgs& a, const float* highres, int highres_ld, 
 }
 
 // ---------------------------------------------------------- FP64 forward
+// M_k(D) = int_0^D t^k e^{-t} dt for k = 0, 1, 2: power series
+// sum_n (-1)^n D^{k+n+1} / (n! (k+n+1)) below D = 1/2, closed forms
+// (1 - e^{-D}, M_0 - D e^{-D}, 2 M_1 - D^2 e^{-D}) above.
+__device__ void exp_moments(double D, double& M0, double& M1, double& M2) {
+  if (D < 0.5) {
+    double term = D, s0 = 0.0, s1 = 0.0, s2 = 0.0;   // term = (-1)^n D^{n+1} / n!
+    for (int n = 0; n < 40; ++n) {
+      s0 += term / (n + 1);
+      s1 += term * D / (n + 2);
+      s2 += term * D * D / (n + 3);
+      term *= -D / (n + 1);
+      if (fabs(term) < 1e-30) break;
+    }
+    M0 = s0;
+    M1 = s1;
+    M2 = s2;
+  } else {
+    const double e = exp(-D);
+    M0 = -expm1(-D);
+    M1 = M0 - D * e;
+    M2 = 2.0 * M1 - D * D * e;
+  }
+}
+
 // The plain FP64 path: one thread per wavenumber point, one block per
 // (sample, 128-point chunk), FP64 tables, exp/expm1 in double.
 constexpr int kF64Block = 128;
@@ -1089,13 +1186,13 @@ __global__ void __launch_bounds__(kF64Block) k_forward64(FwdArgs a) {
   const double nu = T.nu0 + (double)col * T.dnu;
   const int nu_pad = T.nu_pad, np = T.n_p;
   const bool lin = S.interp == HR2_INTERP_LINEAR;   // interpolation space of the tables
-  double I[NMU];
-  double chip = 0.0, Sp = 0.0;
-  for (int j = L; j >= 0; --j) {
-    const LevelDev& lv = S.levels[j];
-    const double wT = swT[j], wp = lv.wp64;
-    const size_t row = ((size_t)sa[j] * np + lv.pcell) * nu_pad + col;
-    double chi = 0.0;
+  const bool para = S.sc == HR2_SC_PARABOLIC;
+  // chi and S of level jj
+  auto level = [&](int jj, double& chi, double& Sv) {
+    const LevelDev& lv = S.levels[jj];
+    const double wT = swT[jj], wp = lv.wp64;
+    const size_t row = ((size_t)sa[jj] * np + lv.pcell) * nu_pad + col;
+    chi = 0.0;
     for (int s = 0; s < S.n_species; ++s) {
       const double* t = T.sig64 + (size_t)S.species[s] * T.n_T * np * nu_pad + row;
       const double* t10 = t + (size_t)np * nu_pad;
@@ -1107,33 +1204,66 @@ __global__ void __launch_bounds__(kF64Block) k_forward64(FwdArgs a) {
     }
     for (int p = 0; p < 2; ++p) {
       if (!T.has_cia[p]) continue;
-      const double* t = T.cia64 + (size_t)p * T.n_T * nu_pad + (size_t)sa[j] * nu_pad + col;
+      const double* t = T.cia64 + (size_t)p * T.n_T * nu_pad + (size_t)sa[jj] * nu_pad + col;
       const double kcia =
           lin ? (1.0 - wT) * exp10(t[0]) + wT * exp10(t[nu_pad]) : exp10((1.0 - wT) * t[0] + wT * t[nu_pad]);
-      chi += xh2 * (p == 0 ? xh2 : xhe) * sN[j] * kcia;
+      chi += xh2 * (p == 0 ? xh2 : xhe) * sN[jj] * kcia;
     }
-    const double Sj = kC1 * nu * nu * nu / expm1(kC2 * nu / sT[j]);
-    if (j == L) {
+    Sv = kC1 * nu * nu * nu / expm1(kC2 * nu / sT[jj]);
+  };
+  // optical depth of layer jj (levels jj, jj+1): trapezoid of chi plus the gray cloud's share
+  auto layer_dtau = [&](int jj, double chi_top, double chi_bot) {
+    const LevelDev& lv = S.levels[jj];
+    double dtau = (chi_top + chi_bot) * lv.half_dp64 * c;
+    if (sc[5] > sc[4]) {
+      const double lo = fmax(lv.p_dyn64, sc[4]), hi = fmin(S.levels[jj + 1].p_dyn64, sc[5]);
+      if (hi > lo) dtau += sc[3] * (hi - lo) / (sc[5] - sc[4]);
+    }
+    return dtau;
+  };
+  double I[NMU];
+  double chi_u, S_u, chi_c = 0.0, S_c = 0.0, chi_d = 0.0, S_d = 0.0;
+  level(L, chi_u, S_u);
 #pragma unroll
-      for (int m = 0; m < NMU; ++m) I[m] = Sj;
-    } else {
-      double dtau = (chi + chip) * lv.half_dp64 * c;
-      if (sc[5] > sc[4]) {   // gray cloud share of layer j (levels j, j+1)
-        const double lo = fmax(lv.p_dyn64, sc[4]), hi = fmin(S.levels[j + 1].p_dyn64, sc[5]);
-        if (hi > lo) dtau += sc[3] * (hi - lo) / (sc[5] - sc[4]);
-      }
+  for (int m = 0; m < NMU; ++m) I[m] = S_u;
+  if (L >= 1) level(L - 1, chi_c, S_c);
+  for (int j = L - 1; j >= 0; --j) {
+    // layer j between level j (S_c, above) and level j+1 (S_u, below)
+    const double dtau = layer_dtau(j, chi_c, chi_u);
+    double dtau_d = 0.0;
+    if (j >= 1) {
+      level(j - 1, chi_d, S_d);
+      dtau_d = layer_dtau(j - 1, chi_d, chi_c);
+    }
 #pragma unroll
-      for (int m = 0; m < NMU; ++m) {
-        if (m < S.n_mu) {
-          const double D = dtau / S.mu64[m];
-          const double e = exp(-D);
+    for (int m = 0; m < NMU; ++m) {
+      if (m < S.n_mu) {
+        const double D = dtau / S.mu64[m];
+        const double e = exp(-D);
+        if (para) {
+          // parabolic source through levels j-1, j, j+1 (linear for the top
+          // layer): I_j = I_{j+1} e^{-D} + S_j M0 + c1 M1 + c2 M2
+          if (!(D > 0.0)) continue;
+          double M0, M1, M2;
+          exp_moments(D, M0, M1, M2);
+          const double du = (S_u - S_c) / D;
+          double c1 = du, c2 = 0.0;
+          const double Dd = dtau_d / S.mu64[m];
+          if (j >= 1 && Dd > 0.0) {
+            c2 = (du - (S_c - S_d) / Dd) / (D + Dd);
+            c1 = du - c2 * D;
+          }
+          I[m] = I[m] * e + S_c * M0 + c1 * M1 + c2 * M2;
+        } else {
           const double q = (D > 0.0) ? -expm1(-D) / D : 1.0;
-          I[m] = I[m] * e + (1.0 - q) * Sj + (q - e) * Sp;
+          I[m] = I[m] * e + (1.0 - q) * S_c + (q - e) * S_u;
         }
       }
     }
-    chip = chi;
-    Sp = Sj;
+    chi_u = chi_c;
+    S_u = S_c;
+    chi_c = chi_d;
+    S_c = S_d;
   }
   double F = 0.0;
 #pragma unroll

@@ -28,6 +28,8 @@ HR2_INTERP_LOG10, HR2_INTERP_LINEAR = 0, 1
 INTERP = {"log10": HR2_INTERP_LOG10, "linear": HR2_INTERP_LINEAR}
 HR2_PROFILE_FE, HR2_PROFILE_MILNE = 0, 1
 PROFILE = {"fe": HR2_PROFILE_FE, "milne": HR2_PROFILE_MILNE}
+HR2_SC_LINEAR, HR2_SC_PARABOLIC = 0, 1
+SC = {"linear": HR2_SC_LINEAR, "parabolic": HR2_SC_PARABOLIC}
 
 EXPORTED = [
     "hr2_ctx_create", "hr2_ctx_destroy", "hr2_last_error", "hr2_ctx_memory", "hr2_set_launch_config",
@@ -58,7 +60,8 @@ class SetupDesc(C.Structure):
                 ("fe_elements", C.c_int), ("fe_order", C.c_int), ("resolving_power", C.c_double),
                 ("n_bins", C.c_int), ("bin_edges", C.POINTER(C.c_double)), ("obs_flux", C.POINTER(C.c_double)),
                 ("obs_sigma", C.POINTER(C.c_double)), ("r_he", C.c_double), ("radius_cm", C.c_double),
-                ("level_cache", C.c_int), ("interp", C.c_int), ("profile", C.c_int), ("cloud", C.c_int)]
+                ("level_cache", C.c_int), ("interp", C.c_int), ("profile", C.c_int), ("cloud", C.c_int),
+                ("sc", C.c_int)]
 
 
 class LaunchCfg(C.Structure):
@@ -252,10 +255,12 @@ def hr2_tables_destroy(ctx, tables):
 
 def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_elements, fe_order,
                      resolving_power, bin_edges, p_top=1e-4, p_bot=100.0, r_he=0.17, radius_cm=7.1492e9,
-                     obs_flux=None, obs_sigma=None, level_cache=True, interp="log10", profile="fe", cloud=False):
+                     obs_flux=None, obs_sigma=None, level_cache=True, interp="log10", profile="fe", cloud=False,
+                     sc="linear"):
     """interp: "log10" (HR2_INTERP_LOG10) or "linear" (HR2_INTERP_LINEAR);
     profile: "fe" (HR2_PROFILE_FE) or "milne" (HR2_PROFILE_MILNE);
-    cloud: add the gray cloud layer of parameters HR2_P_CLOUD..."""
+    cloud: add the gray cloud layer of parameters HR2_P_CLOUD..;
+    sc: "linear" (HR2_SC_LINEAR) or "parabolic" (HR2_SC_PARABOLIC) source interpolation."""
     sp = np.ascontiguousarray(np.asarray(species, dtype=np.int32))
     edges, pe = _dptr(bin_edges)
     keep = [sp, edges]
@@ -268,7 +273,7 @@ def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_el
     d = SetupDesc(int(nu_first), int(n_nu), int(n_layers), float(p_top), float(p_bot), len(sp),
                   sp.ctypes.data_as(_IP), int(n_mu), int(fe_elements), int(fe_order), float(resolving_power),
                   len(edges) - 1, pe, pf, ps, float(r_he), float(radius_cm), int(bool(level_cache)),
-                  INTERP[interp], PROFILE[profile], int(bool(cloud)))
+                  INTERP[interp], PROFILE[profile], int(bool(cloud)), SC[sc])
     h = _VP()
     _check(lib().hr2_setup_create(ctx, tables, C.byref(d), C.byref(h)), ctx)
     return h
