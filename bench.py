@@ -454,6 +454,7 @@ def run_extras(args, local, flush):
         out["serving"] = {"streams": 16, "request_sizes": "32-512", "capacity_models_per_s": cap,
                           "latency": "arrival to lnL on the host", "loads": res}
     out["linear_sigma_option"] = run_linear_option(args, local, flush)
+    out["parabolic_source_option"] = run_linear_option(args, local, flush, sc="parabolic")
     out["nested_sampling"] = run_nested(args, local)
     return out
 
@@ -494,10 +495,11 @@ def run_nested(args, local):
         return res
 
 
-def run_linear_option(args, local, flush):
-    """The benchmark workload with the opacity tables interpolated in sigma instead of
-    log10 sigma (a setup option; a different model, so not the headline): forward +
-    lnL per step, same batch, same L2 flush."""
+def run_linear_option(args, local, flush, **option):
+    """The benchmark workload with a setup option changed (the opacity tables
+    interpolated in sigma instead of log10 sigma by default, or the parabolic source);
+    a different model, so not the headline: forward + lnL per step, same batch, same
+    L2 flush."""
     import dataclasses
 
     import torch
@@ -508,7 +510,8 @@ def run_linear_option(args, local, flush):
 
     dev = torch.device("cuda", local)
     wl = W.WORKLOADS[args.workload]()
-    spec = dataclasses.replace(wl.setups[0], interp="linear")
+    option = option or {"interp": "linear"}
+    spec = dataclasses.replace(wl.setups[0], **option)
     with Engine(local) as eng:
         t = eng.add_tables(wl.table, "fp16", W.make_tables(wl.table))
         s = eng.add_setup(t, spec)
@@ -541,7 +544,7 @@ def run_linear_option(args, local, flush):
         hr2.hr2_profile_enable(eng.ctx, False)
         kms, nl = hr2.hr2_profile_read(eng.ctx, True)
         times = [a.elapsed_time(b) for a, b in evs]
-        return {"workload": wl.name, "interp": "linear", "samples": n, "value": n * steps / (sum(times) / 1e3),
+        return {"workload": wl.name, "option": option, "samples": n, "value": n * steps / (sum(times) / 1e3),
                 "unit": "models/s", "ms_per_step": float(np.mean(times)), "kernel_ms": kms / max(nl, 1)}
 
 
