@@ -155,6 +155,29 @@ def test_mixed_absorber_counts_in_one_batch(eng, ks):
             _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, sp.n_nu)
 
 
+# ------------------------------------------------------------ the largest shapes the ABI accepts
+@pytest.mark.parametrize("storage", ["fp16-level-gridded", "fp16-direct", "fp64"])
+def test_maximum_sizes(eng, storage):
+    """HR2_MAX_LEVELS - 1 layers, HR2_MAX_SPECIES absorbers (the 16-absorber kernel, whose
+    per-warp pipeline takes 37 KB of shared memory), HR2_MAX_MU angle nodes and
+    HR2_MAX_TNODES temperature nodes (5 cubic elements), on a ragged 300-point range."""
+    K = 16
+    spec = W.TableSpec(K, np.linspace(300.0, 3000.0, 10), np.linspace(-4.0, 2.0, 8), 5000.0, 1.0, 330, seed=91)
+    tabs = W.make_tables(spec)
+    setup = W.make_setup(spec, 5011.0, 5310.0, 255, range(K), 8, 5, 3, 300.0, 10)
+    assert setup.n_tnodes == 16
+    st_ = storage[:4]
+    t = eng.add_tables(spec, st_, tabs)
+    s = eng.add_setup(t, setup, level_cache=(storage == "fp16-level-gridded"))
+    theta = W.draw_params(setup, 3, 17, W.Prior(b=(0.9, 0.99), log_x=(-9.0, -4.0)))
+    bins, hi, st = _run(eng, [s], np.zeros(3, np.int32), theta)
+    assert np.all(st == 0)
+    om = oracle_model(tables_as_stored(tabs, st_), setup)
+    tol = FLUX_RTOL if st_ == "fp16" else FP64_RTOL
+    for i in range(3):
+        _compare(om, theta[i], bins[i], hi[i], tol, setup.n_nu)
+
+
 # ------------------------------------------------------------ linear-sigma interpolation option
 @pytest.mark.parametrize("storage", ["fp16-level-gridded", "fp64"])
 @pytest.mark.parametrize("case", TINY[1:], ids=[f"nu{c[0]}_L{c[1]}_K{c[2]}_mu{c[5]}" for c in TINY[1:]])
