@@ -341,8 +341,9 @@ constexpr float kL2Lo = (float)(kLog2_10 - (double)kL2Hi);
 // comes from its series instead of from 1 - e^{-D}
 constexpr float kThinD = 0.25f;
 
-// One warp computes one sample on one 64-point wavenumber tile (two points
-// per lane), sweeping the levels from the top (j = 0) to the bottom (j = L):
+// One warp computes one sample on one kTileNu-point wavenumber tile (kPairs
+// packed pairs of points per lane), sweeping the levels from the top (j = 0)
+// to the bottom (j = L):
 //   log10 sigma_s: bilinear in (T, log10 p) written as corner 00 plus
 //                  weighted differences (exact partition of unity)
 //   chi_j = sum_s x_s c sigma_s + CIA     (Sects. 2.3, 2.8; 2^(A_s + ...))
@@ -403,7 +404,7 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
 }
 
 // Per-warp shared-memory layout of the cached path:
-//   rows[2][2 K + 4][64] floats, per stage (double-buffered by level
+//   rows[2][2 K + 4][kTileNu] floats, per stage (double-buffered by level
 //     parity): the rows of T cells a and a+1 of every absorber ([a][s],
 //     [a+1][s]), then the CIA rows [a][pair], [a+1][pair];
 //   recs[4][16]: the level records, a ring of four (level j in slot j & 3);
