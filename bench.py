@@ -605,12 +605,22 @@ def _hbm_peak():
         return 6400.0, "fallback"
 
 
+def _code_only(src: str) -> str:
+    """C++ source without comments and whitespace (what the compiler sees as tokens)."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return re.sub(r"\s+", "", src)
+
+
 def _kernel_hash() -> str:
+    """Hash of the forward kernel's code (comments and whitespace ignored), to tell whether
+    the committed DRAM counters still belong to it."""
     import hashlib
     h = hashlib.sha256()
     for f in ("kern_forward.cu", "hr2_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_1910_01070_b300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1910_01070_b300", "csrc", f)) as fh:
+            h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]
 
 
