@@ -161,9 +161,11 @@ typedef struct {
   int level_cache;            /* FP16 tables only.  Nonzero: interpolate the
                                  tables in p onto this setup's levels once, at
                                  creation (FP64 arithmetic, stored as FP32
-                                 times log2 10, n_species x levels x n_T x
-                                 columns x 4 bytes of device memory), so that
-                                 each sample interpolates in T only.  Zero:
+                                 times log2 10: per T cell the row and its
+                                 difference to the next T row, n_species x
+                                 levels x (n_T - 1) x columns x 8 bytes of
+                                 device memory), so that each sample
+                                 interpolates in T only.  Zero:
                                  every evaluation interpolates the FP16 tables
                                  bilinearly.  One batch call takes setups of a
                                  single kind.                                    */

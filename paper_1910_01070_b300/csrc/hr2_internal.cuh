@@ -109,8 +109,10 @@ struct SetupDev {
   // level-gridded operand (level_cache): the tables interpolated in p onto
   // the levels, FP32, columns local to the setup's tiles
   int cached;
-  const float* lvl32;            // [n_tiles][n_lev][n_T][n_species][kTileNu]
-  const float* cia32;            // [n_tiles][n_T][2][kTileNu]
+  // per T cell a: the row of T row a and the difference to row a+1,
+  // interleaved per pair of columns ({g[2q], g[2q+1], dg[2q], dg[2q+1]})
+  const float* lvl32;            // [n_tiles][n_lev][n_T - 1][n_species][kTileNu / 2][4]
+  const float* cia32;            // [n_tiles][n_T - 1][2][kTileNu / 2][4]
   // temperature profile (HR2_PROFILE_*); Milne's profile reads its Hopf
   // function from hopf_q [kHopfN] (built at setup creation)
   int profile;

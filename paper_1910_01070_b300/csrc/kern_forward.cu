@@ -337,9 +337,19 @@ __device__ __forceinline__ unsigned int ldh2(const __half* p) {
 // log2(10) as an FP32 head and tail
 constexpr float kL2Hi = 3.32192802f;
 constexpr float kL2Lo = (float)(kLog2_10 - (double)kL2Hi);
-// below this optical thickness D the linear-source factor (1 - e^{-D}) / D
-// comes from its series instead of from 1 - e^{-D}
+// below this optical thickness D the parabolic-source moments come from
+// their power series instead of from differences of exponentials
 constexpr float kThinD = 0.25f;
+// below this D the linear-source layer factor 1 - e^{-D} comes from its
+// series D - D^2/2 + D^3/6 (truncation <= D^3/24 = 1.3e-6 relative); above it
+// from the difference of the two exponentials (rounding ~2^-22 / D <= 7.6e-6
+// relative, ~1e-6 typical)
+constexpr float kThinLin = 0.03125f;
+// added to every layer's optical depth on the linear-source path, so that
+// dtau > 0 and (S_j - S_{j-1}) / dtau stays finite in an opacity-free layer
+// (|S| < 3e18); a layer this thin is transparent either way (its factor
+// (1 - e^{-D}) / dtau is 1/mu to FP32 precision below dtau ~ 1e-8)
+constexpr float kTinyTau = 1e-20f;
 
 // One warp computes one sample on one kTileNu-point wavenumber tile (kPairs
 // packed pairs of points per lane), sweeping the levels from the top (j = 0)
@@ -360,13 +370,18 @@ constexpr float kThinD = 0.25f;
 // i.e. the formal solution (Eq. 1) integrated by parts for a piecewise-
 // linear source.  Each E_l comes directly from the cumulative tau_l, so the
 // small bias of the hardware exponential cannot compound over the layers.
-// For optically thin layers (D < kThinD) the difference is taken as
-//   E_l - E_{l+1} = E_l D q(D),  q = 1 - D/2 + D^2/6 - ... (no cancellation).
+// For optically thin layers (D < kThinLin) the difference is taken as
+//   E_l - E_{l+1} = E_l (D - D^2/2 + D^3/6)   (no cancellation),
+// chosen per point without a branch.
 //   F+ = 2 pi sum_k w_k mu_k I_0(mu_k)                             (Eq. 8)
 __device__ __forceinline__ v2 ldf2(const float* p) {
   return __ldg(reinterpret_cast<const unsigned long long*>(p));
 }
-__device__ __forceinline__ v2 lds2f(const float* p) { return *reinterpret_cast<const unsigned long long*>(p); }
+// a pair of columns of the level-gridded operand: value and T difference
+struct __align__(16) RowDiff {
+  v2 g, dg;
+};
+__device__ __forceinline__ RowDiff lds_rd(const float* p) { return *reinterpret_cast<const RowDiff*>(p); }
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
 // ---- per-warp bulk-copy pipeline (Blackwell bulk async copies + mbarrier)
@@ -404,9 +419,9 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
 }
 
 // Per-warp shared-memory layout of the cached path:
-//   rows[2][2 K + 4][kTileNu] floats, per stage (double-buffered by level
-//     parity): the rows of T cells a and a+1 of every absorber ([a][s],
-//     [a+1][s]), then the CIA rows [a][pair], [a+1][pair];
+//   rows[2][K + 2][2 kTileNu] floats, per stage (double-buffered by level
+//     parity): T cell a of every absorber ([s][q][row, difference] as the
+//     operand stores it), then the two CIA pairs of cell a;
 //   recs[4][16]: the level records, a ring of four (level j in slot j & 3);
 //   bar[2]: one mbarrier per stage.
 struct WarpPipe {
@@ -426,9 +441,9 @@ __device__ __forceinline__ WarpPipe warp_pipe(unsigned char* base, int max_k) {
   return w;
 }
 
-// Issue stage st: one bulk copy of the absorber rows of one level (T cells
-// acell and acell+1, 2 K x kTileNu floats), one of the CIA rows (4 x kTileNu
-// floats, when copy_cia: the stage does not hold those of acell yet) and up
+// Issue stage st: one bulk copy of T cell acell of every absorber at one
+// level (K x 2 kTileNu floats), one of the CIA pairs of that cell (2 x 2
+// kTileNu floats, when copy_cia: the stage does not hold those of acell yet) and up
 // to two level records (rec_a -> record slot slot_a, rec_b -> slot_b; NULL to
 // skip), all counted on the stage's barrier.  One lane issues everything.
 __device__ __forceinline__ void issue_stage(const WarpPipe& w, int st, int K, const float* lvl_level,
@@ -443,8 +458,8 @@ __device__ __forceinline__ void issue_stage(const WarpPipe& w, int st, int K, co
     unsigned long long* bar = w.bar + st;
     mbar_expect_tx(bar, bytes);
     float* dst = w.rows + (size_t)st * (2 * K + 4) * kTileNu;
-    if (rows_bytes) bulk_copy(dst, lvl_level + (size_t)acell * K * kTileNu, rows_bytes, bar);
-    if (has_cia) bulk_copy(dst + (size_t)2 * K * kTileNu, cia_tile + (size_t)acell * 2 * kTileNu, cia_bytes, bar);
+    if (rows_bytes) bulk_copy(dst, lvl_level + (size_t)acell * 2 * K * kTileNu, rows_bytes, bar);
+    if (has_cia) bulk_copy(dst + (size_t)2 * K * kTileNu, cia_tile + (size_t)acell * 4 * kTileNu, cia_bytes, bar);
     if (rec_a) bulk_copy(w.recs + (size_t)slot_a * 16, rec_a, (unsigned)sizeof(LevRec), bar);
     if (rec_b) bulk_copy(w.recs + (size_t)slot_b * 16, rec_b, (unsigned)sizeof(LevRec), bar);
   }
@@ -472,21 +487,24 @@ struct NuConst {
   v2 c1n[kPairs];                                 // c1 nu^3 of both points
 };
 
-// Level sweep state of one pair: chi and S of the level above, S_0 and the
+// Level sweep state of one pair: chi and S of the level above and the
 // cumulative optical depth tau_j; for the parabolic source also the slope
 // dS/dtau and the optical depth of the layer above.
 struct LevelState {
-  v2 chip, Sp, S0, tau, dup, dtp;
+  v2 chip, Sp, tau, dup, dtp;
 };
 
 // Physics of one level for the lane's wavenumbers, given chi_j: the Planck
-// source, and for j > 0 the layer above it added to the telescoped sum.
-template <int NMU, bool PARA>
+// source, and the layer above it added to the telescoped sum.  SX: some
+// level of this sample may have h c nu / k T < 0.0625 on this tile, where
+// 1 - e^{-x} of the Planck function needs its series (decided per item).
+template <int NMU, bool PARA, bool SX>
 __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], const float upl, const float upl_lo,
                                               const float rdnu, const float half_dp, const float dtau_cloud,
                                               float& hdp_prev,
                                               const NuConst& nc, const float thin_dtau, const float thin_all,
-                                              const v2* sMnl, const v2* sImu, const v2* sMu, v2 (&acc)[kPairs][NMU],
+                                              const v2* sMnl, const v2* sImu, const v2* sMu, const v2* sPoly,
+                                              const float* sThr, v2 (&acc)[kPairs][NMU],
                                               v2 (&E)[kPairs][NMU], LevelState (&st)[kPairs]) {
   const float kLn2f = 0.6931471805599453f;
   const v2 one = pk(1.f);
@@ -496,7 +514,8 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
   // hc nu / kT is smallest at pair 0's first point, which decides whether
   // the small-x form is needed anywhere in the warp.
   v2 Sj[kPairs];
-  const bool small_x = __any_sync(0xffffffffu, -(upl * nc.nu0[0]) * kLn2f < 0.0625f);
+  bool small_x = false;
+  if constexpr (SX) small_x = __any_sync(0xffffffffu, -(upl * nc.nu0[0]) * kLn2f < 0.0625f);
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
     const float p0 = upl * nc.nu0[p];
@@ -505,7 +524,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
     const float t0 = fmaf(h0, y0 * kLn2f, h0);
     const v2 t = pk(t0, t0 * rdnu);
     v2 om = sub2(one, t);
-    if (small_x) {
+    if (SX && small_x) {
       // 1 - e^{-x} without cancellation for small x
       const float x0 = -p0 * kLn2f;
       const v2 x = pk(x0, x0 * nc.ratio[p]);
@@ -516,13 +535,47 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
     }
     Sj[p] = mul2(mul2(nc.c1n[p], t), rcp_2(om));
   }
-  if (j == 0) {
+  if constexpr (!PARA) {
+    // Linear source, layer j-1 between levels j-1 (top, S_{j-1}) and j
+    // (bottom, S_j): it adds (E_{j-1} - E_j) (S_j - S_{j-1}) / dtau to mu's
+    // sum, with E_{j-1} - E_j = E_{j-1} (1 - e^{-D}), D = dtau / mu.
+    // (S_j - S_{j-1}) / dtau is shared by the nodes.  Where D < kThinLin,
+    // 1 - e^{-D} is the polynomial P_k(dtau) = dtau (a1 + dtau (a2 + dtau a3)),
+    // a_n = (-1)^(n+1) / (n! mu_k^n) (sPoly), chosen per point without a
+    // branch.  Level 0 enters the same way as a layer of optical depth
+    // kTinyTau below a zero source (nothing above it has been added yet):
+    // it adds S_0 / mu, the S_0 term of I_0 = S_0 + mu sum_l ..., so that
+    // I_0(mu) = mu * acc.  Nodes beyond the setup's count are padded with
+    // mu = 1 and zero weight.
+    (void)thin_dtau;
+    (void)thin_all;
+    v2 dt[kPairs], rdS[kPairs];
 #pragma unroll
-    for (int p = 0; p < kPairs; ++p) st[p].S0 = Sj[p];
-  } else {
+    for (int p = 0; p < kPairs; ++p) {
+      // gas trapezoid + gray cloud + kTinyTau
+      dt[p] = fma2(pk(hdp_prev), add2(chi[p], st[p].chip), pk(dtau_cloud + kTinyTau));
+      rdS[p] = mul2(sub2(Sj[p], st[p].Sp), rcp_2(dt[p]));
+      st[p].tau = add2(st[p].tau, dt[p]);
+    }
+#pragma unroll
+    for (int k = 0; k < NMU; ++k) {
+      const v2 mk = sMnl[k], a1 = sPoly[3 * k], a2 = sPoly[3 * k + 1], a3 = sPoly[3 * k + 2];
+      const float thr = sThr[k];   // kThinLin * mu_k
+#pragma unroll
+      for (int p = 0; p < kPairs; ++p) {
+        const v2 En = ex2_2(mul2(st[p].tau, mk));   // e^{-tau_j / mu}
+        const v2 X = sub2(E[p][k], En);
+        const v2 Xs = mul2(E[p][k], mul2(dt[p], fma2(dt[p], fma2(dt[p], a3, a2), a1)));
+        const float2 dtf = up(dt[p]), xf = up(X), xsf = up(Xs);
+        const v2 cc = pk(dtf.x < thr ? xsf.x : xf.x, dtf.y < thr ? xsf.y : xf.y);
+        acc[p][k] = fma2(cc, rdS[p], acc[p][k]);
+        E[p][k] = En;
+      }
+    }
+  } else if (j > 0) {
     // layer j-1 between levels j-1 (top, Sp) and j (bottom, Sj)
     v2 dt[kPairs], rr[kPairs], dS[kPairs];
-    float dmin = 3.0e38f, dmax = 0.f;
+    float dmin = 3.0e38f;
 #pragma unroll
     for (int p = 0; p < kPairs; ++p) {
       dt[p] = fma2(pk(hdp_prev), add2(chi[p], st[p].chip), pk(dtau_cloud));   // gas trapezoid + gray cloud
@@ -531,113 +584,58 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
       st[p].tau = add2(st[p].tau, dt[p]);
       const float2 dtf = up(dt[p]);
       dmin = fminf(dmin, fminf(dtf.x, dtf.y));
-      dmax = fmaxf(dmax, fmaxf(dtf.x, dtf.y));
     }
     const bool thin = __any_sync(0xffffffffu, dmin < thin_dtau);
-    if constexpr (PARA) {
-      // Parabolic source (Sect. 2.1, higher-order interpolant): over layer
-      // j-1 the source is the parabola through levels j-2, j-1, j; in
-      // vertical optical depth below level j-1 it is S_{j-1} + c1 t + c2 t^2
-      // (divided differences; the top layer keeps c2 = 0), along the ray
-      // t -> mu t.  The layer adds E_{j-1} [S_{j-1} M0 + mu c1 M1 + mu^2 c2 M2]
-      // with M_k = int_0^D t^k e^{-t} dt, D = dtau / mu, taken from
-      //   E M0 = E_{j-1} - E_j, E M1 = E M0 - D E_j, E M2 = 2 E M1 - D^2 E_j,
-      // or, where D < kThinD, from the power series of M_k times E_{j-1}.
-      // I_0 = sum of the layers + E_L S_L (added after the sweep).
-      (void)dmax;
+    (void)thin_all;
+    // Parabolic source (Sect. 2.1, higher-order interpolant): over layer
+    // j-1 the source is the parabola through levels j-2, j-1, j; in
+    // vertical optical depth below level j-1 it is S_{j-1} + c1 t + c2 t^2
+    // (divided differences; the top layer keeps c2 = 0), along the ray
+    // t -> mu t.  The layer adds E_{j-1} [S_{j-1} M0 + mu c1 M1 + mu^2 c2 M2]
+    // with M_k = int_0^D t^k e^{-t} dt, D = dtau / mu, taken from
+    //   E M0 = E_{j-1} - E_j, E M1 = E M0 - D E_j, E M2 = 2 E M1 - D^2 E_j,
+    // or, where D < kThinD, from the power series of M_k times E_{j-1}.
+    // I_0 = sum of the layers + E_L S_L (added after the sweep).
 #pragma unroll
-      for (int p = 0; p < kPairs; ++p) {
-        const v2 du = mul2(dS[p], rr[p]);
-        v2 c1 = du, c2 = pk(0.f);
-        if (j >= 2) {
-          c2 = mul2(sub2(du, st[p].dup), rcp_2(add2(dt[p], st[p].dtp)));
-          c1 = sub2(du, mul2(c2, dt[p]));
-        }
-        st[p].dup = du;
-        st[p].dtp = dt[p];
-#pragma unroll
-        for (int k = 0; k < NMU; ++k) {
-          const v2 mk = sMnl[k], im = sImu[k], mu = sMu[k];
-          const v2 En = ex2_2(mul2(st[p].tau, mk));
-          const v2 D = mul2(dt[p], im);
-          const v2 D2 = mul2(D, D);
-          v2 m0 = sub2(E[p][k], En);
-          v2 m1 = sub2(m0, mul2(D, En));
-          v2 m2 = sub2(add2(m1, m1), mul2(D2, En));
-          if (thin) {
-            const v2 Ek = E[p][k];
-            const v2 q0 = mul2(D, fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
-                                                                  pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), pk(1.f)));
-            const v2 q1 = mul2(D2, fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 840.f), pk(1.f / 144.f)),
-                                                                   pk(-1.f / 30.f)), pk(1.f / 8.f)), pk(-1.f / 3.f)), pk(0.5f)));
-            const v2 q2 = mul2(mul2(D2, D), fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 960.f), pk(1.f / 168.f)),
-                                                                            pk(-1.f / 36.f)), pk(0.1f)), pk(-0.25f)),
-                                                 pk(1.f / 3.f)));
-            const v2 s0 = mul2(Ek, q0), s1 = mul2(Ek, q1), s2 = mul2(Ek, q2);
-            const float2 Df = up(D), a0 = up(m0), a1 = up(m1), a2 = up(m2), b0 = up(s0), b1 = up(s1), b2 = up(s2);
-            const bool tx = Df.x < kThinD, ty = Df.y < kThinD;
-            m0 = pk(tx ? b0.x : a0.x, ty ? b0.y : a0.y);
-            m1 = pk(tx ? b1.x : a1.x, ty ? b1.y : a1.y);
-            m2 = pk(tx ? b2.x : a2.x, ty ? b2.y : a2.y);
-          }
-          v2 a = fma2(st[p].Sp, m0, acc[p][k]);
-          a = fma2(mul2(mu, c1), m1, a);
-          acc[p][k] = fma2(mul2(mul2(mu, mu), c2), m2, a);
-          E[p][k] = En;
-        }
+    for (int p = 0; p < kPairs; ++p) {
+      const v2 du = mul2(dS[p], rr[p]);
+      v2 c1 = du, c2 = pk(0.f);
+      if (j >= 2) {
+        c2 = mul2(sub2(du, st[p].dup), rcp_2(add2(dt[p], st[p].dtp)));
+        c1 = sub2(du, mul2(c2, dt[p]));
       }
-    } else {
-    const bool allthin = thin && __all_sync(0xffffffffu, dmax < thin_all);
-    // The three regimes are separate loops so that the decision is taken once
-    // per level.  Nodes beyond the setup's count are padded with mu = 1 and
-    // zero weight.
-    if (allthin) {
-      // every lane's layer is optically thin for every node: series only,
-      // (E_{j-1} - E_j) / dtau = E_{j-1} q(D) / mu
+      st[p].dup = du;
+      st[p].dtp = dt[p];
 #pragma unroll
       for (int k = 0; k < NMU; ++k) {
-        const v2 mk = sMnl[k], im = sImu[k];
-#pragma unroll
-        for (int p = 0; p < kPairs; ++p) {
-          const v2 En = ex2_2(mul2(st[p].tau, mk));   // e^{-tau_j / mu}
-          const v2 D = mul2(dt[p], im);
-          const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
-                                                            pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
-          acc[p][k] = fma2(mul2(mul2(E[p][k], qs), im), dS[p], acc[p][k]);
-          E[p][k] = En;
+        const v2 mk = sMnl[k], im = sImu[k], mu = sMu[k];
+        const v2 En = ex2_2(mul2(st[p].tau, mk));
+        const v2 D = mul2(dt[p], im);
+        const v2 D2 = mul2(D, D);
+        v2 m0 = sub2(E[p][k], En);
+        v2 m1 = sub2(m0, mul2(D, En));
+        v2 m2 = sub2(add2(m1, m1), mul2(D2, En));
+        if (thin) {
+          const v2 Ek = E[p][k];
+          const v2 q0 = mul2(D, fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
+                                                                pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), pk(1.f)));
+          const v2 q1 = mul2(D2, fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 840.f), pk(1.f / 144.f)),
+                                                                 pk(-1.f / 30.f)), pk(1.f / 8.f)), pk(-1.f / 3.f)), pk(0.5f)));
+          const v2 q2 = mul2(mul2(D2, D), fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 960.f), pk(1.f / 168.f)),
+                                                                          pk(-1.f / 36.f)), pk(0.1f)), pk(-0.25f)),
+                                               pk(1.f / 3.f)));
+          const v2 s0 = mul2(Ek, q0), s1 = mul2(Ek, q1), s2 = mul2(Ek, q2);
+          const float2 Df = up(D), a0 = up(m0), a1 = up(m1), a2 = up(m2), b0 = up(s0), b1 = up(s1), b2 = up(s2);
+          const bool tx = Df.x < kThinD, ty = Df.y < kThinD;
+          m0 = pk(tx ? b0.x : a0.x, ty ? b0.y : a0.y);
+          m1 = pk(tx ? b1.x : a1.x, ty ? b1.y : a1.y);
+          m2 = pk(tx ? b2.x : a2.x, ty ? b2.y : a2.y);
         }
+        v2 a = fma2(st[p].Sp, m0, acc[p][k]);
+        a = fma2(mul2(mu, c1), m1, a);
+        acc[p][k] = fma2(mul2(mul2(mu, mu), c2), m2, a);
+        E[p][k] = En;
       }
-    } else if (thin) {
-      // some are thin: the series where D < kThinD, the difference elsewhere
-#pragma unroll
-      for (int k = 0; k < NMU; ++k) {
-        const v2 mk = sMnl[k], im = sImu[k];
-#pragma unroll
-        for (int p = 0; p < kPairs; ++p) {
-          const v2 En = ex2_2(mul2(st[p].tau, mk));
-          const v2 c = mul2(sub2(E[p][k], En), rr[p]);
-          const v2 D = mul2(dt[p], im);
-          const v2 qs = fma2(D, fma2(D, fma2(D, fma2(D, fma2(D, pk(-1.f / 720.f), pk(1.f / 120.f)),
-                                                            pk(-1.f / 24.f)), pk(1.f / 6.f)), pk(-0.5f)), one);
-          const v2 cs = mul2(mul2(E[p][k], qs), im);
-          const float2 Df = up(D), csf = up(cs), cf = up(c);
-          const v2 cc = pk(Df.x < kThinD ? csf.x : cf.x, Df.y < kThinD ? csf.y : cf.y);
-          acc[p][k] = fma2(cc, dS[p], acc[p][k]);
-          E[p][k] = En;
-        }
-      }
-    } else {
-#pragma unroll
-      for (int k = 0; k < NMU; ++k) {
-        const v2 mk = sMnl[k];
-#pragma unroll
-        for (int p = 0; p < kPairs; ++p) {
-          const v2 En = ex2_2(mul2(st[p].tau, mk));
-          acc[p][k] = fma2(mul2(sub2(E[p][k], En), rr[p]), dS[p], acc[p][k]);   // (E_{j-1} - E_j) / dtau
-          E[p][k] = En;
-        }
-      }
-    }
     }
   }
 #pragma unroll
@@ -654,10 +652,11 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
 // level-gridded operand through the warp's bulk-copy pipeline (rows of level
 // j+1 and the record of level j+2 land while level j is computed).
 // Otherwise the FP16 tables are read and interpolated bilinearly in place.
-template <int NMU, bool CACHED, int KT, bool LIN, bool PARA>
+template <int NMU, bool CACHED, int KT, bool LIN, bool PARA, bool SX>
 __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
                                            const v2* sA2, const v2* sAc2, const void* const* sPtr,
-                                           const v2* sMnl, const v2* sImu, const v2* sMu, const WarpPipe& wp_,
+                                           const v2* sMnl, const v2* sImu, const v2* sMu, const v2* sPoly,
+                                           const float* sThr, const WarpPipe& wp_,
                                            unsigned& phase_base) {
   const int lane = threadIdx.x & 31;
   const SampleDev& sd = a.samp[i];
@@ -690,8 +689,8 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
   }
   // dtau below which some node is thin (largest mu, padded nodes included),
   // and below which every node is (smallest mu)
-  const float thin_dtau = kThinD * S.mu[NMU - 1];
-  const float thin_all = kThinD * S.mu[0];
+  const float thin_dtau = (PARA ? kThinD : kThinLin) * S.mu[NMU - 1];
+  const float thin_all = (PARA ? kThinD : kThinLin) * S.mu[0];
   const int K = S.n_species;
   const int L = S.n_lev - 1;
   const int nT = T.n_T;
@@ -708,7 +707,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     }
   LevelState st[kPairs];
 #pragma unroll
-  for (int p = 0; p < kPairs; ++p) st[p].chip = st[p].Sp = st[p].S0 = st[p].tau = st[p].dup = st[p].dtp = pk(0.f);
+  for (int p = 0; p < kPairs; ++p) st[p].chip = st[p].Sp = st[p].tau = st[p].dup = st[p].dtp = pk(0.f);
   float hdp_prev = 0.f;
 
   if constexpr (CACHED) {
@@ -723,9 +722,9 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     //                                        j+1), record j+2
     //                    compute level j
     if (phase_base == 0xffffffffu) return;       // this warp's pipeline failed earlier
-    const float* lvl_tile = S.lvl32 + (size_t)tile * (L + 1) * nT * K * kTileNu;
-    const float* cia_tile = S.cia32 + (size_t)tile * nT * 2 * kTileNu;
-    const size_t lvl_step = (size_t)nT * K * kTileNu;
+    const float* lvl_tile = S.lvl32 + (size_t)tile * (L + 1) * (nT - 1) * K * 2 * kTileNu;
+    const float* cia_tile = S.cia32 + (size_t)tile * (nT - 1) * 4 * kTileNu;
+    const size_t lvl_step = (size_t)(nT - 1) * K * 2 * kTileNu;
     const bool has_cia = cia0 || cia1;
     const unsigned ph = phase_base;
     const int acell0 = __ldg(&rec[0].acell);
@@ -733,6 +732,9 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     if (ph & 1u) cia_cell1 = acell0; else cia_cell0 = acell0;
     issue_stage(wp_, (int)(ph & 1u), K, lvl_tile, cia_tile, acell0, has_cia, rec, 0, L >= 1 ? rec + 1 : nullptr, 1,
                 lane);
+    // unrolled by two so that the loop-carried sweep state alternates between
+    // two register sets instead of being moved back at the end of each level
+#pragma unroll 2
     for (int j = 0; j <= L; ++j) {
       const unsigned g = ph + (unsigned)j;
       const int stg = (int)(g & 1u);
@@ -759,25 +761,25 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       const float4 r2 = *reinterpret_cast<const float4*>(rj + 8);
       const float4 r3 = *reinterpret_cast<const float4*>(rj + 12);
       const v2 wT = pk(r0.y);
-      const float* rowa = wp_.rows + (size_t)stg * (2 * K + 4) * kTileNu + 2 * lane;   // [a][s]
-      const float* rowb = rowa + (size_t)K * kTileNu;                                   // [a+1][s]
+      // stage: [s][q][row, T difference] for pairs q of columns; lane l's
+      // pair p is q = l + 32 p
+      const float* rows = wp_.rows + (size_t)stg * (2 * K + 4) * kTileNu + 4 * lane;
       // chi = sum_s W_s 2^(log2 10 * log10 sigma_s), W_s = x_s c 10^off_s 2^-shift
       v2 chA[kPairs], chB[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chA[p] = chB[p] = pk(0.f);
       if constexpr (KT > 0) {
         // every setup of the batch has K = KT or KT - 1 absorbers; a padded
-        // absorber has weight 0 and reads finite rows of the stage
+        // absorber has weight 0 and reads finite values of the stage
 #pragma unroll
         for (int s = 0; s < KT; s += 2) {
           const v2 w0 = sW2[s], w1 = sW2[s + 1];
 #pragma unroll
           for (int p = 0; p < kPairs; ++p) {
-            const int o = s * kTileNu + 64 * p;
-            const v2 p0 = lds2f(rowa + o), p1 = lds2f(rowb + o);
-            const v2 q0 = lds2f(rowa + o + kTileNu), q1 = lds2f(rowb + o + kTileNu);
-            chA[p] = fma2(w0, row_value<LIN>(fma2(wT, sub2(p1, p0), p0)), chA[p]);
-            chB[p] = fma2(w1, row_value<LIN>(fma2(wT, sub2(q1, q0), q0)), chB[p]);
+            const RowDiff x = lds_rd(rows + s * 2 * kTileNu + 128 * p);
+            const RowDiff y = lds_rd(rows + (s + 1) * 2 * kTileNu + 128 * p);
+            chA[p] = fma2(w0, row_value<LIN>(fma2(wT, x.dg, x.g)), chA[p]);
+            chB[p] = fma2(w1, row_value<LIN>(fma2(wT, y.dg, y.g)), chB[p]);
           }
         }
       } else {
@@ -786,46 +788,43 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
         const v2 w0 = sW2[s], w1 = sW2[s + 1];
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {
-          const int o = s * kTileNu + 64 * p;
-          const v2 p0 = lds2f(rowa + o), p1 = lds2f(rowb + o);
-          const v2 q0 = lds2f(rowa + o + kTileNu), q1 = lds2f(rowb + o + kTileNu);
-          chA[p] = fma2(w0, row_value<LIN>(fma2(wT, sub2(p1, p0), p0)), chA[p]);
-          chB[p] = fma2(w1, row_value<LIN>(fma2(wT, sub2(q1, q0), q0)), chB[p]);
+          const RowDiff x = lds_rd(rows + s * 2 * kTileNu + 128 * p);
+          const RowDiff y = lds_rd(rows + (s + 1) * 2 * kTileNu + 128 * p);
+          chA[p] = fma2(w0, row_value<LIN>(fma2(wT, x.dg, x.g)), chA[p]);
+          chB[p] = fma2(w1, row_value<LIN>(fma2(wT, y.dg, y.g)), chB[p]);
         }
       }
       if (s < K) {
         const v2 w0 = sW2[s];
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {
-          const int o = s * kTileNu + 64 * p;
-          const v2 p0 = lds2f(rowa + o), p1 = lds2f(rowb + o);
-          chA[p] = fma2(w0, row_value<LIN>(fma2(wT, sub2(p1, p0), p0)), chA[p]);
+          const RowDiff x = lds_rd(rows + s * 2 * kTileNu + 128 * p);
+          chA[p] = fma2(w0, row_value<LIN>(fma2(wT, x.dg, x.g)), chA[p]);
         }
       }
       }
-      const float* ca = rowa + (size_t)2 * K * kTileNu;   // [a][pair], then [a+1][pair]
+      const float* ca = rows + (size_t)2 * K * kTileNu;   // CIA pair 0, then pair 1
       if (cia0) {
         const v2 w = pk(r3.y);
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {
-          const v2 c0 = lds2f(ca + 64 * p), c1 = lds2f(ca + 2 * kTileNu + 64 * p);
-          chB[p] = fma2(w, row_value<LIN>(fma2(wT, sub2(c1, c0), c0)), chB[p]);
+          const RowDiff x = lds_rd(ca + 128 * p);
+          chB[p] = fma2(w, row_value<LIN>(fma2(wT, x.dg, x.g)), chB[p]);
         }
       }
       if (cia1) {
         const v2 w = pk(r3.z);
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {
-          const v2 c0 = lds2f(ca + kTileNu + 64 * p), c1 = lds2f(ca + 3 * kTileNu + 64 * p);
-          chA[p] = fma2(w, row_value<LIN>(fma2(wT, sub2(c1, c0), c0)), chA[p]);
+          const RowDiff x = lds_rd(ca + 2 * kTileNu + 128 * p);
+          chA[p] = fma2(w, row_value<LIN>(fma2(wT, x.dg, x.g)), chA[p]);
         }
       }
       v2 chi[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
-      level_physics<NMU, PARA>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
-                               sMu, acc, E,
-                         st);
+      level_physics<NMU, PARA, SX>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
+                               sMu, sPoly, sThr, acc, E, st);
       __syncwarp();  // every lane is done with stage stg and record j before they are refilled
     }
     phase_base = ph + (unsigned)(L + 1);
@@ -893,17 +892,16 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       v2 chi[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
-      level_physics<NMU, PARA>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
-                               sMu, acc, E,
-                         st);
+      level_physics<NMU, PARA, SX>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
+                               sMu, sPoly, sThr, acc, E, st);
     }
   }
-  // I_0(mu_k) = S_0 + mu_k acc_k (telescoped linear source) or
+  // I_0(mu_k) = mu_k acc_k (telescoped linear source, S_0 included) or
   // acc_k + E_L S_L (parabolic source);  F+ = sum_k 2 pi w_k mu_k I_0(mu_k)
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
     float F0 = 0.f, F1 = 0.f;
-    const float2 s0 = up(st[p].S0), sL = up(st[p].Sp);
+    const float2 sL = up(st[p].Sp);
 #pragma unroll
     for (int k = 0; k < NMU; ++k) {
       const float2 f = up(acc[p][k]);
@@ -913,13 +911,27 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
         F0 = fmaf(wk, fmaf(e.x, sL.x, f.x), F0);
         F1 = fmaf(wk, fmaf(e.y, sL.y, f.y), F1);
       } else {
-        F0 = fmaf(wk, fmaf(mk, f.x, s0.x), F0);
-        F1 = fmaf(wk, fmaf(mk, f.y, s0.y), F1);
+        F0 = fmaf(wk, mk * f.x, F0);
+        F1 = fmaf(wk, mk * f.y, F1);
       }
     }
     if (in0[p]) out[kout[p]] = F0;
     if (in1[p]) out[kout[p] + 1] = F1;
   }
+}
+
+// Whether some level of sample i has h c nu / k T_j < 0.0625 at the first
+// point of the tile (the smallest wavenumber the warp sees), i.e. whether the
+// Planck function may need its small-x form anywhere in the sweep.  The
+// same test as the per-level one inside the sweep, taken once per item over
+// all levels (warp-uniform).
+__device__ __forceinline__ bool item_small_x(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile) {
+  const int lane = threadIdx.x & 31;
+  const LevRec* rec = a.recs + (size_t)i * a.rec_ld;
+  const float nu_min = (float)(T.nu0 + (double)((S.tile0 + tile) * kTileNu) * T.dnu);
+  bool f = false;
+  for (int j = lane; j < S.n_lev; j += 32) f |= -(__ldg(&rec[j].upl) * nu_min) * 0.6931471805599453f < 0.0625f;
+  return __any_sync(0xffffffffu, f);
 }
 
 template <int NMU, bool CACHED, int KT, bool LIN, bool PARA>
@@ -928,6 +940,8 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
   __shared__ int s_item;
   __shared__ const void* sPtr[HR2_MAX_SPECIES];
   __shared__ v2 sMnl[NMU], sImu[NMU], sMu[NMU];
+  __shared__ v2 sPoly[3 * NMU];   // a1..a3 of the thin-layer series per node
+  __shared__ float sThr[NMU];     // kThinLin * mu_k
   __shared__ v2 sA2[kMaxWarps][HR2_MAX_SPECIES];
   __shared__ v2 sAc2[kMaxWarps][HR2_MAX_SPECIES];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -972,6 +986,11 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
       sMnl[threadIdx.x] = pk(S.mu_nlog2e[threadIdx.x]);
       sImu[threadIdx.x] = pk(S.inv_mu[threadIdx.x]);
       sMu[threadIdx.x] = pk(S.mu[threadIdx.x]);
+      const float im = S.inv_mu[threadIdx.x];
+      sPoly[3 * threadIdx.x] = pk(im);
+      sPoly[3 * threadIdx.x + 1] = pk(-0.5f * im * im);
+      sPoly[3 * threadIdx.x + 2] = pk((1.f / 6.f) * im * im * im);
+      sThr[threadIdx.x] = kThinLin * S.mu[threadIdx.x];
     }
     const int local = sb * a.warps + warp;
     const bool active = local < plan->count[g];
@@ -985,9 +1004,14 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
       }
     }
     __syncthreads();
-    if (active)
-      solve_tile<NMU, CACHED, KT, LIN, PARA>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu, wp_,
-                                             phase_base);
+    if (active) {
+      if (item_small_x(a, S, T, i, tile))
+        solve_tile<NMU, CACHED, KT, LIN, PARA, true>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu,
+                                                     sPoly, sThr, wp_, phase_base);
+      else
+        solve_tile<NMU, CACHED, KT, LIN, PARA, false>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu,
+                                                      sPoly, sThr, wp_, phase_base);
+    }
   }
 }
 

@@ -394,61 +394,94 @@ cudaError_t build_w_values(const TablesDev* d_tab, int nu_first, double R, int n
 }
 
 // ------------------------------------------------------- level-gridded operand
-// lvl[t][j][a][s][c] = log2(10) * ((1 - w_p) v[sp][a][b_j][col] + w_p v[sp][a][b_j+1][col])
+// The p part of the bilinear interpolation (Sect. 2.8), done once per setup
+// in FP64 for the setup's kTileNu-point tiles t, levels j (p cell b_j,
+// weight w_p), absorbers s (table species sp = species[s]) and T rows a:
+//   g(a) = log2(10) ((1 - w_p) v[sp][a][b_j][col] + w_p v[sp][a][b_j+1][col])
 // (log10 option) or (1 - w_p) 10^v[sp][a][b_j][col] + w_p 10^v[sp][a][b_j+1][col]
-// (linear option), v the stored FP16 value log10 sigma - off_s, for the
-// setup's kTileNu-point tiles t, levels j (p cell b_j, weight w_p), T rows a,
-// absorbers s (table species sp = species[s]) and columns c < kTileNu (table
-// column (tile0 + t)*kTileNu + c): the p part of the bilinear interpolation
-// (Sect. 2.8), done once per setup in FP64.  The rows of T cells a and a+1
-// of every absorber at one level form one contiguous block of 2 K x kTileNu
-// floats, fetched with a single bulk copy.
+// (linear option), v the stored FP16 value log10 sigma - off_s, table column
+// col = (tile0 + t) kTileNu + c.  It is stored per T cell a (T rows a and
+// a+1, n_T - 1 cells) as the row g(a) and the difference g(a+1) - g(a), the
+// two interleaved per pair of neighbouring columns:
+//   lvl[t][j][a][s][q] = { g(a)[2q], g(a)[2q+1], (g(a+1)-g(a))[2q], (g(a+1)-g(a))[2q+1] }
+// for q < kTileNu / 2, so that one T cell of every absorber at one level is
+// one contiguous block of K x 2 kTileNu floats (one bulk copy), and the
+// kernel reads a pair's value and difference with one 16-byte load.
 struct SpeciesList {
   int sp[HR2_MAX_SPECIES];
 };
 
+__device__ __forceinline__ double level_value(const TablesDev& t, size_t row0, double wp, int linear) {
+  const double v0 = (double)__half2float(t.sig16[row0]);
+  const double v1 = (double)__half2float(t.sig16[row0 + t.nu_pad]);
+  return linear ? (1.0 - wp) * exp10(v0) + wp * exp10(v1) : kLog2_10 * ((1.0 - wp) * v0 + wp * v1);
+}
+
 __global__ void k_level_cache(const TablesDev* tab, const LevelDev* lev, int n_species, SpeciesList list, int n_lev,
                               int tile0, int n_tiles, int linear, float* out) {
   const TablesDev& t = *tab;
-  const long long total = (long long)n_tiles * n_lev * t.n_T * n_species * kTileNu;
+  const int n_cells = t.n_T - 1;
+  const long long total = (long long)n_tiles * n_lev * n_cells * n_species * (2 * kTileNu);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     long long r = idx;
-    const int c = (int)(r % kTileNu);
-    r /= kTileNu;
+    const int e = (int)(r % 4);
+    r /= 4;
+    const int q = (int)(r % (kTileNu / 2));
+    r /= kTileNu / 2;
     const int s = (int)(r % n_species);
     r /= n_species;
-    const int a = (int)(r % t.n_T);
-    r /= t.n_T;
+    const int a = (int)(r % n_cells);
+    r /= n_cells;
     const int j = (int)(r % n_lev);
     const int tt = (int)(r / n_lev);
     const LevelDev lv = lev[j];
+    const int c = 2 * q + (e & 1);
     const size_t row0 = (((size_t)list.sp[s] * t.n_T + a) * t.n_p + lv.pcell) * t.nu_pad + (size_t)(tile0 + tt) * kTileNu + c;
-    const double v0 = (double)__half2float(t.sig16[row0]);
-    const double v1 = (double)__half2float(t.sig16[row0 + t.nu_pad]);
-    out[idx] = linear ? (float)((1.0 - lv.wp64) * exp10(v0) + lv.wp64 * exp10(v1))
-                      : (float)(kLog2_10 * ((1.0 - lv.wp64) * v0 + lv.wp64 * v1));
+    const double g0 = level_value(t, row0, lv.wp64, linear);
+    if (e < 2) {
+      out[idx] = (float)g0;
+    } else {
+      const double g1 = level_value(t, row0 + (size_t)t.n_p * t.nu_pad, lv.wp64, linear);
+      out[idx] = (float)(g1 - g0);
+    }
   }
 }
 
-// cia[t][a][p][c] = log2(10) * v_cia[p][a][(tile0 + t)*kTileNu + c] (log10
-// option) or 10^v_cia[...] (linear option); 0 for an absent pair
+// CIA operand, per tile t, T cell a and pair p, the same interleaving of the
+// row h(a) and the difference h(a+1) - h(a), h(a) = log2(10) v_cia[p][a][col]
+// (log10 option) or 10^v_cia[p][a][col] (linear option):
+//   cia[t][a][p][q] = { h(a)[2q], h(a)[2q+1], (h(a+1)-h(a))[2q], (h(a+1)-h(a))[2q+1] }
+// (zeros for an absent pair)
 __global__ void k_cia_cache(const TablesDev* tab, int tile0, int n_tiles, int linear, float* out) {
   const TablesDev& t = *tab;
-  const long long total = (long long)n_tiles * t.n_T * 2 * kTileNu;
+  const int n_cells = t.n_T - 1;
+  const long long total = (long long)n_tiles * n_cells * 2 * (2 * kTileNu);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     long long r = idx;
-    const int c = (int)(r % kTileNu);
-    r /= kTileNu;
+    const int e = (int)(r % 4);
+    r /= 4;
+    const int q = (int)(r % (kTileNu / 2));
+    r /= kTileNu / 2;
     const int p = (int)(r % 2);
     r /= 2;
-    const int a = (int)(r % t.n_T);
-    const int tt = (int)(r / t.n_T);
-    const double v = t.has_cia[p] ? (double)__half2float(
-                                        t.cia16[((size_t)p * t.n_T + a) * t.nu_pad + (size_t)(tile0 + tt) * kTileNu + c])
-                                  : 0.0;
-    out[idx] = !t.has_cia[p] ? 0.f : (linear ? (float)exp10(v) : (float)(kLog2_10 * v));
+    const int a = (int)(r % n_cells);
+    const int tt = (int)(r / n_cells);
+    if (!t.has_cia[p]) {
+      out[idx] = 0.f;
+      continue;
+    }
+    const size_t col = (size_t)(tile0 + tt) * kTileNu + 2 * q + (e & 1);
+    const double v0 = (double)__half2float(t.cia16[((size_t)p * t.n_T + a) * t.nu_pad + col]);
+    const double h0 = linear ? exp10(v0) : kLog2_10 * v0;
+    if (e < 2) {
+      out[idx] = (float)h0;
+    } else {
+      const double v1 = (double)__half2float(t.cia16[((size_t)p * t.n_T + a + 1) * t.nu_pad + col]);
+      const double h1 = linear ? exp10(v1) : kLog2_10 * v1;
+      out[idx] = (float)(h1 - h0);
+    }
   }
 }
 
