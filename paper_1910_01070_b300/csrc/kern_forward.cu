@@ -186,8 +186,9 @@ __global__ void k_prep(FwdArgs a) {
     r.upl_lo = (float)(upl - (double)r.upl);
     r.half_dp = (float)ldexp(lv.half_dp64, (int)shift);
     r.rdnu = (float)exp(-kC2 * T.dnu / Tj);
-    r.wh2h2 = (float)exp2(b0);
-    r.wh2he = (float)exp2(b1);
+    // zero for an absent pair: the cached path adds both pairs unconditionally
+    r.wh2h2 = T.has_cia[0] ? (float)exp2(b0) : 0.f;
+    r.wh2he = T.has_cia[1] ? (float)exp2(b1) : 0.f;
     r.dtau_cloud = 0.f;
     if (S.cloud && j > 0 && pcb > pct) {   // layer j-1 between levels j-1 and j
       const double lo = fmax(S.levels[j - 1].p_dyn64, pct), hi = fmin(lv.p_dyn64, pcb);
@@ -463,6 +464,33 @@ __device__ __forceinline__ void issue_stage(const WarpPipe& w, int st, int K, co
     if (rec_a) bulk_copy(w.recs + (size_t)slot_a * 16, rec_a, (unsigned)sizeof(LevRec), bar);
     if (rec_b) bulk_copy(w.recs + (size_t)slot_b * 16, rec_b, (unsigned)sizeof(LevRec), bar);
   }
+}
+
+// The in-sweep refill of a stage as straight-line code: every lane runs it,
+// and only where `on` (lane 0, a level left to fetch) do the predicated
+// instructions arm the stage's barrier with `bytes` and issue the copies
+// (rows if do_rows, the CIA pairs of the cell if do_cia, one level record if
+// do_rec), so the sweep has no branch around them.
+__device__ __forceinline__ void issue_stage_pred(unsigned long long* bar, unsigned bytes, bool on, float* dst_rows,
+                                                 const float* src_rows, unsigned rows_bytes, bool do_rows,
+                                                 float* dst_cia, const float* src_cia, bool do_cia, float* dst_rec,
+                                                 const LevRec* src_rec, bool do_rec) {
+  asm volatile(
+      "{\n"
+      " .reg .pred pon, prw, pci, prc;\n"
+      " setp.ne.b32 pon, %0, 0;\n"
+      " setp.ne.and.b32 prw, %1, 0, pon;\n"
+      " setp.ne.and.b32 pci, %2, 0, pon;\n"
+      " setp.ne.and.b32 prc, %3, 0, pon;\n"
+      " @pon mbarrier.arrive.expect_tx.shared::cta.b64 _, [%4], %5;\n"
+      " @prw cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%6], [%7], %8, [%4];\n"
+      " @pci cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%9], [%10], %13, [%4];\n"
+      " @prc cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%11], [%12], %14, [%4];\n"
+      "}\n" ::"r"((int)on),
+      "r"((int)do_rows), "r"((int)do_cia), "r"((int)do_rec), "r"(smem_u32(bar)), "r"(bytes), "r"(smem_u32(dst_rows)),
+      "l"(src_rows), "r"(rows_bytes), "r"(smem_u32(dst_cia)), "l"(src_cia), "r"(smem_u32(dst_rec)), "l"(src_rec),
+      "n"(4 * kTileNu * (int)sizeof(float)), "n"((int)sizeof(LevRec))
+      : "memory");
 }
 
 // Absorption per molecule from a T-interpolated operand value: 2^x on the
@@ -747,13 +775,25 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
         return;
       }
       __syncwarp();
-      if (j < L) {
-        const int acell_n = __float_as_int(wp_.recs[((j + 1) & 3) * 16 + 8]);
+      {
+        // refill the other stage with level j+1 (rows of its T cell, taken
+        // from record j+1, and the CIA pairs where that stage holds another
+        // cell) and record j+2
+        const bool more = j < L;
+        const int acell_n = more ? __float_as_int(wp_.recs[((j + 1) & 3) * 16 + 8]) : 0;
         const int sn = (int)((g + 1u) & 1u);
-        const bool copy_cia = has_cia && (sn ? cia_cell1 : cia_cell0) != acell_n;
-        if (sn) cia_cell1 = acell_n; else cia_cell0 = acell_n;
-        issue_stage(wp_, sn, K, lvl_tile + (size_t)(j + 1) * lvl_step, cia_tile, acell_n, copy_cia,
-                    (j + 2 <= L) ? rec + (j + 2) : nullptr, (j + 2) & 3, nullptr, 0, lane);
+        const bool copy_cia = more && has_cia && (sn ? cia_cell1 : cia_cell0) != acell_n;
+        cia_cell1 = (more && sn) ? acell_n : cia_cell1;
+        cia_cell0 = (more && !sn) ? acell_n : cia_cell0;
+        const bool do_rec = j + 2 <= L;
+        const unsigned rows_bytes = (unsigned)(2 * K * kTileNu * sizeof(float));
+        const unsigned bytes = rows_bytes + (copy_cia ? 4u * kTileNu * (unsigned)sizeof(float) : 0u) +
+                               (do_rec ? (unsigned)sizeof(LevRec) : 0u);
+        float* dst = wp_.rows + (size_t)sn * (2 * K + 4) * kTileNu;
+        issue_stage_pred(wp_.bar + sn, bytes, more && lane == 0, dst,
+                         lvl_tile + (size_t)(j + 1) * lvl_step + (size_t)acell_n * 2 * K * kTileNu, rows_bytes,
+                         rows_bytes != 0u, dst + (size_t)2 * K * kTileNu, cia_tile + (size_t)acell_n * 4 * kTileNu,
+                         copy_cia, wp_.recs + (size_t)((j + 2) & 3) * 16, rec + (j + 2), do_rec);
       }
       const float* rj = wp_.recs + (j & 3) * 16;
       const float4 r0 = *reinterpret_cast<const float4*>(rj);
@@ -803,21 +843,17 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
         }
       }
       }
-      const float* ca = rows + (size_t)2 * K * kTileNu;   // CIA pair 0, then pair 1
-      if (cia0) {
-        const v2 w = pk(r3.y);
+      // CIA pair 0, then pair 1; an absent pair has weight 0 and zero rows in
+      // the operand (the stage holds finite values for it either way)
+      const float* ca = rows + (size_t)2 * K * kTileNu;
+      {
+        const v2 w0 = pk(r3.y), w1 = pk(r3.z);
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {
           const RowDiff x = lds_rd(ca + 128 * p);
-          chB[p] = fma2(w, row_value<LIN>(fma2(wT, x.dg, x.g)), chB[p]);
-        }
-      }
-      if (cia1) {
-        const v2 w = pk(r3.z);
-#pragma unroll
-        for (int p = 0; p < kPairs; ++p) {
-          const RowDiff x = lds_rd(ca + 2 * kTileNu + 128 * p);
-          chA[p] = fma2(w, row_value<LIN>(fma2(wT, x.dg, x.g)), chA[p]);
+          const RowDiff y = lds_rd(ca + 2 * kTileNu + 128 * p);
+          chB[p] = fma2(w0, row_value<LIN>(fma2(wT, x.dg, x.g)), chB[p]);
+          chA[p] = fma2(w1, row_value<LIN>(fma2(wT, y.dg, y.g)), chA[p]);
         }
       }
       v2 chi[kPairs];
