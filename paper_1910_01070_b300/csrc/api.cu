@@ -667,6 +667,22 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
       goto fail_tmp;
     }
   }
+  {
+    float4* d_nu = nullptr;
+    float2* d_c1n = nullptr;
+    const size_t n_pairs = (size_t)h.n_tiles * (kTileNu / 2);
+    if ((rc = dalloc_t(ctx, &d_nu, n_pairs))) goto fail_tmp;
+    track(d_nu);
+    if ((rc = dalloc_t(ctx, &d_c1n, n_pairs))) goto fail_tmp;
+    track(d_c1n);
+    h.nu_pair = d_nu;
+    h.c1n_pair = d_c1n;
+    if ((e = build_nu_pairs(tab->dev, h.tile0, h.n_tiles, d_nu, d_c1n, 0)) != cudaSuccess ||
+        (e = cudaDeviceSynchronize()) != cudaSuccess) {
+      rc = fail(HR2_ECUDA, "setup wavenumber constants: %s", cudaGetErrorString(e));
+      goto fail_tmp;
+    }
+  }
   if (d->level_cache && th.storage == HR2_STORE_FP16_OFFSET) {
     float *d_lvl = nullptr, *d_cia = nullptr;
     // per tile, level, T cell and absorber: 2 kTileNu floats (row and T difference)

@@ -351,6 +351,7 @@ constexpr float kThinLin = 0.03125f;
 // (|S| < 3e18); a layer this thin is transparent either way (its factor
 // (1 - e^{-D}) / dtau is 1/mu to FP32 precision below dtau ~ 1e-8)
 constexpr float kTinyTau = 1e-20f;
+constexpr float kLog2eF = 1.44269504088896341f;
 
 // One warp computes one sample on one kTileNu-point wavenumber tile (kPairs
 // packed pairs of points per lane), sweeping the levels from the top (j = 0)
@@ -531,8 +532,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
                                               const float rdnu, const float half_dp, const float dtau_cloud,
                                               float& hdp_prev,
                                               const NuConst& nc, const float thin_dtau, const float thin_all,
-                                              const v2* sMnl, const v2* sImu, const v2* sMu, const v2* sPoly,
-                                              const float* sThr, v2 (&acc)[kPairs][NMU],
+                                              const v2* sMnl, const v2* sImu, const v2* sMu, v2 (&acc)[kPairs][NMU],
                                               v2 (&E)[kPairs][NMU], LevelState (&st)[kPairs]) {
   const float kLn2f = 0.6931471805599453f;
   const v2 one = pk(1.f);
@@ -568,34 +568,35 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
     // (bottom, S_j): it adds (E_{j-1} - E_j) (S_j - S_{j-1}) / dtau to mu's
     // sum, with E_{j-1} - E_j = E_{j-1} (1 - e^{-D}), D = dtau / mu.
     // (S_j - S_{j-1}) / dtau is shared by the nodes.  Where D < kThinLin,
-    // 1 - e^{-D} is the polynomial P_k(dtau) = dtau (a1 + dtau (a2 + dtau a3)),
-    // a_n = (-1)^(n+1) / (n! mu_k^n) (sPoly), chosen per point without a
-    // branch.  Level 0 enters the same way as a layer of optical depth
+    // 1 - e^{-D} is the polynomial D (1 - D/2 + D^2/6), chosen per point
+    // without a branch.  Level 0 enters the same way as a layer of optical depth
     // kTinyTau below a zero source (nothing above it has been added yet):
     // it adds S_0 / mu, the S_0 term of I_0 = S_0 + mu sum_l ..., so that
     // I_0(mu) = mu * acc.  Nodes beyond the setup's count are padded with
     // mu = 1 and zero weight.
     (void)thin_dtau;
     (void)thin_all;
+    // st.tau holds -log2(e) tau_j, so that E_j = 2^(st.tau / mu_k)
     v2 dt[kPairs], rdS[kPairs];
 #pragma unroll
     for (int p = 0; p < kPairs; ++p) {
       // gas trapezoid + gray cloud + kTinyTau
       dt[p] = fma2(pk(hdp_prev), add2(chi[p], st[p].chip), pk(dtau_cloud + kTinyTau));
       rdS[p] = mul2(sub2(Sj[p], st[p].Sp), rcp_2(dt[p]));
-      st[p].tau = add2(st[p].tau, dt[p]);
+      st[p].tau = fma2(dt[p], pk(-kLog2eF), st[p].tau);
     }
+    const v2 c2 = pk(-0.5f), c3 = pk(1.f / 6.f);
 #pragma unroll
     for (int k = 0; k < NMU; ++k) {
-      const v2 mk = sMnl[k], a1 = sPoly[3 * k], a2 = sPoly[3 * k + 1], a3 = sPoly[3 * k + 2];
-      const float thr = sThr[k];   // kThinLin * mu_k
+      const v2 im = sImu[k];   // 1 / mu_k
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
-        const v2 En = ex2_2(mul2(st[p].tau, mk));   // e^{-tau_j / mu}
+        const v2 En = ex2_2(mul2(st[p].tau, im));   // e^{-tau_j / mu}
+        const v2 D = mul2(dt[p], im);
         const v2 X = sub2(E[p][k], En);
-        const v2 Xs = mul2(E[p][k], mul2(dt[p], fma2(dt[p], fma2(dt[p], a3, a2), a1)));
-        const float2 dtf = up(dt[p]), xf = up(X), xsf = up(Xs);
-        const v2 cc = pk(dtf.x < thr ? xsf.x : xf.x, dtf.y < thr ? xsf.y : xf.y);
+        const v2 Xs = mul2(E[p][k], mul2(D, fma2(D, fma2(D, c3, c2), one)));
+        const float2 Df = up(D), xf = up(X), xsf = up(Xs);
+        const v2 cc = pk(Df.x < kThinLin ? xsf.x : xf.x, Df.y < kThinLin ? xsf.y : xf.y);
         acc[p][k] = fma2(cc, rdS[p], acc[p][k]);
         E[p][k] = En;
       }
@@ -683,8 +684,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
 template <int NMU, bool CACHED, int KT, bool LIN, bool PARA, bool SX>
 __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
                                            const v2* sA2, const v2* sAc2, const void* const* sPtr,
-                                           const v2* sMnl, const v2* sImu, const v2* sMu, const v2* sPoly,
-                                           const float* sThr, const WarpPipe& wp_,
+                                           const v2* sMnl, const v2* sImu, const v2* sMu, const WarpPipe& wp_,
                                            unsigned& phase_base) {
   const int lane = threadIdx.x & 31;
   const SampleDev& sd = a.samp[i];
@@ -709,11 +709,13 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
   NuConst nc;
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
-    const double nu0d = T.nu0 + (double)(col + 64 * p) * T.dnu, nu1d = nu0d + T.dnu;
-    nc.nu0[p] = (float)nu0d;                               // head
-    nc.nl0[p] = (float)(nu0d - (double)nc.nu0[p]);         // tail
-    nc.ratio[p] = (float)(nu1d / nu0d);
-    nc.c1n[p] = pk((float)(kC1 * nu0d * nu0d * nu0d), (float)(kC1 * nu1d * nu1d * nu1d));
+    const int q = tile * (kTileNu / 2) + lane + 32 * p;   // setup-local pair of columns
+    const float4 f = __ldg(&S.nu_pair[q]);
+    const float2 c = __ldg(&S.c1n_pair[q]);
+    nc.nu0[p] = f.x;    // head
+    nc.nl0[p] = f.y;    // tail
+    nc.ratio[p] = f.z;
+    nc.c1n[p] = pk(c.x, c.y);
   }
   // dtau below which some node is thin (largest mu, padded nodes included),
   // and below which every node is (smallest mu)
@@ -760,9 +762,9 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     if (ph & 1u) cia_cell1 = acell0; else cia_cell0 = acell0;
     issue_stage(wp_, (int)(ph & 1u), K, lvl_tile, cia_tile, acell0, has_cia, rec, 0, L >= 1 ? rec + 1 : nullptr, 1,
                 lane);
-    // unrolled by two so that the loop-carried sweep state alternates between
-    // two register sets instead of being moved back at the end of each level
-#pragma unroll 2
+    // unrolled so that the loop-carried sweep state rotates through register
+    // sets instead of being moved back at the end of each level
+#pragma unroll 4
     for (int j = 0; j <= L; ++j) {
       const unsigned g = ph + (unsigned)j;
       const int stg = (int)(g & 1u);
@@ -860,7 +862,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
       level_physics<NMU, PARA, SX>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
-                               sMu, sPoly, sThr, acc, E, st);
+                               sMu, acc, E, st);
       __syncwarp();  // every lane is done with stage stg and record j before they are refilled
     }
     phase_base = ph + (unsigned)(L + 1);
@@ -929,7 +931,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
       level_physics<NMU, PARA, SX>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
-                               sMu, sPoly, sThr, acc, E, st);
+                               sMu, acc, E, st);
     }
   }
   // I_0(mu_k) = mu_k acc_k (telescoped linear source, S_0 included) or
@@ -976,8 +978,6 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
   __shared__ int s_item;
   __shared__ const void* sPtr[HR2_MAX_SPECIES];
   __shared__ v2 sMnl[NMU], sImu[NMU], sMu[NMU];
-  __shared__ v2 sPoly[3 * NMU];   // a1..a3 of the thin-layer series per node
-  __shared__ float sThr[NMU];     // kThinLin * mu_k
   __shared__ v2 sA2[kMaxWarps][HR2_MAX_SPECIES];
   __shared__ v2 sAc2[kMaxWarps][HR2_MAX_SPECIES];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1022,11 +1022,6 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
       sMnl[threadIdx.x] = pk(S.mu_nlog2e[threadIdx.x]);
       sImu[threadIdx.x] = pk(S.inv_mu[threadIdx.x]);
       sMu[threadIdx.x] = pk(S.mu[threadIdx.x]);
-      const float im = S.inv_mu[threadIdx.x];
-      sPoly[3 * threadIdx.x] = pk(im);
-      sPoly[3 * threadIdx.x + 1] = pk(-0.5f * im * im);
-      sPoly[3 * threadIdx.x + 2] = pk((1.f / 6.f) * im * im * im);
-      sThr[threadIdx.x] = kThinLin * S.mu[threadIdx.x];
     }
     const int local = sb * a.warps + warp;
     const bool active = local < plan->count[g];
@@ -1043,10 +1038,10 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
     if (active) {
       if (item_small_x(a, S, T, i, tile))
         solve_tile<NMU, CACHED, KT, LIN, PARA, true>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu,
-                                                     sPoly, sThr, wp_, phase_base);
+                                                     wp_, phase_base);
       else
         solve_tile<NMU, CACHED, KT, LIN, PARA, false>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu,
-                                                      sPoly, sThr, wp_, phase_base);
+                                                      wp_, phase_base);
     }
   }
 }

@@ -485,6 +485,23 @@ __global__ void k_cia_cache(const TablesDev* tab, int tile0, int n_tiles, int li
   }
 }
 
+// Wavenumber constants of the FP32 forward kernel per pair of columns.
+__global__ void k_nu_pairs(const TablesDev* tab, int tile0, int n_pairs, float4* nu, float2* c1n) {
+  const TablesDev& t = *tab;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n_pairs; q += gridDim.x * blockDim.x) {
+    const double nu0 = t.nu0 + (double)(tile0 * kTileNu + 2 * q) * t.dnu, nu1 = nu0 + t.dnu;
+    const float hi = (float)nu0;
+    nu[q] = make_float4(hi, (float)(nu0 - (double)hi), (float)(nu1 / nu0), 0.f);
+    c1n[q] = make_float2((float)(kC1 * nu0 * nu0 * nu0), (float)(kC1 * nu1 * nu1 * nu1));
+  }
+}
+
+cudaError_t build_nu_pairs(const TablesDev* d_tab, int tile0, int n_tiles, float4* d_nu, float2* d_c1n, cudaStream_t s) {
+  const int n_pairs = n_tiles * (kTileNu / 2);
+  k_nu_pairs<<<(n_pairs + 255) / 256, 256, 0, s>>>(d_tab, tile0, n_pairs, d_nu, d_c1n);
+  return cudaGetLastError();
+}
+
 cudaError_t build_level_cache(const TablesDev* d_tab, const SetupDev& h, float* d_lvl, float* d_cia, cudaStream_t s) {
   SpeciesList list{};
   for (int i = 0; i < h.n_species; ++i) list.sp[i] = h.species[i];
