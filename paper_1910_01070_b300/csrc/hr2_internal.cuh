@@ -155,8 +155,28 @@ struct __align__(16) LevRec {
   float rdnu;        // e^{-h c dnu / (k T_j)}: Planck factor between neighbouring points
   float wh2h2;       // 2^(bh2h2 exactly): the H2-H2 factor as a weight
   float wh2he;       // 2^(bh2he exactly)
-  float dtau_cloud;  // gray cloud optical depth of layer j-1 (between levels j-1 and j)
+  float dtau_cloud;  // gray cloud optical depth of layer j-1 (between levels j-1 and j),
+                     // + kTinyTau on the linear-source path
 };
+
+// The same record as the level-gridded (cached) sweep reads it: the factors
+// it applies to packed pairs of wavenumbers are stored twice, so that they
+// load straight into register pairs.  Written instead of LevRec for setups
+// with the level-gridded operand (a batch holds setups of one kind).
+struct __align__(16) LevRecC {
+  float wT[2];       // weight of T_grid[a_j + 1]
+  float wh2h2[2];    // H2-H2 factor as a weight (0 for an absent pair)
+  float wh2he[2];    // H2-He factor as a weight (0 for an absent pair)
+  float half_dp[2];  // 2^shift (p_{j+1} - p_j) / 2, dyn cm^-2 (layer j)
+  float dtc[2];      // gray cloud optical depth of layer j-1 (+ kTinyTau, linear source)
+  float upl;         // -log2(e) h c / (k T_j): e^{-hc nu/kT} = 2^(upl nu)
+  float rdnu;        // e^{-h c dnu / (k T_j)}
+  int acell;         // a_j
+  int pad[3];
+};
+static_assert(sizeof(LevRecC) == sizeof(LevRec), "both level records are 64 bytes");
+constexpr int kRecCAcell = 12;   // float index of LevRecC::acell
+constexpr int kRecCUpl = 10;     // float index of LevRecC::upl
 
 // Per-sample scalars written by the prep kernel.
 struct SampleDev {

@@ -11,6 +11,7 @@
 //   k_bins       instrument profile + binning via the setup's operator W
 //   k_lnl        Gaussian log-likelihood, FP64, fixed-order warp reduction
 #include <math.h>
+#include <stddef.h>
 
 #include "hr2_internal.cuh"
 
@@ -90,6 +91,13 @@ __device__ void grid_cell(const double* grid, int n, double v, int& a, double& w
   a = lo;
   w = (v - grid[lo]) / (grid[lo + 1] - grid[lo]);
 }
+
+// added to every layer's optical depth on the linear-source path (in the
+// level record), so that dtau > 0 and (S_j - S_{j-1}) / dtau stays finite in
+// an opacity-free layer (|S| < 3e18); a layer this thin is transparent either
+// way (its factor (1 - e^{-D}) / dtau is 1/mu to FP32 precision below
+// dtau ~ 1e-8)
+constexpr float kTinyTau = 1e-20f;
 
 // ------------------------------------------------------------------ prep
 // One warp per sample.  Free chemistry (Sect. 2.4): absorber mixing ratios
@@ -194,7 +202,22 @@ __global__ void k_prep(FwdArgs a) {
       const double lo = fmax(S.levels[j - 1].p_dyn64, pct), hi = fmin(lv.p_dyn64, pcb);
       if (hi > lo) r.dtau_cloud = (float)(tau_c * (hi - lo) / (pcb - pct));
     }
-    rec[j] = r;
+    if (S.sc != HR2_SC_PARABOLIC) r.dtau_cloud += kTinyTau;
+    if (S.cached) {
+      LevRecC rc;
+      rc.wT[0] = rc.wT[1] = r.wT;
+      rc.wh2h2[0] = rc.wh2h2[1] = r.wh2h2;
+      rc.wh2he[0] = rc.wh2he[1] = r.wh2he;
+      rc.half_dp[0] = rc.half_dp[1] = r.half_dp;
+      rc.dtc[0] = rc.dtc[1] = r.dtau_cloud;
+      rc.upl = r.upl;
+      rc.rdnu = r.rdnu;
+      rc.acell = acell;
+      rc.pad[0] = rc.pad[1] = rc.pad[2] = 0;
+      reinterpret_cast<LevRecC*>(rec)[j] = rc;
+    } else {
+      rec[j] = r;
+    }
   }
   status = __reduce_or_sync(0xffffffffu, status);
   if (lane == 0) {
@@ -346,11 +369,6 @@ constexpr float kThinD = 0.25f;
 // from the difference of the two exponentials (rounding ~2^-22 / D <= 7.6e-6
 // relative, ~1e-6 typical)
 constexpr float kThinLin = 0.03125f;
-// added to every layer's optical depth on the linear-source path, so that
-// dtau > 0 and (S_j - S_{j-1}) / dtau stays finite in an opacity-free layer
-// (|S| < 3e18); a layer this thin is transparent either way (its factor
-// (1 - e^{-D}) / dtau is 1/mu to FP32 precision below dtau ~ 1e-8)
-constexpr float kTinyTau = 1e-20f;
 constexpr float kLog2eF = 1.44269504088896341f;
 
 // One warp computes one sample on one kTileNu-point wavenumber tile (kPairs
@@ -382,6 +400,11 @@ __device__ __forceinline__ v2 ldf2(const float* p) {
 // a pair of columns of the level-gridded operand: value and T difference
 struct __align__(16) RowDiff {
   v2 g, dg;
+};
+// the last 16 bytes of a LevRecC before its cell index
+struct __align__(16) RecTail {
+  v2 dtc;
+  float upl, rdnu;
 };
 __device__ __forceinline__ RowDiff lds_rd(const float* p) { return *reinterpret_cast<const RowDiff*>(p); }
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -528,28 +551,26 @@ struct LevelState {
 // level of this sample may have h c nu / k T < 0.0625 on this tile, where
 // 1 - e^{-x} of the Planck function needs its series (decided per item).
 template <int NMU, bool PARA, bool SX>
-__device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], const float upl, const float upl_lo,
-                                              const float rdnu, const float half_dp, const float dtau_cloud,
-                                              float& hdp_prev,
+__device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], const float upl, const float rdnu,
+                                              const v2 half_dp, const v2 dtc, v2& hdp_prev,
                                               const NuConst& nc, const float thin_dtau, const float thin_all,
                                               const v2* sMnl, const v2* sImu, const v2* sMu, v2 (&acc)[kPairs][NMU],
                                               v2 (&E)[kPairs][NMU], LevelState (&st)[kPairs]) {
   const float kLn2f = 0.6931471805599453f;
   const v2 one = pk(1.f);
-  // Planck source.  t at a pair's first point: the exponent upl * nu to
-  // ~2^-46 (head product, its exact FMA error and the tail cross terms),
-  // t = 2^head (1 + ln2 * tail); the neighbour point is t * e^{-hc dnu/kT}.
-  // hc nu / kT is smallest at pair 0's first point, which decides whether
-  // the small-x form is needed anywhere in the warp.
+  // Planck source.  t = e^{-x}, x = hc nu / kT, at a pair's first point is
+  // 2^(upl nu) from the FP32 product (relative error of x ~2e-7: t to
+  // ~2e-7 x, <= 2e-5 where t is above FP32's range floor); the neighbour
+  // point is t * e^{-hc dnu/kT}.  hc nu / kT is smallest at pair 0's first
+  // point, which decides whether the small-x form is needed anywhere in the
+  // warp.
   v2 Sj[kPairs];
   bool small_x = false;
   if constexpr (SX) small_x = __any_sync(0xffffffffu, -(upl * nc.nu0[0]) * kLn2f < 0.0625f);
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
     const float p0 = upl * nc.nu0[p];
-    const float y0 = fmaf(upl, nc.nu0[p], -p0) + fmaf(upl, nc.nl0[p], upl_lo * nc.nu0[p]);
-    const float h0 = ex2f(p0);
-    const float t0 = fmaf(h0, y0 * kLn2f, h0);
+    const float t0 = ex2f(p0);
     const v2 t = pk(t0, t0 * rdnu);
     v2 om = sub2(one, t);
     if (SX && small_x) {
@@ -581,7 +602,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
 #pragma unroll
     for (int p = 0; p < kPairs; ++p) {
       // gas trapezoid + gray cloud + kTinyTau
-      dt[p] = fma2(pk(hdp_prev), add2(chi[p], st[p].chip), pk(dtau_cloud + kTinyTau));
+      dt[p] = fma2(hdp_prev, add2(chi[p], st[p].chip), dtc);
       rdS[p] = mul2(sub2(Sj[p], st[p].Sp), rcp_2(dt[p]));
       st[p].tau = fma2(dt[p], pk(-kLog2eF), st[p].tau);
     }
@@ -607,7 +628,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
     float dmin = 3.0e38f;
 #pragma unroll
     for (int p = 0; p < kPairs; ++p) {
-      dt[p] = fma2(pk(hdp_prev), add2(chi[p], st[p].chip), pk(dtau_cloud));   // gas trapezoid + gray cloud
+      dt[p] = fma2(hdp_prev, add2(chi[p], st[p].chip), dtc);   // gas trapezoid + gray cloud
       rr[p] = rcp_2(dt[p]);
       dS[p] = sub2(Sj[p], st[p].Sp);
       st[p].tau = add2(st[p].tau, dt[p]);
@@ -738,7 +759,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
   LevelState st[kPairs];
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) st[p].chip = st[p].Sp = st[p].tau = st[p].dup = st[p].dtp = pk(0.f);
-  float hdp_prev = 0.f;
+  v2 hdp_prev = pk(0.f);
 
   if constexpr (CACHED) {
     const v2* sW2 = sA2;   // cached path: per-sample absorber weights
@@ -757,7 +778,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     const size_t lvl_step = (size_t)(nT - 1) * K * 2 * kTileNu;
     const bool has_cia = cia0 || cia1;
     const unsigned ph = phase_base;
-    const int acell0 = __ldg(&rec[0].acell);
+    const int acell0 = __ldg(&reinterpret_cast<const LevRecC*>(rec)[0].acell);
     int cia_cell0 = -1, cia_cell1 = -1;   // T cell whose CIA rows stage 0 / 1 holds
     if (ph & 1u) cia_cell1 = acell0; else cia_cell0 = acell0;
     issue_stage(wp_, (int)(ph & 1u), K, lvl_tile, cia_tile, acell0, has_cia, rec, 0, L >= 1 ? rec + 1 : nullptr, 1,
@@ -782,7 +803,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
         // from record j+1, and the CIA pairs where that stage holds another
         // cell) and record j+2
         const bool more = j < L;
-        const int acell_n = more ? __float_as_int(wp_.recs[((j + 1) & 3) * 16 + 8]) : 0;
+        const int acell_n = more ? __float_as_int(wp_.recs[((j + 1) & 3) * 16 + kRecCAcell]) : 0;
         const int sn = (int)((g + 1u) & 1u);
         const bool copy_cia = more && has_cia && (sn ? cia_cell1 : cia_cell0) != acell_n;
         cia_cell1 = (more && sn) ? acell_n : cia_cell1;
@@ -797,12 +818,12 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
                          rows_bytes != 0u, dst + (size_t)2 * K * kTileNu, cia_tile + (size_t)acell_n * 4 * kTileNu,
                          copy_cia, wp_.recs + (size_t)((j + 2) & 3) * 16, rec + (j + 2), do_rec);
       }
+      // record j (LevRecC): {wT, wT, wh2h2, wh2h2}, {wh2he, wh2he, half_dp,
+      // half_dp}, {dtc, dtc, upl, rdnu}
       const float* rj = wp_.recs + (j & 3) * 16;
-      const float4 r0 = *reinterpret_cast<const float4*>(rj);
-      const float4 r1 = *reinterpret_cast<const float4*>(rj + 4);
-      const float4 r2 = *reinterpret_cast<const float4*>(rj + 8);
-      const float4 r3 = *reinterpret_cast<const float4*>(rj + 12);
-      const v2 wT = pk(r0.y);
+      const RowDiff rq0 = lds_rd(rj), rq1 = lds_rd(rj + 4);
+      const RecTail rq2 = *reinterpret_cast<const RecTail*>(rj + 8);
+      const v2 wT = rq0.g;
       // stage: [s][q][row, T difference] for pairs q of columns; lane l's
       // pair p is q = l + 32 p
       const float* rows = wp_.rows + (size_t)stg * (2 * K + 4) * kTileNu + 4 * lane;
@@ -849,7 +870,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       // the operand (the stage holds finite values for it either way)
       const float* ca = rows + (size_t)2 * K * kTileNu;
       {
-        const v2 w0 = pk(r3.y), w1 = pk(r3.z);
+        const v2 w0 = rq0.dg, w1 = rq1.g;
 #pragma unroll
         for (int p = 0; p < kPairs; ++p) {
           const RowDiff x = lds_rd(ca + 128 * p);
@@ -861,7 +882,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       v2 chi[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
-      level_physics<NMU, PARA, SX>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
+      level_physics<NMU, PARA, SX>(j, chi, rq2.upl, rq2.rdnu, rq1.dg, rq2.dtc, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
                                sMu, acc, E, st);
       __syncwarp();  // every lane is done with stage stg and record j before they are refilled
     }
@@ -930,7 +951,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       v2 chi[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
-      level_physics<NMU, PARA, SX>(j, chi, r1.z, r2.y, r3.x, r1.w, r3.w, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
+      level_physics<NMU, PARA, SX>(j, chi, r1.z, r3.x, pk(r1.w), pk(r3.w), hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
                                sMu, acc, E, st);
     }
   }
@@ -968,7 +989,9 @@ __device__ __forceinline__ bool item_small_x(const FwdArgs& a, const SetupDev& S
   const LevRec* rec = a.recs + (size_t)i * a.rec_ld;
   const float nu_min = (float)(T.nu0 + (double)((S.tile0 + tile) * kTileNu) * T.dnu);
   bool f = false;
-  for (int j = lane; j < S.n_lev; j += 32) f |= -(__ldg(&rec[j].upl) * nu_min) * 0.6931471805599453f < 0.0625f;
+  const float* r = reinterpret_cast<const float*>(rec);
+  const int o = S.cached ? kRecCUpl : (int)(offsetof(LevRec, upl) / sizeof(float));
+  for (int j = lane; j < S.n_lev; j += 32) f |= -(__ldg(r + 16 * j + o) * nu_min) * 0.6931471805599453f < 0.0625f;
   return __any_sync(0xffffffffu, f);
 }
 
