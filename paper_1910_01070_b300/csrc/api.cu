@@ -684,17 +684,15 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
     }
   }
   if (d->level_cache && th.storage == HR2_STORE_FP16_OFFSET) {
-    float *d_lvl = nullptr, *d_cia = nullptr;
-    // per tile, level, T cell and absorber: 2 kTileNu floats (row and T difference)
-    const size_t per_tile = (size_t)h.n_lev * std::max(1, h.n_species) * (th.n_T - 1) * 2 * kTileNu;
+    float* d_lvl = nullptr;
+    // per tile, level, T cell and operand row (absorbers, then the two CIA
+    // pairs): 2 kTileNu floats (row and T difference)
+    const size_t per_tile = (size_t)h.n_lev * (h.n_species + 2) * (th.n_T - 1) * 2 * kTileNu;
     if ((rc = dalloc_t(ctx, &d_lvl, per_tile * h.n_tiles))) goto fail_tmp;
     track(d_lvl);
-    if ((rc = dalloc_t(ctx, &d_cia, (size_t)h.n_tiles * (th.n_T - 1) * 2 * 2 * kTileNu))) goto fail_tmp;
-    track(d_cia);
     h.lvl32 = d_lvl;
-    h.cia32 = d_cia;
     h.cached = 1;
-    if ((e = build_level_cache(tab->dev, h, d_lvl, d_cia, 0)) != cudaSuccess ||
+    if ((e = build_level_cache(tab->dev, h, d_lvl, 0)) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
       rc = fail(HR2_ECUDA, "setup level-gridded operand: %s", cudaGetErrorString(e));
       goto fail_tmp;

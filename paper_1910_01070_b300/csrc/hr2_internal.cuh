@@ -110,9 +110,9 @@ struct SetupDev {
   // the levels, FP32, columns local to the setup's tiles
   int cached;
   // per T cell a: the row of T row a and the difference to row a+1,
-  // interleaved per pair of columns ({g[2q], g[2q+1], dg[2q], dg[2q+1]})
-  const float* lvl32;            // [n_tiles][n_lev][n_T - 1][n_species][kTileNu / 2][4]
-  const float* cia32;            // [n_tiles][n_T - 1][2][kTileNu / 2][4]
+  // interleaved per pair of columns ({g[2q], g[2q+1], dg[2q], dg[2q+1]}),
+  // for the absorbers and then the two CIA pairs
+  const float* lvl32;            // [n_tiles][n_lev][n_T - 1][n_species + 2][kTileNu / 2][4]
   // wavenumber constants of the FP32 kernel per pair q of setup-local
   // columns 2q, 2q+1 (tile t holds pairs t kTileNu/2 ...): the first point's
   // wavenumber as an FP32 head and tail, nu_{2q+1} / nu_{2q}, and c1 nu^3 of
@@ -264,8 +264,7 @@ cudaError_t build_w_values(const TablesDev* d_tab, int nu_first, double R, int n
                            const int* d_hi, const double* d_invz, const int* d_rowinfo, const long long* d_rowptr,
                            float* d_w32, double* d_w64, cudaStream_t s);
 cudaError_t build_nu_pairs(const TablesDev* d_tab, int tile0, int n_tiles, float4* d_nu, float2* d_c1n, cudaStream_t s);
-cudaError_t build_level_cache(const TablesDev* d_tab, const SetupDev& h, float* d_lvl, float* d_cia,
-                              cudaStream_t s);
+cudaError_t build_level_cache(const TablesDev* d_tab, const SetupDev& h, float* d_lvl, cudaStream_t s);
 cudaError_t quantise_fp16(const double* d_src, __half* d_dst, long long rows, int n_nu, int nu_pad, double off,
                           cudaStream_t s);
 cudaError_t copy_pad_fp64(const double* d_src, double* d_dst, long long rows, int n_nu, int nu_pad,

@@ -445,75 +445,65 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
 
 // Per-warp shared-memory layout of the cached path:
 //   rows[2][K + 2][2 kTileNu] floats, per stage (double-buffered by level
-//     parity): T cell a of every absorber ([s][q][row, difference] as the
-//     operand stores it), then the two CIA pairs of cell a;
-//   recs[4][16]: the level records, a ring of four (level j in slot j & 3);
+//     parity): one level of one T cell of the operand as it is stored
+//     ([row][q][value, T difference], the K absorbers and the two CIA pairs);
+//   recs[8][16]: the level records, a ring of eight (level j in slot j & 7),
+//     filled four at a time;
 //   bar[2]: one mbarrier per stage.
 struct WarpPipe {
   float* rows;
   float* recs;
   unsigned long long* bar;
 };
+constexpr int kRecRing = 8;
 __host__ __device__ __forceinline__ size_t warp_rows_floats(int max_k) { return (size_t)2 * (2 * max_k + 4) * kTileNu; }
 __host__ __device__ __forceinline__ size_t warp_pipe_bytes(int max_k) {
-  return warp_rows_floats(max_k) * sizeof(float) + 4 * sizeof(LevRec) + 2 * sizeof(unsigned long long);
+  return warp_rows_floats(max_k) * sizeof(float) + kRecRing * sizeof(LevRec) + 2 * sizeof(unsigned long long);
 }
 __device__ __forceinline__ WarpPipe warp_pipe(unsigned char* base, int max_k) {
   WarpPipe w;
   w.rows = reinterpret_cast<float*>(base);
   w.recs = reinterpret_cast<float*>(base + warp_rows_floats(max_k) * sizeof(float));
-  w.bar = reinterpret_cast<unsigned long long*>(base + warp_rows_floats(max_k) * sizeof(float) + 4 * sizeof(LevRec));
+  w.bar = reinterpret_cast<unsigned long long*>(base + warp_rows_floats(max_k) * sizeof(float) +
+                                                kRecRing * sizeof(LevRec));
   return w;
 }
 
-// Issue stage st: one bulk copy of T cell acell of every absorber at one
-// level (K x 2 kTileNu floats), one of the CIA pairs of that cell (2 x 2
-// kTileNu floats, when copy_cia: the stage does not hold those of acell yet) and up
-// to two level records (rec_a -> record slot slot_a, rec_b -> slot_b; NULL to
-// skip), all counted on the stage's barrier.  One lane issues everything.
-__device__ __forceinline__ void issue_stage(const WarpPipe& w, int st, int K, const float* lvl_level,
-                                            const float* cia_tile, int acell, bool copy_cia, const LevRec* rec_a,
-                                            int slot_a, const LevRec* rec_b, int slot_b, int lane) {
+// First fill of a stage for an item: the operand block of level 0 (T cell
+// acell, (K + 2) x 2 kTileNu floats) and the records of levels 0 .. n_rec-1
+// into ring slots 0 .. n_rec-1, counted on the stage's barrier.  One lane
+// issues everything.
+__device__ __forceinline__ void issue_first(const WarpPipe& w, int st, int K, const float* src_rows, const LevRec* rec,
+                                            int n_rec, int lane) {
   if (lane == 0) {
-    const bool has_cia = copy_cia;
-    const unsigned rows_bytes = (unsigned)(2 * K * kTileNu * sizeof(float));
-    const unsigned cia_bytes = has_cia ? (unsigned)(4 * kTileNu * sizeof(float)) : 0u;
-    const unsigned bytes = rows_bytes + cia_bytes + (rec_a ? (unsigned)sizeof(LevRec) : 0u) +
-                           (rec_b ? (unsigned)sizeof(LevRec) : 0u);
+    const unsigned rows_bytes = (unsigned)((K + 2) * 2 * kTileNu * sizeof(float));
+    const unsigned rec_bytes = (unsigned)(n_rec * sizeof(LevRec));
     unsigned long long* bar = w.bar + st;
-    mbar_expect_tx(bar, bytes);
-    float* dst = w.rows + (size_t)st * (2 * K + 4) * kTileNu;
-    if (rows_bytes) bulk_copy(dst, lvl_level + (size_t)acell * 2 * K * kTileNu, rows_bytes, bar);
-    if (has_cia) bulk_copy(dst + (size_t)2 * K * kTileNu, cia_tile + (size_t)acell * 4 * kTileNu, cia_bytes, bar);
-    if (rec_a) bulk_copy(w.recs + (size_t)slot_a * 16, rec_a, (unsigned)sizeof(LevRec), bar);
-    if (rec_b) bulk_copy(w.recs + (size_t)slot_b * 16, rec_b, (unsigned)sizeof(LevRec), bar);
+    mbar_expect_tx(bar, rows_bytes + rec_bytes);
+    bulk_copy(w.rows + (size_t)st * (2 * K + 4) * kTileNu, src_rows, rows_bytes, bar);
+    bulk_copy(w.recs, rec, rec_bytes, bar);
   }
 }
 
 // The in-sweep refill of a stage as straight-line code: every lane runs it,
 // and only where `on` (lane 0, a level left to fetch) do the predicated
 // instructions arm the stage's barrier with `bytes` and issue the copies
-// (rows if do_rows, the CIA pairs of the cell if do_cia, one level record if
-// do_rec), so the sweep has no branch around them.
-__device__ __forceinline__ void issue_stage_pred(unsigned long long* bar, unsigned bytes, bool on, float* dst_rows,
-                                                 const float* src_rows, unsigned rows_bytes, bool do_rows,
-                                                 float* dst_cia, const float* src_cia, bool do_cia, float* dst_rec,
-                                                 const LevRec* src_rec, bool do_rec) {
+// (the operand block, and records if do_rec), so the sweep has no branch
+// around them.
+__device__ __forceinline__ void issue_level_pred(unsigned long long* bar, unsigned bytes, bool on, float* dst_rows,
+                                                 const float* src_rows, unsigned rows_bytes, float* dst_rec,
+                                                 const LevRec* src_rec, unsigned rec_bytes, bool do_rec) {
   asm volatile(
       "{\n"
-      " .reg .pred pon, prw, pci, prc;\n"
+      " .reg .pred pon, prc;\n"
       " setp.ne.b32 pon, %0, 0;\n"
-      " setp.ne.and.b32 prw, %1, 0, pon;\n"
-      " setp.ne.and.b32 pci, %2, 0, pon;\n"
-      " setp.ne.and.b32 prc, %3, 0, pon;\n"
-      " @pon mbarrier.arrive.expect_tx.shared::cta.b64 _, [%4], %5;\n"
-      " @prw cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%6], [%7], %8, [%4];\n"
-      " @pci cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%9], [%10], %13, [%4];\n"
-      " @prc cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%11], [%12], %14, [%4];\n"
+      " setp.ne.and.b32 prc, %1, 0, pon;\n"
+      " @pon mbarrier.arrive.expect_tx.shared::cta.b64 _, [%2], %3;\n"
+      " @pon cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%4], [%5], %6, [%2];\n"
+      " @prc cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%7], [%8], %9, [%2];\n"
       "}\n" ::"r"((int)on),
-      "r"((int)do_rows), "r"((int)do_cia), "r"((int)do_rec), "r"(smem_u32(bar)), "r"(bytes), "r"(smem_u32(dst_rows)),
-      "l"(src_rows), "r"(rows_bytes), "r"(smem_u32(dst_cia)), "l"(src_cia), "r"(smem_u32(dst_rec)), "l"(src_rec),
-      "n"(4 * kTileNu * (int)sizeof(float)), "n"((int)sizeof(LevRec))
+      "r"((int)do_rec), "r"(smem_u32(bar)), "r"(bytes), "r"(smem_u32(dst_rows)), "l"(src_rows), "r"(rows_bytes),
+      "r"(smem_u32(dst_rec)), "l"(src_rec), "r"(rec_bytes)
       : "memory");
 }
 
@@ -765,24 +755,23 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     const v2* sW2 = sA2;   // cached path: per-sample absorber weights
     // Pipeline over the levels (g = phase_base + j counts this warp's levels
     // across items; level g uses stage g & 1, whose barrier completes phase
-    // (g >> 1) & 1).  Record of level j sits in record slot j & 3.  A stage
-    // keeps its CIA rows until a level with another T cell lands in it.
-    //   before the loop: stage of level 0 <- rows(0), records 0 and 1
-    //   level j:         wait stage(j)   -> rows(j) and record j+1 present
-    //                    issue stage(j+1) <- rows(j+1) (cell from record
-    //                                        j+1), record j+2
+    // (g >> 1) & 1).  Record of level j sits in ring slot j & 7.
+    //   before the loop: stage of level 0 <- block(0), records 0 .. 7
+    //   level j:         wait stage(j)    -> block(j) present
+    //                    issue stage(j+1) <- block(j+1) (T cell from record
+    //                                        j+1), and where j = 4m >= 4,
+    //                                        records j+4 .. j+7
     //                    compute level j
+    // (record j+1 is needed at level j; records j+4 .. j+7 land with stage
+    // j+1, before level j+3 reads record j+4)
     if (phase_base == 0xffffffffu) return;       // this warp's pipeline failed earlier
-    const float* lvl_tile = S.lvl32 + (size_t)tile * (L + 1) * (nT - 1) * K * 2 * kTileNu;
-    const float* cia_tile = S.cia32 + (size_t)tile * (nT - 1) * 4 * kTileNu;
-    const size_t lvl_step = (size_t)(nT - 1) * K * 2 * kTileNu;
-    const bool has_cia = cia0 || cia1;
+    const size_t lvl_step = (size_t)(nT - 1) * (K + 2) * 2 * kTileNu;   // one level of the tile
+    const size_t cell_step = (size_t)(K + 2) * 2 * kTileNu;             // one T cell of a level
+    const float* lvl_tile = S.lvl32 + (size_t)tile * (L + 1) * lvl_step;
+    const unsigned rows_bytes = (unsigned)(cell_step * sizeof(float));
     const unsigned ph = phase_base;
     const int acell0 = __ldg(&reinterpret_cast<const LevRecC*>(rec)[0].acell);
-    int cia_cell0 = -1, cia_cell1 = -1;   // T cell whose CIA rows stage 0 / 1 holds
-    if (ph & 1u) cia_cell1 = acell0; else cia_cell0 = acell0;
-    issue_stage(wp_, (int)(ph & 1u), K, lvl_tile, cia_tile, acell0, has_cia, rec, 0, L >= 1 ? rec + 1 : nullptr, 1,
-                lane);
+    issue_first(wp_, (int)(ph & 1u), K, lvl_tile + (size_t)acell0 * cell_step, rec, min(kRecRing, L + 1), lane);
     // unrolled so that the loop-carried sweep state rotates through register
     // sets instead of being moved back at the end of each level
 #pragma unroll 4
@@ -799,28 +788,19 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       }
       __syncwarp();
       {
-        // refill the other stage with level j+1 (rows of its T cell, taken
-        // from record j+1, and the CIA pairs where that stage holds another
-        // cell) and record j+2
         const bool more = j < L;
-        const int acell_n = more ? __float_as_int(wp_.recs[((j + 1) & 3) * 16 + kRecCAcell]) : 0;
+        const int acell_n = more ? __float_as_int(wp_.recs[((j + 1) & (kRecRing - 1)) * 16 + kRecCAcell]) : 0;
         const int sn = (int)((g + 1u) & 1u);
-        const bool copy_cia = more && has_cia && (sn ? cia_cell1 : cia_cell0) != acell_n;
-        cia_cell1 = (more && sn) ? acell_n : cia_cell1;
-        cia_cell0 = (more && !sn) ? acell_n : cia_cell0;
-        const bool do_rec = j + 2 <= L;
-        const unsigned rows_bytes = (unsigned)(2 * K * kTileNu * sizeof(float));
-        const unsigned bytes = rows_bytes + (copy_cia ? 4u * kTileNu * (unsigned)sizeof(float) : 0u) +
-                               (do_rec ? (unsigned)sizeof(LevRec) : 0u);
-        float* dst = wp_.rows + (size_t)sn * (2 * K + 4) * kTileNu;
-        issue_stage_pred(wp_.bar + sn, bytes, more && lane == 0, dst,
-                         lvl_tile + (size_t)(j + 1) * lvl_step + (size_t)acell_n * 2 * K * kTileNu, rows_bytes,
-                         rows_bytes != 0u, dst + (size_t)2 * K * kTileNu, cia_tile + (size_t)acell_n * 4 * kTileNu,
-                         copy_cia, wp_.recs + (size_t)((j + 2) & 3) * 16, rec + (j + 2), do_rec);
+        const bool do_rec = (j & 3) == 0 && j >= 4 && j + 4 <= L;
+        const unsigned rec_bytes = (unsigned)(min(4, max(0, L - j - 3)) * (int)sizeof(LevRec));
+        issue_level_pred(wp_.bar + sn, rows_bytes + (do_rec ? rec_bytes : 0u), more && lane == 0,
+                         wp_.rows + (size_t)sn * (2 * K + 4) * kTileNu,
+                         lvl_tile + (size_t)(j + 1) * lvl_step + (size_t)acell_n * cell_step, rows_bytes,
+                         wp_.recs + (size_t)((j + 4) & (kRecRing - 1)) * 16, rec + (j + 4), rec_bytes, do_rec);
       }
       // record j (LevRecC): {wT, wT, wh2h2, wh2h2}, {wh2he, wh2he, half_dp,
       // half_dp}, {dtc, dtc, upl, rdnu}
-      const float* rj = wp_.recs + (j & 3) * 16;
+      const float* rj = wp_.recs + (j & (kRecRing - 1)) * 16;
       const RowDiff rq0 = lds_rd(rj), rq1 = lds_rd(rj + 4);
       const RecTail rq2 = *reinterpret_cast<const RecTail*>(rj + 8);
       const v2 wT = rq0.g;

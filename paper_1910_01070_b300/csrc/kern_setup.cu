@@ -400,28 +400,42 @@ cudaError_t build_w_values(const TablesDev* d_tab, int nu_first, double R, int n
 //   g(a) = log2(10) ((1 - w_p) v[sp][a][b_j][col] + w_p v[sp][a][b_j+1][col])
 // (log10 option) or (1 - w_p) 10^v[sp][a][b_j][col] + w_p 10^v[sp][a][b_j+1][col]
 // (linear option), v the stored FP16 value log10 sigma - off_s, table column
-// col = (tile0 + t) kTileNu + c.  It is stored per T cell a (T rows a and
-// a+1, n_T - 1 cells) as the row g(a) and the difference g(a+1) - g(a), the
-// two interleaved per pair of neighbouring columns:
+// col = (tile0 + t) kTileNu + c; after the K absorbers come the two CIA pairs
+// (which do not depend on p): h(a) = log2(10) v_cia[pair][a][col] or
+// 10^v_cia[pair][a][col], zero for an absent pair.  Each is stored per T
+// cell a (T rows a and a+1, n_T - 1 cells) as the row and its difference to
+// row a+1, interleaved per pair of neighbouring columns:
 //   lvl[t][j][a][s][q] = { g(a)[2q], g(a)[2q+1], (g(a+1)-g(a))[2q], (g(a+1)-g(a))[2q+1] }
-// for q < kTileNu / 2, so that one T cell of every absorber at one level is
-// one contiguous block of K x 2 kTileNu floats (one bulk copy), and the
-// kernel reads a pair's value and difference with one 16-byte load.
+// for s < K + 2 and q < kTileNu / 2, so that everything one level of one T
+// cell needs is one contiguous block of (K + 2) x 2 kTileNu floats (one bulk
+// copy), and the kernel reads a pair's value and difference with one 16-byte
+// load.  The CIA rows are repeated on every level (2 of the K + 2 rows).
 struct SpeciesList {
   int sp[HR2_MAX_SPECIES];
 };
 
-__device__ __forceinline__ double level_value(const TablesDev& t, size_t row0, double wp, int linear) {
-  const double v0 = (double)__half2float(t.sig16[row0]);
-  const double v1 = (double)__half2float(t.sig16[row0 + t.nu_pad]);
-  return linear ? (1.0 - wp) * exp10(v0) + wp * exp10(v1) : kLog2_10 * ((1.0 - wp) * v0 + wp * v1);
+// row value of operand row s (absorber s < K, else CIA pair s - K) at T row a
+__device__ __forceinline__ double operand_value(const TablesDev& t, const LevelDev& lv, const SpeciesList& list,
+                                                int K, int s, int a, size_t col, int linear) {
+  if (s < K) {
+    const size_t row0 = (((size_t)list.sp[s] * t.n_T + a) * t.n_p + lv.pcell) * t.nu_pad + col;
+    const double v0 = (double)__half2float(t.sig16[row0]);
+    const double v1 = (double)__half2float(t.sig16[row0 + t.nu_pad]);
+    return linear ? (1.0 - lv.wp64) * exp10(v0) + lv.wp64 * exp10(v1)
+                  : kLog2_10 * ((1.0 - lv.wp64) * v0 + lv.wp64 * v1);
+  }
+  const int pair = s - K;
+  if (!t.has_cia[pair]) return 0.0;
+  const double v = (double)__half2float(t.cia16[((size_t)pair * t.n_T + a) * t.nu_pad + col]);
+  return linear ? exp10(v) : kLog2_10 * v;
 }
 
 __global__ void k_level_cache(const TablesDev* tab, const LevelDev* lev, int n_species, SpeciesList list, int n_lev,
                               int tile0, int n_tiles, int linear, float* out) {
   const TablesDev& t = *tab;
   const int n_cells = t.n_T - 1;
-  const long long total = (long long)n_tiles * n_lev * n_cells * n_species * (2 * kTileNu);
+  const int n_rows = n_species + 2;
+  const long long total = (long long)n_tiles * n_lev * n_cells * n_rows * (2 * kTileNu);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     long long r = idx;
@@ -429,58 +443,20 @@ __global__ void k_level_cache(const TablesDev* tab, const LevelDev* lev, int n_s
     r /= 4;
     const int q = (int)(r % (kTileNu / 2));
     r /= kTileNu / 2;
-    const int s = (int)(r % n_species);
-    r /= n_species;
+    const int s = (int)(r % n_rows);
+    r /= n_rows;
     const int a = (int)(r % n_cells);
     r /= n_cells;
     const int j = (int)(r % n_lev);
     const int tt = (int)(r / n_lev);
     const LevelDev lv = lev[j];
-    const int c = 2 * q + (e & 1);
-    const size_t row0 = (((size_t)list.sp[s] * t.n_T + a) * t.n_p + lv.pcell) * t.nu_pad + (size_t)(tile0 + tt) * kTileNu + c;
-    const double g0 = level_value(t, row0, lv.wp64, linear);
+    const size_t col = (size_t)(tile0 + tt) * kTileNu + 2 * q + (e & 1);
+    const double g0 = operand_value(t, lv, list, n_species, s, a, col, linear);
     if (e < 2) {
       out[idx] = (float)g0;
     } else {
-      const double g1 = level_value(t, row0 + (size_t)t.n_p * t.nu_pad, lv.wp64, linear);
+      const double g1 = operand_value(t, lv, list, n_species, s, a + 1, col, linear);
       out[idx] = (float)(g1 - g0);
-    }
-  }
-}
-
-// CIA operand, per tile t, T cell a and pair p, the same interleaving of the
-// row h(a) and the difference h(a+1) - h(a), h(a) = log2(10) v_cia[p][a][col]
-// (log10 option) or 10^v_cia[p][a][col] (linear option):
-//   cia[t][a][p][q] = { h(a)[2q], h(a)[2q+1], (h(a+1)-h(a))[2q], (h(a+1)-h(a))[2q+1] }
-// (zeros for an absent pair)
-__global__ void k_cia_cache(const TablesDev* tab, int tile0, int n_tiles, int linear, float* out) {
-  const TablesDev& t = *tab;
-  const int n_cells = t.n_T - 1;
-  const long long total = (long long)n_tiles * n_cells * 2 * (2 * kTileNu);
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long r = idx;
-    const int e = (int)(r % 4);
-    r /= 4;
-    const int q = (int)(r % (kTileNu / 2));
-    r /= kTileNu / 2;
-    const int p = (int)(r % 2);
-    r /= 2;
-    const int a = (int)(r % n_cells);
-    const int tt = (int)(r / n_cells);
-    if (!t.has_cia[p]) {
-      out[idx] = 0.f;
-      continue;
-    }
-    const size_t col = (size_t)(tile0 + tt) * kTileNu + 2 * q + (e & 1);
-    const double v0 = (double)__half2float(t.cia16[((size_t)p * t.n_T + a) * t.nu_pad + col]);
-    const double h0 = linear ? exp10(v0) : kLog2_10 * v0;
-    if (e < 2) {
-      out[idx] = (float)h0;
-    } else {
-      const double v1 = (double)__half2float(t.cia16[((size_t)p * t.n_T + a + 1) * t.nu_pad + col]);
-      const double h1 = linear ? exp10(v1) : kLog2_10 * v1;
-      out[idx] = (float)(h1 - h0);
     }
   }
 }
@@ -502,13 +478,11 @@ cudaError_t build_nu_pairs(const TablesDev* d_tab, int tile0, int n_tiles, float
   return cudaGetLastError();
 }
 
-cudaError_t build_level_cache(const TablesDev* d_tab, const SetupDev& h, float* d_lvl, float* d_cia, cudaStream_t s) {
+cudaError_t build_level_cache(const TablesDev* d_tab, const SetupDev& h, float* d_lvl, cudaStream_t s) {
   SpeciesList list{};
   for (int i = 0; i < h.n_species; ++i) list.sp[i] = h.species[i];
-  if (h.n_species > 0)
-    k_level_cache<<<4096, 256, 0, s>>>(d_tab, h.levels, h.n_species, list, h.n_lev, h.tile0, h.n_tiles,
-                                       h.interp == HR2_INTERP_LINEAR, d_lvl);
-  k_cia_cache<<<1024, 256, 0, s>>>(d_tab, h.tile0, h.n_tiles, h.interp == HR2_INTERP_LINEAR, d_cia);
+  k_level_cache<<<4096, 256, 0, s>>>(d_tab, h.levels, h.n_species, list, h.n_lev, h.tile0, h.n_tiles,
+                                     h.interp == HR2_INTERP_LINEAR, d_lvl);
   return cudaGetLastError();
 }
 
