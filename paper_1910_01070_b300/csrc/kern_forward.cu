@@ -752,7 +752,13 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
   v2 hdp_prev = pk(0.f);
 
   if constexpr (CACHED) {
-    const v2* sW2 = sA2;   // cached path: per-sample absorber weights
+    // per-sample absorber weights, in registers when the count is fixed
+    v2 wreg[KT > 0 ? KT : 1];
+    if constexpr (KT > 0) {
+#pragma unroll
+      for (int q = 0; q < KT; ++q) wreg[q] = sA2[q];
+    }
+    const v2* sW2 = (KT > 0) ? wreg : sA2;
     // Pipeline over the levels (g = phase_base + j counts this warp's levels
     // across items; level g uses stage g & 1, whose barrier completes phase
     // (g >> 1) & 1).  Record of level j sits in ring slot j & 7.
