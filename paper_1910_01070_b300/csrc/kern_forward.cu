@@ -818,8 +818,9 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chA[p] = chB[p] = pk(0.f);
       if constexpr (KT > 0) {
-        // every setup of the batch has K = KT or KT - 1 absorbers; a padded
+        // every setup of the batch has KT - 4 <= K <= KT absorbers; a padded
         // absorber has weight 0 and reads finite values of the stage
+        // (the CIA rows that follow, or the other stage, both initialised)
 #pragma unroll
         for (int s = 0; s < KT; s += 2) {
           const v2 w0 = sW2[s], w1 = sW2[s + 1];

@@ -121,7 +121,7 @@ def _absorber_spec(K, seed, with_cia=True):
 def test_absorber_counts_level_gridded(eng, K, with_cia):
     """The level-gridded kernel is compiled for an even absorber bound; an odd
     count runs with one zero-weight absorber, whose shared-memory rows are the
-    stage's neighbouring rows (CIA rows, or never-copied zeroed rows without CIA)."""
+    stage's next rows (the CIA rows, zero when the tables have no CIA)."""
     spec, tabs = _absorber_spec(K, 40 + K, with_cia)
     setup = W.make_setup(spec, 5000.0, 5299.0, 20, range(K), 4, 2, 2, 300.0, 6)
     t = eng.add_tables(spec, "fp16", tabs)
@@ -134,10 +134,11 @@ def test_absorber_counts_level_gridded(eng, K, with_cia):
         _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, 300)
 
 
-@pytest.mark.parametrize("ks", [(5, 6), (4, 6), (6, 3, 5)])
+@pytest.mark.parametrize("ks", [(5, 6), (4, 6), (6, 3, 5), (2, 6), (1, 6), (2, 7, 5)])
 def test_mixed_absorber_counts_in_one_batch(eng, ks):
-    """Setups with different absorber counts in one batch: counts K and K-1
-    share the even bound (zero-weight padding), wider mixes take the
+    """Setups with different absorber counts in one batch: counts from K-4 to K
+    share the even bound K (zero-weight padding, up to 4 padded absorbers
+    reading the stage's other values), wider mixes ((1, 6), (2, 7, 5)) take the
     runtime-count kernel.  Every sample matches the oracle of its setup."""
     spec, tabs = _absorber_spec(max(ks), 77)
     t = eng.add_tables(spec, "fp16", tabs)
