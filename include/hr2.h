@@ -262,7 +262,11 @@ int hr2_tables_destroy(hr2_ctx* ctx, hr2_tables* tables);
  * Synchronous.  The tables must outlive the setup. */
 int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tables, const hr2_setup_desc* desc, hr2_setup** out);
 
-/* Replace the observation (HOST [n_bins] each).  Synchronous. */
+/* Replace the observation (HOST [n_bins] each; D finite, sigma > 0, else
+ * HR2_EINVAL).  Also precomputes on the device the likelihood's terms that do
+ * not depend on the model (1 / (2 sigma^2) per bin and the normalisation
+ * sum_b -ln(2 pi sigma_b^2) / 2 of Eq. 19), used when a sample has no error
+ * inflation.  Device memory: (3 n_bins + 1) doubles.  Synchronous. */
 int hr2_setup_set_observation(hr2_ctx* ctx, hr2_setup* setup, const double* obs_flux, const double* obs_sigma);
 
 /* Number of bins / wavenumbers / nonzeros of W of a setup. */

@@ -476,14 +476,20 @@ extern "C" int hr2_setup_set_observation(hr2_ctx* ctx, hr2_setup* s, const doubl
   }
   HR2_CU(cudaSetDevice(ctx->device));
   int rc;
+  // [D][sigma][1 / (2 sigma^2)][sum of -ln(2 pi sigma^2) / 2]
   if (!s->d_obs) {
-    if ((rc = dalloc_t(ctx, &s->d_obs, 2 * (size_t)s->n_bins))) return rc;
+    if ((rc = dalloc_t(ctx, &s->d_obs, 3 * (size_t)s->n_bins + 1))) return rc;
     s->mem.push_back(s->d_obs);
   }
   HR2_CU(cudaMemcpy(s->d_obs, D, sizeof(double) * s->n_bins, cudaMemcpyHostToDevice));
   HR2_CU(cudaMemcpy(s->d_obs + s->n_bins, sigma, sizeof(double) * s->n_bins, cudaMemcpyHostToDevice));
   s->host.obs_D = s->d_obs;
   s->host.obs_sigma = s->d_obs + s->n_bins;
+  s->host.obs_inv2s2 = s->d_obs + 2 * (size_t)s->n_bins;
+  s->host.obs_lnorm = s->d_obs + 3 * (size_t)s->n_bins;
+  HR2_CU(launch_obs_terms(s->host.obs_sigma, s->n_bins, const_cast<double*>(s->host.obs_inv2s2),
+                          const_cast<double*>(s->host.obs_lnorm), 0));
+  HR2_CU(cudaDeviceSynchronize());
   s->has_obs = true;
   HR2_CU(cudaMemcpy(s->dev, &s->host, sizeof(SetupDev), cudaMemcpyHostToDevice));
   return HR2_OK;

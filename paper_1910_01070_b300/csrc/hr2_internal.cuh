@@ -75,6 +75,7 @@ struct LevelDev {
   float half_dp;          // (p_{j+1} - p_j) / 2 for layer j (0 for the last level)
   double p_dyn64, half_dp64;
   double wp64;
+  double lpk;             // log2(p_j / k_B): the level's part of log2 n_j = lpk - log2 T_j
 };
 
 // Device descriptor of one setup (lives in device memory).
@@ -104,6 +105,11 @@ struct SetupDev {
   const double* w64;             // [nnz]
   const double* obs_D;           // [n_bins] or null
   const double* obs_sigma;       // [n_bins] or null
+  // with the observation (k_obs_terms): 1 / (2 sigma_b^2) per bin and
+  // sum_b -ln(2 pi sigma_b^2) / 2, the likelihood's terms that do not depend
+  // on the model when there is no error inflation
+  const double* obs_inv2s2;      // [n_bins] or null
+  const double* obs_lnorm;       // [1] or null
   float cost;                    // relative cost of one work item (scheduling)
   const TablesDev* tables;       // device copy
   // level-gridded operand (level_cache): the tables interpolated in p onto
@@ -242,6 +248,7 @@ struct LnlArgs {
   double* lnl;
 };
 cudaError_t launch_lnl(const LnlArgs& a, cudaStream_t s);
+cudaError_t launch_obs_terms(const double* sigma, int n_bins, double* inv2s2, double* lnorm, cudaStream_t s);
 // Hopf function table (kern_setup.cu) and effective temperatures (kern_forward.cu)
 cudaError_t build_hopf_table(double* d_q, cudaStream_t s);
 cudaError_t launch_teff(const FwdArgs& a, const float* highres, int highres_ld, double* out, cudaStream_t s);

@@ -46,6 +46,30 @@ __device__ double fe_temperature(const SetupDev& S, const double* nodes, double 
   return T;
 }
 
+// The same profile with the Lagrange denominators 1 / prod_{m != i}(xi_i - xi_m)
+// taken once per sample (lw), so that a level costs multiplications only.
+__device__ __forceinline__ double fe_temperature_w(const SetupDev& S, const double* nodes, const double* lw, double x) {
+  const int Ke = S.fe_elements, q = S.fe_order;
+  int k = (int)floor(x * Ke);
+  k = k < 0 ? 0 : (k > Ke - 1 ? Ke - 1 : k);
+  const double loc = x * Ke - k;
+  double T = 0.0;
+  for (int i = 0; i <= q; ++i) {
+    double l = lw[i];
+    for (int m = 0; m <= q; ++m)
+      if (m != i) l *= loc - S.gll[m];
+    T += nodes[k * q + i] * l;
+  }
+  return T;
+}
+
+// 2^b for the FP32 record fields: 2^rint(b) exactly times exp2f of the
+// remainder (|r| <= 1/2, relative error ~2e-7), without FP64 transcendentals.
+__device__ __forceinline__ float exp2_split(double b) {
+  const double n = rint(b);
+  return ldexpf(exp2f((float)(b - n)), (int)n);
+}
+
 // Hopf function q(tau) from the setup's table (linear in ln tau).
 __device__ double hopf_q(const double* tab, double tau) {
   if (!(tau > kHopfTau0)) return tab[0];
@@ -168,54 +192,78 @@ __global__ void k_prep(FwdArgs a) {
 
   const int L = S.n_lev - 1;
   LevRec* rec = a.recs + (size_t)i * a.rec_ld;
+  // per-sample constants of the level records: the Lagrange denominators of
+  // the FE profile, and log2 of the CIA prefactors without the level's number
+  // density, b = log2(x x' c n_j) + off log2 10 - shift = cb + log2(p_j / k_B)
+  // - log2 T_j
+  double lw[HR2_MAX_TNODES];
+  if (S.profile != HR2_PROFILE_MILNE) {
+    for (int q = 0; q <= S.fe_order; ++q) {
+      double d = 1.0;
+      for (int m = 0; m <= S.fe_order; ++m)
+        if (m != q) d *= S.gll[q] - S.gll[m];
+      lw[q] = 1.0 / d;
+    }
+  }
+  const double lxh2 = log2(xh2), lxhe = log2(xhe);
+  const double cb0 = 2.0 * lxh2 + lc + T.off[kCiaH2H2] * kLog2_10 - shift;
+  const double cb1 = lxh2 + lxhe + lc + T.off[kCiaH2He] * kLog2_10 - shift;
+  const float tiny = (S.sc != HR2_SC_PARABOLIC) ? kTinyTau : 0.f;
   for (int j = lane; j <= L; j += 32) {
-    const double Tj = level_temperature(S, th, j, grav);
+    const double Tj = S.profile == HR2_PROFILE_MILNE
+                          ? level_temperature(S, th, j, grav)
+                          : fe_temperature_w(S, th + HR2_P_T0, lw, (double)(L - j) / (double)L);
     if (!(Tj > 0.0) || !isfinite(Tj)) status |= HR2_SAMPLE_BAD_T;
     int acell;
     double wT;
     grid_cell(T.T_grid64, T.n_T, Tj, acell, wT);
     const LevelDev lv = S.levels[j];
-    const double wp = lv.wp64;
-    LevRec r;
-    r.rowoff = acell * T.n_p + lv.pcell;
-    r.acell = acell;
-    r.wT = (float)wT;
-    r.wp = (float)wp;
-    r.wTwp = (float)(wT * wp);
-    const double ntot = lv.p_dyn64 / (kKB * Tj);
-    const double b0 = log2(xh2 * xh2 * c * ntot) + T.off[kCiaH2H2] * kLog2_10 - shift;
-    const double b1 = log2(xh2 * xhe * c * ntot) + T.off[kCiaH2He] * kLog2_10 - shift;
-    r.bh2h2 = (float)b0;
-    r.ch2h2 = (float)(1.0 + kLn2 * (b0 - (double)r.bh2h2));
-    r.bh2he = (float)b1;
-    r.ch2he = (float)(1.0 + kLn2 * (b1 - (double)r.bh2he));
-    const double upl = -kC2 * kLog2e / Tj;
-    r.upl = (float)upl;
-    r.upl_lo = (float)(upl - (double)r.upl);
-    r.half_dp = (float)ldexp(lv.half_dp64, (int)shift);
-    r.rdnu = (float)exp(-kC2 * T.dnu / Tj);
+    const double lT = log2(Tj);
+    const double b0 = cb0 + lv.lpk - lT;    // log2(x_H2^2 c n_j) + off log2 10 - shift
+    const double b1 = cb1 + lv.lpk - lT;    // log2(x_H2 x_He c n_j) + off log2 10 - shift
+    const double upl = -kC2 * kLog2e / Tj;  // e^{-hc nu/kT} = 2^(upl nu)
+    const float half_dp = (float)ldexp(lv.half_dp64, (int)shift);
+    const float rdnu = exp2f((float)(upl * T.dnu));   // e^{-hc dnu/kT}, |argument| << 1
     // zero for an absent pair: the cached path adds both pairs unconditionally
-    r.wh2h2 = T.has_cia[0] ? (float)exp2(b0) : 0.f;
-    r.wh2he = T.has_cia[1] ? (float)exp2(b1) : 0.f;
-    r.dtau_cloud = 0.f;
+    const float wh2h2 = T.has_cia[0] ? exp2_split(b0) : 0.f;
+    const float wh2he = T.has_cia[1] ? exp2_split(b1) : 0.f;
+    float dtc = 0.f;
     if (S.cloud && j > 0 && pcb > pct) {   // layer j-1 between levels j-1 and j
       const double lo = fmax(S.levels[j - 1].p_dyn64, pct), hi = fmin(lv.p_dyn64, pcb);
-      if (hi > lo) r.dtau_cloud = (float)(tau_c * (hi - lo) / (pcb - pct));
+      if (hi > lo) dtc = (float)(tau_c * (hi - lo) / (pcb - pct));
     }
-    if (S.sc != HR2_SC_PARABOLIC) r.dtau_cloud += kTinyTau;
+    dtc += tiny;
     if (S.cached) {
       LevRecC rc;
-      rc.wT[0] = rc.wT[1] = r.wT;
-      rc.wh2h2[0] = rc.wh2h2[1] = r.wh2h2;
-      rc.wh2he[0] = rc.wh2he[1] = r.wh2he;
-      rc.half_dp[0] = rc.half_dp[1] = r.half_dp;
-      rc.dtc[0] = rc.dtc[1] = r.dtau_cloud;
-      rc.upl = r.upl;
-      rc.rdnu = r.rdnu;
+      rc.wT[0] = rc.wT[1] = (float)wT;
+      rc.wh2h2[0] = rc.wh2h2[1] = wh2h2;
+      rc.wh2he[0] = rc.wh2he[1] = wh2he;
+      rc.half_dp[0] = rc.half_dp[1] = half_dp;
+      rc.dtc[0] = rc.dtc[1] = dtc;
+      rc.upl = (float)upl;
+      rc.rdnu = rdnu;
       rc.acell = acell;
       rc.pad[0] = rc.pad[1] = rc.pad[2] = 0;
       reinterpret_cast<LevRecC*>(rec)[j] = rc;
     } else {
+      const double wp = lv.wp64;
+      LevRec r;
+      r.rowoff = acell * T.n_p + lv.pcell;
+      r.acell = acell;
+      r.wT = (float)wT;
+      r.wp = (float)wp;
+      r.wTwp = (float)(wT * wp);
+      r.bh2h2 = (float)b0;
+      r.ch2h2 = (float)(1.0 + kLn2 * (b0 - (double)r.bh2h2));
+      r.bh2he = (float)b1;
+      r.ch2he = (float)(1.0 + kLn2 * (b1 - (double)r.bh2he));
+      r.upl = (float)upl;
+      r.upl_lo = (float)(upl - (double)r.upl);
+      r.half_dp = half_dp;
+      r.rdnu = rdnu;
+      r.wh2h2 = wh2h2;
+      r.wh2he = wh2he;
+      r.dtau_cloud = dtc;
       rec[j] = r;
     }
   }
@@ -1359,10 +1407,84 @@ cudaError_t launch_forward64(const FwdArgs& a, int max_nmu, int max_nu, cudaStre
 
 // ------------------------------------------------------------------ bins
 // D_m,b = f (R_star/d)^2 sum_m W[b][m] F+_m: the instrument profile and the
-// binning as one banded operator (Sects. 2.7-2.8).  One block per sample,
-// one warp per bin, fixed-order butterfly reduction.
-template <bool FP64>
-__global__ void __launch_bounds__(256) k_bins(FwdArgs a, float* bins, int bins_ld) {
+// binning as one banded operator (Sects. 2.7-2.8).  One warp per bin row,
+// lanes over the row's columns, fixed-order butterfly reduction.
+//
+// FP32 path: one block per group of up to kBinGroup samples of one setup
+// (consecutive in the planner's permutation) and kBinRows rows of W
+// (blockIdx.y), so that each row of W is read once for the whole group; each
+// sample's sum runs in the same order as it would alone.  (Groups of 2 gave
+// the shortest step on the 1024-sample workload: 4 and 8 samples per block
+// leave the loads of the rows too serial, 1 reads W once per sample.)  Blocks past the
+// groups write NaN rows for samples whose setup index is out of range (they
+// are in no group).  FP64 path: one block per sample.
+constexpr int kBinGroup = 2;
+constexpr int kBinRows = 32;
+
+__global__ void __launch_bounds__(256) k_bins32(FwdArgs a, float* bins, int bins_ld, int group_blocks) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const float qnan = __int_as_float(0x7fc00000);
+  int blk = blockIdx.x;
+  if (blk >= group_blocks) {
+    if (blockIdx.y != 0) return;
+    const int i = (blk - group_blocks) * blockDim.x + threadIdx.x;
+    if (i < a.n && a.samp[i].setup < 0)
+      for (int b = 0; b < bins_ld; ++b) bins[(size_t)i * bins_ld + b] = qnan;
+    return;
+  }
+  const PlanDev* plan = a.plan;
+  int g = -1, s0 = 0, ns = 0;
+  for (int q = 0; q < plan->n_setups; ++q) {
+    const int c = plan->count[q], nb = (c + kBinGroup - 1) / kBinGroup;
+    if (blk < nb) {
+      g = q;
+      s0 = plan->first[q] + blk * kBinGroup;
+      ns = min(kBinGroup, c - blk * kBinGroup);
+      break;
+    }
+    blk -= nb;
+  }
+  if (g < 0) return;   // beyond the groups of this batch
+  const SetupDev& S = *a.setups[g];
+  const float* F[kBinGroup];
+  float* out[kBinGroup];
+  double scale[kBinGroup];
+  bool bad[kBinGroup];
+#pragma unroll
+  for (int k = 0; k < kBinGroup; ++k) {
+    const int i = a.perm[s0 + min(k, ns - 1)];
+    F[k] = a.highres + (size_t)i * a.highres_ld;
+    out[k] = bins + (size_t)i * bins_ld;
+    scale[k] = a.samp[i].scale;
+    bad[k] = a.samp[i].status != 0;
+  }
+  const int b_end = min(S.n_bins, (int)(blockIdx.y + 1) * kBinRows);
+  for (int b = blockIdx.y * kBinRows + warp; b < b_end; b += nw) {
+    const long long r0 = S.w_rowptr[b], r1 = S.w_rowptr[b + 1];
+    const int c0 = S.w_col0[b];
+    float acc[kBinGroup];
+#pragma unroll
+    for (int k = 0; k < kBinGroup; ++k) acc[k] = 0.f;
+#pragma unroll 2
+    for (long long t = r0 + lane; t < r1; t += 32) {
+      const float w = S.w32[t];
+      const long long c = c0 + (t - r0);
+#pragma unroll
+      for (int k = 0; k < kBinGroup; ++k)
+        if (k < ns) acc[k] = fmaf(w, F[k][c], acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < kBinGroup; ++k) {
+      if (k >= ns) break;
+      float v = acc[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) out[k][b] = bad[k] ? qnan : (float)((double)v * scale[k]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bins64(FwdArgs a, float* bins, int bins_ld) {
   const int i = blockIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const SampleDev& sd = a.samp[i];
@@ -1380,35 +1502,34 @@ __global__ void __launch_bounds__(256) k_bins(FwdArgs a, float* bins, int bins_l
   for (int b = warp; b < S.n_bins; b += nw) {
     const long long r0 = S.w_rowptr[b], r1 = S.w_rowptr[b + 1];
     const int c0 = S.w_col0[b];
-    if (FP64) {
-      const double* F = a.highres64 + (size_t)i * a.highres64_ld + c0;
-      double acc = 0.0;
-      for (long long t = r0 + lane; t < r1; t += 32) acc += S.w64[t] * F[t - r0];
+    const double* F = a.highres64 + (size_t)i * a.highres64_ld + c0;
+    double acc = 0.0;
+    for (long long t = r0 + lane; t < r1; t += 32) acc += S.w64[t] * F[t - r0];
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) out[b] = (float)(acc * sd.scale);
-    } else {
-      const float* F = a.highres + (size_t)i * a.highres_ld + c0;
-      float acc = 0.f;
-      for (long long t = r0 + lane; t < r1; t += 32) acc = fmaf(S.w32[t], F[t - r0], acc);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) out[b] = (float)((double)acc * sd.scale);
-    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[b] = (float)(acc * sd.scale);
   }
 }
 
 cudaError_t launch_bins(const FwdArgs& a, float* bins, int bins_ld, bool fp64, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  if (fp64) k_bins<true><<<a.n, 256, 0, s>>>(a, bins, bins_ld);
-  else k_bins<false><<<a.n, 256, 0, s>>>(a, bins, bins_ld);
+  if (fp64) {
+    k_bins64<<<a.n, 256, 0, s>>>(a, bins, bins_ld);
+  } else {
+    // groups: at most n / kBinGroup + one partial group per setup
+    const int group_blocks = (a.n + kBinGroup - 1) / kBinGroup + a.n_setups;
+    const dim3 grid(group_blocks + (a.n + 255) / 256, (bins_ld + kBinRows - 1) / kBinRows);
+    k_bins32<<<grid, 256, 0, s>>>(a, bins, bins_ld, group_blocks);
+  }
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ lnL
 // ln L = sum_j -(D_j - D_m,j)^2 / (2 s_j^2) - ln(2 pi s_j^2) / 2, with
 // s_j^2 = sigma_j^2 (+ 10^eps) (Eqs. 19, 22-23).  One warp per sample, FP64,
-// fixed-order butterfly reduction.
+// fixed-order butterfly reduction.  Without error inflation (no eps, or a
+// non-finite one) the normalisation sum and 1 / (2 sigma_j^2) come from the
+// observation's precomputed terms, so a bin costs one subtraction and one FMA.
 __global__ void __launch_bounds__(256) k_lnl(LnlArgs a) {
   const int lane = threadIdx.x & 31;
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1420,22 +1541,52 @@ __global__ void __launch_bounds__(256) k_lnl(LnlArgs a) {
   }
   const SetupDev& S = *a.setups[g];
   const double eps = a.log_eps ? a.log_eps[i] : __longlong_as_double(0x7ff8000000000000ll);
-  const double add = isfinite(eps) ? exp10(eps) : 0.0;
   const float* m = a.bins + (size_t)i * a.bins_ld;
   double acc = 0.0;
   int bad = 0;
-  for (int b = lane; b < S.n_bins; b += 32) {
-    const double dm = (double)m[b];
-    if (!isfinite(dm)) bad = 1;
-    const double sg = S.obs_sigma[b];
-    const double s2 = sg * sg + add;
-    const double r = S.obs_D[b] - dm;
-    acc += -r * r / (2.0 * s2) - 0.5 * log(2.0 * kPi * s2);
+  if (!isfinite(eps)) {
+    for (int b = lane; b < S.n_bins; b += 32) {
+      const double dm = (double)m[b];
+      if (!isfinite(dm)) bad = 1;
+      const double r = S.obs_D[b] - dm;
+      acc = fma(-r * r, S.obs_inv2s2[b], acc);
+    }
+  } else {
+    const double add = exp10(eps);
+    for (int b = lane; b < S.n_bins; b += 32) {
+      const double dm = (double)m[b];
+      if (!isfinite(dm)) bad = 1;
+      const double sg = S.obs_sigma[b];
+      const double s2 = sg * sg + add;
+      const double r = S.obs_D[b] - dm;
+      acc += -r * r / (2.0 * s2) - 0.5 * log(2.0 * kPi * s2);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   bad = __reduce_or_sync(0xffffffffu, bad);
+  if (!isfinite(eps)) acc += *S.obs_lnorm;
   if (lane == 0) a.lnl[i] = bad ? -HUGE_VAL : acc;
+}
+
+// The observation's model-independent likelihood terms: 1 / (2 sigma_b^2)
+// and sum_b -ln(2 pi sigma_b^2) / 2 (one warp, FP64, fixed order).
+__global__ void k_obs_terms(const double* sigma, int n_bins, double* inv2s2, double* lnorm) {
+  const int lane = threadIdx.x;
+  double acc = 0.0;
+  for (int b = lane; b < n_bins; b += 32) {
+    const double s2 = sigma[b] * sigma[b];
+    inv2s2[b] = 1.0 / (2.0 * s2);
+    acc += -0.5 * log(2.0 * kPi * s2);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) *lnorm = acc;
+}
+
+cudaError_t launch_obs_terms(const double* sigma, int n_bins, double* inv2s2, double* lnorm, cudaStream_t s) {
+  k_obs_terms<<<1, 32, 0, s>>>(sigma, n_bins, inv2s2, lnorm);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lnl(const LnlArgs& a, cudaStream_t s) {

@@ -244,6 +244,7 @@ __global__ void k_levels(int n_lev, double lt, double lb, const TablesDev* tab, 
   d.p_dyn64 = p;
   d.half_dp = (float)half_dp;
   d.half_dp64 = half_dp;
+  d.lpk = log2(p / kKB);
   lev[j] = d;
 }
 
