@@ -18,7 +18,7 @@ from typing import Dict, Iterable, List, Optional, Sequence, Tuple
 from . import hr2
 
 DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = (
-    (1, 16), (2, 8), (4, 2), (4, 3), (4, 4), (4, 6), (8, 1), (8, 2), (8, 3), (16, 1))
+    (1, 16), (2, 6), (2, 8), (4, 2), (4, 3), (4, 4), (4, 6), (8, 1), (8, 2), (8, 3), (16, 1))
 _LOCK = threading.Lock()
 
 

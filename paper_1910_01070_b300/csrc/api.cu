@@ -57,7 +57,7 @@ struct hr2_ctx {
   int n_sm = 0;
   size_t budget = 0;
   size_t used = 0;
-  hr2_launch_cfg cfg{2, 6};
+  hr2_launch_cfg cfg{2, 8};
   std::mutex mu;
   std::map<void*, size_t> blocks;  // device allocations and their sizes
   std::map<void*, Workspace*> ws;  // per stream
@@ -822,7 +822,7 @@ static int absorber_bound(const BatchShape& sh) {
 static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {
   int w = std::min(std::min(ctx->cfg.warps_per_cta, kForwardMaxThreads / 32), std::max(1, n));
   if (sh.cached) {
-    while (w > 1 && forward32_smem_bytes(w, sh.max_k) > kForwardSmemCap) --w;
+    while (w > 1 && forward32_smem_bytes(w, sh.max_k, forward32_stages(sh.max_mu, sh.para != 0)) > kForwardSmemCap) --w;
   }
   const int target = ctx->cfg.warps_per_cta * ctx->cfg.ctas_per_sm;
   const int ctas = std::max(1, std::min(32, (target + w - 1) / w));

@@ -14,10 +14,16 @@ namespace hr2 {
 constexpr int kTileNu = 128;
 constexpr int kMaxWarps = 16;
 // launch bounds of the FP32 forward kernel: at most 4 warps (samples) per
-// CTA, registers budgeted for 3 resident CTAs (12 warps) per SM; with two
-// packed pairs per lane each warp has enough independent work per level
+// CTA.  The level-gridded linear-source kernels with up to 4 angle nodes keep
+// one shared-memory stage per warp and are budgeted for 4 resident CTAs of 4
+// warps (16 warps per SM, 128 registers); the others (more nodes, the
+// parabolic source, the direct path) keep two stages and are budgeted for 3
+// (12 warps, 170 registers).
 constexpr int kForwardMaxThreads = 128;
 constexpr int kForwardMinBlocks = 3;
+constexpr int kForwardMinBlocksOneStage = 4;
+// shared-memory stages per warp of the level-gridded forward kernel
+__host__ __device__ constexpr int forward32_stages(int nmu, bool para) { return (nmu <= 4 && !para) ? 1 : 2; }
 // dynamic shared memory the cached forward kernel may use per CTA
 constexpr size_t kForwardSmemCap = 200u * 1024u;
 constexpr int kCiaH2H2 = HR2_MAX_SPECIES;      // offset slot of the H2-H2 CIA table
@@ -234,7 +240,7 @@ cudaError_t launch_plan(const FwdArgs& a, int* perm, PlanDev* plan, cudaStream_t
 // every setup of the batch at kt or kt - 1 absorbers (see absorber_bound)
 cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, bool para, int max_k,
                              int kt, cudaStream_t s);
-size_t forward32_smem_bytes(int warps, int max_k);
+size_t forward32_smem_bytes(int warps, int max_k, int stages);
 cudaError_t launch_forward64(const FwdArgs& a, int max_nmu, int max_nu, cudaStream_t s);
 cudaError_t launch_bins(const FwdArgs& a, float* bins, int bins_ld, bool fp64, cudaStream_t s);
 struct LnlArgs {

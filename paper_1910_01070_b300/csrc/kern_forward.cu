@@ -504,15 +504,17 @@ struct WarpPipe {
   unsigned long long* bar;
 };
 constexpr int kRecRing = 8;
-__host__ __device__ __forceinline__ size_t warp_rows_floats(int max_k) { return (size_t)2 * (2 * max_k + 4) * kTileNu; }
-__host__ __device__ __forceinline__ size_t warp_pipe_bytes(int max_k) {
-  return warp_rows_floats(max_k) * sizeof(float) + kRecRing * sizeof(LevRec) + 2 * sizeof(unsigned long long);
+__host__ __device__ __forceinline__ size_t warp_rows_floats(int max_k, int stages) {
+  return (size_t)stages * (2 * max_k + 4) * kTileNu;
 }
-__device__ __forceinline__ WarpPipe warp_pipe(unsigned char* base, int max_k) {
+__host__ __device__ __forceinline__ size_t warp_pipe_bytes(int max_k, int stages) {
+  return warp_rows_floats(max_k, stages) * sizeof(float) + kRecRing * sizeof(LevRec) + 2 * sizeof(unsigned long long);
+}
+__device__ __forceinline__ WarpPipe warp_pipe(unsigned char* base, int max_k, int stages) {
   WarpPipe w;
   w.rows = reinterpret_cast<float*>(base);
-  w.recs = reinterpret_cast<float*>(base + warp_rows_floats(max_k) * sizeof(float));
-  w.bar = reinterpret_cast<unsigned long long*>(base + warp_rows_floats(max_k) * sizeof(float) +
+  w.recs = reinterpret_cast<float*>(base + warp_rows_floats(max_k, stages) * sizeof(float));
+  w.bar = reinterpret_cast<unsigned long long*>(base + warp_rows_floats(max_k, stages) * sizeof(float) +
                                                 kRecRing * sizeof(LevRec));
   return w;
 }
@@ -808,8 +810,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     }
     const v2* sW2 = (KT > 0) ? wreg : sA2;
     // Pipeline over the levels (g = phase_base + j counts this warp's levels
-    // across items; level g uses stage g & 1, whose barrier completes phase
-    // (g >> 1) & 1).  Record of level j sits in ring slot j & 7.
+    // across items).  Record of level j sits in ring slot j & 7.
     //   before the loop: stage of level 0 <- block(0), records 0 .. 7
     //   level j:         wait stage(j)    -> block(j) present
     //                    issue stage(j+1) <- block(j+1) (T cell from record
@@ -817,7 +818,10 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     //                                        records j+4 .. j+7
     //                    compute level j
     // (record j+1 is needed at level j; records j+4 .. j+7 land with stage
-    // j+1, before level j+3 reads record j+4)
+    // j+1, before level j+3 reads record j+4).  With two stages the refill
+    // goes to the other stage before level j is computed; with one stage
+    // (more warps per SM fit) it goes to the same stage as soon as level j's
+    // opacity has read it, and lands while level j's source and layer run.
     if (phase_base == 0xffffffffu) return;       // this warp's pipeline failed earlier
     const size_t lvl_step = (size_t)(nT - 1) * (K + 2) * 2 * kTileNu;   // one level of the tile
     const size_t cell_step = (size_t)(K + 2) * 2 * kTileNu;             // one T cell of a level
@@ -825,33 +829,42 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     const unsigned rows_bytes = (unsigned)(cell_step * sizeof(float));
     const unsigned ph = phase_base;
     const int acell0 = __ldg(&reinterpret_cast<const LevRecC*>(rec)[0].acell);
-    issue_first(wp_, (int)(ph & 1u), K, lvl_tile + (size_t)acell0 * cell_step, rec, min(kRecRing, L + 1), lane);
+    constexpr int kSt = forward32_stages(NMU, PARA);
+    issue_first(wp_, kSt == 1 ? 0 : (int)(ph & 1u), K, lvl_tile + (size_t)acell0 * cell_step, rec,
+                min(kRecRing, L + 1), lane);
     // unrolled so that the loop-carried sweep state rotates through register
     // sets instead of being moved back at the end of each level
 #pragma unroll 4
     for (int j = 0; j <= L; ++j) {
       const unsigned g = ph + (unsigned)j;
-      const int stg = (int)(g & 1u);
-      if (!mbar_wait(wp_.bar + stg, (g >> 1) & 1u)) {
+      // two stages: level g in stage g & 1, phase (g >> 1) & 1 of its barrier;
+      // one stage: every level in stage 0, phase g & 1
+      const int stg = kSt == 1 ? 0 : (int)(g & 1u);
+      const unsigned par = kSt == 1 ? (g & 1u) : ((g >> 1) & 1u);
+      if (!mbar_wait(wp_.bar + stg, par)) {
         // the stage never completed: report, drain it (bounded) and stop using
         // this warp's pipeline
         if (lane == 0 && a.err) atomicOr(a.err, 1);
-        mbar_wait(wp_.bar + stg, (g >> 1) & 1u);
+        mbar_wait(wp_.bar + stg, par);
         phase_base = 0xffffffffu;
         return;
       }
       __syncwarp();
-      {
+      // refill a stage with level j+1 (T cell from record j+1) and, every
+      // fourth level, records j+4 .. j+7: the other stage right away (two
+      // stages), or this stage once this level's opacity has read it (one)
+      auto refill = [&]() {
         const bool more = j < L;
         const int acell_n = more ? __float_as_int(wp_.recs[((j + 1) & (kRecRing - 1)) * 16 + kRecCAcell]) : 0;
-        const int sn = (int)((g + 1u) & 1u);
+        const int sn = kSt == 1 ? 0 : (int)((g + 1u) & 1u);
         const bool do_rec = (j & 3) == 0 && j >= 4 && j + 4 <= L;
         const unsigned rec_bytes = (unsigned)(min(4, max(0, L - j - 3)) * (int)sizeof(LevRec));
         issue_level_pred(wp_.bar + sn, rows_bytes + (do_rec ? rec_bytes : 0u), more && lane == 0,
                          wp_.rows + (size_t)sn * (2 * K + 4) * kTileNu,
                          lvl_tile + (size_t)(j + 1) * lvl_step + (size_t)acell_n * cell_step, rows_bytes,
                          wp_.recs + (size_t)((j + 4) & (kRecRing - 1)) * 16, rec + (j + 4), rec_bytes, do_rec);
-      }
+      };
+      if constexpr (kSt == 2) refill();
       // record j (LevRecC): {wT, wT, wh2h2, wh2h2}, {wh2he, wh2he, half_dp,
       // half_dp}, {dtc, dtc, upl, rdnu}
       const float* rj = wp_.recs + (j & (kRecRing - 1)) * 16;
@@ -917,6 +930,10 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       v2 chi[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
+      if constexpr (kSt == 1) {
+        __syncwarp();   // every lane has read the stage
+        refill();
+      }
       level_physics<NMU, PARA, SX>(j, chi, rq2.upl, rq2.rdnu, rq1.dg, rq2.dtc, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
                                sMu, acc, E, st);
       __syncwarp();  // every lane is done with stage stg and record j before they are refilled
@@ -1031,7 +1048,9 @@ __device__ __forceinline__ bool item_small_x(const FwdArgs& a, const SetupDev& S
 }
 
 template <int NMU, bool CACHED, int KT, bool LIN, bool PARA>
-__global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forward32(FwdArgs a, int max_k) {
+__global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && forward32_stages(NMU, PARA) == 1)
+                                                           ? kForwardMinBlocksOneStage
+                                                           : kForwardMinBlocks) k_forward32(FwdArgs a, int max_k) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];   // cached path: per-warp pipelines
   __shared__ int s_item;
   __shared__ const void* sPtr[HR2_MAX_SPECIES];
@@ -1042,11 +1061,12 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
   WarpPipe wp_{};
   unsigned phase_base = 0;
   if (CACHED) {
-    wp_ = warp_pipe(dyn_smem + (size_t)warp * warp_pipe_bytes(max_k), max_k);
+    constexpr int kSt = forward32_stages(NMU, PARA);
+    wp_ = warp_pipe(dyn_smem + (size_t)warp * warp_pipe_bytes(max_k, kSt), max_k, kSt);
     // zero the stage rows once, so that rows a padded absorber may read are
     // finite before any copy has written them; then order these generic
     // writes before the bulk copies that will overwrite them
-    const int nrow = (int)warp_rows_floats(max_k);
+    const int nrow = (int)warp_rows_floats(max_k, kSt);
     for (int q = lane; q < nrow; q += 32) wp_.rows[q] = 0.f;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();
@@ -1104,11 +1124,11 @@ __global__ void __launch_bounds__(kForwardMaxThreads, kForwardMinBlocks) k_forwa
   }
 }
 
-size_t forward32_smem_bytes(int warps, int max_k) { return (size_t)warps * warp_pipe_bytes(max_k); }
+size_t forward32_smem_bytes(int warps, int max_k, int stages) { return (size_t)warps * warp_pipe_bytes(max_k, stages); }
 
 template <int NMU, bool CACHED, int KT, bool LIN, bool PARA = false>
 static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_t s) {
-  const size_t smem = CACHED ? forward32_smem_bytes(a.warps, max_k) : 0;
+  const size_t smem = CACHED ? forward32_smem_bytes(a.warps, max_k, forward32_stages(NMU, PARA)) : 0;
   if (CACHED) {
     // raise the kernel's dynamic shared-memory limit once (to the largest the
     // library ever asks for), so that later launches, also under stream
