@@ -806,13 +806,14 @@ static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setu
 // memory; the persistent CTAs per SM are raised to keep the configured
 // number of warps per SM.
 struct LaunchShape {
-  int warps, ctas_per_sm;
+  int warps, ctas_per_sm, stages;
 };
 // Compile-time absorber bound of the cached forward kernel: the batch's
 // largest absorber count rounded up to even, when no setup of the batch has
 // more than 4 absorbers fewer (padded absorbers get weight 0 and read finite
 // values of the stage; on the uneven 6-10-absorber batch this is 3 % faster
-// than the runtime-count loop, with identical results), else 0 (runtime count).
+// than the runtime-count loop, with identical results), else 0 (runtime
+// count).
 static int absorber_bound(const BatchShape& sh) {
   if (!sh.cached || sh.max_k < 1) return 0;
   const int kt = (sh.max_k + 1) & ~1;
@@ -821,12 +822,13 @@ static int absorber_bound(const BatchShape& sh) {
 
 static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {
   int w = std::min(std::min(ctx->cfg.warps_per_cta, kForwardMaxThreads / 32), std::max(1, n));
+  const int st = forward32_stages(sh.max_mu, sh.para != 0, absorber_bound(sh), n);
   if (sh.cached) {
-    while (w > 1 && forward32_smem_bytes(w, sh.max_k, forward32_stages(sh.max_mu, sh.para != 0)) > kForwardSmemCap) --w;
+    while (w > 1 && forward32_smem_bytes(w, sh.max_k, st) > kForwardSmemCap) --w;
   }
   const int target = ctx->cfg.warps_per_cta * ctx->cfg.ctas_per_sm;
   const int ctas = std::max(1, std::min(32, (target + w - 1) / w));
-  return {w, ctas};
+  return {w, ctas, st};
 }
 
 extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
@@ -891,7 +893,7 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
     const int grid = ctx->n_sm * ls.ctas_per_sm;
     if (ev.first) HR2_CU(cudaEventRecord(ev.first, s));
     if ((e = launch_forward32(a, sh.max_mu, grid, sh.cached != 0, sh.linear != 0, sh.para != 0, sh.max_k, absorber_bound(sh),
-                              s)) != cudaSuccess)
+                              ls.stages, s)) != cudaSuccess)
       return fail(HR2_ECUDA, "forward32 launch: %s", cudaGetErrorString(e));
     if (ev.second) HR2_CU(cudaEventRecord(ev.second, s));
   }
@@ -1166,7 +1168,7 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
   // forward kernel reads it; everything else is overwritten by the kernels
   if ((e = launch_prep(a, s)) != cudaSuccess || (e = launch_plan(a, (int*)a.perm, (PlanDev*)a.plan, s)) != cudaSuccess ||
       (e = launch_forward32(a, sh.max_mu, ctx->n_sm * ls.ctas_per_sm, sh.cached != 0, sh.linear != 0, sh.para != 0,
-                        sh.max_k, absorber_bound(sh), s)) != cudaSuccess ||
+                        sh.max_k, absorber_bound(sh), ls.stages, s)) != cudaSuccess ||
       (e = launch_bins(a, out_bins, bins_ld, false, s)) != cudaSuccess)
     return fail(HR2_ECUDA, "allocation-free launch: %s", cudaGetErrorString(e));
   return HR2_OK;

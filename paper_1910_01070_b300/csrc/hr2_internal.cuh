@@ -14,17 +14,25 @@ namespace hr2 {
 constexpr int kTileNu = 128;
 constexpr int kMaxWarps = 16;
 // launch bounds of the FP32 forward kernel: at most 4 warps (samples) per
-// CTA.  The level-gridded linear-source kernels with up to 4 angle nodes keep
-// one shared-memory stage per warp and are budgeted for 4 resident CTAs of 4
-// warps (16 warps per SM, 128 registers); the others (more nodes, the
-// parabolic source, the direct path) keep two stages and are budgeted for 3
+// CTA.  The level-gridded linear-source kernels with up to 4 angle nodes are
+// budgeted for 4 resident CTAs of 4 warps (16 warps per SM, 128 registers);
+// the others (more nodes, the parabolic source, the direct path) for 3
 // (12 warps, 170 registers).
 constexpr int kForwardMaxThreads = 128;
 constexpr int kForwardMinBlocks = 3;
-constexpr int kForwardMinBlocksOneStage = 4;
-// shared-memory stages per warp of the level-gridded forward kernel
-__host__ __device__ constexpr int forward32_stages(int nmu, bool para) { return (nmu <= 4 && !para) ? 1 : 2; }
-// dynamic shared memory the cached forward kernel may use per CTA
+constexpr int kForwardMinBlocksSmall = 4;
+// shared-memory stages per warp of the level-gridded forward kernel, for a
+// kernel with nmu angle nodes, compiled absorber bound kt (0: runtime count)
+// and a batch of n samples.  One stage (more warps per SM fit; each level's
+// copy lands while its source and layer run) for the linear-source kernels
+// with up to 4 nodes, and for those with a bound of 8 or more on batches of at
+// least kOneStageMinBatch samples; two (the copy is issued a whole level
+// ahead, which few warps per SM need to hide its latency) otherwise.  The
+// kernels exist in exactly these variants.
+constexpr int kOneStageMinBatch = 16;
+__host__ __device__ constexpr int forward32_stages(int nmu, bool para, int kt, int n) {
+  return (para || kt == 0) ? 2 : (nmu <= 4 ? 1 : ((kt >= 8 && n >= kOneStageMinBatch) ? 1 : 2));
+}// dynamic shared memory the cached forward kernel may use per CTA
 constexpr size_t kForwardSmemCap = 200u * 1024u;
 constexpr int kCiaH2H2 = HR2_MAX_SPECIES;      // offset slot of the H2-H2 CIA table
 constexpr int kCiaH2He = HR2_MAX_SPECIES + 1;  // offset slot of the H2-He CIA table
@@ -239,7 +247,7 @@ cudaError_t launch_plan(const FwdArgs& a, int* perm, PlanDev* plan, cudaStream_t
 // kt: 0, or an even bound on the absorber count of the cached path with
 // every setup of the batch at kt or kt - 1 absorbers (see absorber_bound)
 cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, bool para, int max_k,
-                             int kt, cudaStream_t s);
+                             int kt, int stages, cudaStream_t s);
 size_t forward32_smem_bytes(int warps, int max_k, int stages);
 cudaError_t launch_forward64(const FwdArgs& a, int max_nmu, int max_nu, cudaStream_t s);
 cudaError_t launch_bins(const FwdArgs& a, float* bins, int bins_ld, bool fp64, cudaStream_t s);

@@ -742,7 +742,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
 // level-gridded operand through the warp's bulk-copy pipeline (rows of level
 // j+1 and the record of level j+2 land while level j is computed).
 // Otherwise the FP16 tables are read and interpolated bilinearly in place.
-template <int NMU, bool CACHED, int KT, bool LIN, bool PARA, bool SX>
+template <int NMU, bool CACHED, int KT, bool LIN, bool PARA, bool SX, int ST>
 __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
                                            const v2* sA2, const v2* sAc2, const void* const* sPtr,
                                            const v2* sMnl, const v2* sImu, const v2* sMu, const WarpPipe& wp_,
@@ -829,7 +829,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     const unsigned rows_bytes = (unsigned)(cell_step * sizeof(float));
     const unsigned ph = phase_base;
     const int acell0 = __ldg(&reinterpret_cast<const LevRecC*>(rec)[0].acell);
-    constexpr int kSt = forward32_stages(NMU, PARA);
+    constexpr int kSt = ST;
     issue_first(wp_, kSt == 1 ? 0 : (int)(ph & 1u), K, lvl_tile + (size_t)acell0 * cell_step, rec,
                 min(kRecRing, L + 1), lane);
     // unrolled so that the loop-carried sweep state rotates through register
@@ -1047,10 +1047,10 @@ __device__ __forceinline__ bool item_small_x(const FwdArgs& a, const SetupDev& S
   return __any_sync(0xffffffffu, f);
 }
 
-template <int NMU, bool CACHED, int KT, bool LIN, bool PARA>
-__global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && forward32_stages(NMU, PARA) == 1)
-                                                           ? kForwardMinBlocksOneStage
-                                                           : kForwardMinBlocks) k_forward32(FwdArgs a, int max_k) {
+template <int NMU, bool CACHED, int KT, bool LIN, bool PARA, int ST>
+__global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PARA) ? kForwardMinBlocksSmall
+                                                                                     : kForwardMinBlocks)
+    k_forward32(FwdArgs a, int max_k) {
   extern __shared__ __align__(16) unsigned char dyn_smem[];   // cached path: per-warp pipelines
   __shared__ int s_item;
   __shared__ const void* sPtr[HR2_MAX_SPECIES];
@@ -1061,7 +1061,7 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && forward32_stage
   WarpPipe wp_{};
   unsigned phase_base = 0;
   if (CACHED) {
-    constexpr int kSt = forward32_stages(NMU, PARA);
+    constexpr int kSt = ST;
     wp_ = warp_pipe(dyn_smem + (size_t)warp * warp_pipe_bytes(max_k, kSt), max_k, kSt);
     // zero the stage rows once, so that rows a padded absorber may read are
     // finite before any copy has written them; then order these generic
@@ -1115,10 +1115,10 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && forward32_stage
     __syncthreads();
     if (active) {
       if (item_small_x(a, S, T, i, tile))
-        solve_tile<NMU, CACHED, KT, LIN, PARA, true>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu,
+        solve_tile<NMU, CACHED, KT, LIN, PARA, true, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu,
                                                      wp_, phase_base);
       else
-        solve_tile<NMU, CACHED, KT, LIN, PARA, false>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu,
+        solve_tile<NMU, CACHED, KT, LIN, PARA, false, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu,
                                                       wp_, phase_base);
     }
   }
@@ -1126,9 +1126,9 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && forward32_stage
 
 size_t forward32_smem_bytes(int warps, int max_k, int stages) { return (size_t)warps * warp_pipe_bytes(max_k, stages); }
 
-template <int NMU, bool CACHED, int KT, bool LIN, bool PARA = false>
+template <int NMU, bool CACHED, int KT, bool LIN, bool PARA = false, int ST = 2>
 static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_t s) {
-  const size_t smem = CACHED ? forward32_smem_bytes(a.warps, max_k, forward32_stages(NMU, PARA)) : 0;
+  const size_t smem = CACHED ? forward32_smem_bytes(a.warps, max_k, ST) : 0;
   if (CACHED) {
     // raise the kernel's dynamic shared-memory limit once (to the largest the
     // library ever asks for), so that later launches, also under stream
@@ -1139,31 +1139,48 @@ static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(raised & bit)) {
-      e = cudaFuncSetAttribute(k_forward32<NMU, CACHED, KT, LIN, PARA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_forward32<NMU, CACHED, KT, LIN, PARA, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kForwardSmemCap);
       if (e != cudaSuccess) return e;
       raised |= bit;
     }
     if (smem > kForwardSmemCap) return cudaErrorInvalidValue;
   }
-  k_forward32<NMU, CACHED, KT, LIN, PARA><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
+  k_forward32<NMU, CACHED, KT, LIN, PARA, ST><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
   return cudaGetLastError();
 }
 
+// cached path, compiled absorber bound KT: the stage variants that exist
+// (forward32_stages): one stage for up to 4 nodes, one or two (by the
+// caller's choice) for more nodes with KT >= 8, two otherwise
+template <int NMU, int KT, bool LIN>
+static cudaError_t launch_kt(const FwdArgs& a, int grid, int max_k, int stages, cudaStream_t s) {
+  if constexpr (KT == 0) {
+    return launch_one<NMU, true, 0, LIN, false, 2>(a, grid, max_k, s);
+  } else if constexpr (NMU <= 4) {
+    return launch_one<NMU, true, KT, LIN, false, 1>(a, grid, max_k, s);
+  } else if constexpr (KT >= 8) {
+    return stages == 1 ? launch_one<NMU, true, KT, LIN, false, 1>(a, grid, max_k, s)
+                       : launch_one<NMU, true, KT, LIN, false, 2>(a, grid, max_k, s);
+  } else {
+    return launch_one<NMU, true, KT, LIN, false, 2>(a, grid, max_k, s);
+  }
+}
+
 // cached path: absorber bound kt (0 = any mix of absorber counts, else an
-// even bound with every setup at kt or kt - 1)
+// even bound with every setup at kt - 4 .. kt)
 template <int NMU, bool LIN>
-static cudaError_t launch_cached(const FwdArgs& a, int grid, int max_k, int kt, cudaStream_t s) {
+static cudaError_t launch_cached(const FwdArgs& a, int grid, int max_k, int kt, int stages, cudaStream_t s) {
   switch (kt) {
-    case 0: return launch_one<NMU, true, 0, LIN>(a, grid, max_k, s);
-    case 2: return launch_one<NMU, true, 2, LIN>(a, grid, max_k, s);
-    case 4: return launch_one<NMU, true, 4, LIN>(a, grid, max_k, s);
-    case 6: return launch_one<NMU, true, 6, LIN>(a, grid, max_k, s);
-    case 8: return launch_one<NMU, true, 8, LIN>(a, grid, max_k, s);
-    case 10: return launch_one<NMU, true, 10, LIN>(a, grid, max_k, s);
-    case 12: return launch_one<NMU, true, 12, LIN>(a, grid, max_k, s);
-    case 14: return launch_one<NMU, true, 14, LIN>(a, grid, max_k, s);
-    case 16: return launch_one<NMU, true, 16, LIN>(a, grid, max_k, s);
+    case 0: return launch_kt<NMU, 0, LIN>(a, grid, max_k, stages, s);
+    case 2: return launch_kt<NMU, 2, LIN>(a, grid, max_k, stages, s);
+    case 4: return launch_kt<NMU, 4, LIN>(a, grid, max_k, stages, s);
+    case 6: return launch_kt<NMU, 6, LIN>(a, grid, max_k, stages, s);
+    case 8: return launch_kt<NMU, 8, LIN>(a, grid, max_k, stages, s);
+    case 10: return launch_kt<NMU, 10, LIN>(a, grid, max_k, stages, s);
+    case 12: return launch_kt<NMU, 12, LIN>(a, grid, max_k, stages, s);
+    case 14: return launch_kt<NMU, 14, LIN>(a, grid, max_k, stages, s);
+    case 16: return launch_kt<NMU, 16, LIN>(a, grid, max_k, stages, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -1171,27 +1188,28 @@ static cudaError_t launch_cached(const FwdArgs& a, int grid, int max_k, int kt, 
 // parabolic source: runtime absorber count only (an option, not the fast path)
 template <int NMU>
 static cudaError_t launch_nmu(const FwdArgs& a, int grid, bool cached, bool linear, bool para, int max_k, int kt,
-                              cudaStream_t s) {
+                              int stages, cudaStream_t s) {
   if (para) {
     if (!cached) return linear ? cudaErrorInvalidValue : launch_one<NMU, false, 0, false, true>(a, grid, max_k, s);
     return linear ? launch_one<NMU, true, 0, true, true>(a, grid, max_k, s)
                   : launch_one<NMU, true, 0, false, true>(a, grid, max_k, s);
   }
   if (!cached) return linear ? cudaErrorInvalidValue : launch_one<NMU, false, 0, false>(a, grid, max_k, s);
-  return linear ? launch_cached<NMU, true>(a, grid, max_k, kt, s) : launch_cached<NMU, false>(a, grid, max_k, kt, s);
+  return linear ? launch_cached<NMU, true>(a, grid, max_k, kt, stages, s)
+                : launch_cached<NMU, false>(a, grid, max_k, kt, stages, s);
 }
 
 cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, bool para, int max_k,
-                             int kt, cudaStream_t s) {
+                             int kt, int stages, cudaStream_t s) {
   switch (max_nmu) {
-    case 1: return launch_nmu<1>(a, grid, cached, linear, para, max_k, kt, s);
-    case 2: return launch_nmu<2>(a, grid, cached, linear, para, max_k, kt, s);
-    case 3: return launch_nmu<3>(a, grid, cached, linear, para, max_k, kt, s);
-    case 4: return launch_nmu<4>(a, grid, cached, linear, para, max_k, kt, s);
-    case 5: return launch_nmu<5>(a, grid, cached, linear, para, max_k, kt, s);
-    case 6: return launch_nmu<6>(a, grid, cached, linear, para, max_k, kt, s);
-    case 7: return launch_nmu<7>(a, grid, cached, linear, para, max_k, kt, s);
-    case 8: return launch_nmu<8>(a, grid, cached, linear, para, max_k, kt, s);
+    case 1: return launch_nmu<1>(a, grid, cached, linear, para, max_k, kt, stages, s);
+    case 2: return launch_nmu<2>(a, grid, cached, linear, para, max_k, kt, stages, s);
+    case 3: return launch_nmu<3>(a, grid, cached, linear, para, max_k, kt, stages, s);
+    case 4: return launch_nmu<4>(a, grid, cached, linear, para, max_k, kt, stages, s);
+    case 5: return launch_nmu<5>(a, grid, cached, linear, para, max_k, kt, stages, s);
+    case 6: return launch_nmu<6>(a, grid, cached, linear, para, max_k, kt, stages, s);
+    case 7: return launch_nmu<7>(a, grid, cached, linear, para, max_k, kt, stages, s);
+    case 8: return launch_nmu<8>(a, grid, cached, linear, para, max_k, kt, stages, s);
     default: return cudaErrorInvalidValue;
   }
 }
