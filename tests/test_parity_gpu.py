@@ -391,6 +391,28 @@ def test_small_batches_use_every_warp(eng):
         assert np.array_equal(got[0], ref[0][:m]) and np.array_equal(got[1], ref[1][:m])
 
 
+@pytest.mark.parametrize("K,n_mu", [(12, 8), (9, 6), (6, 4)])
+def test_stage_variants_agree_bitwise(eng, K, n_mu):
+    """The level-gridded kernels with more than 4 angle nodes and an absorber
+    bound of 8 or more run with two shared-memory stages below 16 samples and
+    one stage from 16 up; the two variants (and the one-stage kernels of the
+    other shapes at any batch size) give bit-identical spectra, and both match
+    the oracle."""
+    spec, tabs = _absorber_spec(K, 90 + K)
+    setup = W.make_setup(spec, 5000.0, 5299.0, 24, range(K), n_mu, 3, 2, 300.0, 6)
+    t = eng.add_tables(spec, "fp16", tabs)
+    s = eng.add_setup(t, setup)
+    theta = W.draw_params(setup, 40, 61, W.Prior(b=(0.8, 0.97)))
+    sid = np.zeros(40, np.int32)
+    big = _run(eng, [s], sid, theta)
+    for m in (1, 5, 15):
+        small = _run(eng, [s], sid[:m], theta[:m])
+        assert np.array_equal(small[0], big[0][:m]) and np.array_equal(small[1], big[1][:m])
+    om = oracle_model(tables_as_stored(tabs, "fp16"), setup)
+    for i in (0, 17, 39):
+        _compare(om, theta[i], big[0][i], big[1][i], FLUX_RTOL, 300)
+
+
 def test_launch_shapes_agree_bitwise(eng):
     wl, tabs, stored, setups, st = _workload_on(eng, "uneven2048_3setups", "fp16")
     theta, sid = wl.params(96, seed_offset=3)
