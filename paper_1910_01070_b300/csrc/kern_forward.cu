@@ -859,9 +859,16 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
         const int sn = kSt == 1 ? 0 : (int)((g + 1u) & 1u);
         const bool do_rec = (j & 3) == 0 && j >= 4 && j + 4 <= L;
         const unsigned rec_bytes = (unsigned)(min(4, max(0, L - j - 3)) * (int)sizeof(LevRec));
-        issue_level_pred(wp_.bar + sn, rows_bytes + (do_rec ? rec_bytes : 0u), more && lane == 0,
+        // the stage keeps the CIA rows of the T cell it holds (one stage: level
+        // j's; two: level j-1's, none before this item's first refill): where
+        // level j+1 has the same cell only its absorber rows are copied
+        const int held = kSt == 1 ? __float_as_int(wp_.recs[(j & (kRecRing - 1)) * 16 + kRecCAcell])
+                                  : (j >= 1 ? __float_as_int(wp_.recs[((j - 1) & (kRecRing - 1)) * 16 + kRecCAcell])
+                                            : -1);
+        const unsigned rb = held == acell_n ? rows_bytes - (unsigned)(4 * kTileNu * sizeof(float)) : rows_bytes;
+        issue_level_pred(wp_.bar + sn, rb + (do_rec ? rec_bytes : 0u), more && lane == 0,
                          wp_.rows + (size_t)sn * (2 * K + 4) * kTileNu,
-                         lvl_tile + (size_t)(j + 1) * lvl_step + (size_t)acell_n * cell_step, rows_bytes,
+                         lvl_tile + (size_t)(j + 1) * lvl_step + (size_t)acell_n * cell_step, rb,
                          wp_.recs + (size_t)((j + 4) & (kRecRing - 1)) * 16, rec + (j + 4), rec_bytes, do_rec);
       };
       if constexpr (kSt == 2) refill();
