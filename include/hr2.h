@@ -189,7 +189,8 @@ typedef struct {
                                  call takes setups of a single kind.             */
 } hr2_setup_desc;
 
-/* Launch shape of the persistent forward kernel (chosen by the autotuner). */
+/* Launch shape of the persistent forward kernel (chosen by the autotuner;
+ * a new context starts with 2 warps per CTA and 8 CTAs per SM). */
 typedef struct {
   int warps_per_cta;          /* samples processed together per work item: 1..16;
                                  a batch with fewer samples uses fewer, with
