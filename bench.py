@@ -625,7 +625,7 @@ def _kernel_hash() -> str:
     the committed DRAM counters still belong to it."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("kern_forward.cu", "hr2_internal.cuh"):
+    for f in ("kern_forward.cu", "kern_forward32.cuh", "hr2_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1910_01070_b300", "csrc", f)) as fh:
             h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:16]

@@ -15,7 +15,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhr2.so")
-SOURCES = ["api.cu", "kern_setup.cu", "kern_forward.cu", "kern_nested.cu"]
+SOURCES = ["api.cu", "kern_setup.cu", "kern_forward.cu", "kern_nested.cu", "kern_fwd32_n12.cu", "kern_fwd32_n34.cu",
+           "kern_fwd32_n56.cu", "kern_fwd32_n78.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

@@ -248,6 +248,19 @@ cudaError_t launch_plan(const FwdArgs& a, int* perm, PlanDev* plan, cudaStream_t
 // every setup of the batch at kt or kt - 1 absorbers (see absorber_bound)
 cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, bool para, int max_k,
                              int kt, int stages, cudaStream_t s);
+// the same for one angle-node count (kern_fwd32_n*.cu)
+#define HR2_DECLARE_FWD32(N)                                                                                 \
+  cudaError_t launch_forward32_n##N(const FwdArgs& a, int grid, bool cached, bool linear, bool para, int max_k, \
+                                    int kt, int stages, cudaStream_t s);
+HR2_DECLARE_FWD32(1)
+HR2_DECLARE_FWD32(2)
+HR2_DECLARE_FWD32(3)
+HR2_DECLARE_FWD32(4)
+HR2_DECLARE_FWD32(5)
+HR2_DECLARE_FWD32(6)
+HR2_DECLARE_FWD32(7)
+HR2_DECLARE_FWD32(8)
+#undef HR2_DECLARE_FWD32
 size_t forward32_smem_bytes(int warps, int max_k, int stages);
 cudaError_t launch_forward64(const FwdArgs& a, int max_nmu, int max_nu, cudaStream_t s);
 cudaError_t launch_bins(const FwdArgs& a, float* bins, int bins_ld, bool fp64, cudaStream_t s);

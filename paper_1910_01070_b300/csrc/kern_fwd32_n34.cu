@@ -1,0 +1,17 @@
+// kern_fwd32_n34.cu -- instantiations of the FP32 forward kernel for 3 and 4
+// angle nodes (see kern_forward32.cuh).
+#include "kern_forward32.cuh"
+
+namespace hr2 {
+
+cudaError_t launch_forward32_n3(const FwdArgs& a, int grid, bool cached, bool linear, bool para, int max_k,
+                                int kt, int stages, cudaStream_t s) {
+  return launch_nmu<3>(a, grid, cached, linear, para, max_k, kt, stages, s);
+}
+
+cudaError_t launch_forward32_n4(const FwdArgs& a, int grid, bool cached, bool linear, bool para, int max_k,
+                                int kt, int stages, cudaStream_t s) {
+  return launch_nmu<4>(a, grid, cached, linear, para, max_k, kt, stages, s);
+}
+
+}  // namespace hr2
