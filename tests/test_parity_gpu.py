@@ -109,6 +109,29 @@ def test_cia_only_setup(eng):
         _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, 90)
 
 
+@pytest.mark.parametrize("storage", ["fp16-level-gridded", "fp16-direct", "fp64"])
+def test_low_wavenumbers_small_x_planck(eng, storage):
+    """20-339 cm^-1 with a hot profile: hc nu / kT falls below 1/16 on the first
+    tiles, where 1 - e^{-x} of the Planck function comes from its series (the
+    FP32 kernel runs those items through its small-x sweep), and rises to ~2 on
+    the last ones.  Every path matches the oracle at its tolerance."""
+    spec = W.TableSpec(3, np.linspace(300.0, 4000.0, 8), np.linspace(-4.0, 2.0, 5), 20.0, 1.0, 320, seed=33)
+    tabs = W.make_tables(spec)
+    st, direct = ("fp16", storage == "fp16-direct") if storage.startswith("fp16") else ("fp64", False)
+    setup = W.make_setup(spec, 20.0, 339.0, 30, range(3), 4, 2, 2, 100.0, 5)
+    t = eng.add_tables(spec, st, tabs)
+    s = eng.add_setup(t, setup, level_cache=not direct)
+    theta = W.draw_params(setup, 6, 17, W.Prior(T1=(2500.0, 3800.0), b=(0.85, 0.97)))
+    x_min = 1.4387768775039337 * 20.0 / theta[:, W.P_T0].max()
+    assert x_min < 1.0 / 16.0
+    bins, hi, status = _run(eng, [s], np.zeros(6, np.int32), theta)
+    assert np.all(status == 0)
+    om = oracle_model(tables_as_stored(tabs, st), setup)
+    tol = FLUX_RTOL if st == "fp16" else FP64_RTOL
+    for i in range(6):
+        _compare(om, theta[i], bins[i], hi[i], tol, setup.n_nu)
+
+
 def _absorber_spec(K, seed, with_cia=True):
     spec = W.TableSpec(K, np.linspace(300.0, 2500.0, 5), np.linspace(-4.0, 2.0, 4), 5000.0, 1.0, 300, seed=seed)
     tabs = W.make_tables(spec)
