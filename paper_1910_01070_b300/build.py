@@ -15,8 +15,10 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhr2.so")
-SOURCES = ["api.cu", "kern_setup.cu", "kern_forward.cu", "kern_nested.cu", "kern_fwd32_n12.cu", "kern_fwd32_n34.cu",
-           "kern_fwd32_n56.cu", "kern_fwd32_n78.cu"]
+# (source, object, extra defines): the FP32 forward kernel's instantiations are
+# compiled once per angle-node count, first, since they take longest
+UNITS = [("kern_fwd32_inst.cu", "kern_fwd32_n%d.o" % n, ["-DHR2_FWD32_NMU=%d" % n]) for n in range(1, 9)] + [
+    (src, src.replace(".cu", ".o"), []) for src in ("kern_forward.cu", "kern_nested.cu", "kern_setup.cu", "api.cu")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
@@ -34,9 +36,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     os.makedirs(BUILD, exist_ok=True)
     extra = ["-Xptxas", "-v"] if ptxas_info else []
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    def compile_one(unit):
+        src, obj, defines = unit
+        obj = os.path.join(BUILD, obj)
+        cmd = [NVCC, *ARCH, *FLAGS, *defines, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s%s" % (src, r.stdout, r.stderr))
@@ -44,8 +47,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
             sys.stderr.write(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(UNITS), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(compile_one, UNITS))
     tmp = LIB + ".tmp.%d" % os.getpid()
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -248,7 +248,7 @@ cudaError_t launch_plan(const FwdArgs& a, int* perm, PlanDev* plan, cudaStream_t
 // every setup of the batch at kt or kt - 1 absorbers (see absorber_bound)
 cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, bool para, int max_k,
                              int kt, int stages, cudaStream_t s);
-// the same for one angle-node count (kern_fwd32_n*.cu)
+// the same for one angle-node count (kern_fwd32_inst.cu)
 #define HR2_DECLARE_FWD32(N)                                                                                 \
   cudaError_t launch_forward32_n##N(const FwdArgs& a, int grid, bool cached, bool linear, bool para, int max_k, \
                                     int kt, int stages, cudaStream_t s);

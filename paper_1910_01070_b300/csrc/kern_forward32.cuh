@@ -1,6 +1,6 @@
 // kern_forward32.cuh -- the FP32 forward kernel k_forward32 (level sweep of
 // one sample on one wavenumber tile per warp) and its launch templates,
-// instantiated per angle-node count in kern_fwd32_n*.cu so that the
+// instantiated per angle-node count in kern_fwd32_inst.cu so that the
 // instantiations compile in parallel.
 #pragma once
 #include <math.h>
@@ -859,14 +859,30 @@ static cudaError_t launch_cached(const FwdArgs& a, int grid, int max_k, int kt, 
   }
 }
 
-// parabolic source: runtime absorber count only (an option, not the fast path)
+// parabolic source on the level-gridded path: the same absorber bounds as the
+// linear source, two stages
+template <int NMU, bool LIN>
+static cudaError_t launch_para(const FwdArgs& a, int grid, int max_k, int kt, cudaStream_t s) {
+  switch (kt) {
+    case 0: return launch_one<NMU, true, 0, LIN, true, 2>(a, grid, max_k, s);
+    case 2: return launch_one<NMU, true, 2, LIN, true, 2>(a, grid, max_k, s);
+    case 4: return launch_one<NMU, true, 4, LIN, true, 2>(a, grid, max_k, s);
+    case 6: return launch_one<NMU, true, 6, LIN, true, 2>(a, grid, max_k, s);
+    case 8: return launch_one<NMU, true, 8, LIN, true, 2>(a, grid, max_k, s);
+    case 10: return launch_one<NMU, true, 10, LIN, true, 2>(a, grid, max_k, s);
+    case 12: return launch_one<NMU, true, 12, LIN, true, 2>(a, grid, max_k, s);
+    case 14: return launch_one<NMU, true, 14, LIN, true, 2>(a, grid, max_k, s);
+    case 16: return launch_one<NMU, true, 16, LIN, true, 2>(a, grid, max_k, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 template <int NMU>
 static cudaError_t launch_nmu(const FwdArgs& a, int grid, bool cached, bool linear, bool para, int max_k, int kt,
                               int stages, cudaStream_t s) {
   if (para) {
     if (!cached) return linear ? cudaErrorInvalidValue : launch_one<NMU, false, 0, false, true>(a, grid, max_k, s);
-    return linear ? launch_one<NMU, true, 0, true, true>(a, grid, max_k, s)
-                  : launch_one<NMU, true, 0, false, true>(a, grid, max_k, s);
+    return linear ? launch_para<NMU, true>(a, grid, max_k, kt, s) : launch_para<NMU, false>(a, grid, max_k, kt, s);
   }
   if (!cached) return linear ? cudaErrorInvalidValue : launch_one<NMU, false, 0, false>(a, grid, max_k, s);
   return linear ? launch_cached<NMU, true>(a, grid, max_k, kt, stages, s)
