@@ -91,3 +91,47 @@ def test_one_source_interpolation_per_batch(eng):
     theta = W.draw_params(lin, 2, 3, W.Prior(b=(0.8, 0.95)))
     with pytest.raises(hr2.Hr2Error):
         _run(eng, [s1, s2], np.array([0, 1], np.int32), theta, 64)
+
+
+@pytest.mark.parametrize("ks", [(1, 2), (5, 6), (7, 10), (13, 16), (1, 6)], ids=lambda ks: "k" + "_".join(map(str, ks)))
+def test_parabolic_absorber_bounds(eng, ks):
+    """The parabolic source on the level-gridded operand runs the kernel compiled
+    for the batch's even absorber bound (counts from K-4 to K, zero-weight
+    padding) or, for a wider mix ((1, 6)), the runtime-count kernel.  Every
+    sample matches the oracle of its setup, and a setup's samples come out
+    bit-identical alone (its own bound) and in a mix with a 1-absorber setup
+    (runtime count): padding adds exact zeros in the same summation order."""
+    K = max(ks)
+    spec = W.TableSpec(K, np.linspace(300.0, 2500.0, 5), np.linspace(-4.0, 2.0, 4), 5000.0, 1.0, 300, seed=60 + K)
+    tabs = W.make_tables(spec)
+    t = eng.add_tables(spec, "fp16", tabs)
+    specs = [dataclasses.replace(W.make_setup(spec, 5000.0 + 5 * g, 5260.0 + 9 * g, 14 + 5 * g, range(k), 3, 2, 2,
+                                              300.0, 5), sc="parabolic") for g, k in enumerate(ks)]
+    setups = [eng.add_setup(t, sp) for sp in specs]
+    n = 8
+    sid = np.arange(n, dtype=np.int32) % len(ks)
+    theta = np.concatenate([W.draw_params(specs[g], 1, 200 + i, W.Prior(b=(0.8, 0.97))) for i, g in enumerate(sid)])
+    nn = max(sp.n_nu for sp in specs)
+    b, h, st = _run(eng, setups, sid, theta, nn)
+    assert np.all(st == 0)
+    stored = tables_as_stored(tabs, "fp16")
+    for g, sp in enumerate(specs):
+        om = oracle_model(stored, sp)
+        for i in np.nonzero(sid == g)[0]:
+            ob, otop, ok = om.forward(theta[i], want_top=True)
+            assert ok
+            assert rel_flux_err(h[i, :sp.n_nu], otop) <= FLUX_RTOL
+            assert rel_flux_err(b[i, :sp.n_bins], ob) <= FLUX_RTOL
+    # the widest setup alone, then mixed with a 1-absorber setup (runtime count)
+    one = dataclasses.replace(W.make_setup(spec, 5003.0, 5200.0, 20, range(1), 3, 2, 2, 300.0, 5), sc="parabolic")
+    s_one = eng.add_setup(t, one)
+    g = len(ks) - 1
+    idx = np.nonzero(sid == g)[0]
+    b_alone, h_alone, _ = _run(eng, [setups[g]], np.zeros(len(idx), np.int32), theta[idx], nn)
+    th_one = W.draw_params(one, 3, 9, W.Prior(b=(0.8, 0.97)))
+    mix_sid = np.concatenate([np.zeros(len(idx), np.int32), np.ones(3, np.int32)])
+    b_mix, h_mix, st_mix = _run(eng, [setups[g], s_one], mix_sid, np.concatenate([theta[idx], th_one]), nn)
+    assert np.all(st_mix == 0)
+    ng = specs[g].n_nu
+    assert np.array_equal(h_mix[:len(idx), :ng], h_alone[:, :ng])
+    assert np.array_equal(b_mix[:len(idx), :specs[g].n_bins], b_alone[:, :specs[g].n_bins])
