@@ -204,6 +204,7 @@ struct SampleDev {
   float Ac[HR2_MAX_SPECIES];  // 1 + ln2 * (its tail)
   float W[HR2_MAX_SPECIES];   // 2^(log2(x_s c) + off_s log2(10) - shift): the same factor as a weight
   double scale;               // f (R_* / d)^2
+  float scale32[2];           // the same as an FP32 head and tail
   int status;                 // HR2_SAMPLE_* bits
   int setup;                  // setup index, -1 if invalid
 };

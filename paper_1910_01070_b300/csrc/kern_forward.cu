@@ -128,6 +128,7 @@ __global__ void k_prep(FwdArgs a) {
       sd->status = HR2_SAMPLE_BAD_SETUP;
       sd->setup = -1;
       sd->scale = 0.0;
+      sd->scale32[0] = sd->scale32[1] = 0.f;
       if (a.status) a.status[i] = HR2_SAMPLE_BAD_SETUP;
     }
     return;
@@ -135,12 +136,29 @@ __global__ void k_prep(FwdArgs a) {
   const SetupDev& S = *a.setups[g];
   const TablesDev& T = *S.tables;
   const double* th = a.params + (size_t)i * HR2_NPARAM;
+  const unsigned full = 0xffffffffu;
   int status = 0;
+  // The sample's scalar transcendentals, one per lane so that the warp
+  // evaluates them in one pass of its FP64 units: lane s < K 10^(log10 x_s),
+  // lane kLaneG 10^(log10 g), lanes kLaneC.. the cloud's three powers of 10.
+  constexpr int kLaneG = HR2_MAX_SPECIES, kLaneC = HR2_MAX_SPECIES + 1;
+  double e10 = 0.0;
+  {
+    double arg = 0.0;
+    if (lane < S.n_species) {
+      arg = th[HR2_P_X0 + lane];
+      if (!isfinite(arg)) status |= HR2_SAMPLE_BAD_ABUND;
+    } else if (lane == kLaneG) {
+      arg = th[HR2_P_LOGG];
+    } else if (S.cloud && lane >= kLaneC && lane < kLaneC + 3) {
+      arg = th[HR2_P_CLOUD + (lane - kLaneC)];
+    }
+    e10 = exp10(arg);
+  }
+  // sums in species order
   double sumx = 0.0, mabs = 0.0;
   for (int s = 0; s < S.n_species; ++s) {
-    const double lx = th[HR2_P_X0 + s];
-    if (!isfinite(lx)) status |= HR2_SAMPLE_BAD_ABUND;
-    const double x = exp10(lx);
+    const double x = __shfl_sync(full, e10, s);
     sumx += x;
     mabs += x * S.mass64[s];
   }
@@ -148,12 +166,14 @@ __global__ void k_prep(FwdArgs a) {
   const double xh2 = (1.0 - sumx) / (1.0 + S.r_he);
   const double xhe = S.r_he * xh2;
   const double mmw = mabs + xh2 * kMassH2 + xhe * kMassHe;
-  const double grav = exp10(th[HR2_P_LOGG]);
+  const double grav = __shfl_sync(full, e10, kLaneG);
   const double f = th[HR2_P_F], dcm = th[HR2_P_DIST] * kParsec;
   if (!(f > 0.0) || !(dcm > 0.0) || !isfinite(f) || !isfinite(dcm) || !isfinite(grav) || !(grav > 0.0))
     status |= HR2_SAMPLE_BAD_SCALE;
   const double c = 1.0 / (mmw * kAMU * grav);
-  const double lc = log2(c);
+  // log2 of c, x_H2 and x_He, one per lane
+  const double l2 = log2(lane == 0 ? c : (lane == 1 ? xh2 : xhe));
+  const double lc = __shfl_sync(full, l2, 0);
   const double ratio = S.radius_cm / dcm;
   // integer shift that centres the exponent of the dominant absorber
   double amax = -1e300;
@@ -171,9 +191,9 @@ __global__ void k_prep(FwdArgs a) {
   // gray cloud layer: tau_c spread evenly in pressure over [pct, pcb]
   double tau_c = 0.0, pct = 0.0, pcb = 0.0;
   if (S.cloud) {
-    tau_c = exp10(th[HR2_P_CLOUD]);
-    pct = exp10(th[HR2_P_CLOUD + 1]) * kBar;
-    const double fc = exp10(th[HR2_P_CLOUD + 2]);
+    tau_c = __shfl_sync(full, e10, kLaneC);
+    pct = __shfl_sync(full, e10, kLaneC + 1) * kBar;
+    const double fc = __shfl_sync(full, e10, kLaneC + 2);
     if (!isfinite(tau_c) || !(tau_c >= 0.0) || !(pct > 0.0) || !isfinite(pct) || !(fc > 0.0) || !(fc <= 1.0))
       status |= HR2_SAMPLE_BAD_CLOUD;
     pcb = pct / fc;
@@ -187,14 +207,16 @@ __global__ void k_prep(FwdArgs a) {
   // - log2 T_j
   double lw[HR2_MAX_TNODES];
   if (S.profile != HR2_PROFILE_MILNE) {
-    for (int q = 0; q <= S.fe_order; ++q) {
+    double lwl = 0.0;   // lane q's denominator
+    if (lane <= S.fe_order) {
       double d = 1.0;
       for (int m = 0; m <= S.fe_order; ++m)
-        if (m != q) d *= S.gll[q] - S.gll[m];
-      lw[q] = 1.0 / d;
+        if (m != lane) d *= S.gll[lane] - S.gll[m];
+      lwl = 1.0 / d;
     }
+    for (int q = 0; q <= S.fe_order; ++q) lw[q] = __shfl_sync(full, lwl, q);
   }
-  const double lxh2 = log2(xh2), lxhe = log2(xhe);
+  const double lxh2 = __shfl_sync(full, l2, 1), lxhe = __shfl_sync(full, l2, 2);
   const double cb0 = 2.0 * lxh2 + lc + T.off[kCiaH2H2] * kLog2_10 - shift;
   const double cb1 = lxh2 + lxhe + lc + T.off[kCiaH2He] * kLog2_10 - shift;
   const float tiny = (S.sc != HR2_SC_PARABOLIC) ? kTinyTau : 0.f;
@@ -259,7 +281,10 @@ __global__ void k_prep(FwdArgs a) {
   status = __reduce_or_sync(0xffffffffu, status);
   if (lane == 0) {
     sd->status = status;
-    sd->scale = f * ratio * ratio;
+    const double sc = f * ratio * ratio;
+    sd->scale = sc;
+    sd->scale32[0] = (float)sc;
+    sd->scale32[1] = (float)(sc - (double)(float)sc);
     sd->setup = g;
     if (a.status) a.status[i] = status;
   }
@@ -267,7 +292,9 @@ __global__ void k_prep(FwdArgs a) {
 
 cudaError_t launch_prep(const FwdArgs& a, cudaStream_t s) {
   if (a.n <= 0) return cudaSuccess;
-  k_prep<<<(a.n + 7) / 8, 256, 0, s>>>(a);
+  // one warp per sample, two per block: a 1024-sample batch spreads over
+  // every SM (the per-level work is FP64)
+  k_prep<<<(a.n + 1) / 2, 64, 0, s>>>(a);
   return cudaGetLastError();
 }
 
@@ -632,14 +659,15 @@ __global__ void __launch_bounds__(256) k_bins32(FwdArgs a, float* bins, int bins
   const SetupDev& S = *a.setups[g];
   const float* F[kBinGroup];
   float* out[kBinGroup];
-  double scale[kBinGroup];
+  float scale_hi[kBinGroup], scale_lo[kBinGroup];
   bool bad[kBinGroup];
 #pragma unroll
   for (int k = 0; k < kBinGroup; ++k) {
     const int i = a.perm[s0 + min(k, ns - 1)];
     F[k] = a.highres + (size_t)i * a.highres_ld;
     out[k] = bins + (size_t)i * bins_ld;
-    scale[k] = a.samp[i].scale;
+    scale_hi[k] = a.samp[i].scale32[0];
+    scale_lo[k] = a.samp[i].scale32[1];
     bad[k] = a.samp[i].status != 0;
   }
   const int b_end = min(S.n_bins, (int)(blockIdx.y + 1) * kBinRows);
@@ -663,7 +691,9 @@ __global__ void __launch_bounds__(256) k_bins32(FwdArgs a, float* bins, int bins
       float v = acc[k];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) out[k][b] = bad[k] ? qnan : (float)((double)v * scale[k]);
+      // v f (R/d)^2 with the scale as an FP32 head and tail (FP64 arithmetic
+      // here would run on the SM's few FP64 units once per row)
+      if (lane == 0) out[k][b] = bad[k] ? qnan : fmaf(v, scale_hi[k], v * scale_lo[k]);
     }
   }
 }

@@ -261,7 +261,7 @@ struct LevelState {
 template <int NMU, bool PARA, bool SX>
 __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], const float upl, const float rdnu,
                                               const v2 half_dp, const v2 dtc, v2& hdp_prev,
-                                              const NuConst& nc, const float thin_dtau, const float thin_all,
+                                              const NuConst& nc, const float thin_dtau,
                                               const v2* sMnl, const v2* sImu, const v2* sMu, v2 (&acc)[kPairs][NMU],
                                               v2 (&E)[kPairs][NMU], LevelState (&st)[kPairs]) {
   const float kLn2f = 0.6931471805599453f;
@@ -304,7 +304,6 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
     // I_0(mu) = mu * acc.  Nodes beyond the setup's count are padded with
     // mu = 1 and zero weight.
     (void)thin_dtau;
-    (void)thin_all;
     // st.tau holds -log2(e) tau_j, so that E_j = 2^(st.tau / mu_k)
     v2 dt[kPairs], rdS[kPairs];
 #pragma unroll
@@ -344,7 +343,6 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
       dmin = fminf(dmin, fminf(dtf.x, dtf.y));
     }
     const bool thin = __any_sync(0xffffffffu, dmin < thin_dtau);
-    (void)thin_all;
     // Parabolic source (Sect. 2.1, higher-order interpolant): over layer
     // j-1 the source is the parabola through levels j-2, j-1, j; in
     // vertical optical depth below level j-1 it is S_{j-1} + c1 t + c2 t^2
@@ -446,10 +444,9 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     nc.ratio[p] = f.z;
     nc.c1n[p] = pk(c.x, c.y);
   }
-  // dtau below which some node is thin (largest mu, padded nodes included),
-  // and below which every node is (smallest mu)
-  const float thin_dtau = (PARA ? kThinD : kThinLin) * S.mu[NMU - 1];
-  const float thin_all = (PARA ? kThinD : kThinLin) * S.mu[0];
+  // parabolic source: dtau below which some node is thin (largest mu, padded
+  // nodes included), which turns the warp's power-series moments on
+  const float thin_dtau = kThinD * S.mu[NMU - 1];
   const int K = S.n_species;
   const int L = S.n_lev - 1;
   const int nT = T.n_T;
@@ -609,7 +606,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
         __syncwarp();   // every lane has read the stage
         refill();
       }
-      level_physics<NMU, PARA, SX>(j, chi, rq2.upl, rq2.rdnu, rq1.dg, rq2.dtc, hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
+      level_physics<NMU, PARA, SX>(j, chi, rq2.upl, rq2.rdnu, rq1.dg, rq2.dtc, hdp_prev, nc, thin_dtau, sMnl, sImu,
                                sMu, acc, E, st);
       __syncwarp();  // every lane is done with stage stg and record j before they are refilled
     }
@@ -678,7 +675,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       v2 chi[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
-      level_physics<NMU, PARA, SX>(j, chi, r1.z, r3.x, pk(r1.w), pk(r3.w), hdp_prev, nc, thin_dtau, thin_all, sMnl, sImu,
+      level_physics<NMU, PARA, SX>(j, chi, r1.z, r3.x, pk(r1.w), pk(r3.w), hdp_prev, nc, thin_dtau, sMnl, sImu,
                                sMu, acc, E, st);
     }
   }
