@@ -96,6 +96,33 @@ def test_tiny_grids_match_oracle(eng, storage, case):
     assert np.all(hi[:, n_nu:] == -7.0)      # nothing written past the setup's points
 
 
+@pytest.mark.parametrize("storage", ["fp16-level-gridded", "fp64"])
+def test_bins_scale_over_distances_and_flux_factors(eng, storage):
+    """The bins carry f (R/d)^2 (Eq. 9): over distances from 1e-6 to 1e4 pc and flux
+    factors from 1e-3 to 1e3 the scale spans ~1e-3 .. 1e-29, and every bin still
+    matches the oracle to the flux tolerance (the FP32 path applies it as an FP32
+    head and tail)."""
+    spec = W.TableSpec(3, np.linspace(300.0, 2500.0, 4), np.linspace(-4.0, 2.0, 3), 5000.0, 1.0, 200, seed=12)
+    tabs = W.make_tables(spec)
+    setup = W.make_setup(spec, 5010.0, 5189.0, 20, range(3), 3, 2, 2, 500.0, 6)
+    t = eng.add_tables(spec, storage[:4], tabs)
+    s = eng.add_setup(t, setup, level_cache=(storage == "fp16-level-gridded"))
+    dist_f = [(1e-6, 1e3), (1e-3, 1.0), (1.0, 1e-3), (10.0, 1.0), (1e3, 1e3), (1e4, 1e-3)]
+    theta = W.draw_params(setup, len(dist_f), 23, W.Prior(b=(0.8, 0.97)))
+    for i, (d, f) in enumerate(dist_f):
+        theta[i, W.P_DIST] = d
+        theta[i, W.P_F] = f
+    bins, hi, st = _run(eng, [s], np.zeros(len(dist_f), np.int32), theta)
+    assert np.all(st == 0)
+    om = oracle_model(tables_as_stored(tabs, storage[:4]), setup)
+    tol = FLUX_RTOL if storage.startswith("fp16") else FP64_RTOL
+    scales = []
+    for i in range(len(dist_f)):
+        _compare(om, theta[i], bins[i], hi[i], tol, setup.n_nu)
+        scales.append(np.median(bins[i, :setup.n_bins]))
+    assert max(scales) / min(scales) > 1e20      # the scale really spans that range
+
+
 def test_cia_only_setup(eng):
     spec = W.TableSpec(2, np.linspace(300.0, 2500.0, 4), np.linspace(-4.0, 2.0, 3), 5000.0, 1.0, 90, seed=3)
     tabs = W.make_tables(spec)
