@@ -413,8 +413,8 @@ int hr2_ns_state_init(hr2_ctx* ctx, hr2_ns_state* state, void* stream);
  *   state        hr2_ns_state (updated; lnl_min / lnl_max refreshed)
  *   dead_lnl, dead_logw  double [dead_cap], dead_theta double
  *                [dead_cap][HR2_NPARAM]: dead point k at index k (absolute)
- * Asynchronous on `stream`; one CTA.  Returns HR2_EINVAL for n_live < 1,
- * n_cand < 0 or NULL pointers. */
+ * Asynchronous on `stream`; one warp (the candidates are consumed in
+ * order).  Returns HR2_EINVAL for n_live < 1, n_cand < 0 or NULL pointers. */
 int hr2_ns_absorb(hr2_ctx* ctx, int n_live, double* live_lnl, double* live_theta, int n_cand, const double* cand_lnl,
                   const double* cand_theta, hr2_ns_state* state, double* dead_lnl, double* dead_logw,
                   double* dead_theta, long long dead_cap, void* stream);

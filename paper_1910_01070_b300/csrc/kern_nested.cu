@@ -4,18 +4,23 @@
 //
 // The live set stays on the device, so a sampler's loop
 //   propose -> forward_model_batch -> log_likelihood_batch -> absorb
-// needs no host round trip per replacement.  One CTA processes the
-// candidates in order; every replacement is followed by a block-wide argmin
-// over the live likelihoods.  All threads carry the same running sums (the
-// values they reduce and compare are the same), so the control flow is
-// uniform.
+// needs no host round trip per replacement.  The candidates are consumed
+// strictly in order, so the absorb step is one warp: the live likelihoods
+// sit in shared memory (when they fit), the candidates' likelihoods are
+// fetched 32 at a time and handed along by shuffles, and after every
+// replacement the warp takes the argmin over the live set.  The FP64 sums
+// are evaluated once per replacement by that warp alone (the SM has few
+// FP64 units).  All lanes carry the same running sums, so the control flow
+// is uniform.
 #include <math.h>
 
 #include "hr2_internal.cuh"
 
 namespace hr2 {
 
-constexpr int kNsThreads = 512;
+// live likelihoods held in shared memory by the absorb warp, up to this many
+constexpr int kNsLiveSmem = 4096;
+static_assert(HR2_NPARAM <= 64, "the absorb warp moves a parameter row as two elements per lane");
 
 // ln(e^a + e^b); -inf is the empty sum
 __device__ __forceinline__ double log_add(double a, double b) {
@@ -39,36 +44,19 @@ __device__ __forceinline__ void ns_add(double& log_z, double& info, double lnl, 
 }
 
 // Smallest live value and its index (ties: lowest index; NaN counts as
-// +inf), broadcast to every thread of the block.
-__device__ void block_argmin(const double* v, int n, double& best_v, int& best_i) {
-  __shared__ double s_v[kNsThreads / 32];
-  __shared__ int s_i[kNsThreads / 32];
+// +inf), on every lane of the warp.
+__device__ __forceinline__ void warp_argmin(const double* v, int n, double& best_v, int& best_i) {
+  const int lane = threadIdx.x & 31;
   double bv = INFINITY;
   int bi = 0x7fffffff;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+  for (int j = lane; j < n; j += 32) {
     const double x = isnan(v[j]) ? INFINITY : v[j];
-    if (x < bv || (x == bv && j < bi)) {
+    if (x < bv) {   // a lane visits its indices in increasing order
       bv = x;
       bi = j;
     }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ov < bv || (ov == bv && oi < bi)) {
-      bv = ov;
-      bi = oi;
-    }
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  __syncthreads();   // earlier readers of s_v / s_i are done
-  if (lane == 0) {
-    s_v[warp] = bv;
-    s_i[warp] = bi;
-  }
-  __syncthreads();
-  bv = lane < nw ? s_v[lane] : INFINITY;
-  bi = lane < nw ? s_i[lane] : 0x7fffffff;
+  if (bv == INFINITY) bi = lane < n ? lane : 0x7fffffff;   // lowest index of the +inf values
   for (int o = 16; o > 0; o >>= 1) {
     const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
@@ -81,17 +69,10 @@ __device__ void block_argmin(const double* v, int n, double& best_v, int& best_i
   best_i = bi;
 }
 
-// Largest live value (NaN ignored), broadcast to every thread.
-__device__ double block_max(const double* v, int n) {
-  __shared__ double s_m[kNsThreads / 32];
+// Largest live value (NaN ignored), on every lane.
+__device__ __forceinline__ double warp_max(const double* v, int n) {
   double m = -INFINITY;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) m = fmax(m, v[j]);
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) s_m[warp] = m;
-  __syncthreads();
-  m = lane < nw ? s_m[lane] : -INFINITY;
+  for (int j = threadIdx.x & 31; j < n; j += 32) m = fmax(m, v[j]);
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   return m;
 }
@@ -108,40 +89,67 @@ __global__ void k_ns_init(hr2_ns_state* st) {
   *st = s;
 }
 
-__global__ void __launch_bounds__(kNsThreads) k_ns_absorb(int n_live, double* live_lnl, double* live_theta,
-                                                          int n_cand, const double* cand_lnl,
-                                                          const double* cand_theta, hr2_ns_state* st,
-                                                          double* dead_lnl, double* dead_logw, double* dead_theta,
-                                                          long long dead_cap) {
+__global__ void __launch_bounds__(32) k_ns_absorb(int n_live, double* live_lnl, double* live_theta, int n_cand,
+                                                  const double* cand_lnl, const double* cand_theta,
+                                                  hr2_ns_state* st, double* dead_lnl, double* dead_logw,
+                                                  double* dead_theta, long long dead_cap) {
+  __shared__ double s_live[kNsLiveSmem];
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool in_smem = n_live <= kNsLiveSmem;
+  double* lv = in_smem ? s_live : live_lnl;
+  if (in_smem)
+    for (int j = lane; j < n_live; j += 32) s_live[j] = live_lnl[j];
+  __syncwarp();
   long long n_dead = st->n_dead, n_seen = st->n_seen;
   double log_z = st->log_z, info = st->info;
   const double lw1 = log(-expm1(-1.0 / (double)n_live));   // ln(1 - e^(-1/N))
   double wv;
   int worst;
-  block_argmin(live_lnl, n_live, wv, worst);
-  for (int c = 0; c < n_cand; ++c) {
-    if (n_dead >= dead_cap) break;
-    ++n_seen;
-    const double cl = cand_lnl[c];
-    if (!(cl > wv)) continue;
-    const long long i = n_dead + 1;
-    const double log_w = -(double)(i - 1) / (double)n_live + lw1;
-    for (int t = threadIdx.x; t < HR2_NPARAM; t += blockDim.x) {
-      dead_theta[n_dead * HR2_NPARAM + t] = live_theta[(size_t)worst * HR2_NPARAM + t];
-      live_theta[(size_t)worst * HR2_NPARAM + t] = cand_theta[(size_t)c * HR2_NPARAM + t];
+  warp_argmin(lv, n_live, wv, worst);
+  bool full_cap = false;
+  for (int c0 = 0; c0 < n_cand && !full_cap; c0 += 32) {
+    const double mine = c0 + lane < n_cand ? cand_lnl[c0 + lane] : 0.0;
+    const int m = min(32, n_cand - c0);
+    for (int k = 0; k < m; ++k) {
+      if (n_dead >= dead_cap) {
+        full_cap = true;
+        break;
+      }
+      ++n_seen;
+      const double cl = __shfl_sync(full, mine, k);
+      if (!(cl > wv)) continue;
+      const long long c = c0 + k;
+      const long long i = n_dead + 1;
+      const double log_w = -(double)(i - 1) / (double)n_live + lw1;
+      // the leaving point's parameters to the dead list, the candidate's in
+      // its place (HR2_NPARAM <= 64: two elements per lane at most)
+      const size_t lrow = (size_t)worst * HR2_NPARAM, crow = (size_t)c * HR2_NPARAM,
+                   drow = (size_t)n_dead * HR2_NPARAM;
+      const bool two = lane + 32 < HR2_NPARAM;
+      const double a0 = live_theta[lrow + lane], b0 = cand_theta[crow + lane];
+      const double a1 = two ? live_theta[lrow + lane + 32] : 0.0, b1 = two ? cand_theta[crow + lane + 32] : 0.0;
+      dead_theta[drow + lane] = a0;
+      live_theta[lrow + lane] = b0;
+      if (two) {
+        dead_theta[drow + lane + 32] = a1;
+        live_theta[lrow + lane + 32] = b1;
+      }
+      if (lane == 0) {
+        dead_lnl[n_dead] = wv;
+        dead_logw[n_dead] = log_w;
+        lv[worst] = cl;
+      }
+      ns_add(log_z, info, wv, log_w);
+      n_dead = i;
+      __syncwarp();   // the replaced live value is visible to the next argmin
+      warp_argmin(lv, n_live, wv, worst);
     }
-    if (threadIdx.x == 0) {
-      dead_lnl[n_dead] = wv;
-      dead_logw[n_dead] = log_w;
-      live_lnl[worst] = cl;
-    }
-    ns_add(log_z, info, wv, log_w);
-    n_dead = i;
-    __syncthreads();   // the replaced live value is visible to the next argmin
-    block_argmin(live_lnl, n_live, wv, worst);
   }
-  const double vmax = block_max(live_lnl, n_live);
-  if (threadIdx.x == 0) {
+  const double vmax = warp_max(lv, n_live);
+  if (in_smem)
+    for (int j = lane; j < n_live; j += 32) live_lnl[j] = s_live[j];
+  if (lane == 0) {
     st->n_dead = n_dead;
     st->n_seen = n_seen;
     st->log_z = log_z;
@@ -169,7 +177,7 @@ cudaError_t launch_ns_init(hr2_ns_state* st, cudaStream_t s) {
 cudaError_t launch_ns_absorb(int n_live, double* live_lnl, double* live_theta, int n_cand, const double* cand_lnl,
                              const double* cand_theta, hr2_ns_state* st, double* dead_lnl, double* dead_logw,
                              double* dead_theta, long long dead_cap, cudaStream_t s) {
-  k_ns_absorb<<<1, kNsThreads, 0, s>>>(n_live, live_lnl, live_theta, n_cand, cand_lnl, cand_theta, st, dead_lnl,
+  k_ns_absorb<<<1, 32, 0, s>>>(n_live, live_lnl, live_theta, n_cand, cand_lnl, cand_theta, st, dead_lnl,
                                        dead_logw, dead_theta, dead_cap);
   return cudaGetLastError();
 }

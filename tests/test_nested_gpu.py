@@ -31,7 +31,8 @@ def _t(a):
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
 
 
-@pytest.mark.parametrize("n_live,n_cand,cap", [(1, 50, 100), (37, 400, 10 ** 4), (300, 3000, 10 ** 4), (64, 500, 40)])
+@pytest.mark.parametrize("n_live,n_cand,cap", [(1, 50, 100), (37, 400, 10 ** 4), (300, 3000, 10 ** 4), (64, 500, 40),
+                                               (4096, 700, 10 ** 4), (5000, 700, 10 ** 4)])
 def test_absorb_and_finalize_match_the_oracle(eng, n_live, n_cand, cap):
     rng = np.random.default_rng(n_live + n_cand)
     live = np.round(rng.normal(-100.0, 30.0, n_live), 1)          # rounding makes ties
