@@ -5,13 +5,13 @@
 // The live set stays on the device, so a sampler's loop
 //   propose -> forward_model_batch -> log_likelihood_batch -> absorb
 // needs no host round trip per replacement.  The candidates are consumed
-// strictly in order, so the absorb step is one warp: the live likelihoods
-// sit in shared memory (when they fit), the candidates' likelihoods are
-// fetched 32 at a time and handed along by shuffles, and after every
-// replacement the warp takes the argmin over the live set.  The FP64 sums
-// are evaluated once per replacement by that warp alone (the SM has few
-// FP64 units).  All lanes carry the same running sums, so the control flow
-// is uniform.
+// strictly in order, so the absorb step is one warp: integer keys of the
+// live likelihoods sit in shared memory (when they fit), the candidates'
+// likelihoods are fetched 32 at a time and handed along by shuffles, and
+// after every replacement the warp takes the argmin over the keys.  ln Z and
+// H (FP64, of which the SM has few units) are folded in once the call's
+// replacements are known, in the same order.  All lanes carry the same
+// running sums, so the control flow is uniform.
 #include <math.h>
 
 #include "hr2_internal.cuh"
@@ -43,29 +43,49 @@ __device__ __forceinline__ void ns_add(double& log_z, double& info, double lnl, 
   log_z = z_new;
 }
 
-// Smallest live value and its index (ties: lowest index; NaN counts as
-// +inf), on every lane of the warp.
-__device__ __forceinline__ void warp_argmin(const double* v, int n, double& best_v, int& best_i) {
+// Order-preserving integer key of a live likelihood, so that the warp's
+// argmin and the candidates' test run on integer compares (the SM's FP64
+// units are few): NaN counts as +inf, -0 as +0.
+constexpr long long kNsKeyInf = 0x7ff0000000000000LL;
+__device__ __forceinline__ long long ns_key(double x) {
+  const long long b = __double_as_longlong(x);
+  const long long mag = b & 0x7fffffffffffffffLL;
+  if (mag > kNsKeyInf) return kNsKeyInf;
+  if (mag == 0) return 0;
+  return b < 0 ? (b ^ 0x7fffffffffffffffLL) : b;
+}
+__device__ __forceinline__ double ns_unkey(long long k) {
+  return __longlong_as_double(k < 0 ? (k ^ 0x7fffffffffffffffLL) : k);
+}
+// a candidate's key: a NaN candidate is never above the live minimum
+__device__ __forceinline__ long long ns_cand_key(double x) {
+  return isnan(x) ? (long long)0x8000000000000000ULL : ns_key(x);
+}
+
+// Key of the smallest live value and its index (ties: lowest index), on
+// every lane; keys from shared memory, or formed from the values in place.
+template <bool SMEM>
+__device__ __forceinline__ void warp_argmin(const long long* key, const double* v, int n, long long& best_k,
+                                            int& best_i) {
   const int lane = threadIdx.x & 31;
-  double bv = INFINITY;
+  long long bk = 0x7fffffffffffffffLL;
   int bi = 0x7fffffff;
   for (int j = lane; j < n; j += 32) {
-    const double x = isnan(v[j]) ? INFINITY : v[j];
-    if (x < bv) {   // a lane visits its indices in increasing order
-      bv = x;
+    const long long k = SMEM ? key[j] : ns_key(v[j]);
+    if (k < bk) {   // a lane visits its indices in increasing order
+      bk = k;
       bi = j;
     }
   }
-  if (bv == INFINITY) bi = lane < n ? lane : 0x7fffffff;   // lowest index of the +inf values
   for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+    const long long ok = __shfl_xor_sync(0xffffffffu, bk, o);
     const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ov < bv || (ov == bv && oi < bi)) {
-      bv = ov;
+    if (ok < bk || (ok == bk && oi < bi)) {
+      bk = ok;
       bi = oi;
     }
   }
-  best_v = bv;
+  best_k = bk;
   best_i = bi;
 }
 
@@ -89,27 +109,27 @@ __global__ void k_ns_init(hr2_ns_state* st) {
   *st = s;
 }
 
+template <bool SMEM>
 __global__ void __launch_bounds__(32) k_ns_absorb(int n_live, double* live_lnl, double* live_theta, int n_cand,
                                                   const double* cand_lnl, const double* cand_theta,
                                                   hr2_ns_state* st, double* dead_lnl, double* dead_logw,
                                                   double* dead_theta, long long dead_cap) {
-  __shared__ double s_live[kNsLiveSmem];
+  __shared__ long long s_key[SMEM ? kNsLiveSmem : 1];
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const bool in_smem = n_live <= kNsLiveSmem;
-  double* lv = in_smem ? s_live : live_lnl;
-  if (in_smem)
-    for (int j = lane; j < n_live; j += 32) s_live[j] = live_lnl[j];
+  if (SMEM)
+    for (int j = lane; j < n_live; j += 32) s_key[j] = ns_key(live_lnl[j]);
   __syncwarp();
-  long long n_dead = st->n_dead, n_seen = st->n_seen;
-  double log_z = st->log_z, info = st->info;
+  const long long dead0 = st->n_dead;
+  long long n_dead = dead0, n_seen = st->n_seen;
   const double lw1 = log(-expm1(-1.0 / (double)n_live));   // ln(1 - e^(-1/N))
-  double wv;
+  long long wk;
   int worst;
-  warp_argmin(lv, n_live, wv, worst);
+  warp_argmin<SMEM>(s_key, live_lnl, n_live, wk, worst);
   bool full_cap = false;
   for (int c0 = 0; c0 < n_cand && !full_cap; c0 += 32) {
     const double mine = c0 + lane < n_cand ? cand_lnl[c0 + lane] : 0.0;
+    const long long mine_k = ns_cand_key(mine);
     const int m = min(32, n_cand - c0);
     for (int k = 0; k < m; ++k) {
       if (n_dead >= dead_cap) {
@@ -117,45 +137,48 @@ __global__ void __launch_bounds__(32) k_ns_absorb(int n_live, double* live_lnl, 
         break;
       }
       ++n_seen;
+      if (!(__shfl_sync(full, mine_k, k) > wk)) continue;   // not strictly above the live minimum
       const double cl = __shfl_sync(full, mine, k);
-      if (!(cl > wv)) continue;
       const long long c = c0 + k;
-      const long long i = n_dead + 1;
-      const double log_w = -(double)(i - 1) / (double)n_live + lw1;
-      // the leaving point's parameters to the dead list, the candidate's in
-      // its place (HR2_NPARAM <= 64: two elements per lane at most)
+      // the leaving point's parameters go to the dead list and the
+      // candidate's take its place (HR2_NPARAM <= 64: two elements per
+      // lane); loaded here, stored after the next argmin, which does not
+      // need them (a lane stores and later loads only its own elements)
       const size_t lrow = (size_t)worst * HR2_NPARAM, crow = (size_t)c * HR2_NPARAM,
                    drow = (size_t)n_dead * HR2_NPARAM;
       const bool two = lane + 32 < HR2_NPARAM;
       const double a0 = live_theta[lrow + lane], b0 = cand_theta[crow + lane];
       const double a1 = two ? live_theta[lrow + lane + 32] : 0.0, b1 = two ? cand_theta[crow + lane + 32] : 0.0;
+      if (lane == 0) {
+        // dead point i = n_dead + 1: its likelihood and ln w_i; ln Z and H
+        // follow after the loop, in the same order
+        dead_lnl[n_dead] = ns_unkey(wk);
+        dead_logw[n_dead] = -(double)n_dead / (double)n_live + lw1;
+        live_lnl[worst] = cl;
+        if (SMEM) s_key[worst] = ns_key(cl);
+      }
+      ++n_dead;
+      __syncwarp();   // the replaced live value is visible to the next argmin
+      warp_argmin<SMEM>(s_key, live_lnl, n_live, wk, worst);
       dead_theta[drow + lane] = a0;
       live_theta[lrow + lane] = b0;
       if (two) {
         dead_theta[drow + lane + 32] = a1;
         live_theta[lrow + lane + 32] = b1;
       }
-      if (lane == 0) {
-        dead_lnl[n_dead] = wv;
-        dead_logw[n_dead] = log_w;
-        lv[worst] = cl;
-      }
-      ns_add(log_z, info, wv, log_w);
-      n_dead = i;
-      __syncwarp();   // the replaced live value is visible to the next argmin
-      warp_argmin(lv, n_live, wv, worst);
     }
   }
-  const double vmax = warp_max(lv, n_live);
-  if (in_smem)
-    for (int j = lane; j < n_live; j += 32) live_lnl[j] = s_live[j];
+  __syncwarp();   // lane 0's dead-list entries are visible to every lane
+  double log_z = st->log_z, info = st->info;
+  for (long long d = dead0; d < n_dead; ++d) ns_add(log_z, info, dead_lnl[d], dead_logw[d]);
+  const double vmax = warp_max(live_lnl, n_live);
   if (lane == 0) {
     st->n_dead = n_dead;
     st->n_seen = n_seen;
     st->log_z = log_z;
     st->info = info;
     st->log_x = -(double)n_dead / (double)n_live;
-    st->lnl_min = wv;
+    st->lnl_min = ns_unkey(wk);
     st->lnl_max = vmax;
   }
 }
@@ -177,8 +200,12 @@ cudaError_t launch_ns_init(hr2_ns_state* st, cudaStream_t s) {
 cudaError_t launch_ns_absorb(int n_live, double* live_lnl, double* live_theta, int n_cand, const double* cand_lnl,
                              const double* cand_theta, hr2_ns_state* st, double* dead_lnl, double* dead_logw,
                              double* dead_theta, long long dead_cap, cudaStream_t s) {
-  k_ns_absorb<<<1, 32, 0, s>>>(n_live, live_lnl, live_theta, n_cand, cand_lnl, cand_theta, st, dead_lnl,
+  if (n_live <= kNsLiveSmem)
+    k_ns_absorb<true><<<1, 32, 0, s>>>(n_live, live_lnl, live_theta, n_cand, cand_lnl, cand_theta, st, dead_lnl,
                                        dead_logw, dead_theta, dead_cap);
+  else
+    k_ns_absorb<false><<<1, 32, 0, s>>>(n_live, live_lnl, live_theta, n_cand, cand_lnl, cand_theta, st, dead_lnl,
+                                        dead_logw, dead_theta, dead_cap);
   return cudaGetLastError();
 }
 

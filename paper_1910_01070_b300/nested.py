@@ -71,28 +71,45 @@ class GpuBackend:
         return lnl
 
     def init_live(self, theta: np.ndarray) -> None:
-        th = self.torch.as_tensor(theta, device=self.dev)
-        self.live_theta.copy_(th)
-        self.live_lnl.copy_(self._score(self.live_theta))
+        with self._on_stream():
+            th = self.torch.as_tensor(theta, device=self.dev)
+            self.live_theta.copy_(th)
+            self.live_lnl.copy_(self._score(self.live_theta))
 
     def live_theta_host(self) -> np.ndarray:
-        return self.live_theta.cpu().numpy()
+        return self._read(lambda t: t.cpu().numpy(), self.live_theta)
+
+    def _on_stream(self):
+        """Copies made by torch go to the backend's stream (or the current one)."""
+        torch = self.torch
+        s = self.stream
+        if s is None:
+            s = torch.cuda.current_stream(self.dev)
+        elif isinstance(s, int):
+            s = torch.cuda.ExternalStream(s, device=self.dev)
+        return torch.cuda.stream(s)
+
+    def _read(self, fn, *args):
+        """fn(*args) reading device results, after the backend's stream is done."""
+        with self._on_stream():
+            return fn(*args)
 
     def step(self, cand: np.ndarray) -> Dict:
-        th = self.torch.as_tensor(np.ascontiguousarray(cand), device=self.dev)
+        with self._on_stream():
+            th = self.torch.as_tensor(np.ascontiguousarray(cand), device=self.dev)
         lnl = self._score(th)
         hr2.hr2_ns_absorb(self.ctx, self.live_lnl, self.live_theta, lnl, th, self.state, self.dead_lnl,
                           self.dead_logw, self.dead_theta, self.stream)
-        return hr2.ns_state_read(self.state)
+        return self._read(hr2.ns_state_read, self.state)
 
     def finalize(self):
         hr2.hr2_ns_finalize(self.ctx, self.live_lnl, self.state, self.out, self.stream)
-        o = self.out.cpu().numpy()
+        o = self._read(lambda t: t.cpu().numpy(), self.out)
         return float(o[0]), float(o[1])
 
     def dead(self, n: int):
-        return (self.dead_lnl[:n].cpu().numpy(), self.dead_logw[:n].cpu().numpy(),
-                self.dead_theta[:n].cpu().numpy())
+        return self._read(lambda: (self.dead_lnl[:n].cpu().numpy(), self.dead_logw[:n].cpu().numpy(),
+                                   self.dead_theta[:n].cpu().numpy()))
 
 
 def log_add(a: float, b: float) -> float:

@@ -114,3 +114,10 @@ def test_driver_on_the_forward_model(eng):
         ref = oracle.lnL(D, sig, om.forward(dth[k])[0])
         assert dl[k] == pytest.approx(ref, rel=1e-5, abs=1e-3)
     assert np.allclose(dw, [N.log_shell_weight(i, 128) for i in range(1, res["n_dead"] + 1)], rtol=1e-14, atol=1e-14)
+    # the same run on a side stream of the backend's own gives the same dead points
+    side = torch.cuda.Stream()
+    be2 = GpuBackend(eng.ctx, [s], 0, n_live=128, stream=side)
+    res2 = NestedSampler(be2, lo, hi, batch=512, seed=4).run(dlogz=0.5, max_rounds=6)
+    assert res2["n_dead"] == res["n_dead"] and res2["log_z"] == res["log_z"]
+    dl2, _, dth2 = be2.dead(res2["n_dead"])
+    assert np.array_equal(dl2, dl) and np.array_equal(dth2, dth)
