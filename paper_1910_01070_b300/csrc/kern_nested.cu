@@ -150,10 +150,9 @@ __global__ void __launch_bounds__(32) k_ns_absorb(int n_live, double* live_lnl, 
       const double a0 = live_theta[lrow + lane], b0 = cand_theta[crow + lane];
       const double a1 = two ? live_theta[lrow + lane + 32] : 0.0, b1 = two ? cand_theta[crow + lane + 32] : 0.0;
       if (lane == 0) {
-        // dead point i = n_dead + 1: its likelihood and ln w_i; ln Z and H
+        // dead point i = n_dead + 1: its likelihood; ln w_i, ln Z and H
         // follow after the loop, in the same order
         dead_lnl[n_dead] = ns_unkey(wk);
-        dead_logw[n_dead] = -(double)n_dead / (double)n_live + lw1;
         live_lnl[worst] = cl;
         if (SMEM) s_key[worst] = ns_key(cl);
       }
@@ -168,7 +167,9 @@ __global__ void __launch_bounds__(32) k_ns_absorb(int n_live, double* live_lnl, 
       }
     }
   }
-  __syncwarp();   // lane 0's dead-list entries are visible to every lane
+  // ln w_i = -(i-1)/N + ln(1 - e^(-1/N)) of the call's dead points, one per lane
+  for (long long d = dead0 + lane; d < n_dead; d += 32) dead_logw[d] = -(double)d / (double)n_live + lw1;
+  __syncwarp();   // the dead-list entries are visible to every lane
   double log_z = st->log_z, info = st->info;
   for (long long d = dead0; d < n_dead; ++d) ns_add(log_z, info, dead_lnl[d], dead_logw[d]);
   const double vmax = warp_max(live_lnl, n_live);
