@@ -383,8 +383,10 @@ int hr2_effective_temperature(hr2_ctx* ctx, int n_setups, const hr2_setup* const
  * the live set (the lowest likelihood, L*_i) has prior mass X_i = exp(-i/N)
  * inside its contour and shell weight w_i = X_{i-1} - X_i (X_0 = 1);
  * ln Z = ln sum_i L*_i w_i and the information H = sum_i p_i ln(L*_i / Z),
- * p_i = L*_i w_i / Z, accumulate in FP64 log-sum-exp, one dead point at a
- * time in order.  The sampler itself (MultiNest in the paper) is the
+ * p_i = L*_i w_i / Z, accumulate in FP64 log-sum-exp: each absorb call
+ * folds its dead points into the running (ln Z, H) with a fixed-order warp
+ * reduction (the closed form of adding them one at a time; equal to
+ * rounding, deterministic).  The sampler itself (MultiNest in the paper) is the
  * caller's; this is the part that runs per likelihood batch. */
 typedef struct {
   long long n_dead;   /* dead points so far (i of the last one)              */
@@ -420,7 +422,7 @@ int hr2_ns_absorb(hr2_ctx* ctx, int n_live, double* live_lnl, double* live_theta
                   double* dead_theta, long long dead_cap, void* stream);
 
 /* hr2_ns_finalize: ln Z and H with the live points added, each with weight
- * X_n / N, in index order: out (DEVICE double [2]) = {ln Z, H}.  The state
+ * X_n / N (fixed-order reduction): out (DEVICE double [2]) = {ln Z, H}.  The state
  * is not modified.  Asynchronous on `stream`. */
 int hr2_ns_finalize(hr2_ctx* ctx, int n_live, const double* live_lnl, const hr2_ns_state* state, double* out,
                     void* stream);

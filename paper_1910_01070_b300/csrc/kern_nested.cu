@@ -9,9 +9,9 @@
 // live likelihoods sit in shared memory (when they fit), the candidates'
 // likelihoods are fetched 32 at a time and handed along by shuffles, and
 // after every replacement the warp takes the argmin over the keys.  ln Z and
-// H (FP64, of which the SM has few units) are folded in once the call's
-// replacements are known, in the same order.  All lanes carry the same
-// running sums, so the control flow is uniform.
+// H (FP64, of which the SM has few units) take the call's dead points in one
+// fixed-order warp reduction once the replacements are known.  All lanes
+// carry the same values, so the control flow is uniform.
 #include <math.h>
 
 #include "hr2_internal.cuh"
@@ -22,25 +22,41 @@ namespace hr2 {
 constexpr int kNsLiveSmem = 4096;
 static_assert(HR2_NPARAM <= 64, "the absorb warp moves a parameter row as two elements per lane");
 
-// ln(e^a + e^b); -inf is the empty sum
-__device__ __forceinline__ double log_add(double a, double b) {
-  if (a == -INFINITY) return b;
-  if (b == -INFINITY) return a;
-  const double m = fmax(a, b);
-  return m + log(exp(a - m) + exp(b - m));
-}
-
-// Fold a point of likelihood e^lnl and prior weight e^log_w into ln Z and H.
-// H = sum_k p_k ln L_k - ln Z (p_k = L_k w_k / Z), updated in Skilling's
-// running form: H' = e^(lw - Z') lnl + e^(Z - Z') (H + Z) - Z'.
-__device__ __forceinline__ void ns_add(double& log_z, double& info, double lnl, double log_w) {
-  const double lw = lnl + log_w;
-  const double z_new = log_add(log_z, lw);
-  double h = 0.0;
-  if (lw > -INFINITY) h += exp(lw - z_new) * lnl;
-  if (log_z > -INFINITY) h += exp(log_z - z_new) * (info + log_z);
-  info = h - z_new;
-  log_z = z_new;
+// Fold points k = 0 .. n-1 of likelihood e^lnl[k] and prior weight
+// e^(logw ? logw[k] : logw_c) into ln Z and H, on every lane of the warp.
+// Z' = Z + sum_k L_k w_k and H' = sum over all points of p ln L - ln Z'
+// (p = L w / Z'), the closed form of Skilling's one-point-at-a-time update
+//   Z' = ln(e^Z + L w),  H' = e^(lw - Z') lnl + e^(Z - Z') (H + Z) - Z',
+// evaluated as a fixed-order warp reduction instead of a chain of FP64
+// exponentials and logarithms (~3.6 us per point on this SM); the two agree
+// to rounding.  A term with lnL = -inf adds nothing; a NaN likelihood
+// makes ln Z NaN, as in the one-point form.
+__device__ void ns_fold(double& log_z, double& info, long long n, const double* lnl, const double* logw,
+                        double logw_c) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const double z0 = log_z, h0 = info;
+  double m = -INFINITY;
+  for (long long k = lane; k < n; k += 32) m = fmax(m, lnl[k] + (logw ? logw[k] : logw_c));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(full, m, o));
+  m = fmax(m, z0);
+  double sum = 0.0;
+  for (long long k = lane; k < n; k += 32) {
+    const double lw = lnl[k] + (logw ? logw[k] : logw_c);
+    if (lw != -INFINITY) sum += exp(lw - m);
+  }
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(full, sum, o);
+  if (z0 != -INFINITY) sum += exp(z0 - m);
+  const double z1 = m + log(sum);   // -inf when every term is empty
+  double t = 0.0;
+  for (long long k = lane; k < n; k += 32) {
+    const double l = lnl[k], lw = l + (logw ? logw[k] : logw_c);
+    if (lw > -INFINITY) t += exp(lw - z1) * l;
+  }
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(full, t, o);
+  if (z0 > -INFINITY) t += exp(z0 - z1) * (h0 + z0);
+  info = t - z1;
+  log_z = z1;
 }
 
 // Order-preserving integer key of a live likelihood, so that the warp's
@@ -171,7 +187,7 @@ __global__ void __launch_bounds__(32) k_ns_absorb(int n_live, double* live_lnl, 
   for (long long d = dead0 + lane; d < n_dead; d += 32) dead_logw[d] = -(double)d / (double)n_live + lw1;
   __syncwarp();   // the dead-list entries are visible to every lane
   double log_z = st->log_z, info = st->info;
-  for (long long d = dead0; d < n_dead; ++d) ns_add(log_z, info, dead_lnl[d], dead_logw[d]);
+  if (n_dead > dead0) ns_fold(log_z, info, n_dead - dead0, dead_lnl + dead0, dead_logw + dead0, 0.0);
   const double vmax = warp_max(live_lnl, n_live);
   if (lane == 0) {
     st->n_dead = n_dead;
@@ -184,13 +200,16 @@ __global__ void __launch_bounds__(32) k_ns_absorb(int n_live, double* live_lnl, 
   }
 }
 
-// Live remainder: each live point with weight X_n / N, in index order.
-__global__ void k_ns_finalize(int n_live, const double* live_lnl, const hr2_ns_state* st, double* out) {
+// Live remainder: each live point with weight X_n / N.
+__global__ void __launch_bounds__(32) k_ns_finalize(int n_live, const double* live_lnl, const hr2_ns_state* st,
+                                                    double* out) {
   double log_z = st->log_z, info = st->info;
   const double log_w = -(double)st->n_dead / (double)n_live - log((double)n_live);
-  for (int j = 0; j < n_live; ++j) ns_add(log_z, info, live_lnl[j], log_w);
-  out[0] = log_z;
-  out[1] = info;
+  ns_fold(log_z, info, n_live, live_lnl, nullptr, log_w);
+  if ((threadIdx.x & 31) == 0) {
+    out[0] = log_z;
+    out[1] = info;
+  }
 }
 
 cudaError_t launch_ns_init(hr2_ns_state* st, cudaStream_t s) {
@@ -212,7 +231,7 @@ cudaError_t launch_ns_absorb(int n_live, double* live_lnl, double* live_theta, i
 
 cudaError_t launch_ns_finalize(int n_live, const double* live_lnl, const hr2_ns_state* st, double* out,
                                cudaStream_t s) {
-  k_ns_finalize<<<1, 1, 0, s>>>(n_live, live_lnl, st, out);
+  k_ns_finalize<<<1, 32, 0, s>>>(n_live, live_lnl, st, out);
   return cudaGetLastError();
 }
 
