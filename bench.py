@@ -310,8 +310,9 @@ def run_hr2(args, world, rank, local):
         hr2.hr2_evaluate_host(eng.ctx, [s16], h_sid[k % 4], h_par[k % 4], h_out, None, None, stream)
         e2e_t.append(time.perf_counter() - t0)
     e2e_total = max_over_ranks(world, sum(e2e_t))
+    # copied per step: parameters and setup indices in; lnL and the library's status word out
     e2e = {"value": world * n * args.steps / e2e_total, "unit": "models/s",
-           "h2d_bytes_per_step": n * (8 * hr2.HR2_NPARAM + 4), "d2h_bytes_per_step": n * 8,
+           "h2d_bytes_per_step": n * (8 * hr2.HR2_NPARAM + 4), "d2h_bytes_per_step": n * 8 + 8,
            "ms_per_step": 1e3 * e2e_total / args.steps, "api": "hr2_evaluate_host (pinned host buffers)"}
 
     fp64 = None

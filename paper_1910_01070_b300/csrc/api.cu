@@ -43,6 +43,7 @@ struct Workspace {
   int* perm = nullptr;
   PlanDev* plan = nullptr;
   unsigned int* counter = nullptr;   // [0] work counter, [1] error word
+  unsigned int* h_counter = nullptr; // pinned host copy of counter (kept across growth)
   float* highres = nullptr;
   double* highres64 = nullptr;
   double* io_params = nullptr;
@@ -135,7 +136,9 @@ static void ws_free(hr2_ctx* ctx, Workspace* w) {
   dfree(ctx, w->io_logeps);
   dfree(ctx, w->io_lnl);
   dfree(ctx, w->io_bins);
+  unsigned int* keep = w->h_counter;
   *w = Workspace();
+  w->h_counter = keep;
 }
 
 static bool stream_capturing(cudaStream_t s) {
@@ -154,7 +157,14 @@ static int ws_ensure(hr2_ctx* ctx, cudaStream_t stream, int n, int lev, int nu, 
                      Workspace** out) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   Workspace*& w = ctx->ws[(void*)stream];
-  if (!w) w = new Workspace();
+  if (!w) {
+    w = new Workspace();
+    // pinned word for reading the error flag with the batch's own copies
+    if (cudaHostAlloc((void**)&w->h_counter, 2 * sizeof(unsigned int), cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      w->h_counter = nullptr;
+    }
+  }
   *out = w;
   bool grow = n > w->n_cap || lev > w->lev_cap || (nu > 0 && (n > w->n_cap || nu > w->nu_cap || !w->highres)) ||
               (nu64 > 0 && (n > w->n_cap || nu64 > w->nu64_cap || !w->highres64)) || io > w->io_cap ||
@@ -164,6 +174,7 @@ static int ws_ensure(hr2_ctx* ctx, cudaStream_t stream, int n, int lev, int nu, 
     return fail(HR2_EBUSY, "workspace must grow (n=%d) while the stream is capturing; call hr2_reserve first", n);
   HR2_CU(cudaStreamSynchronize(stream));
   Workspace nw;
+  nw.h_counter = w->h_counter;
   nw.n_cap = std::max(n, w->n_cap);
   nw.lev_cap = std::max(lev, w->lev_cap);
   nw.nu_cap = std::max(nu, w->nu_cap);
@@ -229,6 +240,7 @@ extern "C" int hr2_ctx_destroy(hr2_ctx* ctx) {
   while (!ctx->tables.empty()) hr2_tables_destroy(ctx, ctx->tables.back());
   for (auto& kv : ctx->ws) {
     ws_free(ctx, kv.second);
+    if (kv.second->h_counter) cudaFreeHost(kv.second->h_counter);
     delete kv.second;
   }
   ctx->ws.clear();
@@ -974,6 +986,13 @@ extern "C" int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* co
   HR2_CU(cudaMemcpyAsync(out_lnL, w->io_lnl, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
   if (out_bins)
     HR2_CU(cudaMemcpyAsync(out_bins, w->io_bins, sizeof(float) * (size_t)n * ld, cudaMemcpyDeviceToHost, s));
+  if (w->h_counter) {
+    // the error word comes back with the results: no second round trip
+    HR2_CU(cudaMemcpyAsync(w->h_counter, w->counter, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
+    HR2_CU(cudaStreamSynchronize(s));
+    if (w->h_counter[1] & 1u) return fail(HR2_ETIMEDOUT, "a bounded device-side wait gave up during the last batch");
+    return HR2_OK;
+  }
   HR2_CU(cudaStreamSynchronize(s));
   return check_device_error(w);
 }
