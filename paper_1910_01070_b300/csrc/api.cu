@@ -619,6 +619,20 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
     h.wflux[k] = 0.f;
   }
   for (int i = 0; i <= d->fe_order; ++i) h.gll[i] = quad[2 * d->n_mu + i];
+  if (d->profile != HR2_PROFILE_MILNE) {
+    int* d_fek = nullptr;
+    double* d_feb = nullptr;
+    if ((rc = dalloc_t(ctx, &d_fek, h.n_lev))) goto fail_all;
+    track(d_fek);
+    if ((rc = dalloc_t(ctx, &d_feb, (size_t)h.n_lev * (d->fe_order + 1)))) goto fail_all;
+    track(d_feb);
+    h.fe_k = d_fek;
+    h.fe_b = d_feb;
+    if ((e = build_fe_basis(h.n_lev, d->fe_elements, d->fe_order, h.gll, d_fek, d_feb, 0)) != cudaSuccess) {
+      rc = fail(HR2_ECUDA, "setup profile basis: %s", cudaGetErrorString(e));
+      goto fail_all;
+    }
+  }
 
   // instrument profile + binning operator
   if ((rc = dalloc_t(ctx, &d_edges, d->n_bins + 1)) || (rc = dalloc_t(ctx, &d_lo, d->n_nu)) ||

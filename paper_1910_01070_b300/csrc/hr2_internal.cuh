@@ -109,6 +109,10 @@ struct SetupDev {
   double mu64[HR2_MAX_MU], wmu64[HR2_MAX_MU];  // Gauss-Legendre nodes and weights on [0,1]
   int fe_elements, fe_order, n_tnodes;
   double gll[HR2_MAX_TNODES];    // Gauss-Lobatto nodes on [0,1] (fe_order+1 of them)
+  // finite-element profile at the levels (set up once): element of level j
+  // and the values of its fe_order+1 Lagrange basis functions there
+  const int* fe_k;               // [n_lev]
+  const double* fe_b;            // [n_lev][fe_order + 1]
   double r_he, radius_cm;
   int n_bins;
   long long w_nnz;
@@ -279,6 +283,8 @@ cudaError_t launch_lnl(const LnlArgs& a, cudaStream_t s);
 cudaError_t launch_obs_terms(const double* sigma, int n_bins, double* inv2s2, double* lnorm, cudaStream_t s);
 // Hopf function table (kern_setup.cu) and effective temperatures (kern_forward.cu)
 cudaError_t build_hopf_table(double* d_q, cudaStream_t s);
+cudaError_t build_fe_basis(int n_lev, int fe_elements, int fe_order, const double* gll, int* d_k, double* d_b,
+                           cudaStream_t s);
 cudaError_t launch_teff(const FwdArgs& a, const float* highres, int highres_ld, double* out, cudaStream_t s);
 // nested-sampling evidence bookkeeping (kern_nested.cu)
 cudaError_t launch_ns_init(hr2_ns_state* st, cudaStream_t s);

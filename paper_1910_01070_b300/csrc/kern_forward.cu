@@ -35,20 +35,13 @@ __device__ double fe_temperature(const SetupDev& S, const double* nodes, double 
   return T;
 }
 
-// The same profile with the Lagrange denominators 1 / prod_{m != i}(xi_i - xi_m)
-// taken once per sample (lw), so that a level costs multiplications only.
-__device__ __forceinline__ double fe_temperature_w(const SetupDev& S, const double* nodes, const double* lw, double x) {
-  const int Ke = S.fe_elements, q = S.fe_order;
-  int k = (int)floor(x * Ke);
-  k = k < 0 ? 0 : (k > Ke - 1 ? Ke - 1 : k);
-  const double loc = x * Ke - k;
+// The same profile at level j from the setup's basis values there (element
+// fe_k[j], basis fe_b[j][i]): fe_order+1 products per level.
+__device__ __forceinline__ double fe_temperature_level(const SetupDev& S, const double* nodes, int j) {
+  const int q = S.fe_order, k = S.fe_k[j];
+  const double* b = S.fe_b + (size_t)j * (q + 1);
   double T = 0.0;
-  for (int i = 0; i <= q; ++i) {
-    double l = lw[i];
-    for (int m = 0; m <= q; ++m)
-      if (m != i) l *= loc - S.gll[m];
-    T += nodes[k * q + i] * l;
-  }
+  for (int i = 0; i <= q; ++i) T += nodes[k * q + i] * b[i];
   return T;
 }
 
@@ -201,21 +194,9 @@ __global__ void k_prep(FwdArgs a) {
 
   const int L = S.n_lev - 1;
   LevRec* rec = a.recs + (size_t)i * a.rec_ld;
-  // per-sample constants of the level records: the Lagrange denominators of
-  // the FE profile, and log2 of the CIA prefactors without the level's number
-  // density, b = log2(x x' c n_j) + off log2 10 - shift = cb + log2(p_j / k_B)
-  // - log2 T_j
-  double lw[HR2_MAX_TNODES];
-  if (S.profile != HR2_PROFILE_MILNE) {
-    double lwl = 0.0;   // lane q's denominator
-    if (lane <= S.fe_order) {
-      double d = 1.0;
-      for (int m = 0; m <= S.fe_order; ++m)
-        if (m != lane) d *= S.gll[lane] - S.gll[m];
-      lwl = 1.0 / d;
-    }
-    for (int q = 0; q <= S.fe_order; ++q) lw[q] = __shfl_sync(full, lwl, q);
-  }
+  // per-sample constants of the level records: log2 of the CIA prefactors
+  // without the level's number density, b = log2(x x' c n_j) + off log2 10 -
+  // shift = cb + log2(p_j / k_B) - log2 T_j
   const double lxh2 = __shfl_sync(full, l2, 1), lxhe = __shfl_sync(full, l2, 2);
   const double cb0 = 2.0 * lxh2 + lc + T.off[kCiaH2H2] * kLog2_10 - shift;
   const double cb1 = lxh2 + lxhe + lc + T.off[kCiaH2He] * kLog2_10 - shift;
@@ -223,7 +204,7 @@ __global__ void k_prep(FwdArgs a) {
   for (int j = lane; j <= L; j += 32) {
     const double Tj = S.profile == HR2_PROFILE_MILNE
                           ? level_temperature(S, th, j, grav)
-                          : fe_temperature_w(S, th + HR2_P_T0, lw, (double)(L - j) / (double)L);
+                          : fe_temperature_level(S, th + HR2_P_T0, j);
     if (!(Tj > 0.0) || !isfinite(Tj)) status |= HR2_SAMPLE_BAD_T;
     int acell;
     double wT;

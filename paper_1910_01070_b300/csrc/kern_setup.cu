@@ -248,6 +248,42 @@ __global__ void k_levels(int n_lev, double lt, double lb, const TablesDev* tab, 
   lev[j] = d;
 }
 
+// The finite-element profile's basis at every level (Sect. 2.5.1, Eqs.
+// 12-16): level j sits at x = (L - j) / L on [0,1] (x = 0 bottom), in element
+// k = floor(x K_e) (clamped) at local coordinate loc = x K_e - k, where basis
+// function i is prod_{m != i} (loc - xi_m) / (xi_i - xi_m).  Taken once per
+// setup, so that a sample's level temperature is fe_order+1 products.
+struct GllNodes {
+  double v[HR2_MAX_TNODES];
+};
+__global__ void k_fe_basis(int n_lev, int Ke, int q, GllNodes xi, int* fe_k, double* fe_b) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n_lev) return;
+  const int L = n_lev - 1;
+  const double x = (double)(L - j) / (double)L;
+  int k = (int)floor(x * Ke);
+  k = k < 0 ? 0 : (k > Ke - 1 ? Ke - 1 : k);
+  const double loc = x * Ke - k;
+  for (int i = 0; i <= q; ++i) {
+    double d = 1.0;
+    for (int m = 0; m <= q; ++m)
+      if (m != i) d *= xi.v[i] - xi.v[m];
+    double l = 1.0 / d;
+    for (int m = 0; m <= q; ++m)
+      if (m != i) l *= loc - xi.v[m];
+    fe_b[(size_t)j * (q + 1) + i] = l;
+  }
+  fe_k[j] = k;
+}
+
+cudaError_t build_fe_basis(int n_lev, int fe_elements, int fe_order, const double* gll, int* d_k, double* d_b,
+                           cudaStream_t s) {
+  GllNodes xi{};
+  for (int i = 0; i <= fe_order && i < HR2_MAX_TNODES; ++i) xi.v[i] = gll[i];
+  k_fe_basis<<<(n_lev + 127) / 128, 128, 0, s>>>(n_lev, fe_elements, fe_order, xi, d_k, d_b);
+  return cudaGetLastError();
+}
+
 cudaError_t build_setup_levels(int n_lev, double p_top, double p_bot, const TablesDev* d_tab, LevelDev* d_levels,
                                cudaStream_t s) {
   k_levels<<<(n_lev + 127) / 128, 128, 0, s>>>(n_lev, log10(p_top), log10(p_bot), d_tab, d_levels);
