@@ -421,6 +421,24 @@ int hr2_ns_absorb(hr2_ctx* ctx, int n_live, double* live_lnl, double* live_theta
                   const double* cand_theta, hr2_ns_state* state, double* dead_lnl, double* dead_logw,
                   double* dead_theta, long long dead_cap, void* stream);
 
+/* hr2_ns_propose: candidates for the next round of a minimal nested sampler
+ * (a stand-in for MultiNest's ellipsoidal proposals, Sect. 3.2), drawn on the
+ * device: uniform in the bounding box of the live points, widened by
+ * `enlarge` x its span on each side and clipped to the prior box [prior_lo,
+ * prior_hi]; a parameter with prior_lo == prior_hi stays at prior_lo.  Uniform
+ * deviates: SplitMix64 (Steele, Lea & Flood 2014) of (seed, counter + i *
+ * HR2_NPARAM + p), so a call consumes n * HR2_NPARAM counter values and equal
+ * arguments give equal draws.  All pointers are DEVICE:
+ *   live_theta          double [n_live][HR2_NPARAM]
+ *   prior_lo, prior_hi  double [HR2_NPARAM]
+ *   box                 double [HR2_NPARAM][2] (written: the proposal box)
+ *   out_theta           double [n][HR2_NPARAM] (written)
+ * Asynchronous on `stream`.  Returns HR2_EINVAL for n_live < 1, n < 0,
+ * enlarge < 0 (or NaN) or NULL pointers. */
+int hr2_ns_propose(hr2_ctx* ctx, int n_live, const double* live_theta, const double* prior_lo,
+                   const double* prior_hi, double enlarge, int n, double* box, double* out_theta,
+                   unsigned long long seed, unsigned long long counter, void* stream);
+
 /* hr2_ns_finalize: ln Z and H with the live points added, each with weight
  * X_n / N (fixed-order reduction): out (DEVICE double [2]) = {ln Z, H}.  The state
  * is not modified.  Asynchronous on `stream`. */

@@ -1073,6 +1073,19 @@ extern "C" int hr2_ns_absorb(hr2_ctx* ctx, int n_live, double* live_lnl, double*
   return HR2_OK;
 }
 
+extern "C" int hr2_ns_propose(hr2_ctx* ctx, int n_live, const double* live_theta, const double* prior_lo,
+                              const double* prior_hi, double enlarge, int n, double* box, double* out_theta,
+                              unsigned long long seed, unsigned long long counter, void* stream) {
+  if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
+  if (n_live < 1 || n < 0 || !(enlarge >= 0.0)) return fail(HR2_EINVAL, "need n_live >= 1, n >= 0, enlarge >= 0");
+  if (!live_theta || !prior_lo || !prior_hi || !box || (n && !out_theta)) return fail(HR2_EINVAL, "NULL argument");
+  HR2_CU(cudaSetDevice(ctx->device));
+  cudaError_t e = launch_ns_propose(n_live, live_theta, prior_lo, prior_hi, enlarge, n, box, out_theta, seed, counter,
+                                    (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(HR2_ECUDA, "ns propose launch: %s", cudaGetErrorString(e));
+  return HR2_OK;
+}
+
 extern "C" int hr2_ns_finalize(hr2_ctx* ctx, int n_live, const double* live_lnl, const hr2_ns_state* state,
                                double* out, void* stream) {
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");

@@ -288,6 +288,9 @@ cudaError_t build_fe_basis(int n_lev, int fe_elements, int fe_order, const doubl
 cudaError_t launch_teff(const FwdArgs& a, const float* highres, int highres_ld, double* out, cudaStream_t s);
 // nested-sampling evidence bookkeeping (kern_nested.cu)
 cudaError_t launch_ns_init(hr2_ns_state* st, cudaStream_t s);
+cudaError_t launch_ns_propose(int n_live, const double* live_theta, const double* lo, const double* hi,
+                              double enlarge, int n, double* box, double* out, unsigned long long seed,
+                              unsigned long long counter, cudaStream_t s);
 cudaError_t launch_ns_absorb(int n_live, double* live_lnl, double* live_theta, int n_cand, const double* cand_lnl,
                              const double* cand_theta, hr2_ns_state* st, double* dead_lnl, double* dead_logw,
                              double* dead_theta, long long dead_cap, cudaStream_t s);

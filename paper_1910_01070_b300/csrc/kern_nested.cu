@@ -212,6 +212,75 @@ __global__ void __launch_bounds__(32) k_ns_finalize(int n_live, const double* li
   }
 }
 
+// ------------------------------------------------------------ proposals
+// Candidates of the minimal sampler: uniform in the bounding box of the live
+// points, widened by `enlarge` x its span on each side and clipped to the
+// prior box; a parameter with lo == hi stays at lo.  The uniform deviates come
+// from SplitMix64 (Steele, Lea & Flood 2014, the finaliser of a Weyl sequence)
+// at counter values counter + i HR2_NPARAM + p, top 53 bits -> [0, 1).
+__device__ __forceinline__ double ns_uniform(unsigned long long seed, unsigned long long ctr) {
+  unsigned long long z = seed + (ctr + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+// block p: the live points' range of parameter p -> the proposal box
+__global__ void __launch_bounds__(256) k_ns_box(int n_live, const double* live_theta, const double* lo,
+                                                const double* hi, double enlarge, double* box) {
+  __shared__ double s_mn[8], s_mx[8];
+  const int p = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double mn = INFINITY, mx = -INFINITY;
+  for (int j = threadIdx.x; j < n_live; j += blockDim.x) {
+    const double v = live_theta[(size_t)j * HR2_NPARAM + p];
+    mn = fmin(mn, v);
+    mx = fmax(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if (lane == 0) {
+    s_mn[warp] = mn;
+    s_mx[warp] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      mn = fmin(mn, s_mn[w]);
+      mx = fmax(mx, s_mx[w]);
+    }
+    const double span = mx - mn;
+    box[2 * p] = fmax(lo[p], mn - enlarge * span);
+    box[2 * p + 1] = fmin(hi[p], mx + enlarge * span);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ns_draw(int n, const double* lo, const double* hi, const double* box,
+                                                 unsigned long long seed, unsigned long long counter, double* out) {
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * HR2_NPARAM) return;
+  const int p = (int)(idx % HR2_NPARAM);
+  double v = lo[p];
+  if (hi[p] > lo[p]) {
+    const double a = box[2 * p], b = box[2 * p + 1];
+    v = a + (b - a) * ns_uniform(seed, counter + (unsigned long long)idx);
+  }
+  out[idx] = v;
+}
+
+cudaError_t launch_ns_propose(int n_live, const double* live_theta, const double* lo, const double* hi,
+                              double enlarge, int n, double* box, double* out, unsigned long long seed,
+                              unsigned long long counter, cudaStream_t s) {
+  k_ns_box<<<HR2_NPARAM, 256, 0, s>>>(n_live, live_theta, lo, hi, enlarge, box);
+  if (n > 0) {
+    const long long total = (long long)n * HR2_NPARAM;
+    k_ns_draw<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(n, lo, hi, box, seed, counter, out);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ns_init(hr2_ns_state* st, cudaStream_t s) {
   k_ns_init<<<1, 1, 0, s>>>(st);
   return cudaGetLastError();

@@ -38,7 +38,7 @@ EXPORTED = [
     "hr2_setup_destroy", "forward_model_batch", "forward_model_batch_noalloc", "log_likelihood_batch",
     "hr2_evaluate_host", "hr2_profile_enable",
     "hr2_profile_read", "hr2_stream_check", "hr2_nodes_from_b", "hr2_version",
-    "hr2_ns_state_init", "hr2_ns_absorb", "hr2_ns_finalize", "hr2_effective_temperature",
+    "hr2_ns_state_init", "hr2_ns_absorb", "hr2_ns_propose", "hr2_ns_finalize", "hr2_effective_temperature",
 ]
 
 
@@ -122,6 +122,8 @@ def lib():
                                                         _VP, _VP]),
                 "hr2_ns_absorb": (C.c_int, [_VP, C.c_int, _VP, _VP, C.c_int, _VP, _VP, _VP, _VP, _VP, _VP,
                                             C.c_longlong, _VP]),
+                "hr2_ns_propose": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, C.c_double, C.c_int, _VP, _VP,
+                                             C.c_ulonglong, C.c_ulonglong, _VP]),
                 "hr2_ns_finalize": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, _VP]),
             }
             for name, (res, args) in sig.items():
@@ -416,6 +418,20 @@ def hr2_ns_absorb(ctx, live_lnl, live_theta, cand_lnl, cand_theta, state, dead_l
         _tensor_ptr(dead_logw, f, "dead_logw", (cap,)), _tensor_ptr(dead_theta, f, "dead_theta", (cap, HR2_NPARAM)),
         cap, _stream_ptr(stream))
     _check(rc, ctx)
+
+
+def hr2_ns_propose(ctx, live_theta, prior_lo, prior_hi, enlarge, box, out_theta, seed, counter, stream=None):
+    """CUDA float64 tensors: live [N, HR2_NPARAM], prior box [HR2_NPARAM] each, box [HR2_NPARAM, 2] (written),
+    candidates [n, HR2_NPARAM] (written).  Uses n * HR2_NPARAM counter values from `counter` on."""
+    import torch
+    f = torch.float64
+    n_live, n = int(live_theta.shape[0]), int(out_theta.shape[0])
+    _check(lib().hr2_ns_propose(
+        ctx, n_live, _tensor_ptr(live_theta, f, "live_theta", (n_live, HR2_NPARAM)),
+        _tensor_ptr(prior_lo, f, "prior_lo", (HR2_NPARAM,)), _tensor_ptr(prior_hi, f, "prior_hi", (HR2_NPARAM,)),
+        float(enlarge), n, _tensor_ptr(box, f, "box", (HR2_NPARAM, 2)),
+        _tensor_ptr(out_theta, f, "out_theta", (n, HR2_NPARAM)), int(seed) & (2 ** 64 - 1),
+        int(counter) & (2 ** 64 - 1), _stream_ptr(stream)), ctx)
 
 
 def hr2_ns_finalize(ctx, live_lnl, state, out, stream=None):

@@ -17,8 +17,10 @@ simplest valid stand-in:
 
 A candidate drawn from a box that held the whole constrained region
 {L > L*} stays a uniform draw from every later, smaller region, so one
-batch serves many replacements.  Per round the host sees only the live
-points (for the box), the candidates it draws and the small state struct.
+batch serves many replacements.  With a GPU backend the box and the
+candidates are made on the device (hr2_ns_propose, SplitMix64 deviates), so
+per round the host reads only the small state struct; a backend without
+that call gets the live points and draws the candidates on the host.
 """
 from __future__ import annotations
 
@@ -102,6 +104,27 @@ class GpuBackend:
                           self.dead_logw, self.dead_theta, self.stream)
         return self._read(hr2.ns_state_read, self.state)
 
+    def step_device(self, n: int, lo: np.ndarray, hi: np.ndarray, enlarge: float, seed: int, counter: int) -> Dict:
+        """One round with the candidates drawn on the device (hr2_ns_propose):
+        no host copy of the live set or of the candidates."""
+        torch = self.torch
+        with self._on_stream():
+            if getattr(self, "_prior", None) is None or not (np.array_equal(self._prior[0], lo) and
+                                                             np.array_equal(self._prior[1], hi)):
+                self._prior = (np.array(lo, dtype=np.float64), np.array(hi, dtype=np.float64))
+                self._prior_dev = (torch.as_tensor(self._prior[0], device=self.dev),
+                                   torch.as_tensor(self._prior[1], device=self.dev))
+                self._box = torch.empty((hr2.HR2_NPARAM, 2), dtype=torch.float64, device=self.dev)
+            if getattr(self, "_cand", None) is None or self._cand.shape[0] != n:
+                self._cand = torch.empty((n, hr2.HR2_NPARAM), dtype=torch.float64, device=self.dev)
+        th = self._cand
+        hr2.hr2_ns_propose(self.ctx, self.live_theta, self._prior_dev[0], self._prior_dev[1], enlarge, self._box, th,
+                           seed, counter, self.stream)
+        lnl = self._score(th)
+        hr2.hr2_ns_absorb(self.ctx, self.live_lnl, self.live_theta, lnl, th, self.state, self.dead_lnl,
+                          self.dead_logw, self.dead_theta, self.stream)
+        return self._read(hr2.ns_state_read, self.state)
+
     def finalize(self):
         hr2.hr2_ns_finalize(self.ctx, self.live_lnl, self.state, self.out, self.stream)
         o = self._read(lambda t: t.cpu().numpy(), self.out)
@@ -124,8 +147,10 @@ def log_add(a: float, b: float) -> float:
 class NestedSampler:
     """lo, hi: prior box per parameter ([HR2_NPARAM] each; lo == hi fixes a parameter)."""
 
-    def __init__(self, backend, lo, hi, batch: int = 1024, enlarge: float = 0.25, seed: int = 0):
+    def __init__(self, backend, lo, hi, batch: int = 1024, enlarge: float = 0.25, seed: int = 0,
+                 device_proposals: bool = True):
         self.b = backend
+        self.device_proposals = bool(device_proposals)
         self.lo = np.asarray(lo, dtype=np.float64)
         self.hi = np.asarray(hi, dtype=np.float64)
         self.free = self.hi > self.lo
@@ -146,12 +171,18 @@ class NestedSampler:
         n_evals = n_live
         st = None
         rounds = 0
+        device = self.device_proposals and hasattr(self.b, "step_device")
+        seed = int(self.rng.integers(0, 2 ** 63)) if device else 0
         for rounds in range(1, max_rounds + 1):
-            live = self.b.live_theta_host()
-            span = live.max(axis=0) - live.min(axis=0)
-            blo = np.maximum(self.lo, live.min(axis=0) - self.enlarge * span)
-            bhi = np.minimum(self.hi, live.max(axis=0) + self.enlarge * span)
-            st = self.b.step(self._draw(self.batch, blo, bhi))
+            if device:
+                st = self.b.step_device(self.batch, self.lo, self.hi, self.enlarge, seed,
+                                        (rounds - 1) * self.batch * len(self.lo))
+            else:
+                live = self.b.live_theta_host()
+                span = live.max(axis=0) - live.min(axis=0)
+                blo = np.maximum(self.lo, live.min(axis=0) - self.enlarge * span)
+                bhi = np.minimum(self.hi, live.max(axis=0) + self.enlarge * span)
+                st = self.b.step(self._draw(self.batch, blo, bhi))
             n_evals += self.batch
             if st["log_z"] > -math.inf and log_add(st["log_z"], st["lnl_max"] + st["log_x"]) - st["log_z"] < dlogz:
                 break

@@ -121,3 +121,68 @@ def test_driver_on_the_forward_model(eng):
     assert res2["n_dead"] == res["n_dead"] and res2["log_z"] == res["log_z"]
     dl2, _, dth2 = be2.dead(res2["n_dead"])
     assert np.array_equal(dl2, dl) and np.array_equal(dth2, dth)
+    # the host-drawn proposals (the path of a backend without hr2_ns_propose)
+    be3 = GpuBackend(eng.ctx, [s], 0, n_live=128)
+    res3 = NestedSampler(be3, lo, hi, batch=512, seed=4, device_proposals=False).run(dlogz=0.5, max_rounds=6)
+    dl3, _, dth3 = be3.dead(res3["n_dead"])
+    assert res3["n_dead"] > 0 and np.all(np.diff(dl3) >= 0)
+    k = res3["n_dead"] - 1
+    assert dl3[k] == pytest.approx(oracle.lnL(D, sig, om.forward(dth3[k])[0]), rel=1e-5, abs=1e-3)
+
+
+def test_device_proposals_stay_in_the_box_and_are_reproducible(eng):
+    """hr2_ns_propose: the box is the live points' range widened by enlarge x span
+    and clipped to the prior; every draw lies in it, fixed parameters stay at
+    their value, equal (seed, counter) give equal draws, row i uses counters
+    counter + i HR2_NPARAM .. (so a shifted counter shifts the rows), and each
+    free parameter's draws are uniform on its interval."""
+    from scipy import stats
+    rng = np.random.default_rng(5)
+    P = hr2.HR2_NPARAM
+    lo, hi = np.zeros(P), np.zeros(P)
+    free = np.arange(P) % 3 != 2
+    lo[free], hi[free] = -1.0 - rng.random(free.sum()), 1.0 + rng.random(free.sum())
+    lo[~free] = hi[~free] = rng.normal(size=(~free).sum())
+    live = np.repeat(lo[None, :], 300, axis=0)
+    live[:, free] = rng.uniform(-0.5, 0.8, (300, free.sum()))
+    live[0, 0] = lo[0]                                   # reaches the prior edge: the box is clipped there
+    enlarge = 0.25
+    span = live.max(0) - live.min(0)
+    ref_lo = np.maximum(lo, live.min(0) - enlarge * span)
+    ref_hi = np.minimum(hi, live.max(0) + enlarge * span)
+    d_live, d_lo, d_hi = _t(live), _t(lo), _t(hi)
+    box = torch.empty((P, 2), dtype=torch.float64, device="cuda")
+    n = 4096
+
+    def draw(n, seed, counter):
+        out = torch.empty((n, P), dtype=torch.float64, device="cuda")
+        hr2.hr2_ns_propose(eng.ctx, d_live, d_lo, d_hi, enlarge, box, out, seed, counter)
+        torch.cuda.synchronize()
+        return out.cpu().numpy()
+
+    a = draw(n, 11, 0)
+    b = box.cpu().numpy()
+    assert np.allclose(b[free, 0], ref_lo[free], rtol=1e-15, atol=1e-15)
+    assert np.allclose(b[free, 1], ref_hi[free], rtol=1e-15, atol=1e-15)
+    assert b[0, 0] == lo[0]
+    assert np.all(a[:, free] >= b[free, 0]) and np.all(a[:, free] < b[free, 1])
+    assert np.array_equal(a[:, ~free], np.repeat(lo[None, ~free], n, axis=0))
+    assert np.array_equal(draw(n, 11, 0), a)
+    assert np.array_equal(draw(n - 1, 11, P), a[1:])
+    assert not np.array_equal(draw(n, 12, 0), a)
+    u = (a[:, free] - b[free, 0]) / (b[free, 1] - b[free, 0])
+    for col in u.T:
+        assert stats.kstest(col, "uniform").pvalue > 1e-4
+    assert abs(np.corrcoef(u[:, 0], u[:, 1])[0, 1]) < 0.06
+
+
+def test_device_proposals_argument_errors(eng):
+    P = hr2.HR2_NPARAM
+    live = _t(np.zeros((4, P)))
+    lo, hi = _t(np.zeros(P)), _t(np.ones(P))
+    box = torch.empty((P, 2), dtype=torch.float64, device="cuda")
+    out = torch.empty((8, P), dtype=torch.float64, device="cuda")
+    with pytest.raises(hr2.Hr2Error):
+        hr2.hr2_ns_propose(eng.ctx, live, lo, hi, -0.5, box, out, 1, 0)
+    with pytest.raises(hr2.Hr2Error):
+        hr2.hr2_ns_propose(eng.ctx, live[:0], lo, hi, 0.25, box, out, 1, 0)
