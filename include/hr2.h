@@ -332,7 +332,7 @@ int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups
  * forward_model_batch, except that out_highres is REQUIRED: the F+ buffer is
  * an output here, not scratch.
  *   - Limit: the batch must fit the array, roughly n * (L+1) * 64 bytes plus
- *     n * 148 bytes plus 1 KB (about 1024 samples of 121 levels); larger
+ *     n * 220 bytes plus 1 KB (about 1024 samples of 121 levels); larger
  *     batches, FP64 tables or a NULL out_highres return HR2_EINVAL with a
  *     message giving the bytes needed.
  *   - The first call on a device looks up the array's device address (once
