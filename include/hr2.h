@@ -70,7 +70,10 @@ typedef enum {
  * free-chemistry variant):
  *   [HR2_P_LOGG]      log10 g, g in cm s^-2
  *   [HR2_P_F]         calibration factor f of the radius-distance relation
- *   [HR2_P_DIST]      distance d in parsec
+ *   [HR2_P_DIST]      distance d in parsec; the FP16/FP32 path scales the
+ *                     binned flux by f (R/d)^2 held as an FP32 head and tail,
+ *                     so that factor must lie in FP32's normal range
+ *                     (1.2e-38 .. 3.4e38; R < d gives at most f)
  *   [HR2_P_T0 + i]    finite-element nodal temperature i in K, i = 0 is the
  *                     bottom of the atmosphere (T_1 of Sect. 2.5.1); the setup
  *                     uses fe_elements*fe_order+1 of them
