@@ -786,12 +786,28 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
     }
     __syncthreads();
     if (active) {
-      if (item_small_x(a, S, T, i, tile))
-        solve_tile<NMU, CACHED, KT, LIN, PARA, true, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu,
-                                                     wp_, phase_base);
-      else
-        solve_tile<NMU, CACHED, KT, LIN, PARA, false, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu,
-                                                      wp_, phase_base);
+      const bool sx = item_small_x(a, S, T, i, tile);
+      // a batch compiled for a bound KT >= 8 holds setups with KT-4 .. KT
+      // absorbers: each item runs the sweep compiled for its own setup's
+      // even bound, so that a setup pads at most one absorber (the linear
+      // source; the parabolic one keeps the batch's bound)
+#define HR2_SOLVE(KB)                                                                                              \
+  (sx ? solve_tile<NMU, CACHED, KB, LIN, PARA, true, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, \
+                                                          sMu, wp_, phase_base)                                    \
+      : solve_tile<NMU, CACHED, KB, LIN, PARA, false, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl,     \
+                                                           sImu, sMu, wp_, phase_base))
+      if constexpr (KT >= 8 && !PARA) {
+        const int kc = (S.n_species + 1) & ~1;
+        if (kc <= KT - 4)
+          HR2_SOLVE((KT >= 8 ? KT - 4 : KT));
+        else if (kc <= KT - 2)
+          HR2_SOLVE((KT >= 8 ? KT - 2 : KT));
+        else
+          HR2_SOLVE(KT);
+      } else {
+        HR2_SOLVE(KT);
+      }
+#undef HR2_SOLVE
     }
   }
 }
