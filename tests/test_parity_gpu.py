@@ -184,11 +184,13 @@ def test_absorber_counts_level_gridded(eng, K, with_cia):
         _compare(om, theta[i], bins[i], hi[i], FLUX_RTOL, 300)
 
 
-@pytest.mark.parametrize("ks", [(5, 6), (4, 6), (6, 3, 5), (2, 6), (1, 6), (2, 7, 5)])
+@pytest.mark.parametrize("ks", [(5, 6), (4, 6), (6, 3, 5), (2, 6), (1, 6), (2, 7, 5), (8, 5, 7), (10, 6, 9, 7),
+                                (12, 9), (16, 13, 12)])
 def test_mixed_absorber_counts_in_one_batch(eng, ks):
     """Setups with different absorber counts in one batch: counts from K-4 to K
     share the even bound K (zero-weight padding, up to 4 padded absorbers
-    reading the stage's other values), wider mixes ((1, 6), (2, 7, 5)) take the
+    reading the stage's other values; from a bound of 8 up each item runs its
+    own setup's even bound), wider mixes ((1, 6), (2, 7, 5)) take the
     runtime-count kernel.  Every sample matches the oracle of its setup."""
     spec, tabs = _absorber_spec(max(ks), 77)
     t = eng.add_tables(spec, "fp16", tabs)
