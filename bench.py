@@ -373,10 +373,11 @@ def _gpu_workload(wl, eng, dev, seed_offset=0):
 
 def run_extras(args, local, flush):
     """The uneven three-setup batch (one persistent launch over 2048 samples of 12 setup
-    variants) and the continuous-batching serving loop on those setups."""
+    variants, launch shape autotuned on the batch) and the continuous-batching serving
+    loop on those setups."""
     import torch
 
-    from paper_1910_01070_b300 import hr2, serving
+    from paper_1910_01070_b300 import autotune, hr2, serving
     from paper_1910_01070_b300 import workloads as W
     from paper_1910_01070_b300.engine import Engine
 
@@ -397,6 +398,9 @@ def run_extras(args, local, flush):
         for k in range(3):
             hr2.forward_model_batch(eng.ctx, setups, pool[k][1], pool[k][0], bins, None, None, stream)
         torch.cuda.synchronize()
+        # the launch shape tuned on this batch (timed candidates, no cache)
+        best, tried = autotune.tune(eng.ctx, setups, pool[0][1], pool[0][0], bins,
+                                    [autotune.setup_info_from_spec(s) for s in wl.setups], use_cache=False)
         steps = max(3, min(args.steps, 40))
         evs = []
         hr2.hr2_profile_read(eng.ctx, True)
@@ -427,7 +431,8 @@ def run_extras(args, local, flush):
                                "p99_ms": float(np.percentile(times, 99)),
                                "kernel_ms": kms / max(nl, 1),
                                "alu_frac": ops / (kms / max(nl, 1) / 1e3) / 1e12 / peak,
-                               "launch": list(hr2.hr2_get_launch_config(eng.ctx))}
+                               "launch": list(hr2.hr2_get_launch_config(eng.ctx)),
+                               "autotuned": {"candidates": len(tried), "best": list(best)}}
         # serving: 16 nested-sampling-like streams over the 12 setups, Poisson arrivals
         shapes = [(s.n_bins, s.n_nu, s.n_layers + 1) for s in wl.setups]
         res = []

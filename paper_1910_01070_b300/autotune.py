@@ -1,9 +1,9 @@
 """Autotuner for the launch shape of the persistent forward kernel.
 
-The forward kernel's tile is fixed (64 wavenumbers, two per lane); what is
-tuned is how many samples share one work item (warps per CTA, which also
-sets the per-CTA shared-memory pipeline size) and how many persistent CTAs
-run per SM.  For a batch shape the tuner times every candidate with the
+The forward kernel's tile is fixed (128 wavenumbers, two packed pairs per
+lane); what is tuned is how many samples share one work item (warps per CTA,
+which also sets the per-CTA shared-memory pipeline size) and how many
+persistent CTAs run per SM.  For a batch shape the tuner times every candidate with the
 library's kernel-event instrumentation (hr2_profile_*) on the caller's real
 inputs, keeps the fastest, and caches the choice in a JSON file keyed by the
 shape, so later runs (and the serving loop) reuse it without re-timing.
