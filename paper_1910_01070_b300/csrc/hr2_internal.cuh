@@ -95,7 +95,7 @@ struct LevelDev {
 // Device descriptor of one setup (lives in device memory).
 struct SetupDev {
   int nu_first, n_nu;     // table columns used
-  int tile0, n_tiles;     // 64-aligned tiles (in table columns) covering the range
+  int tile0, n_tiles;     // kTileNu-aligned tiles (in table columns) covering the range
   int n_lev;              // levels = layers + 1
   int n_species;
   int species[HR2_MAX_SPECIES];
