@@ -481,6 +481,99 @@ def test_each_cia_pair_closed_form(oracle_lib, which):
     assert np.allclose(dtau, expect, rtol=1e-8)
 
 
+def test_several_absorbers_through_a_species_map_closed_form(oracle_lib):
+    """Sects. 2.3, 2.8: chi is the sum over the setup's absorbers of x_s times
+    the cross-section of the TABLE species the setup maps s to, and the mean
+    molecular weight sums x_s times that table species' mass.  Three table
+    species with different constant cross-sections and masses, used through
+    the non-identity map [2, 0]; abundances large and unequal, so that using
+    one absorber's x for all, the setup index instead of the table index (for
+    sigma or for the mass), or dropping an absorber changes dtau far beyond
+    1e-8."""
+    spec = W.TableSpec(3, np.linspace(400.0, 2400.0, 4), np.linspace(-4.0, 2.0, 3), 6000.0, 1.0, 8, seed=5,
+                       cia=False)
+    tabs = W.make_tables(spec)
+    lsig = np.array([-22.0, -25.0, -23.5])
+    tabs["log10_sigma"] = np.broadcast_to(lsig[:, None, None, None], tabs["log10_sigma"].shape).copy()
+    tabs["species_mass"] = np.array([10.0, 60.0, 250.0])
+    setup = W.make_setup(spec, 6000.0, 6007.0, 5, [2, 0], 2, 1, 1, 0.0, 2)
+    m = oracle.Model(tabs, setup.as_dict())
+    x = np.array([0.04, 0.15])                    # setup absorbers 0 (table 2) and 1 (table 0)
+    th = _theta([1300.0, 900.0], logx=tuple(np.log10(x)))
+    dtau, ok = m.layer_dtau(th, 3)
+    assert ok
+    xh2 = (1 - x.sum()) / 1.17
+    mmw = x[0] * 250.0 + x[1] * 10.0 + xh2 * 2.01588 + 0.17 * xh2 * 4.002602
+    chi = x[0] * 10 ** lsig[2] + x[1] * 10 ** lsig[0]
+    p = 10 ** np.linspace(-4.0, 2.0, 6) * 1e6
+    expect = chi * np.diff(p) / (mmw * AMU * 10 ** 4.75)
+    assert np.allclose(dtau, expect, rtol=1e-8)
+
+
+def test_abundances_and_gravity_scaled_together_leave_the_spectrum(oracle_lib):
+    """Sects. 2.3, 2.8 with hydrostatic columns: dtau is proportional to
+    x_s / (mmw g).  When every absorber has the mass of the H2/He fill,
+    mmw does not depend on the abundances, so scaling all x_s and g by the
+    same factor leaves every layer's optical depth, and so the spectrum,
+    unchanged (no CIA, whose x_H2^2 term would break it)."""
+    spec = W.TableSpec(3, np.linspace(400.0, 2400.0, 4), np.linspace(-4.0, 2.0, 3), 6000.0, 1.0, 24, seed=8,
+                       cia=False)
+    tabs = W.make_tables(spec)
+    m_fill = (2.01588 + 0.17 * 4.002602) / 1.17
+    tabs["species_mass"] = np.full(3, m_fill)
+    setup = W.make_setup(spec, 6000.0, 6023.0, 6, [1, 2, 0], 3, 2, 1, 0.0, 4)
+    m = oracle.Model(tabs, setup.as_dict())
+    logx = (-3.1, -4.4, -2.6)
+    th = _theta([1900.0, 1400.0, 800.0], logx=logx)
+    th2 = _theta([1900.0, 1400.0, 800.0], logg=4.75 + math.log10(3.0), logx=tuple(v + math.log10(3.0) for v in logx))
+    _, top, ok = m.forward(th, want_top=True)
+    _, top2, ok2 = m.forward(th2, want_top=True)
+    assert ok and ok2
+    assert np.allclose(top2, top, rtol=1e-12)
+    d1, _ = m.layer_dtau(th, 7)
+    d2, _ = m.layer_dtau(th2, 7)
+    assert np.allclose(d2, d1, rtol=1e-12)
+    # the same scaling of one absorber only does change the optical depth
+    th3 = th.copy()
+    th3[19] += math.log10(3.0)
+    d3, _ = m.layer_dtau(th3, 7)
+    assert not np.allclose(d3, d1, rtol=1e-3)
+
+
+def test_log10_cia_interpolated_linearly_in_temperature(oracle_lib):
+    """Sect. 2.8, reading R3 applied to CIA: log10 k is interpolated linearly
+    in T.  Tables with log10 k(T) = a + b T (different for the two pairs) are
+    then reproduced exactly between the T nodes, so on a profile whose levels
+    fall between nodes, dtau is the trapezoid of
+    x_H2^2 n 10^(a0 + b0 T) + x_H2 x_He n 10^(a1 + b1 T); swapped cell
+    weights or swapped pairs fail."""
+    spec = W.TableSpec(1, np.linspace(400.0, 2400.0, 5), np.linspace(-4.0, 2.0, 3), 6000.0, 1.0, 8, seed=5)
+    tabs = W.make_tables(spec)
+    tabs["log10_sigma"] = np.full(tabs["log10_sigma"].shape, -300.0)
+    Tg = spec.T_grid
+    a0, b0, a1, b1 = -46.0, 6.0e-4, -45.2, -3.5e-4
+    tabs["log10_cia_h2h2"] = np.broadcast_to((a0 + b0 * Tg)[:, None], (5, 8)).copy()
+    tabs["log10_cia_h2he"] = np.broadcast_to((a1 + b1 * Tg)[:, None], (5, 8)).copy()
+    setup = W.make_setup(spec, 6000.0, 6007.0, 6, [0], 2, 2, 1, 0.0, 2)
+    m = oracle.Model(tabs, setup.as_dict())
+    x = 1e-3
+    th = _theta([2230.0, 1610.0, 720.0], logx=(math.log10(x),))
+    T, _ = m.level_temperatures(th)
+    assert np.all(np.min(np.abs(T[:, None] - Tg[None, :]), axis=1) > 20.0)   # no level on a node
+    assert m.cia_coeff("h2h2", T[3], 2) == pytest.approx(10 ** (a0 + b0 * T[3]), rel=1e-12)
+    assert m.cia_coeff("h2he", T[3], 2) == pytest.approx(10 ** (a1 + b1 * T[3]), rel=1e-12)
+    dtau, ok = m.layer_dtau(th, 3)
+    assert ok
+    xh2 = (1 - x) / 1.17
+    xhe = 0.17 * xh2
+    mmw = x * tabs["species_mass"][0] + xh2 * 2.01588 + xhe * 4.002602
+    p = 10 ** np.linspace(-4.0, 2.0, 7) * 1e6
+    n = p / (KB * T)
+    chi = xh2 * xh2 * n * 10 ** (a0 + b0 * T) + xh2 * xhe * n * 10 ** (a1 + b1 * T)
+    expect = 0.5 * (chi[:-1] + chi[1:]) * np.diff(p) / (mmw * AMU * 10 ** 4.75)
+    assert np.allclose(dtau, expect, rtol=1e-8)
+
+
 def test_wavenumber_offset_indexes_the_table(oracle_lib):
     """Setup point k reads table column nu_first + k."""
     spec = W.TableSpec(1, np.linspace(400.0, 2400.0, 4), np.linspace(-4.0, 2.0, 3), 6000.0, 1.0, 40, seed=5,
