@@ -27,6 +27,7 @@ import threading
 import time
 
 import numpy as np
+from typing import Optional
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -54,6 +55,9 @@ def parse():
     p.add_argument("--sweep-nu", type=int, default=290001, help="wavenumber points of the swept tables")
     p.add_argument("--sweep-modes", default="direct,cached")
     p.add_argument("--sweep-batches", default="1,2,4,8,16,32,64,128,256")
+    p.add_argument("--peaks", action="store_true",
+                   help="instead of the main line: microbenchmarks of the special-function unit (ex2, rcp) and "
+                        "the FMA pipe, with the SM clock sampled during each")
     return p.parse_args()
 
 
@@ -138,13 +142,64 @@ def max_over_ranks(world, x: float) -> float:
     return float(t.item())
 
 
-def mufu_ops_per_model(setup, n_cia: int) -> float:
-    """Exponentials the method needs per model: per wavenumber, one per absorber,
-    CIA pair and Planck source on every level, and one transmission factor per
-    layer and angle node."""
+def method_work_per_model(setup, n_cia: int) -> dict:
+    """Special-function and FP32 work the method needs per model (the algorithmic
+    count, independent of how the kernel issues it).  Per wavenumber:
+      ex2: one 10^x per absorber and per CIA pair present on every level, one
+           Planck exponential per level, one transmission factor e^{-tau/mu} per
+           layer and angle node: (L+1)(K + n_cia + 1) + L N_mu;
+      rcp: one 1/dtau per layer (shared by the nodes) and one 1/(e^x - 1) per
+           level: L + (L+1);
+      fp32: per level 2 per absorber and CIA pair (the T interpolation and the
+           abundance-weighted sum), 3 for the Planck function (x, e^x - 1 and the
+           product), 5 for the layer (trapezoid, source difference, slope,
+           cumulative tau), and 3 per angle node (exponent, difference of the
+           transmissions, accumulation): (L+1)(2(K + n_cia) + 8) + 3 L N_mu."""
     L = setup.n_layers
     K = len(setup.species)
-    return float(setup.n_nu) * ((L + 1) * (K + n_cia + 1) + L * setup.n_mu)
+    nu = float(setup.n_nu)
+    return {"ex2": nu * ((L + 1) * (K + n_cia + 1) + L * setup.n_mu),
+            "rcp": nu * (L + (L + 1)),
+            "fp32": nu * ((L + 1) * (2 * (K + n_cia) + 8) + 3 * L * setup.n_mu)}
+
+
+def mufu_ops_per_model(setup, n_cia: int) -> float:
+    """Exponentials the method needs per model (see method_work_per_model)."""
+    return method_work_per_model(setup, n_cia)["ex2"]
+
+
+def unit_peaks(rates: dict, n_sm: int) -> dict:
+    """Peak rates at the maximum SM clock from the measured operations per SM clock:
+    ex2 and rcp of the special-function unit and scalar FP32 FMA."""
+    f = SM_MAX_MHZ * 1e6
+    return {"ex2_per_s": rates["ex2"]["ops_per_clk_sm"] * n_sm * f,
+            "rcp_per_s": rates["rcp"]["ops_per_clk_sm"] * n_sm * f,
+            "fp32_per_s": rates["ffma"]["ops_per_clk_sm"] * n_sm * f,
+            "ops_per_clk_sm": {k: rates[k]["ops_per_clk_sm"] for k in ("ex2", "rcp", "ex2_rcp", "ffma", "ffma2")},
+            "ex2_rcp_share_one_unit": rates["ex2_rcp"].get("mix_over_shared_prediction"),
+            "sm_mhz": SM_MAX_MHZ}
+
+
+def roofline_of(work: dict, kernel_ms: float, peaks: dict, counters: Optional[dict]) -> dict:
+    """The forward kernel against its roofs.  MUFU: the special-function time the method
+    needs (ex2 / ex2 rate + rcp / rcp rate) over the kernel time, reported as
+    ex2-equivalents per second (rcp weighted by the ratio of the rates).  FMA: the
+    method's FP32 operations over the FMA rate.  DRAM and L2: the ncu counters of the
+    same kernel source (committed under profiles/), else null.  binding = the largest."""
+    t = kernel_ms / 1e3
+    t_mufu = work["ex2"] / peaks["ex2_per_s"] + work["rcp"] / peaks["rcp_per_s"]
+    ex2_eq = work["ex2"] + work["rcp"] * peaks["ex2_per_s"] / peaks["rcp_per_s"]
+    fr = {"mufu": t_mufu / t, "fma": work["fp32"] / peaks["fp32_per_s"] / t}
+    hbm_peak, hbm_src = _hbm_peak()
+    if counters:
+        fr["dram"] = counters["dram_bytes"] / t / 1e9 / hbm_peak
+        if counters.get("l2_frac") is not None:
+            fr["l2"] = counters["l2_frac"] * counters.get("kernel_ms_ncu", kernel_ms) / kernel_ms
+    return {"bound": "alu", "achieved": ex2_eq / t / 1e12, "peak": peaks["ex2_per_s"] / 1e12,
+            "unit": "Tex2-eq/s", "frac": fr["mufu"],
+            "binding": max(fr.values()), "binding_unit": max(fr, key=fr.get), "fractions": fr,
+            "work_per_launch": work, "peak_source": "hr2_measure_unit_rate in this run (ops per SM clock) x SMs "
+                                                     "x %d MHz" % SM_MAX_MHZ}
 
 
 def cpu_baseline(wl, n_samples: int):
@@ -264,6 +319,11 @@ def run_hr2(args, world, rank, local):
         times = [a.elapsed_time(b) for a, b in evs]
         return times, kms, launches
 
+    # the special-function and FMA rates of this GPU, measured before the timed region
+    props = torch.cuda.get_device_properties(local)
+    rates = measure_unit_rates(local, clocks=False)
+    peaks = unit_peaks(rates, props.multi_processor_count)
+
     clocks = ClockSampler(local)
     clocks.start()
     times, kms, launches = timed([s16], args.steps, args.warmup)
@@ -273,28 +333,18 @@ def run_hr2(args, world, rank, local):
     value = world * n * args.steps / (total_ms / 1e3)
     lat = np.asarray(times)
     n_cia = int(wl.table.cia) * 2
-    ops = mufu_ops_per_model(setup, n_cia) * n
+    work = {k: v * n for k, v in method_work_per_model(setup, n_cia).items()}
     kernel_ms = kms / max(launches, 1)
-    props = torch.cuda.get_device_properties(local)
-    peak_ops = props.multi_processor_count * 32 * 2032e6 / 1e12     # ex2 per clock per SM (measured 32)
-    achieved = ops / (kernel_ms / 1e3) / 1e12
-    traffic = None
-    if os.path.exists(PROFILE_TRAFFIC):
-        with open(PROFILE_TRAFFIC) as f:
-            tr = json.load(f)
-        if tr.get("kernel_source_hash") == _kernel_hash():
-            traffic = tr.get("bytes_per_launch")
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "Texp/s",
-                "frac": achieved / peak_ops, "traffic": traffic,
-                "kernel": "k_forward32", "kernel_ms": kernel_ms,
-                "note": "exponentials required by the method per launch / event-timed kernel time; peak = "
-                        "SMs x 32 ex2/clk/SM (measured) x 2032 MHz"}
+    counters = committed_counters()
+    roofline = roofline_of(work, kernel_ms, peaks, counters)
+    roofline.update({"traffic": counters["dram_bytes"] if counters else None, "kernel": "k_forward32",
+                     "kernel_ms": kernel_ms, "counters": counters["source"] if counters else None})
     hbm_peak, hbm_src = _hbm_peak()
     hbm = None
-    if traffic:
-        gbs = traffic / (kernel_ms / 1e3) / 1e9
+    if counters:
+        gbs = counters["dram_bytes"] / (kernel_ms / 1e3) / 1e9
         hbm = {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "frac": gbs / hbm_peak, "peak_source": hbm_src,
-               "traffic_bytes_per_launch": traffic}
+               "traffic_bytes_per_launch": counters["dram_bytes"]}
 
     # end to end through the host-buffer entry point (pinned buffers)
     h_par = [torch.as_tensor(p[0].cpu().numpy()).pin_memory() for p in pool]
@@ -419,18 +469,19 @@ def run_extras(args, local, flush):
         kms, nl = hr2.hr2_profile_read(eng.ctx, True)
         times = [a.elapsed_time(b) for a, b in evs]
         cap = n * steps / (sum(times) / 1e3)
-        ops = 0.0
+        work = {"ex2": 0.0, "rcp": 0.0, "fp32": 0.0}
         for p in range(3):
             for g, s in enumerate(wl.setups):
-                ops += float(np.sum(pool[p][2] == g)) * mufu_ops_per_model(s, 2)
-        ops /= 3
+                for k, v in method_work_per_model(s, 2).items():
+                    work[k] += float(np.sum(pool[p][2] == g)) * v / 3
         props = torch.cuda.get_device_properties(local)
-        peak = props.multi_processor_count * 32 * 2032e6 / 1e12
+        peaks = unit_peaks(measure_unit_rates(local, clocks=False), props.multi_processor_count)
+        rl = roofline_of(work, kms / max(nl, 1), peaks, None)
         out["uneven_batch"] = {"workload": wl.name, "samples": n, "setups": len(wl.setups),
                                "value": cap, "unit": "models/s", "ms_per_step": float(np.mean(times)),
                                "p99_ms": float(np.percentile(times, 99)),
                                "kernel_ms": kms / max(nl, 1),
-                               "alu_frac": ops / (kms / max(nl, 1) / 1e3) / 1e12 / peak,
+                               "mufu_frac": rl["fractions"]["mufu"], "fma_frac": rl["fractions"]["fma"],
                                "launch": list(hr2.hr2_get_launch_config(eng.ctx)),
                                "autotuned": {"candidates": len(tried), "best": list(best)}}
         # serving: 16 nested-sampling-like streams over the 12 setups, Poisson arrivals
@@ -608,6 +659,59 @@ def run_sweep_large(args, local):
     return res
 
 
+UNIT_KINDS = (("ex2_rcp", 0), ("rcp", 1), ("ex2", 2), ("ffma", 3), ("ffma2", 4))
+
+
+def measure_unit_rates(local, iters=20000, clocks=True):
+    """Throughput of the special-function unit and the FMA pipe (hr2_measure_unit_rate),
+    per kind: operations per clock per SM at the clock the kernel ran at.  The
+    interleaved ex2/rcp kind is compared with what one shared unit would give."""
+    from paper_1910_01070_b300 import hr2
+    from paper_1910_01070_b300.build import build
+    build()
+    out = {}
+    for name, kind in UNIT_KINDS:
+        cs = ClockSampler(local) if clocks else None
+        if cs:
+            cs.start()
+        r = hr2.hr2_measure_unit_rate(local, kind, iters)
+        if cs:
+            r["clocks"] = cs.stop()
+        out[name] = r
+    # the interleaved chains tell whether ex2 and rcp share one unit: if they do,
+    # a mixed op takes the mean of the two single-kind times
+    t_mix = 1.0 / out["ex2_rcp"]["ops_per_clk_sm"]
+    t_shared = 0.5 / out["ex2"]["ops_per_clk_sm"] + 0.5 / out["rcp"]["ops_per_clk_sm"]
+    out["ex2_rcp"]["shared_unit_prediction_ops_per_clk_sm"] = 1.0 / t_shared
+    out["ex2_rcp"]["mix_over_shared_prediction"] = t_shared / t_mix
+    return out
+
+
+def run_peaks(args, local):
+    rates = measure_unit_rates(local)
+    line = {"peaks": "arithmetic units", "sm_max_mhz": SM_MAX_MHZ, "rates": rates,
+            "note": "ops_per_clk_sm: operations per SM per clock at the clock the kernel ran at (clock64 over "
+                    "the global timer); 8 CTAs x 256 threads per SM, 16 independent chains per thread"}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+SM_MAX_MHZ = 2032.0
+
+
+def committed_counters() -> Optional[dict]:
+    """ncu counters of the forward kernel committed under profiles/ (DRAM bytes per launch
+    and L2 throughput as a fraction of peak), if they belong to the current kernel source."""
+    if not os.path.exists(PROFILE_TRAFFIC):
+        return None
+    with open(PROFILE_TRAFFIC) as f:
+        tr = json.load(f)
+    if tr.get("kernel_source_hash") != _kernel_hash():
+        return None
+    return {"dram_bytes": tr.get("bytes_per_launch"), "l2_frac": tr.get("l2_throughput_frac"),
+            "kernel_ms_ncu": tr.get("kernel_ms_ncu"), "source": tr.get("source")}
+
+
 def _hbm_peak():
     """Measured copy bandwidth of this machine's B300 (GB/s), else the recipe's fallback."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -645,6 +749,9 @@ def main():
     elif args.sweep_large:
         if rank == 0:
             run_sweep_large(args, local)
+    elif args.peaks:
+        if rank == 0:
+            run_peaks(args, local)
     else:
         run_hr2(args, world, rank, local)
     if world > 1:

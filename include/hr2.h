@@ -360,11 +360,74 @@ int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2_setup* con
 int hr2_profile_enable(hr2_ctx* ctx, int on);
 int hr2_profile_read(hr2_ctx* ctx, int reset, double* kernel_ms, int* launches);
 
+/* hr2_measure_unit_rate: (No counterpart in the paper.)  Throughput of one
+ * arithmetic unit of `device`, measured by a microbenchmark kernel at full
+ * occupancy (8 CTAs of 256 threads per SM, 16 independent dependency chains
+ * per thread, `iters` steps per chain, one warm-up launch of iters/16 steps
+ * first).  These are the denominators of the forward kernel's roofline:
+ *   HR2_UNIT_EX2_RCP  half the chains y <- 2^(-y), half y <- 1/y + 1: the
+ *                     two special functions interleaved (ops counts both)
+ *   HR2_UNIT_RCP      y <- 1/y + 1, rcp.approx.ftz and an FP32 addition
+ *   HR2_UNIT_EX2      y <- 2^(-y), ex2.approx.ftz after an FP32 negation
+ *   HR2_UNIT_FFMA     scalar FP32 fused multiply-add
+ *   HR2_UNIT_FFMA2    packed f32x2 fused multiply-add (ops counts
+ *                     instructions, each two FMAs)
+ * `out` (HOST) receives the CUDA-event time, the operations, operations per
+ * second, operations per SM cycle (the cycles being the median over SMs of the
+ * span from an SM's first CTA start to its last CTA end, in that SM's
+ * clock64) and the SM clock those cycles imply over the event time.  Synchronous;
+ * allocates and frees its own small buffers.  Returns HR2_EINVAL for an
+ * unknown kind or iters < 1, HR2_ECUDA on a CUDA error. */
+#define HR2_UNIT_EX2_RCP 0
+#define HR2_UNIT_RCP 1
+#define HR2_UNIT_EX2 2
+#define HR2_UNIT_FFMA 3
+#define HR2_UNIT_FFMA2 4
+#define HR2_UNIT_KINDS 5
+typedef struct {
+  double ms;              /* kernel time (CUDA events)                     */
+  double ops;             /* operations executed                           */
+  double ops_per_s;
+  double sm_ghz;          /* SM cycles of the run / event time             */
+  double ops_per_clk_sm;  /* ops / n_sm / SM cycles of the run (median SM) */
+  int n_sm;
+} hr2_unit_rate;
+int hr2_measure_unit_rate(int device, int kind, long long iters, hr2_unit_rate* out);
+
 /* Wait for `stream` and report whether a bounded device-side wait of the
  * last batch on that stream gave up (HR2_ETIMEDOUT; its outputs are then not
  * valid).  No counterpart in the paper.  hr2_evaluate_host checks the same
  * word itself. */
 int hr2_stream_check(hr2_ctx* ctx, void* stream);
+
+/* hr2_noalloc_check: the same report for forward_model_batch_noalloc, whose
+ * error word lives in the shared static array: waits for `stream`, then
+ * reads the word the last allocation-free call (on any stream of this
+ * device) left.  A 4-byte device-to-host copy; allocates nothing.  No
+ * counterpart in the paper. */
+int hr2_noalloc_check(hr2_ctx* ctx, void* stream);
+
+/* hr2_set_wait_limit / hr2_get_wait_limit: SM clock cycles (>= 0) that a
+ * device-side pipeline wait of the forward kernel may take before it gives
+ * up; default 2e9 (about 1 s).  A wait that gives up sets the batch's error
+ * word (HR2_ETIMEDOUT from hr2_stream_check, hr2_evaluate_host or
+ * hr2_noalloc_check), waits again for its own copies to land (as long as the
+ * limit, and at least 1e7 cycles) and stops its warp; the batch's outputs
+ * are then not valid, and the next batch starts from a clean state.  The
+ * limit applies to batches launched after the call.  No counterpart in the
+ * paper.  HR2_EINVAL for cycles < 0. */
+int hr2_set_wait_limit(hr2_ctx* ctx, long long cycles);
+int hr2_get_wait_limit(const hr2_ctx* ctx, long long* cycles);
+
+/* hr2_set_wait_fault: test hook for the path above (no counterpart in the
+ * paper).  While on, the level-gridded forward kernel arms the barrier of each
+ * work item's first pipeline stage for 16 bytes more than its copies deliver:
+ * a flag that nothing sets, so that the stage's wait runs out after the wait
+ * limit every time (its copies still land; the drain then waits at least
+ * ~1e7 cycles for them).  Nothing faults, traps or hangs; the batch reports
+ * HR2_ETIMEDOUT.  Off by default; a context's later batches are unaffected
+ * once it is off again. */
+int hr2_set_wait_fault(hr2_ctx* ctx, int on);
 
 /* hr2_effective_temperature: T_eff of each sample (Sect. 2.6): its F+ (the
  * high-resolution output of forward_model_batch, before the distance

@@ -18,7 +18,8 @@ LIB = os.path.join(HERE, "libhr2.so")
 # (source, object, extra defines): the FP32 forward kernel's instantiations are
 # compiled once per angle-node count, first, since they take longest
 UNITS = [("kern_fwd32_inst.cu", "kern_fwd32_n%d.o" % n, ["-DHR2_FWD32_NMU=%d" % n]) for n in range(1, 9)] + [
-    (src, src.replace(".cu", ".o"), []) for src in ("kern_forward.cu", "kern_nested.cu", "kern_setup.cu", "api.cu")]
+    (src, src.replace(".cu", ".o"), [])
+    for src in ("kern_forward.cu", "kern_nested.cu", "kern_setup.cu", "kern_peaks.cu", "api.cu")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

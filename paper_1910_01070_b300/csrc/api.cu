@@ -59,6 +59,8 @@ struct hr2_ctx {
   size_t budget = 0;
   size_t used = 0;
   hr2_launch_cfg cfg{2, 8};
+  long long wait_limit = kDefaultWaitCycles;   // bounded device-side waits, SM clock cycles
+  bool wait_fault = false;                     // test hook: first stages wait for bytes that never come
   std::mutex mu;
   std::map<void*, size_t> blocks;  // device allocations and their sizes
   std::map<void*, Workspace*> ws;  // per stream
@@ -276,6 +278,25 @@ extern "C" int hr2_set_launch_config(hr2_ctx* ctx, const hr2_launch_cfg* cfg) {
 extern "C" int hr2_get_launch_config(const hr2_ctx* ctx, hr2_launch_cfg* cfg) {
   if (!ctx || !cfg) return fail(HR2_EINVAL, "NULL argument");
   *cfg = ctx->cfg;
+  return HR2_OK;
+}
+
+extern "C" int hr2_set_wait_limit(hr2_ctx* ctx, long long cycles) {
+  if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
+  if (cycles < 0) return fail(HR2_EINVAL, "wait limit %lld < 0", cycles);
+  ctx->wait_limit = cycles;
+  return HR2_OK;
+}
+
+extern "C" int hr2_set_wait_fault(hr2_ctx* ctx, int on) {
+  if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
+  ctx->wait_fault = on != 0;
+  return HR2_OK;
+}
+
+extern "C" int hr2_get_wait_limit(const hr2_ctx* ctx, long long* cycles) {
+  if (!ctx || !cycles) return fail(HR2_EINVAL, "NULL argument");
+  *cycles = ctx->wait_limit;
   return HR2_OK;
 }
 
@@ -607,6 +628,7 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
     h.inv_mu[k] = (float)(1.0 / mu);
     h.mu_nlog2e[k] = (float)(-kLog2e / mu);
     h.wflux[k] = (float)(2.0 * kPi * w * mu);
+    h.lwmu[k] = (float)std::log2(2.0 * kPi * w * mu * mu);
   }
   // nodes beyond n_mu (up to the kernel's compile-time count) are padding:
   // mu = 1 with zero weight, so they add nothing to F+
@@ -617,6 +639,7 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
     h.inv_mu[k] = 1.f;
     h.mu_nlog2e[k] = (float)(-kLog2e);
     h.wflux[k] = 0.f;
+    h.lwmu[k] = -1e4f;
   }
   for (int i = 0; i <= d->fe_order; ++i) h.gll[i] = quad[2 * d->n_mu + i];
   if (d->profile != HR2_PROFILE_MILNE) {
@@ -893,6 +916,8 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
   const LaunchShape ls = shape_for(ctx, sh, n);
   a.warps = ls.warps;
   a.err = (int*)(w->counter + 1);
+  a.wait_limit = ctx->wait_limit;
+  a.tx_extra = ctx->wait_fault ? 16u : 0u;
   cudaError_t e;
   if ((e = launch_prep(a, s)) != cudaSuccess) return fail(HR2_ECUDA, "prep launch: %s", cudaGetErrorString(e));
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -1147,6 +1172,9 @@ std::mutex g_noalloc_mu;
 void* g_noalloc_addr[kNoallocMaxDevices] = {};
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+// the array's layout: plan, then {work counter, error word}, then the batch's
+// permutation, per-sample records and per-level records
+size_t noalloc_counter_offset() { return align256(sizeof(PlanDev)); }
 
 // Device address of the array on the current device (looked up once per device).
 int noalloc_scratch(int device, void** out) {
@@ -1179,7 +1207,7 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
     return fail(HR2_EINVAL, "setup_of_sample, params, out_bins and out_highres are required");
   if (bins_ld < sh.max_bins) return fail(HR2_EINVAL, "bins_ld %d < largest n_bins %d", bins_ld, sh.max_bins);
   if (highres_ld < sh.max_nu) return fail(HR2_EINVAL, "highres_ld %d < largest n_nu %d", highres_ld, sh.max_nu);
-  const size_t off_counter = align256(sizeof(PlanDev));
+  const size_t off_counter = noalloc_counter_offset();
   const size_t off_perm = off_counter + 256;
   const size_t off_samp = off_perm + align256(sizeof(int) * (size_t)n);
   const size_t off_recs = off_samp + align256(sizeof(SampleDev) * (size_t)n);
@@ -1209,6 +1237,8 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
   a.highres_ld = highres_ld;
   const LaunchShape ls = shape_for(ctx, sh, n);
   a.warps = ls.warps;
+  a.wait_limit = ctx->wait_limit;
+  a.tx_extra = ctx->wait_fault ? 16u : 0u;
   cudaError_t e;
   // the planner resets the work counter to zero on the device before the
   // forward kernel reads it; everything else is overwritten by the kernels
@@ -1217,5 +1247,21 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
                         sh.max_k, absorber_bound(sh), ls.stages, s)) != cudaSuccess ||
       (e = launch_bins(a, out_bins, bins_ld, false, s)) != cudaSuccess)
     return fail(HR2_ECUDA, "allocation-free launch: %s", cudaGetErrorString(e));
+  return HR2_OK;
+}
+
+extern "C" int hr2_noalloc_check(hr2_ctx* ctx, void* stream) {
+  if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
+  HR2_CU(cudaSetDevice(ctx->device));
+  HR2_CU(cudaStreamSynchronize((cudaStream_t)stream));
+  char* base = nullptr;
+  int rc = noalloc_scratch(ctx->device, (void**)&base);
+  if (rc) return rc;
+  unsigned int word = 0;
+  // the error word follows the work counter in the array (see the layout in
+  // forward_model_batch_noalloc); a 4-byte copy allocates nothing
+  HR2_CU(cudaMemcpy(&word, base + noalloc_counter_offset() + sizeof(unsigned int), sizeof(word),
+                    cudaMemcpyDeviceToHost));
+  if (word & 1u) return fail(HR2_ETIMEDOUT, "a bounded device-side wait gave up during the last allocation-free batch");
   return HR2_OK;
 }

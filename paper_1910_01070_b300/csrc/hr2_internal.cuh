@@ -12,6 +12,8 @@ namespace hr2 {
 // Wavenumber tile of one work item: 32 lanes x 2 packed pairs of
 // consecutive points (lane l holds columns 2l, 2l+1, 64+2l, 65+2l).
 constexpr int kTileNu = 128;
+// distance in points between a lane's consecutive packed pairs
+constexpr int kPairStride = 64;
 constexpr int kMaxWarps = 16;
 // launch bounds of the FP32 forward kernel: at most 4 warps (samples) per
 // CTA.  The level-gridded linear-source kernels with up to 4 angle nodes are
@@ -106,6 +108,10 @@ struct SetupDev {
   float mu[HR2_MAX_MU];
   float inv_mu[HR2_MAX_MU];
   float wflux[HR2_MAX_MU];       // 2 pi w_k mu_k
+  // log2(2 pi w_k mu_k^2): the node's share of F+ = sum_k 2 pi w_k mu_k^2
+  // (I_0(mu_k) / mu_k), folded into its transmission exponential (-1e4 for a
+  // padded node of zero weight)
+  float lwmu[HR2_MAX_MU];
   double mu64[HR2_MAX_MU], wmu64[HR2_MAX_MU];  // Gauss-Legendre nodes and weights on [0,1]
   int fe_elements, fe_order, n_tnodes;
   double gll[HR2_MAX_TNODES];    // Gauss-Lobatto nodes on [0,1] (fe_order+1 of them)
@@ -170,13 +176,13 @@ struct __align__(16) LevRec {
   float wTwp;        // wT * wp
   float bh2h2;       // head of log2(x_H2^2 c n_j) + off_cia log2(10) - shift
   float bh2he;       // head of log2(x_H2 x_He c n_j) + off_cia log2(10) - shift
-  float upl;         // head of -log2(e) h c / (k T_j): e^{-hc nu/kT} = 2^(upl nu)
+  float upl;         // log2(e) h c / (k T_j): e^{hc nu/kT} = 2^(upl nu)
   float half_dp;     // 2^shift (p_{j+1} - p_j) / 2, dyn cm^-2 (layer j)
   int acell;         // a_j
-  float upl_lo;      // tail of upl
+  float r64;         // e^{64 h c dnu / (k T_j)}: Planck factor between points 64 apart
   float ch2h2;       // 1 + ln2 * (tail of bh2h2)
   float ch2he;       // 1 + ln2 * (tail of bh2he)
-  float rdnu;        // e^{-h c dnu / (k T_j)}: Planck factor between neighbouring points
+  float rnu;         // e^{h c dnu / (k T_j)}: Planck factor between neighbouring points
   float wh2h2;       // 2^(bh2h2 exactly): the H2-H2 factor as a weight
   float wh2he;       // 2^(bh2he exactly)
   float dtau_cloud;  // gray cloud optical depth of layer j-1 (between levels j-1 and j),
@@ -193,14 +199,17 @@ struct __align__(16) LevRecC {
   float wh2he[2];    // H2-He factor as a weight (0 for an absent pair)
   float half_dp[2];  // 2^shift (p_{j+1} - p_j) / 2, dyn cm^-2 (layer j)
   float dtc[2];      // gray cloud optical depth of layer j-1 (+ kTinyTau, linear source)
-  float upl;         // -log2(e) h c / (k T_j): e^{-hc nu/kT} = 2^(upl nu)
-  float rdnu;        // e^{-h c dnu / (k T_j)}
+  float upl;         // log2(e) h c / (k T_j): e^{hc nu/kT} = 2^(upl nu)
+  float rnu;         // e^{h c dnu / (k T_j)}
   int acell;         // a_j
-  int pad[3];
+  int lvl_off;       // floats from a tile's operand to this level's block of T cell a_j
+  float r64;         // e^{64 h c dnu / (k T_j)}
+  int pad;
 };
 static_assert(sizeof(LevRecC) == sizeof(LevRec), "both level records are 64 bytes");
-constexpr int kRecCAcell = 12;   // float index of LevRecC::acell
+constexpr int kRecCAcell = 12;   // float index of LevRecC::acell (lvl_off follows)
 constexpr int kRecCUpl = 10;     // float index of LevRecC::upl
+constexpr int kRecCR64 = 14;     // float index of LevRecC::r64
 
 // Per-sample scalars written by the prep kernel.
 struct SampleDev {
@@ -244,7 +253,11 @@ struct FwdArgs {
   SampleDev* samp;          // [n]
   int warps;                // samples per work item
   int* err;                 // device error word (bit 0: a bounded wait gave up), or null
+  long long wait_limit;     // SM clock cycles a pipeline wait may take before it gives up
+  unsigned tx_extra;        // test hook: bytes each item's first stage waits for in vain (0)
 };
+// default of the context's wait limit: ~1 s of SM clock
+constexpr long long kDefaultWaitCycles = 2000000000ll;
 
 // Launchers (kern_*.cu).
 cudaError_t launch_prep(const FwdArgs& a, cudaStream_t s);

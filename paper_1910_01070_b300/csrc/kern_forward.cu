@@ -213,9 +213,10 @@ __global__ void k_prep(FwdArgs a) {
     const double lT = log2(Tj);
     const double b0 = cb0 + lv.lpk - lT;    // log2(x_H2^2 c n_j) + off log2 10 - shift
     const double b1 = cb1 + lv.lpk - lT;    // log2(x_H2 x_He c n_j) + off log2 10 - shift
-    const double upl = -kC2 * kLog2e / Tj;  // e^{-hc nu/kT} = 2^(upl nu)
+    const double upl = kC2 * kLog2e / Tj;   // e^{hc nu/kT} = 2^(upl nu)
     const float half_dp = (float)ldexp(lv.half_dp64, (int)shift);
-    const float rdnu = exp2f((float)(upl * T.dnu));   // e^{-hc dnu/kT}, |argument| << 1
+    const float rnu = exp2f((float)(upl * T.dnu));           // e^{hc dnu/kT}, argument << 1
+    const float r64 = exp2f((float)(upl * T.dnu * kPairStride));   // e^{64 hc dnu/kT}
     // zero for an absent pair: the cached path adds both pairs unconditionally
     const float wh2h2 = T.has_cia[0] ? exp2_split(b0) : 0.f;
     const float wh2he = T.has_cia[1] ? exp2_split(b1) : 0.f;
@@ -233,9 +234,12 @@ __global__ void k_prep(FwdArgs a) {
       rc.half_dp[0] = rc.half_dp[1] = half_dp;
       rc.dtc[0] = rc.dtc[1] = dtc;
       rc.upl = (float)upl;
-      rc.rdnu = rdnu;
+      rc.rnu = rnu;
       rc.acell = acell;
-      rc.pad[0] = rc.pad[1] = rc.pad[2] = 0;
+      // the level's operand block of T cell acell within a tile
+      rc.lvl_off = (j * (T.n_T - 1) + acell) * (S.n_species + 2) * 2 * kTileNu;
+      rc.r64 = r64;
+      rc.pad = 0;
       reinterpret_cast<LevRecC*>(rec)[j] = rc;
     } else {
       const double wp = lv.wp64;
@@ -250,9 +254,9 @@ __global__ void k_prep(FwdArgs a) {
       r.bh2he = (float)b1;
       r.ch2he = (float)(1.0 + kLn2 * (b1 - (double)r.bh2he));
       r.upl = (float)upl;
-      r.upl_lo = (float)(upl - (double)r.upl);
+      r.r64 = r64;
       r.half_dp = half_dp;
-      r.rdnu = rdnu;
+      r.rnu = rnu;
       r.wh2h2 = wh2h2;
       r.wh2he = wh2he;
       r.dtau_cloud = dtc;

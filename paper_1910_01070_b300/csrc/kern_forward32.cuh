@@ -120,7 +120,7 @@ struct __align__(16) RowDiff {
 // the last 16 bytes of a LevRecC before its cell index
 struct __align__(16) RecTail {
   v2 dtc;
-  float upl, rdnu;
+  float upl, rnu;
 };
 __device__ __forceinline__ RowDiff lds_rd(const float* p) { return *reinterpret_cast<const RowDiff*>(p); }
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -142,14 +142,19 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned 
       : "memory");
   return ok != 0;
 }
-// Bounded wait on a phase: gives up after ~1 s of SM clock and reports it.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// Bounded wait on a phase: gives up after `limit` SM clock cycles (the
+// context's wait limit, ~1 s by default) and reports it.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit) {
   if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity))
-    if (clock64() - t0 > 2000000000ll) return false;
+    if (clock64() - t0 > limit) return false;
   return true;
 }
+// least limit of the wait that lets a stage's copies land after a wait gave
+// up (~5 ms of SM clock, far beyond a copy's latency): the drain waits as long
+// as the context's limit allows, and at least this long
+constexpr long long kDrainMinCycles = 10000000ll;
 // bytes (multiple of 16) from global src to shared dst (both 16-byte aligned),
 // completion counted on bar
 __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
@@ -190,14 +195,16 @@ __device__ __forceinline__ WarpPipe warp_pipe(unsigned char* base, int max_k, in
 // First fill of a stage for an item: the operand block of level 0 (T cell
 // acell, (K + 2) x 2 kTileNu floats) and the records of levels 0 .. n_rec-1
 // into ring slots 0 .. n_rec-1, counted on the stage's barrier.  One lane
-// issues everything.
+// issues everything.  tx_extra (0 except under the context's wait-fault test
+// hook) arms the barrier for bytes that never arrive, so that its bounded
+// wait runs out.
 __device__ __forceinline__ void issue_first(const WarpPipe& w, int st, int K, const float* src_rows, const LevRec* rec,
-                                            int n_rec, int lane) {
+                                            int n_rec, int lane, unsigned tx_extra) {
   if (lane == 0) {
     const unsigned rows_bytes = (unsigned)((K + 2) * 2 * kTileNu * sizeof(float));
     const unsigned rec_bytes = (unsigned)(n_rec * sizeof(LevRec));
     unsigned long long* bar = w.bar + st;
-    mbar_expect_tx(bar, rows_bytes + rec_bytes);
+    mbar_expect_tx(bar, rows_bytes + rec_bytes + tx_extra);
     bulk_copy(w.rows + (size_t)st * (2 * K + 4) * kTileNu, src_rows, rows_bytes, bar);
     bulk_copy(w.recs, rec, rec_bytes, bar);
   }
@@ -254,43 +261,53 @@ struct LevelState {
   v2 chip, Sp, tau, dup, dtp;
 };
 
+// Accumulators of the emergent flux per pair: one for the linear source
+// (every angle node's share folded in), one per node for the parabolic one.
+template <int NMU, bool PARA>
+struct FluxAcc {
+  static constexpr int N = PARA ? NMU : 1;
+};
+
 // Physics of one level for the lane's wavenumbers, given chi_j: the Planck
 // source, and the layer above it added to the telescoped sum.  SX: some
 // level of this sample may have h c nu / k T < 0.0625 on this tile, where
-// 1 - e^{-x} of the Planck function needs its series (decided per item).
+// e^{x} - 1 of the Planck function needs its series (decided per item).
 template <int NMU, bool PARA, bool SX>
-__device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], const float upl, const float rdnu,
-                                              const v2 half_dp, const v2 dtc, v2& hdp_prev,
-                                              const NuConst& nc, const float thin_dtau,
-                                              const v2* sMnl, const v2* sImu, const v2* sMu, v2 (&acc)[kPairs][NMU],
-                                              v2 (&E)[kPairs][NMU], LevelState (&st)[kPairs]) {
+__device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], const float upl, const float rnu,
+                                              const float r64, const v2 half_dp, const v2 dtc, v2& hdp_prev,
+                                              const NuConst& nc, const float thin_dtau, const v2* sMnl,
+                                              const v2* sImu, const v2* sMu, const v2* sLw,
+                                              v2 (&acc)[kPairs][FluxAcc<NMU, PARA>::N], v2 (&E)[kPairs][NMU],
+                                              LevelState (&st)[kPairs]) {
   const float kLn2f = 0.6931471805599453f;
   const v2 one = pk(1.f);
-  // Planck source.  t = e^{-x}, x = hc nu / kT, at a pair's first point is
-  // 2^(upl nu) from the FP32 product (relative error of x ~2e-7: t to
-  // ~2e-7 x, <= 2e-5 where t is above FP32's range floor); the neighbour
-  // point is t * e^{-hc dnu/kT}.  hc nu / kT is smallest at pair 0's first
-  // point, which decides whether the small-x form is needed anywhere in the
-  // warp.
+  // Planck source S = c1 nu^3 / (e^x - 1), x = hc nu / kT.  e^x at pair 0's
+  // first point is 2^(upl nu) from the FP32 product (relative error of x
+  // ~2e-7: e^x to ~2e-7 x); its neighbour is that times e^{hc dnu/kT}, and
+  // each further pair 64 points up the previous one times e^{64 hc dnu/kT}.
+  // Past FP32's range (x > 88) e^x is +inf and S = c1 nu^3 * 0 = 0, where the
+  // true S is below FP32's normal range anyway.  hc nu / kT is smallest at
+  // pair 0's first point, which decides whether the small-x form is needed
+  // anywhere in the warp.
   v2 Sj[kPairs];
   bool small_x = false;
-  if constexpr (SX) small_x = __any_sync(0xffffffffu, -(upl * nc.nu0[0]) * kLn2f < 0.0625f);
+  if constexpr (SX) small_x = __any_sync(0xffffffffu, upl * nc.nu0[0] * kLn2f < 0.0625f);
+  const float z00 = ex2f(upl * nc.nu0[0]);
+  v2 z = pk(z00, z00 * rnu);
+  const v2 r64p = pk(r64);
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
-    const float p0 = upl * nc.nu0[p];
-    const float t0 = ex2f(p0);
-    const v2 t = pk(t0, t0 * rdnu);
-    v2 om = sub2(one, t);
+    if (p > 0) z = mul2(z, r64p);
+    v2 em = sub2(z, one);
     if (SX && small_x) {
-      // 1 - e^{-x} without cancellation for small x
-      const float x0 = -p0 * kLn2f;
+      // e^x - 1 without cancellation for small x: x (1 + x/2 + x^2/6 + x^3/24)
+      const float x0 = upl * nc.nu0[p] * kLn2f;
       const v2 x = pk(x0, x0 * nc.ratio[p]);
-      const v2 ser = mul2(x, fma2(mul2(x, pk(-0.5f)),
-                                  fma2(mul2(x, pk(-1.f / 3.f)), fma2(pk(-0.25f), x, one), one), one));
-      const float2 xf = up(x), sf = up(ser), of = up(om);
-      om = pk(xf.x < 0.0625f ? sf.x : of.x, xf.y < 0.0625f ? sf.y : of.y);
+      const v2 ser = mul2(x, fma2(x, fma2(x, fma2(x, pk(1.f / 24.f), pk(1.f / 6.f)), pk(0.5f)), one));
+      const float2 xf = up(x), sf = up(ser), of = up(em);
+      em = pk(xf.x < 0.0625f ? sf.x : of.x, xf.y < 0.0625f ? sf.y : of.y);
     }
-    Sj[p] = mul2(mul2(nc.c1n[p], t), rcp_2(om));
+    Sj[p] = mul2(nc.c1n[p], rcp_2(em));
   }
   if constexpr (!PARA) {
     // Linear source, layer j-1 between levels j-1 (top, S_{j-1}) and j
@@ -300,12 +317,18 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
     // 1 - e^{-D} is the polynomial D (1 - D/2 + D^2/6), chosen per point
     // without a branch.  Level 0 enters the same way as a layer of optical depth
     // kTinyTau below a zero source (nothing above it has been added yet):
-    // it adds S_0 / mu, the S_0 term of I_0 = S_0 + mu sum_l ..., so that
-    // I_0(mu) = mu * acc.  Nodes beyond the setup's count are padded with
-    // mu = 1 and zero weight.
+    // it adds S_0 / mu, the S_0 term of I_0 = S_0 + mu sum_l ...
+    // F+ = sum_k 2 pi w_k mu_k I_0(mu_k) = sum_k (2 pi w_k mu_k^2) sum_l ...:
+    // each node's E carries its factor 2 pi w_k mu_k^2 in the exponent
+    // (E_j = 2^(log2 e (-tau_j / mu_k) + log2(2 pi w_k mu_k^2))), so the nodes'
+    // terms of a layer add up before the one multiplication by the shared
+    // slope, into one accumulator that ends as F+ itself.  Nodes beyond the
+    // setup's count are padded with mu = 1 and a factor 2^-10000 = 0.
     (void)thin_dtau;
-    // st.tau holds -log2(e) tau_j, so that E_j = 2^(st.tau / mu_k)
-    v2 dt[kPairs], rdS[kPairs];
+    (void)sMnl;
+    (void)sMu;
+    // st.tau holds -log2(e) tau_j
+    v2 dt[kPairs], rdS[kPairs], sum[kPairs];
 #pragma unroll
     for (int p = 0; p < kPairs; ++p) {
       // gas trapezoid + gray cloud + kTinyTau
@@ -316,20 +339,23 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
     const v2 c2 = pk(-0.5f), c3 = pk(1.f / 6.f);
 #pragma unroll
     for (int k = 0; k < NMU; ++k) {
-      const v2 im = sImu[k];   // 1 / mu_k
+      const v2 im = sImu[k], lw = sLw[k];   // 1 / mu_k, log2(2 pi w_k mu_k^2)
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
-        const v2 En = ex2_2(mul2(st[p].tau, im));   // e^{-tau_j / mu}
+        const v2 En = ex2_2(fma2(st[p].tau, im, lw));   // 2 pi w mu^2 e^{-tau_j / mu}
         const v2 D = mul2(dt[p], im);
         const v2 X = sub2(E[p][k], En);
         const v2 Xs = mul2(E[p][k], mul2(D, fma2(D, fma2(D, c3, c2), one)));
         const float2 Df = up(D), xf = up(X), xsf = up(Xs);
         const v2 cc = pk(Df.x < kThinLin ? xsf.x : xf.x, Df.y < kThinLin ? xsf.y : xf.y);
-        acc[p][k] = fma2(cc, rdS[p], acc[p][k]);
+        sum[p] = k == 0 ? cc : add2(sum[p], cc);
         E[p][k] = En;
       }
     }
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) acc[p][0] = fma2(sum[p], rdS[p], acc[p][0]);
   } else if (j > 0) {
+    (void)sLw;
     // layer j-1 between levels j-1 (top, Sp) and j (bottom, Sj)
     v2 dt[kPairs], rr[kPairs], dS[kPairs];
     float dmin = 3.0e38f;
@@ -411,8 +437,8 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
 template <int NMU, bool CACHED, int KT, bool LIN, bool PARA, bool SX, int ST>
 __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
                                            const v2* sA2, const v2* sAc2, const void* const* sPtr,
-                                           const v2* sMnl, const v2* sImu, const v2* sMu, const WarpPipe& wp_,
-                                           unsigned& phase_base) {
+                                           const v2* sMnl, const v2* sImu, const v2* sMu, const v2* sLw,
+                                           const WarpPipe& wp_, unsigned& phase_base) {
   const int lane = threadIdx.x & 31;
   const SampleDev& sd = a.samp[i];
   float* out = a.highres + (size_t)i * a.highres_ld;
@@ -453,14 +479,16 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
   const bool cia0 = T.has_cia[0] != 0, cia1 = T.has_cia[1] != 0;
   const LevRec* __restrict__ rec = a.recs + (size_t)i * a.rec_ld;
 
-  v2 acc[kPairs][NMU], E[kPairs][NMU];
+  // linear source: E of each node starts at its flux factor 2 pi w mu^2
+  // (tau = 0); parabolic: at 1, with one accumulator per node
+  v2 acc[kPairs][FluxAcc<NMU, PARA>::N], E[kPairs][NMU];
 #pragma unroll
-  for (int p = 0; p < kPairs; ++p)
+  for (int p = 0; p < kPairs; ++p) {
 #pragma unroll
-    for (int k = 0; k < NMU; ++k) {
-      acc[p][k] = pk(0.f);
-      E[p][k] = pk(1.f);
-    }
+    for (int k = 0; k < FluxAcc<NMU, PARA>::N; ++k) acc[p][k] = pk(0.f);
+#pragma unroll
+    for (int k = 0; k < NMU; ++k) E[p][k] = PARA ? pk(1.f) : ex2_2(sLw[k]);
+  }
   LevelState st[kPairs];
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) st[p].chip = st[p].Sp = st[p].tau = st[p].dup = st[p].dtp = pk(0.f);
@@ -488,15 +516,18 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     // (more warps per SM fit) it goes to the same stage as soon as level j's
     // opacity has read it, and lands while level j's source and layer run.
     if (phase_base == 0xffffffffu) return;       // this warp's pipeline failed earlier
-    const size_t lvl_step = (size_t)(nT - 1) * (K + 2) * 2 * kTileNu;   // one level of the tile
     const size_t cell_step = (size_t)(K + 2) * 2 * kTileNu;             // one T cell of a level
-    const float* lvl_tile = S.lvl32 + (size_t)tile * (L + 1) * lvl_step;
+    const float* lvl_tile = S.lvl32 + (size_t)tile * (L + 1) * (nT - 1) * cell_step;
     const unsigned rows_bytes = (unsigned)(cell_step * sizeof(float));
+    const unsigned cia_bytes = (unsigned)(4 * kTileNu * sizeof(float));
     const unsigned ph = phase_base;
-    const int acell0 = __ldg(&reinterpret_cast<const LevRecC*>(rec)[0].acell);
+    // T cell of the level whose block the stage holds (its CIA rows stay valid
+    // for a later level of the same cell); the stage's first fill copies them
+    int acell_held = __ldg(&reinterpret_cast<const LevRecC*>(rec)[0].acell);
     constexpr int kSt = ST;
-    issue_first(wp_, kSt == 1 ? 0 : (int)(ph & 1u), K, lvl_tile + (size_t)acell0 * cell_step, rec,
-                min(kRecRing, L + 1), lane);
+    issue_first(wp_, kSt == 1 ? 0 : (int)(ph & 1u), K, lvl_tile + (size_t)acell_held * cell_step, rec,
+                min(kRecRing, L + 1), lane, a.tx_extra);
+    int acell_prev = -1;   // two stages: T cell of the block in the other stage
     // unrolled so that the loop-carried sweep state rotates through register
     // sets instead of being moved back at the end of each level
 #pragma unroll 4
@@ -506,42 +537,48 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       // one stage: every level in stage 0, phase g & 1
       const int stg = kSt == 1 ? 0 : (int)(g & 1u);
       const unsigned par = kSt == 1 ? (g & 1u) : ((g >> 1) & 1u);
-      if (!mbar_wait(wp_.bar + stg, par)) {
+      if (!mbar_wait(wp_.bar + stg, par, a.wait_limit)) {
         // the stage never completed: report, drain it (bounded) and stop using
         // this warp's pipeline
         if (lane == 0 && a.err) atomicOr(a.err, 1);
-        mbar_wait(wp_.bar + stg, par);
+        mbar_wait(wp_.bar + stg, par, max(a.wait_limit, kDrainMinCycles));
         phase_base = 0xffffffffu;
         return;
       }
       __syncwarp();
-      // refill a stage with level j+1 (T cell from record j+1) and, every
-      // fourth level, records j+4 .. j+7: the other stage right away (two
-      // stages), or this stage once this level's opacity has read it (one)
+      // refill a stage with level j+1 and, every fourth level, records
+      // j+4 .. j+7: the other stage right away (two stages), or this stage once
+      // this level's opacity has read it (one).  Record j+1 gives the block's T
+      // cell and its offset in the tile's operand; where the stage already
+      // holds that cell's CIA rows (one stage: level j's cell; two: level
+      // j-1's, none before this item's first refill) only the absorber rows
+      // are copied.
       auto refill = [&]() {
         const bool more = j < L;
-        const int acell_n = more ? __float_as_int(wp_.recs[((j + 1) & (kRecRing - 1)) * 16 + kRecCAcell]) : 0;
+        const int2 nx = more ? *reinterpret_cast<const int2*>(wp_.recs + ((j + 1) & (kRecRing - 1)) * 16 + kRecCAcell)
+                             : make_int2(0, 0);
         const int sn = kSt == 1 ? 0 : (int)((g + 1u) & 1u);
         const bool do_rec = (j & 3) == 0 && j >= 4 && j + 4 <= L;
         const unsigned rec_bytes = (unsigned)(min(4, max(0, L - j - 3)) * (int)sizeof(LevRec));
-        // the stage keeps the CIA rows of the T cell it holds (one stage: level
-        // j's; two: level j-1's, none before this item's first refill): where
-        // level j+1 has the same cell only its absorber rows are copied
-        const int held = kSt == 1 ? __float_as_int(wp_.recs[(j & (kRecRing - 1)) * 16 + kRecCAcell])
-                                  : (j >= 1 ? __float_as_int(wp_.recs[((j - 1) & (kRecRing - 1)) * 16 + kRecCAcell])
-                                            : -1);
-        const unsigned rb = held == acell_n ? rows_bytes - (unsigned)(4 * kTileNu * sizeof(float)) : rows_bytes;
+        const int held = kSt == 1 ? acell_held : acell_prev;
+        const unsigned rb = held == nx.x ? rows_bytes - cia_bytes : rows_bytes;
         issue_level_pred(wp_.bar + sn, rb + (do_rec ? rec_bytes : 0u), more && lane == 0,
-                         wp_.rows + (size_t)sn * (2 * K + 4) * kTileNu,
-                         lvl_tile + (size_t)(j + 1) * lvl_step + (size_t)acell_n * cell_step, rb,
+                         wp_.rows + (size_t)sn * (2 * K + 4) * kTileNu, lvl_tile + nx.y, rb,
                          wp_.recs + (size_t)((j + 4) & (kRecRing - 1)) * 16, rec + (j + 4), rec_bytes, do_rec);
+        if (kSt == 1) {
+          acell_held = nx.x;
+        } else {
+          acell_prev = acell_held;
+          acell_held = nx.x;
+        }
       };
       if constexpr (kSt == 2) refill();
       // record j (LevRecC): {wT, wT, wh2h2, wh2h2}, {wh2he, wh2he, half_dp,
-      // half_dp}, {dtc, dtc, upl, rdnu}
+      // half_dp}, {dtc, dtc, upl, rnu}, {acell, lvl_off, r64, -}
       const float* rj = wp_.recs + (j & (kRecRing - 1)) * 16;
       const RowDiff rq0 = lds_rd(rj), rq1 = lds_rd(rj + 4);
       const RecTail rq2 = *reinterpret_cast<const RecTail*>(rj + 8);
+      const float r64 = rj[kRecCR64];
       const v2 wT = rq0.g;
       // stage: [s][q][row, T difference] for pairs q of columns; lane l's
       // pair p is q = l + 32 p
@@ -551,9 +588,9 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chA[p] = chB[p] = pk(0.f);
       if constexpr (KT > 0) {
-        // every setup of the batch has KT - 4 <= K <= KT absorbers; a padded
-        // absorber has weight 0 and reads finite values of the stage
-        // (the CIA rows that follow, or the other stage, both initialised)
+        // the item's setup has at most KT absorbers; a padded absorber has
+        // weight 0 and reads finite values of the stage (the CIA rows that
+        // follow, or the other stage, both initialised)
 #pragma unroll
         for (int s = 0; s < KT; s += 2) {
           const v2 w0 = sW2[s], w1 = sW2[s + 1];
@@ -606,9 +643,11 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
         __syncwarp();   // every lane has read the stage
         refill();
       }
-      level_physics<NMU, PARA, SX>(j, chi, rq2.upl, rq2.rdnu, rq1.dg, rq2.dtc, hdp_prev, nc, thin_dtau, sMnl, sImu,
-                               sMu, acc, E, st);
-      __syncwarp();  // every lane is done with stage stg and record j before they are refilled
+      level_physics<NMU, PARA, SX>(j, chi, rq2.upl, rq2.rnu, r64, rq1.dg, rq2.dtc, hdp_prev, nc, thin_dtau, sMnl,
+                                   sImu, sMu, sLw, acc, E, st);
+      // two stages: every lane is done with stage stg before the next level
+      // refills it (one stage: the refill already followed the sync above)
+      if constexpr (kSt == 2) __syncwarp();
     }
     phase_base = ph + (unsigned)(L + 1);
   } else {
@@ -675,28 +714,30 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       v2 chi[kPairs];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
-      level_physics<NMU, PARA, SX>(j, chi, r1.z, r3.x, pk(r1.w), pk(r3.w), hdp_prev, nc, thin_dtau, sMnl, sImu,
-                               sMu, acc, E, st);
+      level_physics<NMU, PARA, SX>(j, chi, r1.z, r3.x, r2.y, pk(r1.w), pk(r3.w), hdp_prev, nc, thin_dtau, sMnl,
+                                   sImu, sMu, sLw, acc, E, st);
     }
   }
-  // I_0(mu_k) = mu_k acc_k (telescoped linear source, S_0 included) or
-  // acc_k + E_L S_L (parabolic source);  F+ = sum_k 2 pi w_k mu_k I_0(mu_k)
+  // Linear source: the accumulator is F+ (the nodes' flux factors folded
+  // in).  Parabolic source: I_0(mu_k) = acc_k + E_L S_L and
+  // F+ = sum_k 2 pi w_k mu_k I_0(mu_k).
 #pragma unroll
   for (int p = 0; p < kPairs; ++p) {
     float F0 = 0.f, F1 = 0.f;
-    const float2 sL = up(st[p].Sp);
+    if constexpr (PARA) {
+      const float2 sL = up(st[p].Sp);
 #pragma unroll
-    for (int k = 0; k < NMU; ++k) {
-      const float2 f = up(acc[p][k]);
-      const float mk = S.mu[k], wk = S.wflux[k];
-      if constexpr (PARA) {
+      for (int k = 0; k < NMU; ++k) {
+        const float2 f = up(acc[p][k]);
+        const float wk = S.wflux[k];
         const float2 e = up(E[p][k]);
         F0 = fmaf(wk, fmaf(e.x, sL.x, f.x), F0);
         F1 = fmaf(wk, fmaf(e.y, sL.y, f.y), F1);
-      } else {
-        F0 = fmaf(wk, mk * f.x, F0);
-        F1 = fmaf(wk, mk * f.y, F1);
       }
+    } else {
+      const float2 f = up(acc[p][0]);
+      F0 = f.x;
+      F1 = f.y;
     }
     if (in0[p]) out[kout[p]] = F0;
     if (in1[p]) out[kout[p] + 1] = F1;
@@ -715,7 +756,7 @@ __device__ __forceinline__ bool item_small_x(const FwdArgs& a, const SetupDev& S
   bool f = false;
   const float* r = reinterpret_cast<const float*>(rec);
   const int o = S.cached ? kRecCUpl : (int)(offsetof(LevRec, upl) / sizeof(float));
-  for (int j = lane; j < S.n_lev; j += 32) f |= -(__ldg(r + 16 * j + o) * nu_min) * 0.6931471805599453f < 0.0625f;
+  for (int j = lane; j < S.n_lev; j += 32) f |= (__ldg(r + 16 * j + o) * nu_min) * 0.6931471805599453f < 0.0625f;
   return __any_sync(0xffffffffu, f);
 }
 
@@ -726,7 +767,7 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
   extern __shared__ __align__(16) unsigned char dyn_smem[];   // cached path: per-warp pipelines
   __shared__ int s_item;
   __shared__ const void* sPtr[HR2_MAX_SPECIES];
-  __shared__ v2 sMnl[NMU], sImu[NMU], sMu[NMU];
+  __shared__ v2 sMnl[NMU], sImu[NMU], sMu[NMU], sLw[NMU];
   __shared__ v2 sA2[kMaxWarps][HR2_MAX_SPECIES];
   __shared__ v2 sAc2[kMaxWarps][HR2_MAX_SPECIES];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -772,6 +813,7 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
       sMnl[threadIdx.x] = pk(S.mu_nlog2e[threadIdx.x]);
       sImu[threadIdx.x] = pk(S.inv_mu[threadIdx.x]);
       sMu[threadIdx.x] = pk(S.mu[threadIdx.x]);
+      sLw[threadIdx.x] = pk(S.lwmu[threadIdx.x]);
     }
     const int local = sb * a.warps + warp;
     const bool active = local < plan->count[g];
@@ -793,9 +835,9 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
       // source; the parabolic one keeps the batch's bound)
 #define HR2_SOLVE(KB)                                                                                              \
   (sx ? solve_tile<NMU, CACHED, KB, LIN, PARA, true, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, \
-                                                          sMu, wp_, phase_base)                                    \
+                                                          sMu, sLw, wp_, phase_base)                               \
       : solve_tile<NMU, CACHED, KB, LIN, PARA, false, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl,     \
-                                                           sImu, sMu, wp_, phase_base))
+                                                           sImu, sMu, sLw, wp_, phase_base))
       if constexpr (KT >= 8 && !PARA) {
         const int kc = (S.n_species + 1) & ~1;
         if (kc <= KT - 4)

@@ -39,6 +39,8 @@ EXPORTED = [
     "hr2_evaluate_host", "hr2_profile_enable",
     "hr2_profile_read", "hr2_stream_check", "hr2_nodes_from_b", "hr2_version",
     "hr2_ns_state_init", "hr2_ns_absorb", "hr2_ns_propose", "hr2_ns_finalize", "hr2_effective_temperature",
+    "hr2_measure_unit_rate", "hr2_noalloc_check", "hr2_set_wait_limit", "hr2_get_wait_limit",
+    "hr2_set_wait_fault",
 ]
 
 
@@ -62,6 +64,14 @@ class SetupDesc(C.Structure):
                 ("obs_sigma", C.POINTER(C.c_double)), ("r_he", C.c_double), ("radius_cm", C.c_double),
                 ("level_cache", C.c_int), ("interp", C.c_int), ("profile", C.c_int), ("cloud", C.c_int),
                 ("sc", C.c_int)]
+
+
+class UnitRate(C.Structure):
+    _fields_ = [("ms", C.c_double), ("ops", C.c_double), ("ops_per_s", C.c_double), ("sm_ghz", C.c_double),
+                ("ops_per_clk_sm", C.c_double), ("n_sm", C.c_int)]
+
+
+HR2_UNIT_EX2_RCP, HR2_UNIT_RCP, HR2_UNIT_EX2, HR2_UNIT_FFMA, HR2_UNIT_FFMA2, HR2_UNIT_KINDS = 0, 1, 2, 3, 4, 5
 
 
 class LaunchCfg(C.Structure):
@@ -125,6 +135,11 @@ def lib():
                 "hr2_ns_propose": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, C.c_double, C.c_int, _VP, _VP,
                                              C.c_ulonglong, C.c_ulonglong, _VP]),
                 "hr2_ns_finalize": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, _VP]),
+                "hr2_measure_unit_rate": (C.c_int, [C.c_int, C.c_int, C.c_longlong, C.POINTER(UnitRate)]),
+                "hr2_noalloc_check": (C.c_int, [_VP, _VP]),
+                "hr2_set_wait_limit": (C.c_int, [_VP, C.c_longlong]),
+                "hr2_get_wait_limit": (C.c_int, [_VP, C.POINTER(C.c_longlong)]),
+                "hr2_set_wait_fault": (C.c_int, [_VP, C.c_int]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -450,6 +465,24 @@ def ns_state_read(state) -> dict:
     return {name: getattr(st, name) for name, _ in NsState._fields_ if name != "reserved"}
 
 
+def hr2_noalloc_check(ctx, stream=None):
+    _check(lib().hr2_noalloc_check(ctx, _stream_ptr(stream)), ctx)
+
+
+def hr2_set_wait_limit(ctx, cycles: int):
+    _check(lib().hr2_set_wait_limit(ctx, int(cycles)), ctx)
+
+
+def hr2_set_wait_fault(ctx, on: bool):
+    _check(lib().hr2_set_wait_fault(ctx, 1 if on else 0), ctx)
+
+
+def hr2_get_wait_limit(ctx) -> int:
+    v = C.c_longlong()
+    _check(lib().hr2_get_wait_limit(ctx, C.byref(v)), ctx)
+    return v.value
+
+
 def hr2_stream_check(ctx, stream=None):
     """Synchronise the stream; raises Hr2Error(HR2_ETIMEDOUT) if a bounded device wait gave up."""
     _check(lib().hr2_stream_check(ctx, _stream_ptr(stream)), ctx)
@@ -460,3 +493,13 @@ def hr2_nodes_from_b(T1: float, b) -> np.ndarray:
     out = np.zeros(len(b) + 1)
     _check(lib().hr2_nodes_from_b(len(out), float(T1), pb, out.ctypes.data_as(_DP)))
     return out
+
+
+def hr2_measure_unit_rate(device: int, kind: int, iters: int) -> dict:
+    """Microbenchmark of one arithmetic unit (HR2_UNIT_*): time, operations, rate and the SM clock."""
+    r = UnitRate()
+    rc = lib().hr2_measure_unit_rate(device, kind, iters, C.byref(r))
+    if rc != HR2_OK:
+        raise Hr2Error(rc, "hr2_measure_unit_rate(kind=%d) failed" % kind)
+    return {"ms": r.ms, "ops": r.ops, "ops_per_s": r.ops_per_s, "sm_ghz": r.sm_ghz,
+            "ops_per_clk_sm": r.ops_per_clk_sm, "n_sm": r.n_sm}

@@ -86,7 +86,8 @@ def _struct_fields(src, name):
 
 
 @pytest.mark.parametrize("cname,pyname", [("hr2_setup_desc", "SetupDesc"), ("hr2_table_desc", "TableDesc"),
-                                          ("hr2_launch_cfg", "LaunchCfg"), ("hr2_ns_state", "NsState")])
+                                          ("hr2_launch_cfg", "LaunchCfg"), ("hr2_ns_state", "NsState"),
+                                          ("hr2_unit_rate", "UnitRate")])
 def test_binding_structs_follow_the_header(cname, pyname):
     """The ctypes mirrors list the header's fields in the header's order."""
     assert [f[0] for f in getattr(hr2, pyname)._fields_] == _struct_fields(_header(), cname)
