@@ -4,6 +4,7 @@
 // of kern_forward.cu.
 #include <stdarg.h>
 #include <stdio.h>
+#include <string.h>
 
 #include <algorithm>
 #include <cmath>
@@ -869,6 +870,20 @@ static int absorber_bound(const BatchShape& sh) {
   return (kt - sh.min_k <= 4 && kt <= HR2_MAX_SPECIES) ? kt : 0;
 }
 
+// The angle-node constants of each setup as packed pairs of equal floats.
+static void fill_node_constants(FwdArgs& a, int n_setups, const hr2_setup* const* setups) {
+  auto pair = [](float f) {
+    unsigned u;
+    memcpy(&u, &f, sizeof(u));
+    return ((unsigned long long)u << 32) | u;
+  };
+  for (int g = 0; g < n_setups; ++g)
+    for (int k = 0; k < HR2_MAX_MU; ++k) {
+      a.node_im[g][k] = pair(setups[g]->host.inv_mu[k]);
+      a.node_lw[g][k] = pair(setups[g]->host.lwmu[k]);
+    }
+}
+
 static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {
   int w = std::min(std::min(ctx->cfg.warps_per_cta, kForwardMaxThreads / 32), std::max(1, n));
   const int st = forward32_stages(sh.max_mu, sh.para != 0, absorber_bound(sh), n);
@@ -918,6 +933,7 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
   a.err = (int*)(w->counter + 1);
   a.wait_limit = ctx->wait_limit;
   a.tx_extra = ctx->wait_fault ? 16u : 0u;
+  fill_node_constants(a, n_setups, setups);
   cudaError_t e;
   if ((e = launch_prep(a, s)) != cudaSuccess) return fail(HR2_ECUDA, "prep launch: %s", cudaGetErrorString(e));
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -1239,6 +1255,7 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
   a.warps = ls.warps;
   a.wait_limit = ctx->wait_limit;
   a.tx_extra = ctx->wait_fault ? 16u : 0u;
+  fill_node_constants(a, n_setups, setups);
   cudaError_t e;
   // the planner resets the work counter to zero on the device before the
   // forward kernel reads it; everything else is overwritten by the kernels

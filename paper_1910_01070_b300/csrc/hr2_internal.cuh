@@ -209,7 +209,6 @@ struct __align__(16) LevRecC {
 static_assert(sizeof(LevRecC) == sizeof(LevRec), "both level records are 64 bytes");
 constexpr int kRecCAcell = 12;   // float index of LevRecC::acell (lvl_off follows)
 constexpr int kRecCUpl = 10;     // float index of LevRecC::upl
-constexpr int kRecCR64 = 14;     // float index of LevRecC::r64
 
 // Per-sample scalars written by the prep kernel.
 struct SampleDev {
@@ -255,6 +254,12 @@ struct FwdArgs {
   int* err;                 // device error word (bit 0: a bounded wait gave up), or null
   long long wait_limit;     // SM clock cycles a pipeline wait may take before it gives up
   unsigned tx_extra;        // test hook: bytes each item's first stage waits for in vain (0)
+  // angle-node constants of the linear-source sweep per setup g and node k,
+  // each as a pair of equal floats (one packed operand): 1/mu_k and
+  // log2(2 pi w_k mu_k^2); kernel parameters, so that the sweep reads them
+  // through the constant cache instead of shared memory
+  unsigned long long node_im[HR2_MAX_SETUPS][HR2_MAX_MU];
+  unsigned long long node_lw[HR2_MAX_SETUPS][HR2_MAX_MU];
 };
 // default of the context's wait limit: ~1 s of SM clock
 constexpr long long kDefaultWaitCycles = 2000000000ll;

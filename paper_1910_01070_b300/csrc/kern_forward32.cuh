@@ -276,7 +276,7 @@ template <int NMU, bool PARA, bool SX>
 __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], const float upl, const float rnu,
                                               const float r64, const v2 half_dp, const v2 dtc, v2& hdp_prev,
                                               const NuConst& nc, const float thin_dtau, const v2* sMnl,
-                                              const v2* sImu, const v2* sMu, const v2* sLw,
+                                              const v2* sImu, const v2* sMu, const FwdArgs& a, int gs,
                                               v2 (&acc)[kPairs][FluxAcc<NMU, PARA>::N], v2 (&E)[kPairs][NMU],
                                               LevelState (&st)[kPairs]) {
   const float kLn2f = 0.6931471805599453f;
@@ -326,6 +326,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
     // setup's count are padded with mu = 1 and a factor 2^-10000 = 0.
     (void)thin_dtau;
     (void)sMnl;
+    (void)sImu;
     (void)sMu;
     // st.tau holds -log2(e) tau_j
     v2 dt[kPairs], rdS[kPairs], sum[kPairs];
@@ -339,7 +340,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
     const v2 c2 = pk(-0.5f), c3 = pk(1.f / 6.f);
 #pragma unroll
     for (int k = 0; k < NMU; ++k) {
-      const v2 im = sImu[k], lw = sLw[k];   // 1 / mu_k, log2(2 pi w_k mu_k^2)
+      const v2 im = a.node_im[gs][k], lw = a.node_lw[gs][k];   // 1 / mu_k, log2(2 pi w_k mu_k^2)
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
         const v2 En = ex2_2(fma2(st[p].tau, im, lw));   // 2 pi w mu^2 e^{-tau_j / mu}
@@ -355,7 +356,8 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
 #pragma unroll
     for (int p = 0; p < kPairs; ++p) acc[p][0] = fma2(sum[p], rdS[p], acc[p][0]);
   } else if (j > 0) {
-    (void)sLw;
+    (void)a;
+    (void)gs;
     // layer j-1 between levels j-1 (top, Sp) and j (bottom, Sj)
     v2 dt[kPairs], rr[kPairs], dS[kPairs];
     float dmin = 3.0e38f;
@@ -437,7 +439,7 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
 template <int NMU, bool CACHED, int KT, bool LIN, bool PARA, bool SX, int ST>
 __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
                                            const v2* sA2, const v2* sAc2, const void* const* sPtr,
-                                           const v2* sMnl, const v2* sImu, const v2* sMu, const v2* sLw,
+                                           const v2* sMnl, const v2* sImu, const v2* sMu, int gs,
                                            const WarpPipe& wp_, unsigned& phase_base) {
   const int lane = threadIdx.x & 31;
   const SampleDev& sd = a.samp[i];
@@ -487,7 +489,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
 #pragma unroll
     for (int k = 0; k < FluxAcc<NMU, PARA>::N; ++k) acc[p][k] = pk(0.f);
 #pragma unroll
-    for (int k = 0; k < NMU; ++k) E[p][k] = PARA ? pk(1.f) : ex2_2(sLw[k]);
+    for (int k = 0; k < NMU; ++k) E[p][k] = PARA ? pk(1.f) : ex2_2(a.node_lw[gs][k]);
   }
   LevelState st[kPairs];
 #pragma unroll
@@ -502,7 +504,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       for (int q = 0; q < KT; ++q) wreg[q] = sA2[q];
     }
     const v2* sW2 = (KT > 0) ? wreg : sA2;
-    // Pipeline over the levels (g = phase_base + j counts this warp's levels
+    // Pipeline over the levels (gph = phase_base + j counts this warp's levels
     // across items).  Record of level j sits in ring slot j & 7.
     //   before the loop: stage of level 0 <- block(0), records 0 .. 7
     //   level j:         wait stage(j)    -> block(j) present
@@ -524,6 +526,10 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     // T cell of the level whose block the stage holds (its CIA rows stay valid
     // for a later level of the same cell); the stage's first fill copies them
     int acell_held = __ldg(&reinterpret_cast<const LevRecC*>(rec)[0].acell);
+    // Planck ratio of the current level; each level reads the last quarter of
+    // the next record ({T cell, block offset, its ratio}) for the refill and
+    // carries the ratio on
+    float r64_cur = __ldg(&reinterpret_cast<const LevRecC*>(rec)[0].r64);
     constexpr int kSt = ST;
     issue_first(wp_, kSt == 1 ? 0 : (int)(ph & 1u), K, lvl_tile + (size_t)acell_held * cell_step, rec,
                 min(kRecRing, L + 1), lane, a.tx_extra);
@@ -532,11 +538,11 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     // sets instead of being moved back at the end of each level
 #pragma unroll 4
     for (int j = 0; j <= L; ++j) {
-      const unsigned g = ph + (unsigned)j;
-      // two stages: level g in stage g & 1, phase (g >> 1) & 1 of its barrier;
-      // one stage: every level in stage 0, phase g & 1
-      const int stg = kSt == 1 ? 0 : (int)(g & 1u);
-      const unsigned par = kSt == 1 ? (g & 1u) : ((g >> 1) & 1u);
+      const unsigned gph = ph + (unsigned)j;
+      // two stages: level gph in stage gph & 1, phase (gph >> 1) & 1 of its
+      // barrier; one stage: every level in stage 0, phase gph & 1
+      const int stg = kSt == 1 ? 0 : (int)(gph & 1u);
+      const unsigned par = kSt == 1 ? (gph & 1u) : ((gph >> 1) & 1u);
       if (!mbar_wait(wp_.bar + stg, par, a.wait_limit)) {
         // the stage never completed: report, drain it (bounded) and stop using
         // this warp's pipeline
@@ -553,11 +559,11 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       // holds that cell's CIA rows (one stage: level j's cell; two: level
       // j-1's, none before this item's first refill) only the absorber rows
       // are copied.
+      const int4 q3n = *reinterpret_cast<const int4*>(wp_.recs + ((j + 1) & (kRecRing - 1)) * 16 + kRecCAcell);
       auto refill = [&]() {
         const bool more = j < L;
-        const int2 nx = more ? *reinterpret_cast<const int2*>(wp_.recs + ((j + 1) & (kRecRing - 1)) * 16 + kRecCAcell)
-                             : make_int2(0, 0);
-        const int sn = kSt == 1 ? 0 : (int)((g + 1u) & 1u);
+        const int2 nx = more ? make_int2(q3n.x, q3n.y) : make_int2(0, 0);
+        const int sn = kSt == 1 ? 0 : (int)((gph + 1u) & 1u);
         const bool do_rec = (j & 3) == 0 && j >= 4 && j + 4 <= L;
         const unsigned rec_bytes = (unsigned)(min(4, max(0, L - j - 3)) * (int)sizeof(LevRec));
         const int held = kSt == 1 ? acell_held : acell_prev;
@@ -578,7 +584,8 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       const float* rj = wp_.recs + (j & (kRecRing - 1)) * 16;
       const RowDiff rq0 = lds_rd(rj), rq1 = lds_rd(rj + 4);
       const RecTail rq2 = *reinterpret_cast<const RecTail*>(rj + 8);
-      const float r64 = rj[kRecCR64];
+      const float r64 = r64_cur;
+      r64_cur = __int_as_float(q3n.z);
       const v2 wT = rq0.g;
       // stage: [s][q][row, T difference] for pairs q of columns; lane l's
       // pair p is q = l + 32 p
@@ -644,7 +651,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
         refill();
       }
       level_physics<NMU, PARA, SX>(j, chi, rq2.upl, rq2.rnu, r64, rq1.dg, rq2.dtc, hdp_prev, nc, thin_dtau, sMnl,
-                                   sImu, sMu, sLw, acc, E, st);
+                                   sImu, sMu, a, gs, acc, E, st);
       // two stages: every lane is done with stage stg before the next level
       // refills it (one stage: the refill already followed the sync above)
       if constexpr (kSt == 2) __syncwarp();
@@ -715,7 +722,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
       level_physics<NMU, PARA, SX>(j, chi, r1.z, r3.x, r2.y, pk(r1.w), pk(r3.w), hdp_prev, nc, thin_dtau, sMnl,
-                                   sImu, sMu, sLw, acc, E, st);
+                                   sImu, sMu, a, gs, acc, E, st);
     }
   }
   // Linear source: the accumulator is F+ (the nodes' flux factors folded
@@ -767,7 +774,7 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
   extern __shared__ __align__(16) unsigned char dyn_smem[];   // cached path: per-warp pipelines
   __shared__ int s_item;
   __shared__ const void* sPtr[HR2_MAX_SPECIES];
-  __shared__ v2 sMnl[NMU], sImu[NMU], sMu[NMU], sLw[NMU];
+  __shared__ v2 sMnl[NMU], sImu[NMU], sMu[NMU];
   __shared__ v2 sA2[kMaxWarps][HR2_MAX_SPECIES];
   __shared__ v2 sAc2[kMaxWarps][HR2_MAX_SPECIES];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -813,7 +820,6 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
       sMnl[threadIdx.x] = pk(S.mu_nlog2e[threadIdx.x]);
       sImu[threadIdx.x] = pk(S.inv_mu[threadIdx.x]);
       sMu[threadIdx.x] = pk(S.mu[threadIdx.x]);
-      sLw[threadIdx.x] = pk(S.lwmu[threadIdx.x]);
     }
     const int local = sb * a.warps + warp;
     const bool active = local < plan->count[g];
@@ -835,9 +841,9 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
       // source; the parabolic one keeps the batch's bound)
 #define HR2_SOLVE(KB)                                                                                              \
   (sx ? solve_tile<NMU, CACHED, KB, LIN, PARA, true, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, \
-                                                          sMu, sLw, wp_, phase_base)                               \
+                                                          sMu, g, wp_, phase_base)                               \
       : solve_tile<NMU, CACHED, KB, LIN, PARA, false, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl,     \
-                                                           sImu, sMu, sLw, wp_, phase_base))
+                                                           sImu, sMu, g, wp_, phase_base))
       if constexpr (KT >= 8 && !PARA) {
         const int kc = (S.n_species + 1) & ~1;
         if (kc <= KT - 4)
