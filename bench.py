@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--sweep-nu", type=int, default=290001, help="wavenumber points of the swept tables")
     p.add_argument("--sweep-modes", default="direct,cached")
     p.add_argument("--sweep-batches", default="1,2,4,8,16,32,64,128,256")
+    p.add_argument("--no-large", action="store_true",
+                   help="skip the 290001-point, 12-absorber table measurements (batch 1 and 256)")
     p.add_argument("--peaks", action="store_true",
                    help="instead of the main line: microbenchmarks of the special-function unit (ex2, rcp) and "
                         "the FMA pipe, with the SM clock sampled during each")
@@ -510,6 +512,8 @@ def run_extras(args, local, flush):
             res.append(st)
         out["serving"] = {"streams": 16, "request_sizes": "32-512", "capacity_models_per_s": cap,
                           "latency": "arrival to lnL on the host", "loads": res}
+    if not args.no_large:
+        out["large_tables"] = large_table_sweep(local)
     out["linear_sigma_option"] = run_linear_option(args, local, flush)
     out["parabolic_source_option"] = run_linear_option(args, local, flush, sc="parabolic")
     out["nested_sampling"] = run_nested(args, local)
@@ -605,10 +609,28 @@ def run_linear_option(args, local, flush, **option):
                 "unit": "models/s", "ms_per_step": float(np.mean(times)), "kernel_ms": kms / max(nl, 1)}
 
 
-def run_sweep_large(args, local):
-    """Batch sweep on the 290001-point, 12-absorber FP16 tables (2.09 GB), direct FP16
-    interpolation and the level-gridded operand: kernel ms, models/s and the table bytes a
-    model's rows span, to show where HBM binds (small batches) and where the ALU does."""
+PROFILE_TRAFFIC_LARGE = os.path.join(ROOT, "profiles", "traffic_large.json")
+
+
+def large_counters() -> Optional[dict]:
+    """DRAM bytes per launch of the forward kernel on the 290001-point tables (from a
+    capture on a slice of the wavenumbers, scaled by the tile count), per mode and batch,
+    if they belong to the current kernel source."""
+    if not os.path.exists(PROFILE_TRAFFIC_LARGE):
+        return None
+    with open(PROFILE_TRAFFIC_LARGE) as f:
+        tr = json.load(f)
+    if tr.get("kernel_source_hash") != _kernel_hash():
+        return None
+    return tr
+
+
+def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1, 256), print_lines=False,
+                      target_s=0.3):
+    """Batch sweep on the 290001-point, 12-absorber FP16 tables (2.09 GB): the direct FP16
+    interpolation and the level-gridded operand, event-timed kernel per (mode, batch) with the
+    SM clock sampled during each, to show where HBM binds (small batches) and where the ALU
+    does.  Each point repeats its launch for about target_s seconds (at least 3 times)."""
     import torch
 
     from paper_1910_01070_b300 import hr2
@@ -618,19 +640,20 @@ def run_sweep_large(args, local):
 
     build()
     dev = torch.device("cuda", local)
-    wl = W.large_l100_k12_nu290001_b256(args.sweep_nu)
+    wl = W.large_l100_k12_nu290001_b256(n_nu)
     s = wl.setups[0]
     res = []
-    modes = [m for m in args.sweep_modes.split(",") if m]
-    batches = [int(b) for b in args.sweep_batches.split(",") if b]
+    hbm_peak, hbm_src = _hbm_peak()
+    counters = large_counters() if n_nu == 290001 else None
     with Engine(local) as eng:
         t = eng.add_tables(wl.table, "fp16")
         setups = {m: eng.add_setup(t, s, level_cache=(m == "cached")) for m in modes}
-        th_all, _ = wl.params(256)
-        # algorithmic bytes one model reads: the FP16 corners (4 per level and point, the
-        # K absorbers plus the two CIA pairs' 2 corners each) on the direct path; on the
-        # level-gridded path the operand blocks, (K + 2) rows of value and T difference
-        # (8 B per point) per level over the setup's 128-point tiles
+        th_all, _ = wl.params(max(batches))
+        # algorithmic bytes one model reads: on the direct path the FP16 corners (4 per level
+        # and point for each of the K absorbers, 2 for each of the two CIA pairs), the
+        # per-model count of the scope table; on the level-gridded path the operand blocks,
+        # (K + 2) rows of value and T difference (8 B per point) per level over the setup's
+        # 128-point tiles
         n_tiles = (s.nu_first + s.n_nu - 1) // 128 - s.nu_first // 128 + 1
         algo = {"direct": (s.n_layers + 1) * 4 * s.n_nu * (len(s.species) + 1) * 2,
                 "cached": (s.n_layers + 1) * n_tiles * 128 * (len(s.species) + 2) * 8}
@@ -642,21 +665,43 @@ def run_sweep_large(args, local):
                 bins = torch.empty((b, s.n_bins), dtype=torch.float32, device=dev)
                 eng.forward([h], sd, th, bins)
                 torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                eng.forward([h], sd, th, bins)
+                torch.cuda.synchronize()
+                reps = int(min(200, max(3, target_s / max(time.perf_counter() - t0, 1e-5))))
+                cs = ClockSampler(local)
+                cs.start()
                 hr2.hr2_profile_read(eng.ctx, True)
                 hr2.hr2_profile_enable(eng.ctx, True)
-                reps = 3
                 for _ in range(reps):
                     eng.forward([h], sd, th, bins)
                 torch.cuda.synchronize()
                 hr2.hr2_profile_enable(eng.ctx, False)
+                clk = cs.stop()
                 ms, n = hr2.hr2_profile_read(eng.ctx, True)
                 ms /= max(n, 1)
-                res.append({"workload": wl.name, "mode": mode, "batch": b, "kernel_ms": ms,
-                            "models_per_s": b / (ms / 1e3),
-                            "algorithmic_bytes_per_model": per_model_bytes,
-                            "algorithmic_gbs": b * per_model_bytes / (ms / 1e3) / 1e9})
-                print(json.dumps(res[-1]), flush=True)
-    return res
+                line = {"workload": wl.name, "mode": mode, "batch": b, "kernel_ms": ms, "reps": reps,
+                        "models_per_s": b / (ms / 1e3),
+                        "algorithmic_bytes_per_model": per_model_bytes,
+                        "algorithmic_gbs": b * per_model_bytes / (ms / 1e3) / 1e9,
+                        "algorithmic_hbm_frac": b * per_model_bytes / (ms / 1e3) / 1e9 / hbm_peak,
+                        "clocks": clk}
+                key = "%s_b%d" % (mode, b)
+                if counters and key in counters.get("dram_bytes_per_launch", {}):
+                    dram = counters["dram_bytes_per_launch"][key]
+                    line.update({"dram_bytes_per_launch": dram, "dram_gbs": dram / (ms / 1e3) / 1e9,
+                                 "dram_hbm_frac": dram / (ms / 1e3) / 1e9 / hbm_peak,
+                                 "dram_source": counters.get("source")})
+                res.append(line)
+                if print_lines:
+                    print(json.dumps(line), flush=True)
+    return {"lines": res, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src}
+
+
+def run_sweep_large(args, local):
+    modes = tuple(m for m in args.sweep_modes.split(",") if m)
+    batches = tuple(int(b) for b in args.sweep_batches.split(",") if b)
+    return large_table_sweep(local, args.sweep_nu, modes, batches, print_lines=True)
 
 
 UNIT_KINDS = (("ex2_rcp", 0), ("rcp", 1), ("ex2", 2), ("ffma", 3), ("ffma2", 4))

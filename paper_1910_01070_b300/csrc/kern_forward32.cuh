@@ -847,9 +847,9 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
       if constexpr (KT >= 8 && !PARA) {
         const int kc = (S.n_species + 1) & ~1;
         if (kc <= KT - 4)
-          HR2_SOLVE((KT >= 8 ? KT - 4 : KT));
+          HR2_SOLVE(KT - 4);
         else if (kc <= KT - 2)
-          HR2_SOLVE((KT >= 8 ? KT - 2 : KT));
+          HR2_SOLVE(KT - 2);
         else
           HR2_SOLVE(KT);
       } else {
