@@ -485,13 +485,22 @@ def run_extras(args, local, flush):
                                "kernel_ms": kms / max(nl, 1),
                                "mufu_frac": rl["fractions"]["mufu"], "fma_frac": rl["fractions"]["fma"],
                                "launch": list(hr2.hr2_get_launch_config(eng.ctx)),
-                               "autotuned": {"candidates": len(tried), "best": list(best)}}
+                               "autotuned": {"candidates": len(tried), "best": list(best),
+                                             "shape": "(warps per CTA, CTAs per SM, 128-point tiles per item, "
+                                                      "stages; 0 = by batch shape)",
+                                             "tiles_per_item_tried": sorted({c[2] for c in tried}),
+                                             "fastest_ms": min(tried.values()) if tried else None,
+                                             "default_ms": tried.get(autotune.DEFAULT_SHAPE)}}
         # serving: 16 nested-sampling-like streams over the 12 setups, Poisson arrivals
         shapes = [(s.n_bins, s.n_nu, s.n_layers + 1) for s in wl.setups]
         res = []
-        for load in (0.5, 0.8, 1.2):
-            srv = serving.Server(eng.ctx, setups, shapes, device=local, slots=3, max_batch=2048,
-                                 mem_budget=4 << 30)
+        servers = {}
+        for load, graphs in ((0.5, True), (0.8, True), (1.2, True), (0.8, False)):
+            if graphs not in servers:
+                servers[graphs] = serving.Server(eng.ctx, setups, shapes, device=local, slots=2, max_batch=512,
+                                                 mem_budget=32 << 30, graphs=graphs)
+            srv = servers[graphs]
+            srv.reset()
             streams, templates = [], []
             for k in range(16):
                 g = k % len(wl.setups)
@@ -511,7 +520,8 @@ def run_extras(args, local, flush):
             st["offered_models_per_s"] = load * cap
             res.append(st)
         out["serving"] = {"streams": 16, "request_sizes": "32-512", "capacity_models_per_s": cap,
-                          "latency": "arrival to lnL on the host", "loads": res}
+                          "latency": "arrival to lnL on the host (served requests; rejected ones counted)",
+                          "loads": res}
     if not args.no_large:
         out["large_tables"] = large_table_sweep(local)
     out["linear_sigma_option"] = run_linear_option(args, local, flush)

@@ -192,13 +192,23 @@ typedef struct {
                                  call takes setups of a single kind.             */
 } hr2_setup_desc;
 
-/* Launch shape of the persistent forward kernel (chosen by the autotuner;
- * a new context starts with 2 warps per CTA and 8 CTAs per SM). */
+/* Launch shape of the persistent forward kernel: the work item's tile
+ * (samples x wavenumbers), the persistent grid and the copy-pipeline depth
+ * (chosen by the autotuner; a new context starts with {2, 8, 1, 0}).  Every
+ * shape computes each (sample, wavenumber) the same way: results do not
+ * depend on it. */
 typedef struct {
   int warps_per_cta;          /* samples processed together per work item: 1..16;
                                  a batch with fewer samples uses fewer, with
                                  proportionally more CTAs per SM               */
   int ctas_per_sm;            /* persistent CTAs per SM: 1..32                    */
+  int tiles_per_item;         /* consecutive 128-point wavenumber tiles per work
+                                 item, 1..16 (the item's wavenumber extent)     */
+  int stages;                 /* shared-memory stages per warp of the level-
+                                 gridded kernel: 0 = by batch shape; 1 or 2
+                                 where the kernel exists in both depths (more
+                                 than 4 angle nodes, 8 or more absorbers, linear
+                                 source), else the batch-shape choice stands    */
 } hr2_launch_cfg;
 
 /* ------------------------------------------------------------- contexts */

@@ -1,15 +1,20 @@
 """Autotuner for the launch shape of the persistent forward kernel.
 
-The forward kernel's tile is fixed (128 wavenumbers, two packed pairs per
-lane); what is tuned is how many samples share one work item (warps per CTA,
-which also sets the per-CTA shared-memory pipeline size) and how many
-persistent CTAs run per SM.  For a batch shape the tuner times every candidate with the
-library's kernel-event instrumentation (hr2_profile_*) on the caller's real
-inputs, keeps the fastest, and caches the choice in a JSON file keyed by the
-shape, so later runs (and the serving loop) reuse it without re-timing.
+The shape has four parts (hr2_launch_cfg): the work item's tile, i.e. how
+many samples share one item (warps per CTA, which also sets the per-CTA
+shared-memory pipeline size) and how many consecutive 128-point wavenumber
+tiles one item covers; the number of persistent CTAs per SM; and, where the
+level-gridded kernel exists in both depths, its copy-pipeline depth (one or
+two shared-memory stages per warp).  Every shape computes each (sample,
+wavenumber) the same way, so the choice changes speed only.  For a batch
+shape the tuner times every candidate with the library's kernel-event
+instrumentation (hr2_profile_*) on the caller's real inputs, keeps the
+fastest, and caches the choice in a JSON file keyed by the shape, so later
+runs (and the serving loop) reuse it without re-timing.
 """
 from __future__ import annotations
 
+import itertools
 import json
 import os
 import threading
@@ -17,8 +22,24 @@ from typing import Dict, Iterable, List, Optional, Sequence, Tuple
 
 from . import hr2
 
-DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = (
-    (1, 16), (2, 6), (2, 8), (4, 2), (4, 3), (4, 4), (4, 6), (8, 1), (8, 2), (8, 3), (16, 1))
+Shape = Tuple[int, int, int, int]          # (warps_per_cta, ctas_per_sm, tiles_per_item, stages)
+
+#: (warps per CTA, CTAs per SM) pairs tried
+GRIDS: Tuple[Tuple[int, int], ...] = ((1, 16), (2, 6), (2, 8), (4, 3), (4, 4), (8, 2), (16, 1))
+#: wavenumber tiles per work item tried
+TILES_PER_ITEM: Tuple[int, ...] = (1, 2, 4)
+DEFAULT_SHAPE: Shape = (2, 8, 1, 0)
+
+
+def candidates_for(setups_info: Sequence[Dict]) -> List[Shape]:
+    """Candidate shapes for a batch: every grid with every item width, at the pipeline depth
+    chosen by batch shape (0); with more than 4 angle nodes and 8 or more absorbers (where the
+    level-gridded kernel exists with one and with two stages) both depths as well."""
+    both = any(int(s["n_mu"]) > 4 and int(s["K"]) >= 8 and int(s.get("cached", 1)) for s in setups_info)
+    stages = (0, 1, 2) if both else (0,)
+    return [(w, c, t, st) for (w, c), t, st in itertools.product(GRIDS, TILES_PER_ITEM, stages)]
+
+
 _LOCK = threading.Lock()
 
 
@@ -57,15 +78,22 @@ def save_cache(cache: Dict[str, List[int]], path: Optional[str] = None) -> None:
         os.replace(tmp, path)
 
 
-def pick_best(timings: Dict[Tuple[int, int], float]) -> Tuple[int, int]:
-    """Fastest candidate; ties go to fewer warps, then fewer CTAs (smaller shared-memory footprint)."""
-    return min(timings, key=lambda c: (round(timings[c], 6), c[0], c[1]))
+def pick_best(timings: Dict[Shape, float]) -> Shape:
+    """Fastest candidate; ties go to fewer warps, then fewer CTAs (smaller shared-memory footprint),
+    then narrower items, then the batch-shape depth."""
+    return min(timings, key=lambda c: (round(timings[c], 6),) + tuple(c))
+
+
+def _as_shape(c) -> Shape:
+    c = tuple(int(v) for v in c)
+    return c + DEFAULT_SHAPE[len(c):]
 
 
 def tune(ctx, setups: Sequence, setup_of_sample, params, out_bins, setups_info: Sequence[Dict],
-         candidates: Iterable[Tuple[int, int]] = DEFAULT_CANDIDATES, reps: int = 3, use_cache: bool = True,
-         path: Optional[str] = None, stream=None) -> Tuple[Tuple[int, int], Dict[Tuple[int, int], float]]:
-    """Time each (warps_per_cta, ctas_per_sm) candidate on this batch and set the best on ctx.
+         candidates: Optional[Iterable] = None, reps: int = 3, use_cache: bool = True,
+         path: Optional[str] = None, stream=None) -> Tuple[Shape, Dict[Shape, float]]:
+    """Time each candidate shape (warps_per_cta, ctas_per_sm[, tiles_per_item[, stages]]) on this
+    batch and set the best on ctx.
 
     Returns (best, {candidate: ms per forward-kernel launch}).  With use_cache a cached
     choice for the same shape key is applied without timing.
@@ -74,12 +102,13 @@ def tune(ctx, setups: Sequence, setup_of_sample, params, out_bins, setups_info: 
     key = shape_key(setups_info, int(params.shape[0]))
     cache = load_cache(path) if use_cache else {}
     if use_cache and key in cache:
-        best = tuple(cache[key])
+        best = _as_shape(cache[key])
         hr2.hr2_set_launch_config(ctx, *best)
         return best, {}
+    cands = [_as_shape(c) for c in (candidates if candidates is not None else candidates_for(setups_info))]
     timings = {}
-    for w, c in candidates:
-        hr2.hr2_set_launch_config(ctx, w, c)
+    for c in cands:
+        hr2.hr2_set_launch_config(ctx, *c)
         hr2.forward_model_batch(ctx, setups, setup_of_sample, params, out_bins, None, None, stream)  # warm-up
         torch.cuda.synchronize()
         hr2.hr2_profile_read(ctx, True)
@@ -89,7 +118,7 @@ def tune(ctx, setups: Sequence, setup_of_sample, params, out_bins, setups_info: 
         torch.cuda.synchronize()
         hr2.hr2_profile_enable(ctx, False)
         ms, n = hr2.hr2_profile_read(ctx, True)
-        timings[(w, c)] = ms / max(n, 1)
+        timings[c] = ms / max(n, 1)
     best = pick_best(timings)
     hr2.hr2_set_launch_config(ctx, *best)
     if use_cache:

@@ -59,7 +59,7 @@ struct hr2_ctx {
   int n_sm = 0;
   size_t budget = 0;
   size_t used = 0;
-  hr2_launch_cfg cfg{2, 8};
+  hr2_launch_cfg cfg{2, 8, 1, 0};
   long long wait_limit = kDefaultWaitCycles;   // bounded device-side waits, SM clock cycles
   bool wait_fault = false;                     // test hook: first stages wait for bytes that never come
   std::mutex mu;
@@ -272,6 +272,9 @@ extern "C" int hr2_set_launch_config(hr2_ctx* ctx, const hr2_launch_cfg* cfg) {
   if (!ctx || !cfg) return fail(HR2_EINVAL, "NULL argument");
   if (cfg->warps_per_cta < 1 || cfg->warps_per_cta > kMaxWarps || cfg->ctas_per_sm < 1 || cfg->ctas_per_sm > 32)
     return fail(HR2_EINVAL, "launch config out of range (warps 1..%d, ctas_per_sm 1..32)", kMaxWarps);
+  if (cfg->tiles_per_item < 1 || cfg->tiles_per_item > 16)
+    return fail(HR2_EINVAL, "tiles_per_item %d outside 1..16", cfg->tiles_per_item);
+  if (cfg->stages < 0 || cfg->stages > 2) return fail(HR2_EINVAL, "stages %d is not 0, 1 or 2", cfg->stages);
   ctx->cfg = *cfg;
   return HR2_OK;
 }
@@ -886,7 +889,10 @@ static void fill_node_constants(FwdArgs& a, int n_setups, const hr2_setup* const
 
 static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {
   int w = std::min(std::min(ctx->cfg.warps_per_cta, kForwardMaxThreads / 32), std::max(1, n));
-  const int st = forward32_stages(sh.max_mu, sh.para != 0, absorber_bound(sh), n);
+  int st = forward32_stages(sh.max_mu, sh.para != 0, absorber_bound(sh), n);
+  // a requested pipeline depth where the kernel exists in both depths
+  if (ctx->cfg.stages && forward32_has_both_depths(sh.max_mu, sh.para != 0, absorber_bound(sh)))
+    st = ctx->cfg.stages;
   if (sh.cached) {
     while (w > 1 && forward32_smem_bytes(w, sh.max_k, st) > kForwardSmemCap) --w;
   }
@@ -930,6 +936,7 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
   a.samp = w->samp;
   const LaunchShape ls = shape_for(ctx, sh, n);
   a.warps = ls.warps;
+  a.tiles_per_item = ctx->cfg.tiles_per_item;
   a.err = (int*)(w->counter + 1);
   a.wait_limit = ctx->wait_limit;
   a.tx_extra = ctx->wait_fault ? 16u : 0u;
@@ -1253,6 +1260,7 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
   a.highres_ld = highres_ld;
   const LaunchShape ls = shape_for(ctx, sh, n);
   a.warps = ls.warps;
+  a.tiles_per_item = ctx->cfg.tiles_per_item;
   a.wait_limit = ctx->wait_limit;
   a.tx_extra = ctx->wait_fault ? 16u : 0u;
   fill_node_constants(a, n_setups, setups);

@@ -34,6 +34,11 @@ constexpr int kForwardMinBlocksSmall = 4;
 constexpr int kOneStageMinBatch = 16;
 __host__ __device__ constexpr int forward32_stages(int nmu, bool para, int kt, int n) {
   return (para || kt == 0) ? 2 : (nmu <= 4 ? 1 : ((kt >= 8 && n >= kOneStageMinBatch) ? 1 : 2));
+}
+// whether that kernel exists with one and with two stages (a launch shape may
+// then ask for either)
+__host__ __device__ constexpr bool forward32_has_both_depths(int nmu, bool para, int kt) {
+  return !para && kt >= 8 && nmu > 4;
 }// dynamic shared memory the cached forward kernel may use per CTA
 constexpr size_t kForwardSmemCap = 200u * 1024u;
 constexpr int kCiaH2H2 = HR2_MAX_SPECIES;      // offset slot of the H2-H2 CIA table
@@ -251,6 +256,7 @@ struct FwdArgs {
   int rec_ld;
   SampleDev* samp;          // [n]
   int warps;                // samples per work item
+  int tiles_per_item;       // consecutive kTileNu-point tiles per work item
   int* err;                 // device error word (bit 0: a bounded wait gave up), or null
   long long wait_limit;     // SM clock cycles a pipeline wait may take before it gives up
   unsigned tx_extra;        // test hook: bytes each item's first stage waits for in vain (0)

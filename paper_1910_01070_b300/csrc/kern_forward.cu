@@ -285,9 +285,10 @@ cudaError_t launch_prep(const FwdArgs& a, cudaStream_t s) {
 
 // ------------------------------------------------------------------ plan
 // Counts samples per setup, orders setups by decreasing item cost, lays out
-// work items (setup, tile, sample block) with the sample block fastest so
-// that consecutive items share a wavenumber tile of the table, and writes
-// the samples of each setup contiguously (stable) into perm.
+// work items (setup, group of tiles_per_item consecutive tiles, sample block)
+// with the sample block fastest so that consecutive items share wavenumber
+// tiles of the table, and writes the samples of each setup contiguously
+// (stable) into perm.
 __global__ void k_plan(FwdArgs a, int* perm, PlanDev* plan) {
   __shared__ int cnt[HR2_MAX_SETUPS], base[HR2_MAX_SETUPS];
   const int tid = threadIdx.x;
@@ -322,7 +323,8 @@ __global__ void k_plan(FwdArgs a, int* perm, PlanDev* plan) {
       const int g = order[p];
       plan->order[p] = g;
       plan->item_start[p] = items;
-      items += plan->n_sblocks[g] * a.setups[g]->n_tiles;
+      const int tpi = a.tiles_per_item > 0 ? a.tiles_per_item : 1;
+      items += plan->n_sblocks[g] * ((a.setups[g]->n_tiles + tpi - 1) / tpi);
     }
     plan->item_start[a.n_setups] = items;
     plan->total_items = items;

@@ -810,8 +810,9 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
     const int g = plan->order[pos];
     const int rem = item - plan->item_start[pos];
     const int nsb = plan->n_sblocks[g];
-    const int tile = rem / nsb;
-    const int sb = rem - tile * nsb;
+    // an item covers a.tiles_per_item consecutive tiles of one block of samples
+    const int tgrp = rem / nsb;
+    const int sb = rem - tgrp * nsb;
     const SetupDev& S = *a.setups[g];
     const TablesDev& T = *S.tables;
     if (!CACHED && threadIdx.x < S.n_species)
@@ -834,28 +835,31 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
     }
     __syncthreads();
     if (active) {
-      const bool sx = item_small_x(a, S, T, i, tile);
-      // a batch compiled for a bound KT >= 8 holds setups with KT-4 .. KT
-      // absorbers: each item runs the sweep compiled for its own setup's
-      // even bound, so that a setup pads at most one absorber (the linear
-      // source; the parabolic one keeps the batch's bound)
+      const int t_end = min(S.n_tiles, (tgrp + 1) * a.tiles_per_item);
+      for (int tile = tgrp * a.tiles_per_item; tile < t_end; ++tile) {
+        const bool sx = item_small_x(a, S, T, i, tile);
+        // a batch compiled for a bound KT >= 8 holds setups with KT-4 .. KT
+        // absorbers: each item runs the sweep compiled for its own setup's
+        // even bound, so that a setup pads at most one absorber (the linear
+        // source; the parabolic one keeps the batch's bound)
 #define HR2_SOLVE(KB)                                                                                              \
   (sx ? solve_tile<NMU, CACHED, KB, LIN, PARA, true, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, \
                                                           sMu, g, wp_, phase_base)                               \
       : solve_tile<NMU, CACHED, KB, LIN, PARA, false, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl,     \
                                                            sImu, sMu, g, wp_, phase_base))
-      if constexpr (KT >= 8 && !PARA) {
-        const int kc = (S.n_species + 1) & ~1;
-        if (kc <= KT - 4)
-          HR2_SOLVE(KT - 4);
-        else if (kc <= KT - 2)
-          HR2_SOLVE(KT - 2);
-        else
+        if constexpr (KT >= 8 && !PARA) {
+          const int kc = (S.n_species + 1) & ~1;
+          if (kc <= KT - 4)
+            HR2_SOLVE(KT - 4);
+          else if (kc <= KT - 2)
+            HR2_SOLVE(KT - 2);
+          else
+            HR2_SOLVE(KT);
+        } else {
           HR2_SOLVE(KT);
-      } else {
-        HR2_SOLVE(KT);
-      }
+        }
 #undef HR2_SOLVE
+      }
     }
   }
 }

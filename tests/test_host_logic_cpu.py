@@ -43,6 +43,31 @@ def test_packing_takes_whole_requests_in_order():
     assert [(r.rid, off) for r, off in batch] == [(2, 0), (3, 400)]
 
 
+def test_queue_bound_counts_pending_and_admitted_samples():
+    assert not serving.over_queue_limit(300, 300, 600)
+    assert serving.over_queue_limit(301, 300, 600)
+    assert serving.over_queue_limit(0, 601, 600)
+
+
+def test_cancel_removes_only_the_named_request():
+    pending = collections.deque([_req(0, 10), _req(1, 20)])
+    admitted = collections.deque([_req(2, 30)])
+    r = serving.cancel_from([pending, admitted], 2)
+    assert r.rid == 2 and len(admitted) == 0 and [q.rid for q in pending] == [0, 1]
+    assert serving.cancel_from([pending, admitted], 7) is None
+    assert [q.rid for q in pending] == [0, 1]
+
+
+def test_graph_buckets_cover_every_batch_size():
+    sizes = serving.bucket_sizes(1024)
+    assert sizes == [64, 128, 256, 512, 1024]
+    assert serving.bucket_sizes(300) == [64, 128, 256, 300]
+    assert serving.pick_bucket(sizes, 1) == 64 and serving.pick_bucket(sizes, 65) == 128
+    assert serving.pick_bucket(sizes, 1024) == 1024
+    with pytest.raises(ValueError):
+        serving.pick_bucket(sizes, 1025)
+
+
 def test_retrieval_stream_is_seeded_and_contracts():
     lo = np.zeros(W.NPARAM)
     hi = np.zeros(W.NPARAM)
@@ -69,7 +94,16 @@ def test_autotune_shape_key_and_cache(tmp_path):
     autotune.save_cache({k1: [4, 4]}, path)
     assert autotune.load_cache(path) == {k1: [4, 4]}
     assert autotune.load_cache(str(tmp_path / "missing.json")) == {}
-    assert autotune.pick_best({(8, 2): 7.0, (4, 4): 6.9, (2, 8): 6.9}) == (2, 8)
+    assert autotune.pick_best({(8, 2, 1, 0): 7.0, (4, 4, 1, 0): 6.9, (2, 8, 2, 0): 6.9}) == (2, 8, 2, 0)
+    assert autotune._as_shape([4, 4]) == (4, 4, 1, 0)
+
+
+def test_autotune_candidates_span_the_tile_shape():
+    few = autotune.candidates_for([{"K": 6, "L": 100, "n_mu": 4, "n_nu": 8501, "cached": 1}])
+    assert {c[2] for c in few} == {1, 2, 4} and {c[3] for c in few} == {0}
+    assert len(few) == len(autotune.GRIDS) * 3 and len(set(few)) == len(few)
+    both = autotune.candidates_for([{"K": 12, "L": 100, "n_mu": 8, "n_nu": 290001, "cached": 1}])
+    assert {c[3] for c in both} == {0, 1, 2} and len(both) == 3 * len(few)
 
 
 def _rank_main(rank, world, port, out):

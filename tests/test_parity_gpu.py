@@ -460,19 +460,31 @@ def test_stage_variants_agree_bitwise(eng, K, n_mu):
     for m in (1, 5, 15):
         small = _run(eng, [s], sid[:m], theta[:m])
         assert np.array_equal(small[0], big[0][:m]) and np.array_equal(small[1], big[1][:m])
+    # the depth asked for explicitly (where both exist), with wider items
+    old = hr2.hr2_get_launch_config(eng.ctx)
+    try:
+        for stages in (1, 2):
+            eng.set_launch_config(2, 8, 2, stages)
+            for m in (3, 40):
+                got = _run(eng, [s], sid[:m], theta[:m])
+                assert np.array_equal(got[0], big[0][:m]) and np.array_equal(got[1], big[1][:m])
+    finally:
+        eng.set_launch_config(*old)
     om = oracle_model(tables_as_stored(tabs, "fp16"), setup)
     for i in (0, 17, 39):
         _compare(om, theta[i], big[0][i], big[1][i], FLUX_RTOL, 300)
 
 
 def test_launch_shapes_agree_bitwise(eng):
+    """Every launch shape the autotuner may pick (samples and wavenumber tiles per work item,
+    CTAs per SM) computes each sample and point the same way."""
     wl, tabs, stored, setups, st = _workload_on(eng, "uneven2048_3setups", "fp16")
     theta, sid = wl.params(96, seed_offset=3)
     ref = None
     old = hr2.hr2_get_launch_config(eng.ctx)
     try:
-        for w, c in ((1, 1), (4, 2), (8, 3), (16, 1)):
-            eng.set_launch_config(w, c)
+        for shape in ((1, 1, 1, 0), (4, 2, 1, 0), (8, 3, 2, 0), (16, 1, 4, 0), (2, 8, 3, 0), (2, 8, 16, 0)):
+            eng.set_launch_config(*shape)
             out = _run(eng, setups, sid, theta, highres_ld=10001)
             if ref is None:
                 ref = out
