@@ -101,6 +101,9 @@ typedef enum {
 #define HR2_STORE_FP16_OFFSET 1  /* FP16 of (log10 sigma - off_s), off_s integer */
 #define HR2_STORE_FP64        2  /* FP64 log10 sigma (the plain FP64 path)       */
 
+/* hr2_setup_desc.level_cache: build the level-gridded operand where it fits */
+#define HR2_LEVEL_CACHE_AUTO 2
+
 /* Interpolation space of the opacity tables (Sect. 2.8 names the
  * interpolation of the tables but not the quantity interpolated). */
 #define HR2_INTERP_LOG10  0  /* bilinear in log10 sigma, then 10^x (default)     */
@@ -170,8 +173,14 @@ typedef struct {
                                  device memory), so that each sample
                                  interpolates in T only.  Zero:
                                  every evaluation interpolates the FP16 tables
-                                 bilinearly.  One batch call takes setups of a
-                                 single kind.                                    */
+                                 bilinearly.  HR2_LEVEL_CACHE_AUTO: the
+                                 operand if it fits both the context's budget
+                                 (when one is set) and half the device's free
+                                 memory at creation, else the direct path (the
+                                 linear option, which needs the operand, then
+                                 fails with HR2_ENOMEM).  hr2_setup_memory
+                                 tells which was built.  One batch call takes
+                                 setups of a single kind.                        */
   int interp;                 /* HR2_INTERP_LOG10 or HR2_INTERP_LINEAR.  With
                                  FP16 tables the linear option needs
                                  level_cache (the operand then holds the
@@ -285,6 +294,13 @@ int hr2_setup_set_observation(hr2_ctx* ctx, hr2_setup* setup, const double* obs_
 
 /* Number of bins / wavenumbers / nonzeros of W of a setup. */
 int hr2_setup_info(const hr2_setup* setup, int* n_bins, int* n_nu, long long* w_nnz);
+
+/* Device bytes a setup holds (levels, quadratures, W, observation, Hopf table,
+ * wavenumber constants and, if built, the level-gridded operand), the
+ * operand's share of them, and whether the operand was built (1) or the
+ * setup evaluates the FP16 tables directly (0).  No counterpart in the
+ * paper.  NULL outputs are skipped. */
+int hr2_setup_memory(const hr2_setup* setup, size_t* bytes, size_t* operand_bytes, int* level_gridded);
 
 int hr2_setup_destroy(hr2_ctx* ctx, hr2_setup* setup);
 

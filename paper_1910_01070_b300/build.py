@@ -31,6 +31,13 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
+def _unit_deps(src: str) -> float:
+    """Newest of a unit's source, every header and this script (a header change rebuilds all)."""
+    files = [os.path.join(CSRC, src), os.path.join(INCLUDE, "hr2.h"), __file__]
+    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    return max(os.path.getmtime(f) for f in files)
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps():
         return LIB
@@ -40,6 +47,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     def compile_one(unit):
         src, obj, defines = unit
         obj = os.path.join(BUILD, obj)
+        if not force and os.path.exists(obj) and os.path.getmtime(obj) >= _unit_deps(src):
+            return obj
         cmd = [NVCC, *ARCH, *FLAGS, *defines, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:

@@ -87,6 +87,7 @@ struct hr2_setup {
   SetupDev host{};
   SetupDev* dev = nullptr;
   std::vector<void*> mem;
+  size_t operand_bytes = 0;
   int n_bins = 0;
   bool has_obs = false;
   double* d_obs = nullptr;  // [2][n_bins]: D then sigma
@@ -742,20 +743,39 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
       goto fail_tmp;
     }
   }
-  if (d->level_cache && th.storage == HR2_STORE_FP16_OFFSET) {
+  {
+  // per tile, level, T cell and operand row (absorbers, then the two CIA
+  // pairs): 2 kTileNu floats (row and T difference)
+  const size_t per_tile = (size_t)h.n_lev * (h.n_species + 2) * (th.n_T - 1) * 2 * kTileNu;
+  bool want_operand = d->level_cache != 0 && th.storage == HR2_STORE_FP16_OFFSET;
+  if (want_operand && d->level_cache == HR2_LEVEL_CACHE_AUTO) {
+    // the operand where it fits the context's budget and half the free memory
+    const size_t bytes = per_tile * h.n_tiles * sizeof(float);
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      cudaGetLastError();
+      free_b = 0;
+    }
+    const bool fits = bytes <= free_b / 2 && (!ctx->budget || ctx->used + bytes <= ctx->budget);
+    if (!fits && d->interp == HR2_INTERP_LINEAR) {
+      rc = fail(HR2_ENOMEM, "the linear option needs the level-gridded operand (%zu bytes), which does not fit", bytes);
+      goto fail_tmp;
+    }
+    want_operand = fits;
+  }
+  if (want_operand) {
     float* d_lvl = nullptr;
-    // per tile, level, T cell and operand row (absorbers, then the two CIA
-    // pairs): 2 kTileNu floats (row and T difference)
-    const size_t per_tile = (size_t)h.n_lev * (h.n_species + 2) * (th.n_T - 1) * 2 * kTileNu;
     if ((rc = dalloc_t(ctx, &d_lvl, per_tile * h.n_tiles))) goto fail_tmp;
     track(d_lvl);
     h.lvl32 = d_lvl;
     h.cached = 1;
+    st->operand_bytes = per_tile * h.n_tiles * sizeof(float);
     if ((e = build_level_cache(tab->dev, h, d_lvl, 0)) != cudaSuccess ||
         (e = cudaDeviceSynchronize()) != cudaSuccess) {
       rc = fail(HR2_ECUDA, "setup level-gridded operand: %s", cudaGetErrorString(e));
       goto fail_tmp;
     }
+  }
   }
   if ((rc = dalloc_t(ctx, &st->dev, 1))) goto fail_tmp;
   track(st->dev);
@@ -803,6 +823,19 @@ extern "C" int hr2_setup_info(const hr2_setup* s, int* n_bins, int* n_nu, long l
   if (n_bins) *n_bins = s->host.n_bins;
   if (n_nu) *n_nu = s->host.n_nu;
   if (nnz) *nnz = s->host.w_nnz;
+  return HR2_OK;
+}
+
+extern "C" int hr2_setup_memory(const hr2_setup* s, size_t* bytes, size_t* operand_bytes, int* level_gridded) {
+  if (!s) return fail(HR2_EINVAL, "setup is NULL");
+  size_t total = 0;
+  for (void* p : s->mem) {
+    auto it = s->ctx->blocks.find(p);
+    if (it != s->ctx->blocks.end()) total += it->second;
+  }
+  if (bytes) *bytes = total;
+  if (operand_bytes) *operand_bytes = s->operand_bytes;
+  if (level_gridded) *level_gridded = s->host.cached;
   return HR2_OK;
 }
 

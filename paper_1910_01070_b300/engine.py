@@ -39,7 +39,7 @@ class Engine:
         self.tables.append(h)
         return h
 
-    def add_setup(self, tables, s: W.SetupSpec, obs_flux=None, obs_sigma=None, level_cache: bool = True):
+    def add_setup(self, tables, s: W.SetupSpec, obs_flux=None, obs_sigma=None, level_cache=True):
         h = hr2.hr2_setup_create(self.ctx, tables, s.nu_first, s.n_nu, s.n_layers, s.species, s.n_mu,
                                  s.fe_elements, s.fe_order, s.resolving_power, s.bin_edges, s.p_top, s.p_bot,
                                  s.r_he, s.radius_cm, obs_flux, obs_sigma, level_cache, s.interp, s.profile, s.cloud, s.sc)

@@ -25,6 +25,7 @@ HR2_MAX_TNODES, HR2_MAX_SPECIES, HR2_MAX_MU, HR2_MAX_LEVELS, HR2_MAX_SETUPS = 16
 HR2_P_LOGG, HR2_P_F, HR2_P_DIST, HR2_P_T0, HR2_P_X0, HR2_P_CLOUD, HR2_NPARAM = 0, 1, 2, 3, 19, 35, 38
 HR2_STORE_FP16_OFFSET, HR2_STORE_FP64 = 1, 2
 HR2_INTERP_LOG10, HR2_INTERP_LINEAR = 0, 1
+HR2_LEVEL_CACHE_AUTO = 2
 INTERP = {"log10": HR2_INTERP_LOG10, "linear": HR2_INTERP_LINEAR}
 HR2_PROFILE_FE, HR2_PROFILE_MILNE = 0, 1
 PROFILE = {"fe": HR2_PROFILE_FE, "milne": HR2_PROFILE_MILNE}
@@ -40,7 +41,7 @@ EXPORTED = [
     "hr2_profile_read", "hr2_stream_check", "hr2_nodes_from_b", "hr2_version",
     "hr2_ns_state_init", "hr2_ns_absorb", "hr2_ns_propose", "hr2_ns_finalize", "hr2_effective_temperature",
     "hr2_measure_unit_rate", "hr2_noalloc_check", "hr2_set_wait_limit", "hr2_get_wait_limit",
-    "hr2_set_wait_fault",
+    "hr2_set_wait_fault", "hr2_setup_memory",
 ]
 
 
@@ -141,6 +142,7 @@ def lib():
                 "hr2_set_wait_limit": (C.c_int, [_VP, C.c_longlong]),
                 "hr2_get_wait_limit": (C.c_int, [_VP, C.POINTER(C.c_longlong)]),
                 "hr2_set_wait_fault": (C.c_int, [_VP, C.c_int]),
+                "hr2_setup_memory": (C.c_int, [_VP, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), _IP]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -291,7 +293,7 @@ def hr2_setup_create(ctx, tables, nu_first, n_nu, n_layers, species, n_mu, fe_el
         pf, ps = _DP(), _DP()
     d = SetupDesc(int(nu_first), int(n_nu), int(n_layers), float(p_top), float(p_bot), len(sp),
                   sp.ctypes.data_as(_IP), int(n_mu), int(fe_elements), int(fe_order), float(resolving_power),
-                  len(edges) - 1, pe, pf, ps, float(r_he), float(radius_cm), int(bool(level_cache)),
+                  len(edges) - 1, pe, pf, ps, float(r_he), float(radius_cm), _level_cache_arg(level_cache),
                   INTERP[interp], PROFILE[profile], int(bool(cloud)), SC[sc])
     h = _VP()
     _check(lib().hr2_setup_create(ctx, tables, C.byref(d), C.byref(h)), ctx)
@@ -308,6 +310,22 @@ def hr2_setup_info(setup):
     nb, nn, nnz = C.c_int(), C.c_int(), C.c_longlong()
     _check(lib().hr2_setup_info(setup, C.byref(nb), C.byref(nn), C.byref(nnz)))
     return nb.value, nn.value, nnz.value
+
+
+def hr2_setup_memory(setup):
+    """(device bytes of the setup, bytes of its level-gridded operand, whether the operand was built)."""
+    b, ob, lg = C.c_size_t(), C.c_size_t(), C.c_int()
+    _check(lib().hr2_setup_memory(setup, C.byref(b), C.byref(ob), C.byref(lg)))
+    return b.value, ob.value, bool(lg.value)
+
+
+def _level_cache_arg(v) -> int:
+    """level_cache as the ABI takes it: True/False, or "auto" (HR2_LEVEL_CACHE_AUTO)."""
+    if isinstance(v, str):
+        if v != "auto":
+            raise ValueError("level_cache must be a bool or 'auto'")
+        return HR2_LEVEL_CACHE_AUTO
+    return int(bool(v))
 
 
 def hr2_setup_destroy(ctx, setup):

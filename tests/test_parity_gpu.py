@@ -560,6 +560,41 @@ def test_memory_budget_admission():
         e.close()
 
 
+def test_level_gridded_operand_where_it_fits():
+    """level_cache='auto' builds the level-gridded operand only where it fits the context's budget
+    (and half the free device memory); otherwise the setup evaluates the FP16 tables directly,
+    with the same results as a setup created without the operand.  The operand's size is
+    levels x (T cells) x (absorbers + 2 CIA rows) x tiles of 128 points x 8 bytes."""
+    spec, tabs = _absorber_spec(6, 77)
+    setup = W.make_setup(spec, 5000.0, 5299.0, 24, range(6), 4, 3, 2, 300.0, 6)
+    theta = W.draw_params(setup, 20, 71, W.Prior())
+    sid = np.zeros(20, np.int32)
+    n_tiles = (setup.nu_first + setup.n_nu - 1) // 128 - setup.nu_first // 128 + 1
+    operand = (setup.n_layers + 1) * (len(spec.T_grid) - 1) * (6 + 2) * n_tiles * 128 * 8
+    with Engine(0) as big:
+        t = big.add_tables(spec, "fp16", tabs)
+        s_auto = big.add_setup(t, setup, level_cache="auto")
+        s_direct = big.add_setup(t, setup, level_cache=False)
+        b, ob, lg = hr2.hr2_setup_memory(s_auto)
+        assert lg and ob == operand and b > ob
+        b2, ob2, lg2 = hr2.hr2_setup_memory(s_direct)
+        assert not lg2 and ob2 == 0 and b2 == b - ob
+        ref_direct = _run(big, [s_direct], sid, theta)
+    with Engine(0) as probe:
+        t = probe.add_tables(spec, "fp16", tabs)
+        tables_bytes = probe.memory()[0]
+    # a budget that holds the tables and the setup without the operand, not with it
+    with Engine(0, mem_budget_bytes=tables_bytes + b2 + operand // 2) as small:
+        t = small.add_tables(spec, "fp16", tabs)
+        s = small.add_setup(t, setup, level_cache="auto")
+        assert hr2.hr2_setup_memory(s)[2] is False
+        got = _run(small, [s], sid, theta)
+        assert np.array_equal(got[0], ref_direct[0]) and np.array_equal(got[1], ref_direct[1])
+        with pytest.raises(hr2.Hr2Error) as ei:
+            small.add_setup(t, dataclasses.replace(setup, interp="linear"), level_cache="auto")
+        assert ei.value.code == hr2.HR2_ENOMEM
+
+
 @pytest.mark.slow
 def test_large_tables_sampled(eng):
     """290001-point, 12-absorber FP16 tables (~2 GB), batch 256, 8 nodes, R=1000 -> 2000 bins."""
