@@ -46,7 +46,9 @@ typedef enum {
   HR2_ENOMEM = -2,    /* device allocation failed or memory budget hit    */
   HR2_ECUDA = -3,     /* a CUDA runtime call failed                       */
   HR2_ETIMEDOUT = -4, /* a bounded device-side wait gave up               */
-  HR2_EBUSY = -5      /* workspace cannot grow while the stream captures  */
+  HR2_EBUSY = -5,     /* workspace cannot grow while the stream captures  */
+  HR2_EBOUNDS = -6    /* a device-side index check failed (only in the
+                         bounds-checked build, libhr2_bounds.so)          */
 } hr2_status;
 
 /* per-sample status bits written by forward_model_batch */

@@ -768,6 +768,7 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
     if ((rc = dalloc_t(ctx, &d_lvl, per_tile * h.n_tiles))) goto fail_tmp;
     track(d_lvl);
     h.lvl32 = d_lvl;
+    h.lvl32_tile_floats = (long long)per_tile;
     h.cached = 1;
     st->operand_bytes = per_tile * h.n_tiles * sizeof(float);
     if ((e = build_level_cache(tab->dev, h, d_lvl, 0)) != cudaSuccess ||
@@ -1041,13 +1042,20 @@ extern "C" int log_likelihood_batch(hr2_ctx* ctx, int n_setups, const hr2_setup*
   return HR2_OK;
 }
 
+// The status a batch's device error word stands for.
+static int error_word_status(unsigned word, const char* what) {
+  if (word & (unsigned)kErrBounds)
+    return fail(HR2_EBOUNDS, "a device-side index check failed during %s (bounds-checked build)", what);
+  if (word & (unsigned)kErrWait) return fail(HR2_ETIMEDOUT, "a bounded device-side wait gave up during %s", what);
+  return HR2_OK;
+}
+
 // Reads the device error word of a workspace (the stream must be idle).
 static int check_device_error(const Workspace* w) {
   if (!w || !w->counter) return HR2_OK;
   unsigned int word[2] = {0, 0};
   HR2_CU(cudaMemcpy(word, w->counter, sizeof(word), cudaMemcpyDeviceToHost));
-  if (word[1] & 1u) return fail(HR2_ETIMEDOUT, "a bounded device-side wait gave up during the last batch");
-  return HR2_OK;
+  return error_word_status(word[1], "the last batch");
 }
 
 extern "C" int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
@@ -1085,8 +1093,7 @@ extern "C" int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* co
     // the error word comes back with the results: no second round trip
     HR2_CU(cudaMemcpyAsync(w->h_counter, w->counter, 2 * sizeof(unsigned int), cudaMemcpyDeviceToHost, s));
     HR2_CU(cudaStreamSynchronize(s));
-    if (w->h_counter[1] & 1u) return fail(HR2_ETIMEDOUT, "a bounded device-side wait gave up during the last batch");
-    return HR2_OK;
+    return error_word_status(w->h_counter[1], "the last batch");
   }
   HR2_CU(cudaStreamSynchronize(s));
   return check_device_error(w);
@@ -1320,6 +1327,5 @@ extern "C" int hr2_noalloc_check(hr2_ctx* ctx, void* stream) {
   // forward_model_batch_noalloc); a 4-byte copy allocates nothing
   HR2_CU(cudaMemcpy(&word, base + noalloc_counter_offset() + sizeof(unsigned int), sizeof(word),
                     cudaMemcpyDeviceToHost));
-  if (word & 1u) return fail(HR2_ETIMEDOUT, "a bounded device-side wait gave up during the last allocation-free batch");
-  return HR2_OK;
+  return error_word_status(word, "the last allocation-free batch");
 }

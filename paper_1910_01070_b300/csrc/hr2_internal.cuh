@@ -44,6 +44,27 @@ constexpr size_t kForwardSmemCap = 200u * 1024u;
 constexpr int kCiaH2H2 = HR2_MAX_SPECIES;      // offset slot of the H2-H2 CIA table
 constexpr int kCiaH2He = HR2_MAX_SPECIES + 1;  // offset slot of the H2-He CIA table
 
+// Bounds-checked build (compiled with -DHR2_BOUNDS_CHECK=1; a debugging aid
+// in place of a device memory checker): index checks ahead of the accesses
+// they guard.  A failed check sets bit 1 of the batch's error word (the host
+// reports HR2_EBOUNDS) and the guarded work is skipped, so nothing reads or
+// writes outside its buffer.  In the normal build the checks compile to
+// nothing.
+#ifndef HR2_BOUNDS_CHECK
+#define HR2_BOUNDS_CHECK 0
+#endif
+constexpr int kErrWait = 1;     // error-word bit: a bounded wait gave up
+constexpr int kErrBounds = 2;   // error-word bit: an index check failed (bounds-checked build)
+__device__ __forceinline__ bool bounds_ok(bool ok, int* err) {
+#if HR2_BOUNDS_CHECK
+  if (!ok && err) atomicOr(err, kErrBounds);
+  return ok;
+#else
+  (void)err;
+  return ok || true;
+#endif
+}
+
 // CGS constants (CODATA 2018).
 constexpr double kH = 6.62607015e-27;         // erg s
 constexpr double kC = 2.99792458e10;          // cm s^-1
@@ -148,6 +169,7 @@ struct SetupDev {
   // interleaved per pair of columns ({g[2q], g[2q+1], dg[2q], dg[2q+1]}),
   // for the absorbers and then the two CIA pairs
   const float* lvl32;            // [n_tiles][n_lev][n_T - 1][n_species + 2][kTileNu / 2][4]
+  long long lvl32_tile_floats;   // floats of one tile of that operand
   // wavenumber constants of the FP32 kernel per pair q of setup-local
   // columns 2q, 2q+1 (tile t holds pairs t kTileNu/2 ...): the first point's
   // wavenumber as an FP32 head and tail, nu_{2q+1} / nu_{2q}, and c1 nu^3 of

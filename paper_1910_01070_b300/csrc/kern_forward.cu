@@ -128,6 +128,20 @@ __global__ void k_prep(FwdArgs a) {
   }
   const SetupDev& S = *a.setups[g];
   const TablesDev& T = *S.tables;
+  if constexpr (HR2_BOUNDS_CHECK) {
+    // the sample's record row and the setup's species and level cells
+    bool ok = S.n_lev <= a.rec_ld && S.n_species <= HR2_MAX_SPECIES && S.n_species <= T.n_species;
+    for (int s = 0; s < S.n_species; ++s) ok = ok && S.species[s] >= 0 && S.species[s] < T.n_species;
+    for (int j = lane; ok && j < S.n_lev; j += 32) ok = S.levels[j].pcell >= 0 && S.levels[j].pcell <= T.n_p - 2;
+    if (!bounds_ok(__all_sync(0xffffffffu, ok), lane == 0 ? a.err : nullptr)) {
+      if (lane == 0) {
+        sd->status = HR2_SAMPLE_BAD_SETUP;
+        sd->setup = -1;
+        if (a.status) a.status[i] = HR2_SAMPLE_BAD_SETUP;
+      }
+      return;
+    }
+  }
   const double* th = a.params + (size_t)i * HR2_NPARAM;
   const unsigned full = 0xffffffffu;
   int status = 0;
@@ -209,6 +223,9 @@ __global__ void k_prep(FwdArgs a) {
     int acell;
     double wT;
     grid_cell(T.T_grid64, T.n_T, Tj, acell, wT);
+    if constexpr (HR2_BOUNDS_CHECK) {
+      if (!bounds_ok(acell >= 0 && acell <= T.n_T - 2, a.err)) acell = 0;
+    }
     const LevelDev lv = S.levels[j];
     const double lT = log2(Tj);
     const double b0 = cb0 + lv.lpk - lT;    // log2(x_H2^2 c n_j) + off log2 10 - shift
@@ -661,6 +678,13 @@ __global__ void __launch_bounds__(256) k_bins32(FwdArgs a, float* bins, int bins
   for (int b = blockIdx.y * kBinRows + warp; b < b_end; b += nw) {
     const long long r0 = S.w_rowptr[b], r1 = S.w_rowptr[b + 1];
     const int c0 = S.w_col0[b];
+    if constexpr (HR2_BOUNDS_CHECK) {
+      // the row's weights and the F+ points it reads
+      if (!bounds_ok(r0 >= 0 && r1 >= r0 && r1 <= S.w_nnz && c0 >= 0 && c0 + (r1 - r0) <= S.n_nu &&
+                         S.n_nu <= a.highres_ld && b < bins_ld,
+                     lane == 0 ? a.err : nullptr))
+        continue;
+    }
     float acc[kBinGroup];
 #pragma unroll
     for (int k = 0; k < kBinGroup; ++k) acc[k] = 0.f;

@@ -442,6 +442,32 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
                                            const v2* sMnl, const v2* sImu, const v2* sMu, int gs,
                                            const WarpPipe& wp_, unsigned& phase_base) {
   const int lane = threadIdx.x & 31;
+  if constexpr (HR2_BOUNDS_CHECK) {
+    // the item's output row, wavenumber constants, records and table or
+    // operand blocks, for every level, checked before anything is read or
+    // any copy issued
+    bool ok = i >= 0 && i < a.n && S.n_nu <= a.highres_ld && tile >= 0 && tile < S.n_tiles &&
+              S.n_lev <= a.rec_ld && S.n_species <= HR2_MAX_SPECIES;
+    if constexpr (CACHED) {
+      const long long cell_f = (long long)(S.n_species + 2) * 2 * kTileNu;
+      const int nTc = T.n_T - 1;
+      for (int j = lane; ok && j < S.n_lev; j += 32) {
+        const LevRecC r = reinterpret_cast<const LevRecC*>(a.recs + (size_t)i * a.rec_ld)[j];
+        ok = S.lvl32 != nullptr && r.acell >= 0 && r.acell < nTc &&
+             (long long)r.lvl_off == ((long long)j * nTc + r.acell) * cell_f &&
+             (long long)r.lvl_off + cell_f <= S.lvl32_tile_floats;
+      }
+    } else {
+      ok = ok && (long long)(S.tile0 + tile + 1) * kTileNu <= T.nu_pad;
+      for (int j = lane; ok && j < S.n_lev; j += 32) {
+        const LevRec r = a.recs[(size_t)i * a.rec_ld + j];
+        ok = r.acell >= 0 && r.acell <= T.n_T - 2 && r.rowoff >= 0 && r.rowoff / T.n_p == r.acell &&
+             r.rowoff % T.n_p <= T.n_p - 2;
+      }
+      for (int s = 0; s < S.n_species; ++s) ok = ok && S.species[s] >= 0 && S.species[s] < T.n_species;
+    }
+    if (!bounds_ok(__all_sync(0xffffffffu, ok), lane == 0 ? a.err : nullptr)) return;
+  }
   const SampleDev& sd = a.samp[i];
   float* out = a.highres + (size_t)i * a.highres_ld;
   const int col = (S.tile0 + tile) * kTileNu + 2 * lane;  // table column of pair 0's first point
@@ -546,7 +572,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       if (!mbar_wait(wp_.bar + stg, par, a.wait_limit)) {
         // the stage never completed: report, drain it (bounded) and stop using
         // this warp's pipeline
-        if (lane == 0 && a.err) atomicOr(a.err, 1);
+        if (lane == 0 && a.err) atomicOr(a.err, kErrWait);
         mbar_wait(wp_.bar + stg, par, max(a.wait_limit, kDrainMinCycles));
         phase_base = 0xffffffffu;
         return;

@@ -16,9 +16,10 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libhr2.so")
+# HR2_LIBRARY selects another build of the same library (the bounds-checked one)
+LIB_PATH = os.environ.get("HR2_LIBRARY") or os.path.join(_HERE, "libhr2.so")
 
-HR2_OK, HR2_EINVAL, HR2_ENOMEM, HR2_ECUDA, HR2_ETIMEDOUT, HR2_EBUSY = 0, -1, -2, -3, -4, -5
+HR2_OK, HR2_EINVAL, HR2_ENOMEM, HR2_ECUDA, HR2_ETIMEDOUT, HR2_EBUSY, HR2_EBOUNDS = 0, -1, -2, -3, -4, -5, -6
 HR2_SAMPLE_BAD_T, HR2_SAMPLE_BAD_ABUND, HR2_SAMPLE_BAD_SCALE, HR2_SAMPLE_BAD_SETUP = 1, 2, 4, 8
 HR2_SAMPLE_BAD_CLOUD = 16
 HR2_MAX_TNODES, HR2_MAX_SPECIES, HR2_MAX_MU, HR2_MAX_LEVELS, HR2_MAX_SETUPS = 16, 16, 8, 256, 32
