@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--sweep-nu", type=int, default=290001, help="wavenumber points of the swept tables")
     p.add_argument("--sweep-modes", default="direct,cached")
     p.add_argument("--sweep-batches", default="1,2,4,8,16,32,64,128,256")
+    p.add_argument("--sweep-reps", type=int, default=0,
+                   help="timed launches per sweep point (0: about 0.3 s worth, at least 3)")
     p.add_argument("--no-large", action="store_true",
                    help="skip the 290001-point, 12-absorber table measurements (batch 1 and 256)")
     p.add_argument("--peaks", action="store_true",
@@ -636,7 +638,7 @@ def large_counters() -> Optional[dict]:
 
 
 def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1, 256), print_lines=False,
-                      target_s=0.3):
+                      target_s=0.3, fixed_reps=0):
     """Batch sweep on the 290001-point, 12-absorber FP16 tables (2.09 GB): the direct FP16
     interpolation and the level-gridded operand, event-timed kernel per (mode, batch) with the
     SM clock sampled during each, to show where HBM binds (small batches) and where the ALU
@@ -678,7 +680,7 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
                 t0 = time.perf_counter()
                 eng.forward([h], sd, th, bins)
                 torch.cuda.synchronize()
-                reps = int(min(200, max(3, target_s / max(time.perf_counter() - t0, 1e-5))))
+                reps = fixed_reps or int(min(200, max(3, target_s / max(time.perf_counter() - t0, 1e-5))))
                 cs = ClockSampler(local)
                 cs.start()
                 hr2.hr2_profile_read(eng.ctx, True)
@@ -711,7 +713,7 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
 def run_sweep_large(args, local):
     modes = tuple(m for m in args.sweep_modes.split(",") if m)
     batches = tuple(int(b) for b in args.sweep_batches.split(",") if b)
-    return large_table_sweep(local, args.sweep_nu, modes, batches, print_lines=True)
+    return large_table_sweep(local, args.sweep_nu, modes, batches, print_lines=True, fixed_reps=args.sweep_reps)
 
 
 UNIT_KINDS = (("ex2_rcp", 0), ("rcp", 1), ("ex2", 2), ("ffma", 3), ("ffma2", 4))
