@@ -659,7 +659,11 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
     counters = large_counters() if n_nu == 290001 else None
     with Engine(local) as eng:
         t = eng.add_tables(wl.table, "fp16")
+        # "direct": the FP16 tables read in place (batches up to the context's split_max_batch
+        # in two passes), "direct1": the same in one pass always, "cached": the level-gridded
+        # operand
         setups = {m: eng.add_setup(t, s, level_cache=(m == "cached")) for m in modes}
+        cfg0 = hr2.hr2_get_launch_config(eng.ctx)
         th_all, _ = wl.params(max(batches))
         # algorithmic bytes one model reads: on the direct path the FP16 corners (4 per level
         # and point for each of the K absorbers, 2 for each of the two CIA pairs), the
@@ -669,8 +673,10 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
         n_tiles = (s.nu_first + s.n_nu - 1) // 128 - s.nu_first // 128 + 1
         algo = {"direct": (s.n_layers + 1) * 4 * s.n_nu * (len(s.species) + 1) * 2,
                 "cached": (s.n_layers + 1) * n_tiles * 128 * (len(s.species) + 2) * 8}
+        algo["direct1"] = algo["direct"]
         for mode, h in setups.items():
             per_model_bytes = algo[mode]
+            hr2.hr2_set_launch_config(eng.ctx, *cfg0[:4], 0 if mode == "direct1" else cfg0[4])
             for b in batches:
                 th = torch.as_tensor(th_all[:b], device=dev)
                 sd = torch.zeros(b, dtype=torch.int32, device=dev)
@@ -692,13 +698,14 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
                 clk = cs.stop()
                 ms, n = hr2.hr2_profile_read(eng.ctx, True)
                 ms /= max(n, 1)
-                line = {"workload": wl.name, "mode": mode, "batch": b, "kernel_ms": ms, "reps": reps,
+                passes = 2 if mode != "cached" and b <= hr2.hr2_get_launch_config(eng.ctx)[4] else 1
+                line = {"workload": wl.name, "mode": mode, "batch": b, "passes": passes, "kernel_ms": ms, "reps": reps,
                         "models_per_s": b / (ms / 1e3),
                         "algorithmic_bytes_per_model": per_model_bytes,
                         "algorithmic_gbs": b * per_model_bytes / (ms / 1e3) / 1e9,
                         "algorithmic_hbm_frac": b * per_model_bytes / (ms / 1e3) / 1e9 / hbm_peak,
                         "clocks": clk}
-                key = "%s_b%d" % (mode, b)
+                key = "%s_b%d" % ("direct" if mode == "direct1" and passes == 1 else mode, b)
                 if counters and key in counters.get("dram_bytes_per_launch", {}):
                     dram = counters["dram_bytes_per_launch"][key]
                     line.update({"dram_bytes_per_launch": dram, "dram_gbs": dram / (ms / 1e3) / 1e9,

@@ -205,7 +205,7 @@ typedef struct {
 
 /* Launch shape of the persistent forward kernel: the work item's tile
  * (samples x wavenumbers), the persistent grid and the copy-pipeline depth
- * (chosen by the autotuner; a new context starts with {2, 8, 1, 0}).  Every
+ * (chosen by the autotuner; a new context starts with {2, 8, 1, 0, 2}).  Every
  * shape computes each (sample, wavenumber) the same way: results do not
  * depend on it. */
 typedef struct {
@@ -220,6 +220,15 @@ typedef struct {
                                  where the kernel exists in both depths (more
                                  than 4 angle nodes, 8 or more absorbers, linear
                                  source), else the batch-shape choice stands    */
+  int split_max_batch;        /* setups read from the FP16 tables in place
+                                 (no level-gridded operand), linear source:
+                                 batches of at most this many samples run in
+                                 two passes -- every level's absorption
+                                 coefficient first, one warp per (sample, level,
+                                 tile), then the level sweep -- which keeps many
+                                 more table reads in flight; same results bit
+                                 for bit, n x levels x columns x 4 bytes of
+                                 workspace; 0 = never, at most 65535            */
 } hr2_launch_cfg;
 
 /* ------------------------------------------------------------- contexts */
@@ -381,7 +390,8 @@ int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2_setup* con
 /* -------------------------------------------------------- instrumentation
  * (No counterpart in the paper.)  While enabled, every forward_model_batch
  * records a pair of CUDA events on its stream around the launch of the main
- * forward kernel (k_forward32 / k_forward64), so a caller can time that
+ * forward kernel (k_forward32 / k_forward64; with the two-pass direct path,
+ * around both passes), so a caller can time that
  * kernel alone inside a longer step.  hr2_profile_read waits for the
  * recorded events, returns the summed kernel time in ms and the number of
  * launches, and with reset != 0 forgets them. */

@@ -22,22 +22,26 @@ from typing import Dict, Iterable, List, Optional, Sequence, Tuple
 
 from . import hr2
 
-Shape = Tuple[int, int, int, int]          # (warps_per_cta, ctas_per_sm, tiles_per_item, stages)
+Shape = Tuple[int, int, int, int, int]     # (warps_per_cta, ctas_per_sm, tiles_per_item, stages, split_max_batch)
 
 #: (warps per CTA, CTAs per SM) pairs tried
 GRIDS: Tuple[Tuple[int, int], ...] = ((1, 16), (2, 6), (2, 8), (4, 3), (4, 4), (8, 2), (16, 1))
 #: wavenumber tiles per work item tried
 TILES_PER_ITEM: Tuple[int, ...] = (1, 2, 4)
-DEFAULT_SHAPE: Shape = (2, 8, 1, 0)
+DEFAULT_SHAPE: Shape = (2, 8, 1, 0, 2)
 
 
-def candidates_for(setups_info: Sequence[Dict]) -> List[Shape]:
-    """Candidate shapes for a batch: every grid with every item width, at the pipeline depth
-    chosen by batch shape (0); with more than 4 angle nodes and 8 or more absorbers (where the
-    level-gridded kernel exists with one and with two stages) both depths as well."""
+def candidates_for(setups_info: Sequence[Dict], n: Optional[int] = None) -> List[Shape]:
+    """Candidate shapes for a batch of n samples: every grid with every item width, at the
+    pipeline depth chosen by batch shape (0); with more than 4 angle nodes and 8 or more
+    absorbers (where the level-gridded kernel exists with one and with two stages) both depths
+    as well; with setups that read the FP16 tables in place, the batch in one pass and in two
+    (split_max_batch 0, or the batch-size bucket)."""
     both = any(int(s["n_mu"]) > 4 and int(s["K"]) >= 8 and int(s.get("cached", 1)) for s in setups_info)
     stages = (0, 1, 2) if both else (0,)
-    return [(w, c, t, st) for (w, c), t, st in itertools.product(GRIDS, TILES_PER_ITEM, stages)]
+    direct = any(not int(s.get("cached", 1)) for s in setups_info)
+    splits = (0, 1 << max(0, int(n or 1) - 1).bit_length()) if direct else (DEFAULT_SHAPE[4],)
+    return [(w, c, t, st, sp) for (w, c), t, st, sp in itertools.product(GRIDS, TILES_PER_ITEM, stages, splits)]
 
 
 _LOCK = threading.Lock()
@@ -105,7 +109,8 @@ def tune(ctx, setups: Sequence, setup_of_sample, params, out_bins, setups_info: 
         best = _as_shape(cache[key])
         hr2.hr2_set_launch_config(ctx, *best)
         return best, {}
-    cands = [_as_shape(c) for c in (candidates if candidates is not None else candidates_for(setups_info))]
+    cands = [_as_shape(c) for c in (candidates if candidates is not None
+                                     else candidates_for(setups_info, int(params.shape[0])))]
     timings = {}
     for c in cands:
         hr2.hr2_set_launch_config(ctx, *c)

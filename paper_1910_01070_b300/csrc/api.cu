@@ -52,6 +52,8 @@ struct Workspace {
   double* io_logeps = nullptr;
   double* io_lnl = nullptr;
   float* io_bins = nullptr;
+  float* chi = nullptr;       // two-pass direct path: absorption coefficients
+  size_t chi_cap = 0;         // floats
 };
 
 struct hr2_ctx {
@@ -59,7 +61,7 @@ struct hr2_ctx {
   int n_sm = 0;
   size_t budget = 0;
   size_t used = 0;
-  hr2_launch_cfg cfg{2, 8, 1, 0};
+  hr2_launch_cfg cfg{2, 8, 1, 0, kDefaultSplitMaxBatch};
   long long wait_limit = kDefaultWaitCycles;   // bounded device-side waits, SM clock cycles
   bool wait_fault = false;                     // test hook: first stages wait for bytes that never come
   std::mutex mu;
@@ -140,6 +142,7 @@ static void ws_free(hr2_ctx* ctx, Workspace* w) {
   dfree(ctx, w->io_logeps);
   dfree(ctx, w->io_lnl);
   dfree(ctx, w->io_bins);
+  dfree(ctx, w->chi);
   unsigned int* keep = w->h_counter;
   *w = Workspace();
   w->h_counter = keep;
@@ -212,6 +215,23 @@ bad:
   return rc;
 }
 
+// The workspace's absorption-coefficient buffer of the two-pass direct path,
+// grown to at least `floats` (outside stream capture).
+static int ws_ensure_chi(hr2_ctx* ctx, cudaStream_t stream, Workspace* w, size_t floats) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (w->chi_cap >= floats) return HR2_OK;
+  if (stream_capturing(stream))
+    return fail(HR2_EBUSY, "the two-pass buffer must grow while the stream is capturing; call the batch once first");
+  HR2_CU(cudaStreamSynchronize(stream));
+  dfree(ctx, w->chi);
+  w->chi = nullptr;
+  w->chi_cap = 0;
+  int rc = dalloc_t(ctx, &w->chi, floats);
+  if (rc) return rc;
+  w->chi_cap = floats;
+  return HR2_OK;
+}
+
 // ------------------------------------------------------------ contexts
 extern "C" int hr2_ctx_create(int device, size_t mem_budget_bytes, hr2_ctx** out) {
   if (!out) return fail(HR2_EINVAL, "out is NULL");
@@ -276,6 +296,8 @@ extern "C" int hr2_set_launch_config(hr2_ctx* ctx, const hr2_launch_cfg* cfg) {
   if (cfg->tiles_per_item < 1 || cfg->tiles_per_item > 16)
     return fail(HR2_EINVAL, "tiles_per_item %d outside 1..16", cfg->tiles_per_item);
   if (cfg->stages < 0 || cfg->stages > 2) return fail(HR2_EINVAL, "stages %d is not 0, 1 or 2", cfg->stages);
+  if (cfg->split_max_batch < 0 || cfg->split_max_batch > 65535)   // the absorption pass puts the batch on grid z
+    return fail(HR2_EINVAL, "split_max_batch %d outside 0..65535", cfg->split_max_batch);
   ctx->cfg = *cfg;
   return HR2_OK;
 }
@@ -853,6 +875,7 @@ extern "C" int hr2_setup_destroy(hr2_ctx* ctx, hr2_setup* s) {
 // ------------------------------------------------------------ batch calls
 struct BatchShape {
   int max_lev = 0, max_nu = 0, max_bins = 0, max_mu = 0, max_k = 0, min_k = 1 << 30, storage = 0, cached = 0;
+  int max_tiles = 0;
   int linear = 0, para = 0;
 };
 
@@ -879,6 +902,7 @@ static int check_setups(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setu
     sh->max_mu = std::max(sh->max_mu, s->host.n_mu);
     sh->max_k = std::max(sh->max_k, s->host.n_species);
     sh->min_k = std::min(sh->min_k, s->host.n_species);
+    sh->max_tiles = std::max(sh->max_tiles, s->host.n_tiles);
   }
   sh->storage = t0->host.storage;
   sh->cached = setups[0]->host.cached;
@@ -998,8 +1022,18 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
     a.highres_ld = out_highres ? highres_ld : w->nu_cap;
     if ((e = launch_plan(a, w->perm, w->plan, s)) != cudaSuccess)
       return fail(HR2_ECUDA, "plan launch: %s", cudaGetErrorString(e));
-    const int grid = ctx->n_sm * ls.ctas_per_sm;
+    // (the profiling events bracket both passes of the two-pass path)
     if (ev.first) HR2_CU(cudaEventRecord(ev.first, s));
+    // small batches on tables read in place: the absorption coefficients of
+    // every level first, in parallel, then the sweep
+    if (!sh.cached && !sh.para && n <= ctx->cfg.split_max_batch) {
+      a.chi_ld = (long long)sh.max_tiles * kTileNu;
+      if ((rc = ws_ensure_chi(ctx, s, w, (size_t)n * w->lev_cap * a.chi_ld))) return rc;
+      a.chi = w->chi;
+      if ((e = launch_chi_direct(a, sh.max_lev, sh.max_tiles, s)) != cudaSuccess)
+        return fail(HR2_ECUDA, "absorption pass launch: %s", cudaGetErrorString(e));
+    }
+    const int grid = ctx->n_sm * ls.ctas_per_sm;
     if ((e = launch_forward32(a, sh.max_mu, grid, sh.cached != 0, sh.linear != 0, sh.para != 0, sh.max_k, absorber_bound(sh),
                               ls.stages, s)) != cudaSuccess)
       return fail(HR2_ECUDA, "forward32 launch: %s", cudaGetErrorString(e));

@@ -288,9 +288,16 @@ struct FwdArgs {
   // through the constant cache instead of shared memory
   unsigned long long node_im[HR2_MAX_SETUPS][HR2_MAX_MU];
   unsigned long long node_lw[HR2_MAX_SETUPS][HR2_MAX_MU];
+  // two-pass direct path (small batches on FP16 tables without the operand):
+  // absorption coefficients [n][rec_ld levels][chi_ld setup-local columns],
+  // written by k_chi_direct and read by the sweep; null otherwise
+  float* chi;
+  long long chi_ld;
 };
 // default of the context's wait limit: ~1 s of SM clock
 constexpr long long kDefaultWaitCycles = 2000000000ll;
+// default of the largest batch the direct path evaluates in two passes
+constexpr int kDefaultSplitMaxBatch = 2;
 
 // Launchers (kern_*.cu).
 cudaError_t launch_prep(const FwdArgs& a, cudaStream_t s);
@@ -315,6 +322,8 @@ HR2_DECLARE_FWD32(8)
 size_t forward32_smem_bytes(int warps, int max_k, int stages);
 cudaError_t launch_forward64(const FwdArgs& a, int max_nmu, int max_nu, cudaStream_t s);
 cudaError_t launch_bins(const FwdArgs& a, float* bins, int bins_ld, bool fp64, cudaStream_t s);
+// first pass of the two-pass direct path: chi of every (sample, level, tile)
+cudaError_t launch_chi_direct(const FwdArgs& a, int max_lev, int max_tiles, cudaStream_t s);
 struct LnlArgs {
   const SetupDev* setups[HR2_MAX_SETUPS];
   int n_setups;

@@ -376,6 +376,60 @@ cudaError_t launch_plan(const FwdArgs& a, int* perm, PlanDev* plan, cudaStream_t
 
 size_t forward32_smem_bytes(int warps, int max_k, int stages) { return (size_t)warps * warp_pipe_bytes(max_k, stages); }
 
+// ------------------------------------------------------- two-pass direct path
+// First pass for small batches on FP16 tables read in place: every level's
+// absorption coefficient chi, for all levels and tiles of a sample at once
+// (one warp per (sample, level, tile): far more warps than one per tile have
+// table reads in flight), with the sweep's own arithmetic (direct_level_chi),
+// so that the second pass -- the level sweep reading chi back -- gives the
+// one-pass result bit for bit.  A CTA holds four consecutive levels of one
+// sample and tile, and the tile is the grid's fastest index: the CTAs in
+// flight at one time take neighbouring tiles of the same levels, so they
+// read the same table rows (few distinct pages) at neighbouring columns.
+__global__ void __launch_bounds__(128) k_chi_direct(FwdArgs a) {
+  __shared__ const void* sPtr[HR2_MAX_SPECIES];
+  __shared__ v2 sA2[HR2_MAX_SPECIES], sAc2[HR2_MAX_SPECIES];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.z, tile = blockIdx.x, j = blockIdx.y * 4 + warp;
+  const SampleDev& sd = a.samp[i];
+  const int g = sd.setup;
+  if (g < 0 || g >= a.n_setups || sd.status != 0) return;   // the same for the whole CTA
+  const SetupDev& S = *a.setups[g];
+  if (tile >= S.n_tiles) return;
+  const TablesDev& T = *S.tables;
+  if (threadIdx.x < S.n_species) {
+    sPtr[threadIdx.x] = T.sig16 + (size_t)S.species[threadIdx.x] * T.n_T * T.n_p * T.nu_pad;
+    sA2[threadIdx.x] = pk(sd.A[threadIdx.x]);
+    sAc2[threadIdx.x] = pk(sd.Ac[threadIdx.x]);
+  }
+  __syncthreads();
+  if (j >= S.n_lev) return;
+  const LevRec* rec = a.recs + (size_t)i * a.rec_ld;
+  if constexpr (HR2_BOUNDS_CHECK) {
+    const LevRec r = rec[j];
+    bool ok = S.n_lev <= a.rec_ld && (long long)(tile + 1) * kTileNu <= a.chi_ld &&
+              (long long)(S.tile0 + tile + 1) * kTileNu <= T.nu_pad && r.acell >= 0 && r.acell <= T.n_T - 2 &&
+              r.rowoff >= 0 && r.rowoff / T.n_p == r.acell && r.rowoff % T.n_p <= T.n_p - 2;
+    for (int s = 0; s < S.n_species; ++s) ok = ok && S.species[s] >= 0 && S.species[s] < T.n_species;
+    if (!bounds_ok(ok, lane == 0 ? a.err : nullptr)) return;
+  }
+  const float4* q = reinterpret_cast<const float4*>(rec) + 4 * j;
+  const float4 r0 = __ldg(q), r1 = __ldg(q + 1), r2 = __ldg(q + 2);
+  const int col = (S.tile0 + tile) * kTileNu + 2 * lane;
+  v2 chi[kPairs];
+  direct_level_chi(T, S.n_species, col, r0, r1, r2, sA2, sAc2, sPtr, T.has_cia[0] != 0, T.has_cia[1] != 0, chi);
+  float* out = a.chi + ((size_t)i * a.rec_ld + j) * a.chi_ld + (size_t)tile * kTileNu + 2 * lane;
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) *reinterpret_cast<v2*>(out + 64 * p) = chi[p];
+}
+
+cudaError_t launch_chi_direct(const FwdArgs& a, int max_lev, int max_tiles, cudaStream_t s) {
+  if (a.n <= 0) return cudaSuccess;
+  const dim3 grid(max_tiles, (max_lev + 3) / 4, a.n);
+  k_chi_direct<<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_forward32(const FwdArgs& a, int max_nmu, int grid, bool cached, bool linear, bool para, int max_k,
                              int kt, int stages, cudaStream_t s) {
   switch (max_nmu) {

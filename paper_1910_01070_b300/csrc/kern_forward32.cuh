@@ -430,6 +430,72 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
   hdp_prev = half_dp;
 }
 
+// Absorption coefficient chi of one level for the lane's pairs (table column
+// col of pair 0), read from the FP16 tables in place (the direct path): the
+// level record's quarters r0..r2 give the (T, p) corner row, the weights and
+// the CIA terms; sA2 / sAc2 the sample's absorber exponents and tails, sPtr
+// the absorbers' tables.  log10 sigma is bilinear in (T, log10 p), written as
+// corner 00 plus weighted differences (exact partition of unity); two species
+// per step, the lane's pairs in parallel; then both CIA pairs.
+__device__ __forceinline__ void direct_level_chi(const TablesDev& T, int K, int col, const float4 r0, const float4 r1,
+                                                 const float4 r2, const v2* sA2, const v2* sAc2,
+                                                 const void* const* sPtr, bool cia0, bool cia1, v2 (&chi)[kPairs]) {
+  const int nu_pad = T.nu_pad;
+  const unsigned o10 = (unsigned)(T.n_p * nu_pad);
+  const __half* __restrict__ ciab0 = T.cia16;
+  const __half* __restrict__ ciab1 = T.cia16 + (size_t)T.n_T * nu_pad;
+  const v2 L2hi = pk(kL2Hi), L2lo = pk(kL2Lo);
+  const v2 wT = pk(r0.y);
+  const unsigned rb00 = (unsigned)__float_as_int(r0.x) * (unsigned)nu_pad + (unsigned)col;
+  const unsigned rb10 = rb00 + o10, rb01 = rb00 + (unsigned)nu_pad, rb11 = rb10 + (unsigned)nu_pad;
+  const v2 wp = pk(r0.z), wq = pk(r0.w);
+  v2 chA[kPairs], chB[kPairs];
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) chA[p] = chB[p] = pk(0.f);
+  for (int s = 0; s < K; s += 2) {
+    const bool two = s + 1 < K;
+    const __half* b = static_cast<const __half*>(sPtr[s]);
+    const __half* c = static_cast<const __half*>(sPtr[two ? s + 1 : s]);
+    const v2 A0 = sA2[s], Ac0 = sAc2[s];
+    const v2 A1 = sA2[two ? s + 1 : s], Ac1 = two ? sAc2[s + 1] : pk(0.f);
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+      const unsigned o = 64u * (unsigned)p;
+      const v2 f00 = h2f2(ldh2(b + rb00 + o)), f10 = h2f2(ldh2(b + rb10 + o));
+      const v2 f01 = h2f2(ldh2(b + rb01 + o)), f11 = h2f2(ldh2(b + rb11 + o));
+      const v2 g00 = h2f2(ldh2(c + rb00 + o)), g10 = h2f2(ldh2(c + rb10 + o));
+      const v2 g01 = h2f2(ldh2(c + rb01 + o)), g11 = h2f2(ldh2(c + rb11 + o));
+      const v2 d01 = sub2(f01, f00), e01 = sub2(g01, g00);
+      const v2 d11 = sub2(sub2(f11, f10), d01), e11 = sub2(sub2(g11, g10), e01);
+      const v2 l = fma2(wq, d11, fma2(wp, d01, fma2(wT, sub2(f10, f00), f00)));
+      const v2 m = fma2(wq, e11, fma2(wp, e01, fma2(wT, sub2(g10, g00), g00)));
+      const v2 el = fma2(L2lo, l, fma2(L2hi, l, A0));
+      const v2 em = fma2(L2lo, m, fma2(L2hi, m, A1));
+      chA[p] = fma2(Ac0, ex2_2(el), chA[p]);
+      chB[p] = fma2(Ac1, ex2_2(em), chB[p]);   // zero weight when K is odd and s = K - 1
+    }
+  }
+  if (cia0 || cia1) {
+    const unsigned cb = (unsigned)__float_as_int(r2.x) * (unsigned)nu_pad + (unsigned)col;
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) {
+      const unsigned o = 64u * (unsigned)p;
+      if (cia0) {
+        const v2 c0 = h2f2(ldh2(ciab0 + cb + o)), c1 = h2f2(ldh2(ciab0 + cb + nu_pad + o));
+        const v2 l = fma2(wT, sub2(c1, c0), c0);
+        chB[p] = fma2(pk(r2.z), ex2_2(fma2(L2lo, l, fma2(L2hi, l, pk(r1.x)))), chB[p]);
+      }
+      if (cia1) {
+        const v2 c0 = h2f2(ldh2(ciab1 + cb + o)), c1 = h2f2(ldh2(ciab1 + cb + nu_pad + o));
+        const v2 l = fma2(wT, sub2(c1, c0), c0);
+        chA[p] = fma2(pk(r2.w), ex2_2(fma2(L2lo, l, fma2(L2hi, l, pk(r1.y)))), chA[p]);
+      }
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
+}
+
 // One warp computes one sample on one kTileNu-point wavenumber tile
 // (kPairs packed pairs per lane), sweeping the levels from the top (j = 0)
 // to the bottom (j = L).  CACHED: absorber rows come from the setup's
@@ -684,69 +750,21 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
     }
     phase_base = ph + (unsigned)(L + 1);
   } else {
-    const int nu_pad = T.nu_pad;
-    const unsigned o10 = (unsigned)(T.n_p * nu_pad);
-    const __half* __restrict__ ciab0 = T.cia16;
-    const __half* __restrict__ ciab1 = T.cia16 + (size_t)T.n_T * nu_pad;
-    const v2 L2hi = pk(kL2Hi), L2lo = pk(kL2Lo);
     const float4* rp = reinterpret_cast<const float4*>(rec);
+    // the two-pass path (small batches): the absorption coefficients of every
+    // level were computed by k_chi_direct with the same arithmetic
+    const float* chi_in = a.chi ? a.chi + (size_t)i * a.rec_ld * a.chi_ld + (size_t)tile * kTileNu + 2 * lane
+                                : nullptr;
     for (int j = 0; j <= L; ++j) {
       const float4* q = rp + 4 * j;
       const float4 r0 = __ldg(q), r1 = __ldg(q + 1), r2 = __ldg(q + 2), r3 = __ldg(q + 3);
-      const v2 wT = pk(r0.y);
-      const unsigned rb00 = (unsigned)__float_as_int(r0.x) * (unsigned)nu_pad + (unsigned)col;
-      const unsigned rb10 = rb00 + o10, rb01 = rb00 + (unsigned)nu_pad, rb11 = rb10 + (unsigned)nu_pad;
-      const v2 wp = pk(r0.z), wq = pk(r0.w);
-      v2 chA[kPairs], chB[kPairs];
-#pragma unroll
-      for (int p = 0; p < kPairs; ++p) chA[p] = chB[p] = pk(0.f);
-      // log10 sigma: bilinear in (T, log10 p) written as corner 00 plus weighted
-      // differences (exact partition of unity); two species per step, the
-      // pairs of the lane in parallel
-      int s = 0;
-      for (; s < K; s += 2) {
-        const bool two = s + 1 < K;
-        const __half* b = static_cast<const __half*>(sPtr[s]);
-        const __half* c = static_cast<const __half*>(sPtr[two ? s + 1 : s]);
-        const v2 A0 = sA2[s], Ac0 = sAc2[s];
-        const v2 A1 = sA2[two ? s + 1 : s], Ac1 = two ? sAc2[s + 1] : pk(0.f);
-#pragma unroll
-        for (int p = 0; p < kPairs; ++p) {
-          const unsigned o = 64u * (unsigned)p;
-          const v2 f00 = h2f2(ldh2(b + rb00 + o)), f10 = h2f2(ldh2(b + rb10 + o));
-          const v2 f01 = h2f2(ldh2(b + rb01 + o)), f11 = h2f2(ldh2(b + rb11 + o));
-          const v2 g00 = h2f2(ldh2(c + rb00 + o)), g10 = h2f2(ldh2(c + rb10 + o));
-          const v2 g01 = h2f2(ldh2(c + rb01 + o)), g11 = h2f2(ldh2(c + rb11 + o));
-          const v2 d01 = sub2(f01, f00), e01 = sub2(g01, g00);
-          const v2 d11 = sub2(sub2(f11, f10), d01), e11 = sub2(sub2(g11, g10), e01);
-          const v2 l = fma2(wq, d11, fma2(wp, d01, fma2(wT, sub2(f10, f00), f00)));
-          const v2 m = fma2(wq, e11, fma2(wp, e01, fma2(wT, sub2(g10, g00), g00)));
-          const v2 el = fma2(L2lo, l, fma2(L2hi, l, A0));
-          const v2 em = fma2(L2lo, m, fma2(L2hi, m, A1));
-          chA[p] = fma2(Ac0, ex2_2(el), chA[p]);
-          chB[p] = fma2(Ac1, ex2_2(em), chB[p]);   // zero weight when K is odd and s = K - 1
-        }
-      }
-      if (cia0 || cia1) {
-        const unsigned cb = (unsigned)__float_as_int(r2.x) * (unsigned)nu_pad + (unsigned)col;
-#pragma unroll
-        for (int p = 0; p < kPairs; ++p) {
-          const unsigned o = 64u * (unsigned)p;
-          if (cia0) {
-            const v2 c0 = h2f2(ldh2(ciab0 + cb + o)), c1 = h2f2(ldh2(ciab0 + cb + nu_pad + o));
-            const v2 l = fma2(wT, sub2(c1, c0), c0);
-            chB[p] = fma2(pk(r2.z), ex2_2(fma2(L2lo, l, fma2(L2hi, l, pk(r1.x)))), chB[p]);
-          }
-          if (cia1) {
-            const v2 c0 = h2f2(ldh2(ciab1 + cb + o)), c1 = h2f2(ldh2(ciab1 + cb + nu_pad + o));
-            const v2 l = fma2(wT, sub2(c1, c0), c0);
-            chA[p] = fma2(pk(r2.w), ex2_2(fma2(L2lo, l, fma2(L2hi, l, pk(r1.y)))), chA[p]);
-          }
-        }
-      }
       v2 chi[kPairs];
+      if (chi_in) {
 #pragma unroll
-      for (int p = 0; p < kPairs; ++p) chi[p] = add2(chA[p], chB[p]);
+        for (int p = 0; p < kPairs; ++p) chi[p] = ldf2(chi_in + (size_t)j * a.chi_ld + 64 * p);
+      } else {
+        direct_level_chi(T, K, col, r0, r1, r2, sA2, sAc2, sPtr, cia0, cia1, chi);
+      }
       level_physics<NMU, PARA, SX>(j, chi, r1.z, r3.x, r2.y, pk(r1.w), pk(r3.w), hdp_prev, nc, thin_dtau, sMnl,
                                    sImu, sMu, a, gs, acc, E, st);
     }

@@ -49,8 +49,9 @@ class Engine:
     def set_observation(self, setup, D, sigma):
         hr2.hr2_setup_set_observation(self.ctx, setup, D, sigma)
 
-    def set_launch_config(self, warps_per_cta: int, ctas_per_sm: int, tiles_per_item: int = 1, stages: int = 0):
-        hr2.hr2_set_launch_config(self.ctx, warps_per_cta, ctas_per_sm, tiles_per_item, stages)
+    def set_launch_config(self, warps_per_cta: int, ctas_per_sm: int, tiles_per_item: int = 1, stages: int = 0,
+                          split_max_batch: int = 2):
+        hr2.hr2_set_launch_config(self.ctx, warps_per_cta, ctas_per_sm, tiles_per_item, stages, split_max_batch)
 
     def memory(self):
         return hr2.hr2_ctx_memory(self.ctx)

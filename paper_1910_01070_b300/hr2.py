@@ -78,7 +78,7 @@ HR2_UNIT_EX2_RCP, HR2_UNIT_RCP, HR2_UNIT_EX2, HR2_UNIT_FFMA, HR2_UNIT_FFMA2, HR2
 
 class LaunchCfg(C.Structure):
     _fields_ = [("warps_per_cta", C.c_int), ("ctas_per_sm", C.c_int), ("tiles_per_item", C.c_int),
-                ("stages", C.c_int)]
+                ("stages", C.c_int), ("split_max_batch", C.c_int)]
 
 
 class NsState(C.Structure):
@@ -217,16 +217,17 @@ def hr2_ctx_memory(ctx):
     return u.value, b.value
 
 
-def hr2_set_launch_config(ctx, warps_per_cta: int, ctas_per_sm: int, tiles_per_item: int = 1, stages: int = 0):
-    cfg = LaunchCfg(warps_per_cta, ctas_per_sm, tiles_per_item, stages)
+def hr2_set_launch_config(ctx, warps_per_cta: int, ctas_per_sm: int, tiles_per_item: int = 1, stages: int = 0,
+                          split_max_batch: int = 2):
+    cfg = LaunchCfg(warps_per_cta, ctas_per_sm, tiles_per_item, stages, split_max_batch)
     _check(lib().hr2_set_launch_config(ctx, C.byref(cfg)), ctx)
 
 
 def hr2_get_launch_config(ctx):
-    """(warps_per_cta, ctas_per_sm, tiles_per_item, stages)."""
+    """(warps_per_cta, ctas_per_sm, tiles_per_item, stages, split_max_batch)."""
     cfg = LaunchCfg()
     _check(lib().hr2_get_launch_config(ctx, C.byref(cfg)), ctx)
-    return cfg.warps_per_cta, cfg.ctas_per_sm, cfg.tiles_per_item, cfg.stages
+    return cfg.warps_per_cta, cfg.ctas_per_sm, cfg.tiles_per_item, cfg.stages, cfg.split_max_batch
 
 
 def hr2_reserve(ctx, n: int, n_nu_max: int, stream=None):

@@ -94,8 +94,8 @@ def test_autotune_shape_key_and_cache(tmp_path):
     autotune.save_cache({k1: [4, 4]}, path)
     assert autotune.load_cache(path) == {k1: [4, 4]}
     assert autotune.load_cache(str(tmp_path / "missing.json")) == {}
-    assert autotune.pick_best({(8, 2, 1, 0): 7.0, (4, 4, 1, 0): 6.9, (2, 8, 2, 0): 6.9}) == (2, 8, 2, 0)
-    assert autotune._as_shape([4, 4]) == (4, 4, 1, 0)
+    assert autotune.pick_best({(8, 2, 1, 0, 4): 7.0, (4, 4, 1, 0, 4): 6.9, (2, 8, 2, 0, 4): 6.9}) == (2, 8, 2, 0, 4)
+    assert autotune._as_shape([4, 4]) == (4, 4, 1, 0, autotune.DEFAULT_SHAPE[4])
 
 
 def test_autotune_candidates_span_the_tile_shape():
@@ -104,6 +104,9 @@ def test_autotune_candidates_span_the_tile_shape():
     assert len(few) == len(autotune.GRIDS) * 3 and len(set(few)) == len(few)
     both = autotune.candidates_for([{"K": 12, "L": 100, "n_mu": 8, "n_nu": 290001, "cached": 1}])
     assert {c[3] for c in both} == {0, 1, 2} and len(both) == 3 * len(few)
+    assert {c[4] for c in few} == {autotune.DEFAULT_SHAPE[4]}
+    direct = autotune.candidates_for([{"K": 12, "L": 100, "n_mu": 8, "n_nu": 290001, "cached": 0}], n=3)
+    assert {c[4] for c in direct} == {0, 4} and len(direct) == 2 * len(few)
 
 
 def _rank_main(rank, world, port, out):

@@ -433,6 +433,35 @@ def test_direct_fp16_path_on_uneven_setups(eng):
         _run(eng, [setups[0], direct[1]], np.zeros(2, np.int32), theta[:2])
 
 
+def test_two_pass_direct_path_is_the_one_pass_result(eng):
+    """Small batches on tables read in place run in two passes (every level's absorption
+    coefficient first, then the sweep reading it back) with the one-pass arithmetic: the same
+    spectra bit for bit, for mixed setups, batch sizes around the threshold and a sample with
+    an invalid setup index; and the oracle agrees."""
+    wl, tabs, stored, setups, st = _workload_on(eng, "uneven2048_3setups", "fp16")
+    t = _tables_of("uneven2048_3setups", "fp16")
+    direct = [eng.add_setup(t, s, level_cache=False) for s in wl.setups]
+    theta, sid = wl.params(7, seed_offset=21)
+    sid = sid.copy()
+    sid[5] = -1
+    ld = max(s.n_nu for s in wl.setups)
+    old = hr2.hr2_get_launch_config(eng.ctx)
+    try:
+        eng.set_launch_config(2, 8, 1, 0, 0)
+        one = _run(eng, direct, sid, theta, highres_ld=ld)
+        for m in (1, 3, 7):
+            eng.set_launch_config(2, 8, 1, 0, m)
+            two = _run(eng, direct, sid[:m], theta[:m], highres_ld=ld)
+            for x, y in zip(two, one):
+                assert np.array_equal(x, y[:m], equal_nan=True)
+    finally:
+        eng.set_launch_config(*old)
+    assert one[2][5] == hr2.HR2_SAMPLE_BAD_SETUP and np.all(np.isnan(one[0][5]))
+    for i in (0, 6):
+        g = int(sid[i])
+        _compare(oracle_model(stored, wl.setups[g]), theta[i], one[0][i], one[1][i], FLUX_RTOL, wl.setups[g].n_nu)
+
+
 def test_small_batches_use_every_warp(eng):
     """Batches smaller than a work item (1, 2, 3 samples) give the same results as inside a large batch."""
     wl, tabs, stored, setups, st = _workload_on(eng, "batch1024_l100_k6_nu8501", "fp16")

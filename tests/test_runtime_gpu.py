@@ -53,7 +53,7 @@ def test_autotuner_picks_a_candidate_and_caches_it(uneven, tmp_path):
     th, sd = torch.as_tensor(theta, device="cuda"), torch.as_tensor(sid, device="cuda")
     bins = torch.empty((512, max(s.n_bins for s in wl.setups)), dtype=torch.float32, device="cuda")
     info = [autotune.setup_info_from_spec(s) for s in wl.setups]
-    cands = [(2, 4, 1, 0), (4, 4, 2, 0), (8, 2, 4, 0)]
+    cands = [(2, 4, 1, 0, 4), (4, 4, 2, 0, 4), (8, 2, 4, 0, 4)]
     path = str(tmp_path / "tune.json")
     old = hr2.hr2_get_launch_config(eng.ctx)
     try:
