@@ -296,6 +296,44 @@ def test_optical_depth_closed_form_and_scalings(oracle_lib):
     assert np.allclose(d2, dtau / 2, rtol=1e-12)
 
 
+@pytest.mark.parametrize("sc,cloud", [("linear", False), ("parabolic", False), ("linear", True)])
+def test_forward_flux_is_the_composition_of_its_pinned_steps(oracle_lib, sc, cloud):
+    """F+ of the forward model at every wavenumber (Eq. 8 over the short
+    characteristics of Eqs. 4-7) equals the flux rebuilt here from its steps,
+    each pinned on its own: the layer optical depths (closed forms above), the
+    level temperatures (profile pins), the Planck source (Eq. 2) written here
+    from the exact SI constants, the intensity along each ray (brute force and
+    closed forms above), and numpy's Gauss-Legendre nodes mapped to [0, 1].
+    A slip in how the forward model itself puts these together -- its own
+    optical depth, source or bottom boundary -- fails here even where every
+    step passes alone."""
+    fill = lambda tb: tb["log10_sigma"] - 1.5                # a mix of thin and thick layers
+    m, tabs, setup = _tiny_model(fill=fill, cia=True, n_layers=7, n_mu=4, n_nu=12)
+    if sc != "linear" or cloud:
+        setup.sc = sc
+        setup.cloud = cloud
+        m = oracle.Model(tabs, setup.as_dict())
+    th = _theta([1700.0, 1250.0, 800.0])
+    if cloud:
+        th[35], th[36], th[37] = math.log10(2.5), math.log10(0.01), math.log10(0.1)
+    _, top, ok = m.forward(th, want_top=True)
+    assert ok
+    T, _ = m.level_temperatures(th)
+    x, w = np.polynomial.legendre.leggauss(setup.n_mu)
+    mu, w = 0.5 * (x + 1.0), 0.5 * w
+    intensity = oracle.sc_intensity if sc == "linear" else oracle.sc_intensity_parabolic
+    saw_thin = saw_thick = False
+    for k in range(setup.n_nu):
+        dtau, _ = m.layer_dtau(th, k)
+        saw_thin |= bool(np.any(dtau < 0.05))
+        saw_thick |= bool(np.any(dtau > 1.0))
+        nu = tabs["nu0"] + (setup.nu_first + k) * tabs["dnu"]
+        S = planck_indep(nu, T)
+        F = 2 * math.pi * sum(wk * mk * intensity(dtau, S, S[-1], mk) for wk, mk in zip(w, mu))
+        assert top[k] == pytest.approx(F, rel=1e-10)
+    assert saw_thin and saw_thick
+
+
 def test_cia_enters_quadratically_in_h2(oracle_lib):
     m, tabs, _ = _tiny_model(fill=lambda tb: np.full(tb["log10_sigma"].shape, -300.0), cia=True, species=(0,))
     th = _theta([1500.0, 1200.0, 900.0], logx=(math.log10(0.5),))
