@@ -705,7 +705,8 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
                         "algorithmic_gbs": b * per_model_bytes / (ms / 1e3) / 1e9,
                         "algorithmic_hbm_frac": b * per_model_bytes / (ms / 1e3) / 1e9 / hbm_peak,
                         "clocks": clk}
-                key = "%s_b%d" % ("direct" if mode == "direct1" and passes == 1 else mode, b)
+                # counters per path: "direct2" the two-pass direct path, "direct" the one-pass one
+                key = "%s_b%d" % ("cached" if mode == "cached" else ("direct2" if passes == 2 else "direct"), b)
                 if counters and key in counters.get("dram_bytes_per_launch", {}):
                     dram = counters["dram_bytes_per_launch"][key]
                     line.update({"dram_bytes_per_launch": dram, "dram_gbs": dram / (ms / 1e3) / 1e9,
