@@ -13,9 +13,26 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "hr2_internal.cuh"
 
 using namespace hr2;
+
+// ------------------------------------------------------------ tracing
+// An NVTX range over the host side of an entry point (argument checks,
+// workspace, launches), named after it, so that a timeline profiler (or ncu's
+// --nvtx filter) shows each call over the kernels it launched.  Without a tool
+// attached the push and pop return at once.
+namespace {
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+}  // namespace
+#define HR2_RANGE(name) const NvtxRange hr2_range_(name)
 
 // ------------------------------------------------------------ errors
 static thread_local std::string t_last_error;
@@ -328,6 +345,7 @@ extern "C" int hr2_get_wait_limit(const hr2_ctx* ctx, long long* cycles) {
 }
 
 extern "C" int hr2_reserve(hr2_ctx* ctx, void* stream, int n, int n_nu_max) {
+  HR2_RANGE("hr2_reserve");
   if (!ctx || n < 0 || n_nu_max < 0) return fail(HR2_EINVAL, "invalid argument");
   HR2_CU(cudaSetDevice(ctx->device));
   Workspace* w;
@@ -390,6 +408,7 @@ static int sync_tables_dev(hr2_tables* t) {
 }
 
 extern "C" int hr2_tables_upload_species(hr2_ctx* ctx, hr2_tables* t, int s, const double* v) {
+  HR2_RANGE("hr2_tables_upload_species");
   if (!ctx || !t || !v) return fail(HR2_EINVAL, "NULL argument");
   if (s < 0 || s >= t->host.n_species) return fail(HR2_EINVAL, "species %d outside [0, %d)", s, t->host.n_species);
   HR2_CU(cudaSetDevice(ctx->device));
@@ -408,6 +427,7 @@ extern "C" int hr2_tables_upload_species(hr2_ctx* ctx, hr2_tables* t, int s, con
 
 extern "C" int create_opacity_tables(hr2_ctx* ctx, const hr2_table_desc* d, const double* log10_sigma,
                                      const double* cia_h2h2, const double* cia_h2he, int storage, hr2_tables** out) {
+  HR2_RANGE("create_opacity_tables");
   if (!ctx || !d || !out) return fail(HR2_EINVAL, "NULL argument");
   *out = nullptr;
   if (storage != HR2_STORE_FP16_OFFSET && storage != HR2_STORE_FP64)
@@ -529,6 +549,7 @@ extern "C" int hr2_tables_destroy(hr2_ctx* ctx, hr2_tables* t) {
 
 // ------------------------------------------------------------ setups
 extern "C" int hr2_setup_set_observation(hr2_ctx* ctx, hr2_setup* s, const double* D, const double* sigma) {
+  HR2_RANGE("hr2_setup_set_observation");
   if (!ctx || !s || !D || !sigma) return fail(HR2_EINVAL, "NULL argument");
   for (int b = 0; b < s->n_bins; ++b) {
     if (!std::isfinite(D[b])) return fail(HR2_EINVAL, "obs_flux[%d] is not finite", b);
@@ -556,6 +577,7 @@ extern "C" int hr2_setup_set_observation(hr2_ctx* ctx, hr2_setup* s, const doubl
 }
 
 extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_setup_desc* d, hr2_setup** out) {
+  HR2_RANGE("hr2_setup_create");
   if (!ctx || !tab || !d || !out) return fail(HR2_EINVAL, "NULL argument");
   *out = nullptr;
   const TablesDev& th = tab->host;
@@ -962,6 +984,7 @@ static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {
 extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
                                    const int* setup_of_sample, const double* params, int n, float* out_bins,
                                    int bins_ld, float* out_highres, int highres_ld, int* out_status, void* stream) {
+  HR2_RANGE("forward_model_batch");
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
   if (n < 0) return fail(HR2_EINVAL, "n < 0");
   BatchShape sh;
@@ -1051,6 +1074,7 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
 extern "C" int log_likelihood_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
                                     const int* setup_of_sample, const float* model_bins, int bins_ld,
                                     const double* log_eps, int n, double* out_lnL, void* stream) {
+  HR2_RANGE("log_likelihood_batch");
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
   if (n < 0) return fail(HR2_EINVAL, "n < 0");
   BatchShape sh;
@@ -1095,6 +1119,7 @@ static int check_device_error(const Workspace* w) {
 extern "C" int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
                                  const int* setup_of_sample, const double* params, const double* log_eps, int n,
                                  double* out_lnL, float* out_bins, int bins_ld, void* stream) {
+  HR2_RANGE("hr2_evaluate_host");
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
   if (n < 0) return fail(HR2_EINVAL, "n < 0");
   BatchShape sh;
@@ -1134,6 +1159,7 @@ extern "C" int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* co
 }
 
 extern "C" int hr2_stream_check(hr2_ctx* ctx, void* stream) {
+  HR2_RANGE("hr2_stream_check");
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
   HR2_CU(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
@@ -1152,6 +1178,7 @@ extern "C" int hr2_stream_check(hr2_ctx* ctx, void* stream) {
 extern "C" int hr2_effective_temperature(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
                                          const int* setup_of_sample, const float* highres, int highres_ld, int n,
                                          double* out_teff, void* stream) {
+  HR2_RANGE("hr2_effective_temperature");
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
   if (n < 0) return fail(HR2_EINVAL, "n < 0");
   BatchShape sh;
@@ -1183,6 +1210,7 @@ extern "C" int hr2_ns_state_init(hr2_ctx* ctx, hr2_ns_state* state, void* stream
 extern "C" int hr2_ns_absorb(hr2_ctx* ctx, int n_live, double* live_lnl, double* live_theta, int n_cand,
                              const double* cand_lnl, const double* cand_theta, hr2_ns_state* state, double* dead_lnl,
                              double* dead_logw, double* dead_theta, long long dead_cap, void* stream) {
+  HR2_RANGE("hr2_ns_absorb");
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
   if (n_live < 1 || n_cand < 0 || dead_cap < 0) return fail(HR2_EINVAL, "need n_live >= 1, n_cand >= 0, dead_cap >= 0");
   if (!live_lnl || !live_theta || !state || (n_cand && (!cand_lnl || !cand_theta)) ||
@@ -1198,6 +1226,7 @@ extern "C" int hr2_ns_absorb(hr2_ctx* ctx, int n_live, double* live_lnl, double*
 extern "C" int hr2_ns_propose(hr2_ctx* ctx, int n_live, const double* live_theta, const double* prior_lo,
                               const double* prior_hi, double enlarge, int n, double* box, double* out_theta,
                               unsigned long long seed, unsigned long long counter, void* stream) {
+  HR2_RANGE("hr2_ns_propose");
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
   if (n_live < 1 || n < 0 || !(enlarge >= 0.0)) return fail(HR2_EINVAL, "need n_live >= 1, n >= 0, enlarge >= 0");
   if (!live_theta || !prior_lo || !prior_hi || !box || (n && !out_theta)) return fail(HR2_EINVAL, "NULL argument");
@@ -1210,6 +1239,7 @@ extern "C" int hr2_ns_propose(hr2_ctx* ctx, int n_live, const double* live_theta
 
 extern "C" int hr2_ns_finalize(hr2_ctx* ctx, int n_live, const double* live_lnl, const hr2_ns_state* state,
                                double* out, void* stream) {
+  HR2_RANGE("hr2_ns_finalize");
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
   if (n_live < 1 || !live_lnl || !state || !out) return fail(HR2_EINVAL, "need n_live >= 1 and non-NULL pointers");
   HR2_CU(cudaSetDevice(ctx->device));
@@ -1292,6 +1322,7 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
                                            const int* setup_of_sample, const double* params, int n, float* out_bins,
                                            int bins_ld, float* out_highres, int highres_ld, int* out_status,
                                            void* stream) {
+  HR2_RANGE("forward_model_batch_noalloc");
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
   if (n < 0) return fail(HR2_EINVAL, "n < 0");
   BatchShape sh;
@@ -1350,6 +1381,7 @@ extern "C" int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2
 }
 
 extern "C" int hr2_noalloc_check(hr2_ctx* ctx, void* stream) {
+  HR2_RANGE("hr2_noalloc_check");
   if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
   HR2_CU(cudaSetDevice(ctx->device));
   HR2_CU(cudaStreamSynchronize((cudaStream_t)stream));
