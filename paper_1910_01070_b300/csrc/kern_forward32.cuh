@@ -272,7 +272,7 @@ struct FluxAcc {
 // source, and the layer above it added to the telescoped sum.  SX: some
 // level of this sample may have h c nu / k T < 0.0625 on this tile, where
 // e^{x} - 1 of the Planck function needs its series (decided per item).
-template <int NMU, bool PARA, bool SX>
+template <int NMU, bool PARA, bool SX, bool ONE>
 __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], const float upl, const float rnu,
                                               const float r64, const v2 half_dp, const v2 dtc, v2& hdp_prev,
                                               const NuConst& nc, const float thin_dtau, const v2* sMnl,
@@ -340,7 +340,10 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
     const v2 c2 = pk(-0.5f), c3 = pk(1.f / 6.f);
 #pragma unroll
     for (int k = 0; k < NMU; ++k) {
-      const v2 im = a.node_im[gs][k], lw = a.node_lw[gs][k];   // 1 / mu_k, log2(2 pi w_k mu_k^2)
+      // 1 / mu_k, log2(2 pi w_k mu_k^2); with a single setup in the launch (ONE)
+      // at fixed kernel-parameter offsets, which the arithmetic reads directly
+      const int gk = ONE ? 0 : gs;
+      const v2 im = a.node_im[gk][k], lw = a.node_lw[gk][k];
 #pragma unroll
       for (int p = 0; p < kPairs; ++p) {
         const v2 En = ex2_2(fma2(st[p].tau, im, lw));   // 2 pi w mu^2 e^{-tau_j / mu}
@@ -502,7 +505,7 @@ __device__ __forceinline__ void direct_level_chi(const TablesDev& T, int K, int 
 // level-gridded operand through the warp's bulk-copy pipeline (rows of level
 // j+1 and the record of level j+2 land while level j is computed).
 // Otherwise the FP16 tables are read and interpolated bilinearly in place.
-template <int NMU, bool CACHED, int KT, bool LIN, bool PARA, bool SX, int ST>
+template <int NMU, bool CACHED, int KT, bool LIN, bool PARA, bool SX, int ST, bool ONE>
 __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, const TablesDev& T, int i, int tile,
                                            const v2* sA2, const v2* sAc2, const void* const* sPtr,
                                            const v2* sMnl, const v2* sImu, const v2* sMu, int gs,
@@ -581,7 +584,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
 #pragma unroll
     for (int k = 0; k < FluxAcc<NMU, PARA>::N; ++k) acc[p][k] = pk(0.f);
 #pragma unroll
-    for (int k = 0; k < NMU; ++k) E[p][k] = PARA ? pk(1.f) : ex2_2(a.node_lw[gs][k]);
+    for (int k = 0; k < NMU; ++k) E[p][k] = PARA ? pk(1.f) : ex2_2(a.node_lw[ONE ? 0 : gs][k]);
   }
   LevelState st[kPairs];
 #pragma unroll
@@ -742,7 +745,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
         __syncwarp();   // every lane has read the stage
         refill();
       }
-      level_physics<NMU, PARA, SX>(j, chi, rq2.upl, rq2.rnu, r64, rq1.dg, rq2.dtc, hdp_prev, nc, thin_dtau, sMnl,
+      level_physics<NMU, PARA, SX, ONE>(j, chi, rq2.upl, rq2.rnu, r64, rq1.dg, rq2.dtc, hdp_prev, nc, thin_dtau, sMnl,
                                    sImu, sMu, a, gs, acc, E, st);
       // two stages: every lane is done with stage stg before the next level
       // refills it (one stage: the refill already followed the sync above)
@@ -765,7 +768,7 @@ __device__ __forceinline__ void solve_tile(const FwdArgs& a, const SetupDev& S, 
       } else {
         direct_level_chi(T, K, col, r0, r1, r2, sA2, sAc2, sPtr, cia0, cia1, chi);
       }
-      level_physics<NMU, PARA, SX>(j, chi, r1.z, r3.x, r2.y, pk(r1.w), pk(r3.w), hdp_prev, nc, thin_dtau, sMnl,
+      level_physics<NMU, PARA, SX, ONE>(j, chi, r1.z, r3.x, r2.y, pk(r1.w), pk(r3.w), hdp_prev, nc, thin_dtau, sMnl,
                                    sImu, sMu, a, gs, acc, E, st);
     }
   }
@@ -882,15 +885,35 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
       const int t_end = min(S.n_tiles, (tgrp + 1) * a.tiles_per_item);
       for (int tile = tgrp * a.tiles_per_item; tile < t_end; ++tile) {
         const bool sx = item_small_x(a, S, T, i, tile);
+        // a launch with a single setup runs the sweep with the node constants at
+        // fixed kernel-parameter offsets (g == 0), which the arithmetic reads
+        // directly instead of loading them on every level (level-gridded,
+        // linear source; not in the bounds-checked build)
+        constexpr bool kOneVariant = CACHED && !PARA && !HR2_BOUNDS_CHECK;
+        const bool one = kOneVariant && a.n_setups == 1;
         // a batch compiled for a bound KT >= 8 holds setups with KT-4 .. KT
         // absorbers: each item runs the sweep compiled for its own setup's
         // even bound, so that a setup pads at most one absorber (the linear
         // source; the parabolic one keeps the batch's bound)
-#define HR2_SOLVE(KB)                                                                                              \
-  (sx ? solve_tile<NMU, CACHED, KB, LIN, PARA, true, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, \
-                                                          sMu, g, wp_, phase_base)                               \
-      : solve_tile<NMU, CACHED, KB, LIN, PARA, false, ST>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl,     \
-                                                           sImu, sMu, g, wp_, phase_base))
+#define HR2_SOLVE1(KB, SXV, ONEV)                                                                                   \
+  solve_tile<NMU, CACHED, KB, LIN, PARA, SXV, ST, ONEV>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu, \
+                                                       g, wp_, phase_base)
+#define HR2_SOLVE(KB)                              \
+  do {                                             \
+    if constexpr (kOneVariant) {                   \
+      if (one) {                                   \
+        if (sx)                                    \
+          HR2_SOLVE1(KB, true, true);              \
+        else                                       \
+          HR2_SOLVE1(KB, false, true);             \
+        break;                                     \
+      }                                            \
+    }                                              \
+    if (sx)                                        \
+      HR2_SOLVE1(KB, true, false);                 \
+    else                                           \
+      HR2_SOLVE1(KB, false, false);                \
+  } while (0)
         if constexpr (KT >= 8 && !PARA) {
           const int kc = (S.n_species + 1) & ~1;
           if (kc <= KT - 4)
@@ -903,6 +926,7 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
           HR2_SOLVE(KT);
         }
 #undef HR2_SOLVE
+#undef HR2_SOLVE1
       }
     }
   }
