@@ -418,6 +418,26 @@ def test_uneven_three_setups_sampled_and_alone_equals_mix(eng):
     assert np.array_equal(h2, hi[sub])
 
 
+def test_single_setup_launch_equals_the_mixed_launch(eng):
+    """A launch with one setup runs the sweep compiled with the setup index fixed (the
+    angle-node constants at fixed parameter offsets); the same samples in a launch with
+    several setups run the general sweep.  Same arithmetic: the same bits, for each setup
+    of the uneven batch (6-10 absorbers, 81-121 levels)."""
+    wl, tabs, stored, setups, st = _workload_on(eng, "uneven2048_3setups", "fp16")
+    theta, sid = wl.params(48, seed_offset=31)
+    ld = max(s.n_nu for s in wl.setups)
+    b_mix, h_mix, _ = _run(eng, setups, sid, theta, highres_ld=ld)
+    for g in range(len(setups)):
+        idx = np.nonzero(sid == g)[0]
+        if len(idx) == 0:
+            continue
+        b1, h1, status = _run(eng, [setups[g]], np.zeros(len(idx), np.int32), theta[idx], highres_ld=ld)
+        assert np.all(status == 0)
+        nb = wl.setups[g].n_bins
+        assert np.array_equal(b1[:, :nb], b_mix[idx][:, :nb]), g
+        assert np.array_equal(h1, h_mix[idx]), g
+
+
 def test_direct_fp16_path_on_uneven_setups(eng):
     """The bilinear-in-place FP16 path (no level-gridded operand) on mixed setups."""
     wl, tabs, stored, setups, st = _workload_on(eng, "uneven2048_3setups", "fp16")
