@@ -814,7 +814,7 @@ __device__ __forceinline__ bool item_small_x(const FwdArgs& a, const SetupDev& S
   return __any_sync(0xffffffffu, f);
 }
 
-template <int NMU, bool CACHED, int KT, bool LIN, bool PARA, int ST>
+template <int NMU, bool CACHED, int KT, bool LIN, bool PARA, int ST, bool ONE>
 __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PARA) ? kForwardMinBlocksSmall
                                                                                      : kForwardMinBlocks)
     k_forward32(FwdArgs a, int max_k) {
@@ -885,12 +885,11 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
       const int t_end = min(S.n_tiles, (tgrp + 1) * a.tiles_per_item);
       for (int tile = tgrp * a.tiles_per_item; tile < t_end; ++tile) {
         const bool sx = item_small_x(a, S, T, i, tile);
-        // a launch with a single setup runs the sweep with the node constants at
-        // fixed kernel-parameter offsets (g == 0), which the arithmetic reads
-        // directly instead of loading them on every level (level-gridded,
-        // linear source; not in the bounds-checked build)
-        constexpr bool kOneVariant = CACHED && !PARA && !HR2_BOUNDS_CHECK;
-        const bool one = kOneVariant && a.n_setups == 1;
+        // ONE (a launch with a single setup; chosen by the launcher): the sweep
+        // with the node constants at fixed kernel-parameter offsets (g == 0),
+        // which the arithmetic reads directly instead of loading them on every
+        // level.  A kernel of its own, so that its registers are allocated for
+        // this sweep alone.
         // a batch compiled for a bound KT >= 8 holds setups with KT-4 .. KT
         // absorbers: each item runs the sweep compiled for its own setup's
         // even bound, so that a setup pads at most one absorber (the linear
@@ -898,21 +897,12 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
 #define HR2_SOLVE1(KB, SXV, ONEV)                                                                                   \
   solve_tile<NMU, CACHED, KB, LIN, PARA, SXV, ST, ONEV>(a, S, T, i, tile, sA2[warp], sAc2[warp], sPtr, sMnl, sImu, sMu, \
                                                        g, wp_, phase_base)
-#define HR2_SOLVE(KB)                              \
-  do {                                             \
-    if constexpr (kOneVariant) {                   \
-      if (one) {                                   \
-        if (sx)                                    \
-          HR2_SOLVE1(KB, true, true);              \
-        else                                       \
-          HR2_SOLVE1(KB, false, true);             \
-        break;                                     \
-      }                                            \
-    }                                              \
-    if (sx)                                        \
-      HR2_SOLVE1(KB, true, false);                 \
-    else                                           \
-      HR2_SOLVE1(KB, false, false);                \
+#define HR2_SOLVE(KB)            \
+  do {                           \
+    if (sx)                      \
+      HR2_SOLVE1(KB, true, ONE); \
+    else                         \
+      HR2_SOLVE1(KB, false, ONE); \
   } while (0)
         if constexpr (KT >= 8 && !PARA) {
           const int kc = (S.n_species + 1) & ~1;
@@ -933,7 +923,7 @@ __global__ void __launch_bounds__(kForwardMaxThreads, (CACHED && NMU <= 4 && !PA
 }
 
 
-template <int NMU, bool CACHED, int KT, bool LIN, bool PARA = false, int ST = 2>
+template <int NMU, bool CACHED, int KT, bool LIN, bool PARA = false, int ST = 2, bool ONE = false>
 static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_t s) {
   const size_t smem = CACHED ? forward32_smem_bytes(a.warps, max_k, ST) : 0;
   if (CACHED) {
@@ -946,31 +936,41 @@ static cudaError_t launch_one(const FwdArgs& a, int grid, int max_k, cudaStream_
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(raised & bit)) {
-      e = cudaFuncSetAttribute(k_forward32<NMU, CACHED, KT, LIN, PARA, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(k_forward32<NMU, CACHED, KT, LIN, PARA, ST, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kForwardSmemCap);
       if (e != cudaSuccess) return e;
       raised |= bit;
     }
     if (smem > kForwardSmemCap) return cudaErrorInvalidValue;
   }
-  k_forward32<NMU, CACHED, KT, LIN, PARA, ST><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
+  k_forward32<NMU, CACHED, KT, LIN, PARA, ST, ONE><<<grid, 32 * a.warps, smem, s>>>(a, max_k);
   return cudaGetLastError();
 }
 
 // cached path, compiled absorber bound KT: the stage variants that exist
 // (forward32_stages): one stage for up to 4 nodes, one or two (by the
 // caller's choice) for more nodes with KT >= 8, two otherwise
+template <int NMU, int KT, bool LIN, int ST>
+static cudaError_t launch_cached_st(const FwdArgs& a, int grid, int max_k, cudaStream_t s) {
+  // a launch with a single setup takes the kernel with the node constants at
+  // fixed offsets (not in the bounds-checked build)
+  if constexpr (!HR2_BOUNDS_CHECK) {
+    if (a.n_setups == 1) return launch_one<NMU, true, KT, LIN, false, ST, true>(a, grid, max_k, s);
+  }
+  return launch_one<NMU, true, KT, LIN, false, ST, false>(a, grid, max_k, s);
+}
+
 template <int NMU, int KT, bool LIN>
 static cudaError_t launch_kt(const FwdArgs& a, int grid, int max_k, int stages, cudaStream_t s) {
   if constexpr (KT == 0) {
-    return launch_one<NMU, true, 0, LIN, false, 2>(a, grid, max_k, s);
+    return launch_cached_st<NMU, 0, LIN, 2>(a, grid, max_k, s);
   } else if constexpr (NMU <= 4) {
-    return launch_one<NMU, true, KT, LIN, false, 1>(a, grid, max_k, s);
+    return launch_cached_st<NMU, KT, LIN, 1>(a, grid, max_k, s);
   } else if constexpr (KT >= 8) {
-    return stages == 1 ? launch_one<NMU, true, KT, LIN, false, 1>(a, grid, max_k, s)
-                       : launch_one<NMU, true, KT, LIN, false, 2>(a, grid, max_k, s);
+    return stages == 1 ? launch_cached_st<NMU, KT, LIN, 1>(a, grid, max_k, s)
+                       : launch_cached_st<NMU, KT, LIN, 2>(a, grid, max_k, s);
   } else {
-    return launch_one<NMU, true, KT, LIN, false, 2>(a, grid, max_k, s);
+    return launch_cached_st<NMU, KT, LIN, 2>(a, grid, max_k, s);
   }
 }
 
