@@ -965,6 +965,11 @@ static void fill_node_constants(FwdArgs& a, int n_setups, const hr2_setup* const
       a.node_im[g][k] = pair(setups[g]->host.inv_mu[k]);
       a.node_lw[g][k] = pair(setups[g]->host.lwmu[k]);
     }
+  if (n_setups > 0)
+    for (int k = 0; k < HR2_MAX_MU; ++k) {
+      a.node_mnl0[k] = pair(setups[0]->host.mu_nlog2e[k]);
+      a.node_mu0[k] = pair(setups[0]->host.mu[k]);
+    }
 }
 
 static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {

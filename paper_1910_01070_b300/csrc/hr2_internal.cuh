@@ -288,6 +288,11 @@ struct FwdArgs {
   // through the constant cache instead of shared memory
   unsigned long long node_im[HR2_MAX_SETUPS][HR2_MAX_MU];
   unsigned long long node_lw[HR2_MAX_SETUPS][HR2_MAX_MU];
+  // the parabolic-source sweep's other two node constants of setup 0,
+  // -log2(e)/mu_k and mu_k, for launches with a single setup (the general
+  // sweep reads all three from shared memory)
+  unsigned long long node_mnl0[HR2_MAX_MU];
+  unsigned long long node_mu0[HR2_MAX_MU];
   // two-pass direct path (small batches on FP16 tables without the operand):
   // absorption coefficients [n][rec_ld levels][chi_ld setup-local columns],
   // written by k_chi_direct and read by the sweep; null otherwise

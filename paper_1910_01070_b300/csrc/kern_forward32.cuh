@@ -359,7 +359,6 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
 #pragma unroll
     for (int p = 0; p < kPairs; ++p) acc[p][0] = fma2(sum[p], rdS[p], acc[p][0]);
   } else if (j > 0) {
-    (void)a;
     (void)gs;
     // layer j-1 between levels j-1 (top, Sp) and j (bottom, Sj)
     v2 dt[kPairs], rr[kPairs], dS[kPairs];
@@ -395,7 +394,9 @@ __device__ __forceinline__ void level_physics(int j, const v2 (&chi)[kPairs], co
       st[p].dtp = dt[p];
 #pragma unroll
       for (int k = 0; k < NMU; ++k) {
-        const v2 mk = sMnl[k], im = sImu[k], mu = sMu[k];
+        // single setup (ONE): the constants at fixed kernel-parameter offsets
+        const v2 mk = ONE ? a.node_mnl0[k] : sMnl[k], im = ONE ? a.node_im[0][k] : sImu[k],
+                 mu = ONE ? a.node_mu0[k] : sMu[k];
         const v2 En = ex2_2(mul2(st[p].tau, mk));
         const v2 D = mul2(dt[p], im);
         const v2 D2 = mul2(D, D);
@@ -994,18 +995,28 @@ static cudaError_t launch_cached(const FwdArgs& a, int grid, int max_k, int kt, 
 
 // parabolic source on the level-gridded path: the same absorber bounds as the
 // linear source, two stages
+template <int NMU, int KT, bool LIN>
+static cudaError_t launch_para_kt(const FwdArgs& a, int grid, int max_k, cudaStream_t s) {
+  // a launch with a single setup takes the kernel with the node constants at
+  // fixed offsets (not in the bounds-checked build)
+  if constexpr (!HR2_BOUNDS_CHECK) {
+    if (a.n_setups == 1) return launch_one<NMU, true, KT, LIN, true, 2, true>(a, grid, max_k, s);
+  }
+  return launch_one<NMU, true, KT, LIN, true, 2, false>(a, grid, max_k, s);
+}
+
 template <int NMU, bool LIN>
 static cudaError_t launch_para(const FwdArgs& a, int grid, int max_k, int kt, cudaStream_t s) {
   switch (kt) {
-    case 0: return launch_one<NMU, true, 0, LIN, true, 2>(a, grid, max_k, s);
-    case 2: return launch_one<NMU, true, 2, LIN, true, 2>(a, grid, max_k, s);
-    case 4: return launch_one<NMU, true, 4, LIN, true, 2>(a, grid, max_k, s);
-    case 6: return launch_one<NMU, true, 6, LIN, true, 2>(a, grid, max_k, s);
-    case 8: return launch_one<NMU, true, 8, LIN, true, 2>(a, grid, max_k, s);
-    case 10: return launch_one<NMU, true, 10, LIN, true, 2>(a, grid, max_k, s);
-    case 12: return launch_one<NMU, true, 12, LIN, true, 2>(a, grid, max_k, s);
-    case 14: return launch_one<NMU, true, 14, LIN, true, 2>(a, grid, max_k, s);
-    case 16: return launch_one<NMU, true, 16, LIN, true, 2>(a, grid, max_k, s);
+    case 0: return launch_para_kt<NMU, 0, LIN>(a, grid, max_k, s);
+    case 2: return launch_para_kt<NMU, 2, LIN>(a, grid, max_k, s);
+    case 4: return launch_para_kt<NMU, 4, LIN>(a, grid, max_k, s);
+    case 6: return launch_para_kt<NMU, 6, LIN>(a, grid, max_k, s);
+    case 8: return launch_para_kt<NMU, 8, LIN>(a, grid, max_k, s);
+    case 10: return launch_para_kt<NMU, 10, LIN>(a, grid, max_k, s);
+    case 12: return launch_para_kt<NMU, 12, LIN>(a, grid, max_k, s);
+    case 14: return launch_para_kt<NMU, 14, LIN>(a, grid, max_k, s);
+    case 16: return launch_para_kt<NMU, 16, LIN>(a, grid, max_k, s);
     default: return cudaErrorInvalidValue;
   }
 }

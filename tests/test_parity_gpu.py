@@ -418,13 +418,20 @@ def test_uneven_three_setups_sampled_and_alone_equals_mix(eng):
     assert np.array_equal(h2, hi[sub])
 
 
-def test_single_setup_launch_equals_the_mixed_launch(eng):
+@pytest.mark.parametrize("sc", ["linear", "parabolic"])
+def test_single_setup_launch_equals_the_mixed_launch(eng, sc):
     """A launch with one setup runs the sweep compiled with the setup index fixed (the
     angle-node constants at fixed parameter offsets); the same samples in a launch with
     several setups run the general sweep.  Same arithmetic: the same bits, for each setup
-    of the uneven batch (6-10 absorbers, 81-121 levels)."""
+    of the uneven batch (6-10 absorbers, 81-121 levels; the first four with the parabolic
+    source)."""
     wl, tabs, stored, setups, st = _workload_on(eng, "uneven2048_3setups", "fp16")
     theta, sid = wl.params(48, seed_offset=31)
+    if sc == "parabolic":
+        t = _tables_of("uneven2048_3setups", "fp16")
+        setups = [eng.add_setup(t, dataclasses.replace(s, sc="parabolic")) for s in wl.setups[:4]]
+        keep = sid < 4
+        theta, sid = theta[keep], sid[keep]
     ld = max(s.n_nu for s in wl.setups)
     b_mix, h_mix, _ = _run(eng, setups, sid, theta, highres_ld=ld)
     for g in range(len(setups)):
