@@ -1027,45 +1027,55 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
   a.wait_limit = ctx->wait_limit;
   a.tx_extra = ctx->wait_fault ? 16u : 0u;
   fill_node_constants(a, n_setups, setups);
+  // small batches on tables read in place run in two passes: the absorption
+  // coefficients of every level first, in parallel, then the sweep; their
+  // buffer is sized before anything is launched
+  const bool two_pass = !fp64 && !sh.cached && !sh.para && n <= ctx->cfg.split_max_batch;
+  if (two_pass) {
+    a.chi_ld = (long long)sh.max_tiles * kTileNu;
+    if ((rc = ws_ensure_chi(ctx, s, w, (size_t)n * w->lev_cap * a.chi_ld))) return rc;
+    a.chi = w->chi;
+  }
   cudaError_t e;
   if ((e = launch_prep(a, s)) != cudaSuccess) return fail(HR2_ECUDA, "prep launch: %s", cudaGetErrorString(e));
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
   if (ctx->profiling) {
     HR2_CU(cudaEventCreate(&ev.first));
-    HR2_CU(cudaEventCreate(&ev.second));
+    if ((e = cudaEventCreate(&ev.second)) != cudaSuccess) {
+      cudaEventDestroy(ev.first);
+      return fail(HR2_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+    }
   }
+  // a failed launch after the events exist releases them
+  auto launch_failed = [&](const char* what, cudaError_t err) {
+    if (ev.first) cudaEventDestroy(ev.first);
+    if (ev.second) cudaEventDestroy(ev.second);
+    return fail(HR2_ECUDA, "%s launch: %s", what, cudaGetErrorString(err));
+  };
   if (fp64) {
-    HR2_CU(cudaMemsetAsync(a.err, 0, sizeof(int), s));   // the planner clears it on the FP32 path
-    if (ev.first) HR2_CU(cudaEventRecord(ev.first, s));
+    if ((e = cudaMemsetAsync(a.err, 0, sizeof(int), s)) != cudaSuccess)   // the planner clears it on the FP32 path
+      return launch_failed("error-word clear", e);
+    if (ev.first && (e = cudaEventRecord(ev.first, s)) != cudaSuccess) return launch_failed("event", e);
     a.highres64 = w->highres64;
     a.highres64_ld = w->nu64_cap;
     a.user_highres = out_highres;
     a.highres = out_highres;
     a.highres_ld = highres_ld;
-    if ((e = launch_forward64(a, sh.max_mu, sh.max_nu, s)) != cudaSuccess)
-      return fail(HR2_ECUDA, "forward64 launch: %s", cudaGetErrorString(e));
-    if (ev.second) HR2_CU(cudaEventRecord(ev.second, s));
+    if ((e = launch_forward64(a, sh.max_mu, sh.max_nu, s)) != cudaSuccess) return launch_failed("forward64", e);
+    if (ev.second && (e = cudaEventRecord(ev.second, s)) != cudaSuccess) return launch_failed("event", e);
   } else {
     a.highres = out_highres ? out_highres : w->highres;
     a.highres_ld = out_highres ? highres_ld : w->nu_cap;
-    if ((e = launch_plan(a, w->perm, w->plan, s)) != cudaSuccess)
-      return fail(HR2_ECUDA, "plan launch: %s", cudaGetErrorString(e));
+    if ((e = launch_plan(a, w->perm, w->plan, s)) != cudaSuccess) return launch_failed("plan", e);
     // (the profiling events bracket both passes of the two-pass path)
-    if (ev.first) HR2_CU(cudaEventRecord(ev.first, s));
-    // small batches on tables read in place: the absorption coefficients of
-    // every level first, in parallel, then the sweep
-    if (!sh.cached && !sh.para && n <= ctx->cfg.split_max_batch) {
-      a.chi_ld = (long long)sh.max_tiles * kTileNu;
-      if ((rc = ws_ensure_chi(ctx, s, w, (size_t)n * w->lev_cap * a.chi_ld))) return rc;
-      a.chi = w->chi;
-      if ((e = launch_chi_direct(a, sh.max_lev, sh.max_tiles, s)) != cudaSuccess)
-        return fail(HR2_ECUDA, "absorption pass launch: %s", cudaGetErrorString(e));
-    }
+    if (ev.first && (e = cudaEventRecord(ev.first, s)) != cudaSuccess) return launch_failed("event", e);
+    if (two_pass && (e = launch_chi_direct(a, sh.max_lev, sh.max_tiles, s)) != cudaSuccess)
+      return launch_failed("absorption pass", e);
     const int grid = ctx->n_sm * ls.ctas_per_sm;
     if ((e = launch_forward32(a, sh.max_mu, grid, sh.cached != 0, sh.linear != 0, sh.para != 0, sh.max_k, absorber_bound(sh),
                               ls.stages, s)) != cudaSuccess)
-      return fail(HR2_ECUDA, "forward32 launch: %s", cudaGetErrorString(e));
-    if (ev.second) HR2_CU(cudaEventRecord(ev.second, s));
+      return launch_failed("forward32", e);
+    if (ev.second && (e = cudaEventRecord(ev.second, s)) != cudaSuccess) return launch_failed("event", e);
   }
   if (ev.first) {
     std::lock_guard<std::mutex> lk(ctx->mu);
