@@ -14,9 +14,19 @@ It is solved here by product integration: q piecewise linear on a grid
 (logarithmic near the surface, uniform at depth, q constant beyond the last
 node), the E1 kernel integrated exactly against each hat function through
 the antiderivatives of E1 and t E1 (E2, E3), and the linear system solved
-directly.  The error falls as h^2, so two nested grids are combined by
-Richardson extrapolation.  scipy's exponential integrals and numpy's dense
-solver are the library primitives used.
+directly.  The nodal error of three nested grids (each halving the steps of
+the last) falls as h^2 and then as h^3, so two Richardson steps at the
+coarsest grid's nodes (nodes of all three) remove both terms.  Between nodes a
+grid's solution is carried by the integral equation itself (Nystrom's
+interpolation: the right-hand side evaluated at any tau), but that value's
+error has a part that oscillates with the position inside the cell, which
+Richardson cannot remove; so the finest grid's Nystrom values are kept and
+only the smooth correction (extrapolated minus finest, at the coarse nodes) is
+interpolated onto them, on each side of tau = 1 separately, where the grid
+changes from logarithmic to uniform.  The result is tabulated on the finest
+grid and its midpoints and read by cubic Lagrange interpolation through the
+four nearest nodes.  scipy's exponential integrals and numpy's dense solver
+are the library primitives used.
 """
 from __future__ import annotations
 
@@ -39,9 +49,10 @@ def _grid(m_near: int, m_deep: int, t_deep: float) -> np.ndarray:
     return np.concatenate([[0.0], np.geomspace(1e-9, 1.0, m_near), np.linspace(1.0, t_deep, m_deep)[1:]])
 
 
-def solve_on(t: np.ndarray) -> np.ndarray:
-    """q at the nodes t (t[0] = 0, ascending) from the discretised integral equation."""
-    x = t[:, None]
+def lambda_rows(t: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Rows of the discretised Lambda operator: Lambda[q](x_i) = sum_j rows[i, j] q(t_j)
+    for q piecewise linear on the nodes t (t[0] = 0, ascending) and constant beyond t[-1]."""
+    x = np.asarray(x, dtype=np.float64)[:, None]
     a, c = t[None, :-1], t[None, 1:]
     h = c - a
 
@@ -57,27 +68,65 @@ def solve_on(t: np.ndarray) -> np.ndarray:
     i1 = te1_int(c) - te1_int(a)
     w_left = ((c - x) * i0 - i1) / h          # weight of q at the interval's left node
     w_right = (i1 + (x - a) * i0) / h         # ... and at its right node
-    lam = np.zeros((len(t), len(t)))
+    lam = np.zeros((x.shape[0], len(t)))
     lam[:, :-1] += 0.5 * w_left
     lam[:, 1:] += 0.5 * w_right
-    lam[:, -1] += 0.5 * _en(2, t[-1] - t)     # q held at its last value beyond the grid
-    return np.linalg.solve(np.eye(len(t)) - lam, 0.5 * _en(3, t))
+    lam[:, -1] += 0.5 * _en(2, t[-1] - x[:, 0])   # q held at its last value beyond the grid
+    return lam
+
+
+def solve_on(t: np.ndarray) -> np.ndarray:
+    """q at the nodes t (t[0] = 0, ascending) from the discretised integral equation."""
+    return np.linalg.solve(np.eye(len(t)) - lambda_rows(t, t), 0.5 * _en(3, t))
+
+
+def nystrom(t: np.ndarray, q: np.ndarray, x) -> np.ndarray:
+    """The solution q (on the nodes t) carried to the points x by the integral equation."""
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    return 0.5 * _en(3, x) + lambda_rows(t, x) @ q
+
+
+def _cubic(t: np.ndarray, q: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Cubic Lagrange interpolation of (t, q) at x through the four nearest nodes
+    (the stencil slides inward at the ends)."""
+    k = np.clip(np.searchsorted(t, x) - 2, 0, len(t) - 4)   # first of the four nodes
+    out = np.zeros_like(x)
+    for a in range(4):
+        la = np.ones_like(x)
+        for b in range(4):
+            if b != a:
+                la *= (x - t[k + b]) / (t[k + a] - t[k + b])
+        out += la * q[k + a]
+    return out
 
 
 @functools.lru_cache(maxsize=None)
 def hopf_table():
-    """(tau, q) on the fine grid, Richardson-extrapolated from two nested grids."""
-    coarse = _grid(201, 401, 40.0)
-    fine = _grid(401, 801, 40.0)
-    q_c = solve_on(coarse)
-    q_f = solve_on(fine)
-    # the O(h^2) error is smooth: move the fine solution by a third of its difference
-    # from the coarse one (interpolated onto the fine nodes)
-    q = q_f + (q_f - np.interp(fine, coarse, q_c)) / 3.0
-    return fine, q
+    """(tau, q) on the finest of three nested grids and its midpoints."""
+    grids = [_grid(m + 1, 2 * m + 1, 40.0) for m in (200, 400, 800)]
+    sols = [solve_on(g) for g in grids]
+    coarse, fine = grids[0], grids[-1]
+    # the coarse nodes in the two finer grids (nested: every coarse node is one)
+    i_mid, i_fine = np.searchsorted(grids[1], coarse), np.searchsorted(fine, coarse)
+    assert np.allclose(grids[1][i_mid], coarse, rtol=1e-13, atol=0.0)
+    assert np.allclose(fine[i_fine], coarse, rtol=1e-13, atol=0.0)
+    v0, v1, v2 = sols[0], sols[1][i_mid], sols[2][i_fine]
+    r_coarse = v1 + (v1 - v0) / 3.0          # h^2 term removed (steps h, h/2)
+    r_fine = v2 + (v2 - v1) / 3.0            # ... (steps h/2, h/4)
+    correction = r_fine + (r_fine - r_coarse) / 7.0 - v2     # then the h^3 term
+    tab = np.sort(np.concatenate([fine, 0.5 * (fine[:-1] + fine[1:])]))
+    q = nystrom(fine, sols[2], tab)
+    upper = tab <= 1.0
+    c_up, c_deep = coarse <= 1.0, coarse >= 1.0
+    q[upper] += _cubic(coarse[c_up], correction[c_up], tab[upper])
+    q[~upper] += _cubic(coarse[c_deep], correction[c_deep], tab[~upper])
+    return tab, q
 
 
 def hopf(tau):
-    """q(tau) by linear interpolation in the table (constant beyond its ends)."""
+    """q(tau): cubic Lagrange interpolation in the table (constant beyond its ends)."""
     t, q = hopf_table()
-    return np.interp(tau, t, q)
+    x = np.asarray(tau, dtype=np.float64)
+    xf = np.atleast_1d(x)
+    out = np.where(xf <= t[0], q[0], np.where(xf >= t[-1], q[-1], _cubic(t, q, xf)))
+    return out if x.ndim else float(out[0])

@@ -208,7 +208,8 @@ void or_nodes_from_b(int n_nodes, double T1, const double* b, double* Tnodes) {
   for (int i = 1; i < n_nodes; ++i) Tnodes[i] = b[i - 1] * Tnodes[i - 1];
 }
 
-/* Hopf function q(tau) from the model's table: linear interpolation,
+/* Hopf function q(tau) from the model's table: cubic Lagrange interpolation
+ * through the four nearest nodes (the stencil slides inward at the ends),
  * constant beyond the table's ends. */
 double or_hopf(const or_model* m, double tau) {
   const double* t = m->hopf_tau;
@@ -216,10 +217,19 @@ double or_hopf(const or_model* m, double tau) {
   int n = m->n_hopf;
   if (tau <= t[0]) return q[0];
   if (tau >= t[n - 1]) return q[n - 1];
-  int k = 0;
+  int k = 0;                               /* t[k] < tau <= t[k+1] */
   while (t[k + 1] < tau) ++k;
-  double w = (tau - t[k]) / (t[k + 1] - t[k]);
-  return (1.0 - w) * q[k] + w * q[k + 1];
+  int k0 = k - 1;
+  if (k0 < 0) k0 = 0;
+  if (k0 > n - 4) k0 = n - 4;
+  double sum = 0.0;
+  for (int a = 0; a < 4; ++a) {
+    double l = 1.0;
+    for (int b = 0; b < 4; ++b)
+      if (b != a) l *= (tau - t[k0 + b]) / (t[k0 + a] - t[k0 + b]);
+    sum += l * q[k0 + a];
+  }
+  return sum;
 }
 
 /* Milne's profile (Sect. 2.5): T^4 = 3/4 Tbar^4 [tau_R + q(tau_R)] with

@@ -52,14 +52,18 @@ __device__ __forceinline__ float exp2_split(double b) {
   return ldexpf(exp2f((float)(b - n)), (int)n);
 }
 
-// Hopf function q(tau) from the setup's table (linear in ln tau).
+// Hopf function q(tau) from the setup's table: cubic Lagrange interpolation in
+// ln tau through the four nearest nodes (the stencil slides inward at the
+// table's ends); q(kHopfTau0) below the table, q(kHopfTau1) above it.
 __device__ double hopf_q(const double* tab, double tau) {
   if (!(tau > kHopfTau0)) return tab[0];
   const double u = (log(tau) - log(kHopfTau0)) * ((kHopfN - 1) / (log(kHopfTau1) - log(kHopfTau0)));
   if (!(u < kHopfN - 1)) return tab[kHopfN - 1];
-  const int k = (int)u;
-  const double w = u - (double)k;
-  return (1.0 - w) * tab[k] + w * tab[k + 1];
+  const int k0 = min(max((int)u - 1, 0), kHopfN - 4);
+  const double x = u - (double)k0;              // in [0, 3]: nodes at 0, 1, 2, 3
+  const double a = x - 1.0, b = x - 2.0, c = x - 3.0;
+  return (-a * b * c * tab[k0] + 3.0 * x * b * c * tab[k0 + 1] - 3.0 * x * a * c * tab[k0 + 2] +
+          x * a * b * tab[k0 + 3]) * (1.0 / 6.0);
 }
 
 // Temperature of level j (0 = top) of sample parameters th (Sect. 2.5): the

@@ -35,17 +35,27 @@ def h_function(mu):
 def test_hopf_end_values():
     """q(0) = 1/sqrt(3) and q(inf) = 1/sqrt(3) + (1/(2 sqrt 3)) int_0^1 dmu / (H (a^2 + (pi mu/2)^2)),
     a = 1 - (mu/2) ln((1+mu)/(1-mu)) (the Hopf constant 0.710446...)."""
-    assert hopf.hopf(0.0) == pytest.approx(1 / math.sqrt(3), abs=1e-6)
+    assert hopf.hopf(0.0) == pytest.approx(1 / math.sqrt(3), abs=1e-8)
 
-    def g(mu):
-        a = 1.0 - 0.5 * mu * math.log((1 + mu) / (1 - mu))
-        return 1.0 / (h_function(mu) * (a * a + (math.pi * mu / 2) ** 2))
-
-    tail, _ = integrate.quad(g, 0.0, 1.0, limit=400, epsabs=1e-12)
+    tail, _ = integrate.quad(_g, 0.0, 1.0, limit=400, epsabs=1e-12)
     q_inf = 1 / math.sqrt(3) + tail / (2 * math.sqrt(3))
     assert q_inf == pytest.approx(0.7104460896, abs=1e-9)
-    assert hopf.hopf(40.0) == pytest.approx(q_inf, abs=2e-6)
+    assert hopf.hopf(40.0) == pytest.approx(q_inf, abs=2e-8)
 
+
+
+def _g(mu):
+    a = 1.0 - 0.5 * mu * math.log((1 + mu) / (1 - mu))
+    return 1.0 / (h_function(mu) * (a * a + (math.pi * mu / 2) ** 2))
+
+
+@pytest.mark.parametrize("tau", [0.01, 0.3, 0.8, 2.5])
+def test_hopf_function_matches_chandrasekhars_closed_form(tau):
+    """Between the ends: q(tau) = 1/sqrt(3) + (1/(2 sqrt 3)) int_0^1 g(mu) (1 - e^{-tau/mu}) dmu
+    with g = 1 / (H (a^2 + (pi mu/2)^2)) (Chandrasekhar's solution of Milne's problem),
+    an independent route to the function the integral-equation solve tabulates."""
+    v, _ = integrate.quad(lambda mu: _g(mu) * -math.expm1(-tau / mu), 0.0, 1.0, limit=400, epsabs=1e-12)
+    assert hopf.hopf(tau) == pytest.approx(1 / math.sqrt(3) + v / (2 * math.sqrt(3)), abs=2e-8)
 
 @pytest.mark.parametrize("tau", [0.0, 0.2, 1.0, 4.0])
 def test_milne_flux_is_constant(tau):
@@ -56,14 +66,14 @@ def test_milne_flux_is_constant(tau):
     dn = 0.0
     if tau > 0:
         dn, _ = integrate.quad(lambda t: S(t) * expn(2, tau - t), 0.0, tau, limit=400)
-    assert 2 * up - 2 * dn == pytest.approx(4.0 / 3.0, abs=2e-5)
+    assert 2 * up - 2 * dn == pytest.approx(4.0 / 3.0, abs=2e-8)
 
 
 @pytest.mark.parametrize("mu", [0.2, 0.6, 1.0])
 def test_milne_emergent_intensity_is_the_h_function(mu):
     """I(0, mu) = int_0^inf (t + q(t)) e^{-t/mu} dt / mu = H(mu) / sqrt(3)."""
     v, _ = integrate.quad(lambda t: hopf.hopf(t) * math.exp(-t / mu) / mu, 0.0, 60.0 * mu, limit=400)
-    assert mu + v == pytest.approx(h_function(mu) / math.sqrt(3), abs=1e-5)
+    assert mu + v == pytest.approx(h_function(mu) / math.sqrt(3), abs=1e-8)
 
 
 def _milne_model(n_layers=30):
