@@ -35,6 +35,7 @@ sys.path.insert(0, ROOT)
 METRIC = "forward models/sec and HBM-roofline fraction at 1e-4 rel. flux error; p50/p99 latency"
 WORKLOAD = "batch1024_l100_k6_nu8501"
 PROFILE_TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+PROFILE_TRAFFIC_UNEVEN = os.path.join(ROOT, "profiles", "traffic_uneven.json")
 
 
 def parse():
@@ -49,6 +50,8 @@ def parse():
     p.add_argument("--cpu-samples", type=int, default=64)
     p.add_argument("--no-extras", action="store_true",
                    help="skip the uneven three-setup batch and the serving-loop measurements")
+    p.add_argument("--uneven-only", action="store_true",
+                   help="of the extra records, run only the uneven batch (counter captures of its launch)")
     p.add_argument("--serving-seconds", type=float, default=4.0)
     p.add_argument("--sweep-large", action="store_true",
                    help="instead of the main line: batch sweep on the 290001-point, 12-absorber tables")
@@ -370,7 +373,7 @@ def run_hr2(args, world, rank, local):
            "ms_per_step": 1e3 * e2e_total / args.steps, "api": "hr2_evaluate_host (pinned host buffers)"}
 
     graph = None
-    if rank == 0 and world == 1 and not args.no_extras:
+    if rank == 0 and world == 1 and not args.no_extras and not args.uneven_only:
         graph = graph_replay_timing(eng, [s16], pool, n, setup.n_bins, setup.n_nu, flush, local)
 
     fp64 = None
@@ -496,6 +499,7 @@ def run_extras(args, local, flush):
         evs = []
         hr2.hr2_profile_read(eng.ctx, True)
         hr2.hr2_profile_enable(eng.ctx, True)
+        torch.cuda.nvtx.range_push("uneven_batch_timed")     # ncu filters on this range
         for k in range(steps):
             flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -505,6 +509,7 @@ def run_extras(args, local, flush):
             hr2.log_likelihood_batch(eng.ctx, setups, sd, bins, lnl, None, stream)
             e1.record(stream)
             evs.append((e0, e1))
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         hr2.hr2_profile_enable(eng.ctx, False)
         kms, nl = hr2.hr2_profile_read(eng.ctx, True)
@@ -517,12 +522,17 @@ def run_extras(args, local, flush):
                     work[k] += float(np.sum(pool[p][2] == g)) * v / 3
         props = torch.cuda.get_device_properties(local)
         peaks = unit_peaks(measure_unit_rates(local, clocks=False), props.multi_processor_count)
-        rl = roofline_of(work, kms / max(nl, 1), peaks, None)
+        ctr = committed_counters(PROFILE_TRAFFIC_UNEVEN)
+        rl = roofline_of(work, kms / max(nl, 1), peaks, ctr)
         out["uneven_batch"] = {"workload": wl.name, "samples": n, "setups": len(wl.setups),
                                "value": cap, "unit": "models/s", "ms_per_step": float(np.mean(times)),
                                "p99_ms": float(np.percentile(times, 99)),
                                "kernel_ms": kms / max(nl, 1),
                                "mufu_frac": rl["fractions"]["mufu"], "fma_frac": rl["fractions"]["fma"],
+                               "binding": rl["binding"], "binding_unit": rl["binding_unit"],
+                               "fractions": rl["fractions"],
+                               "traffic": ctr["dram_bytes"] if ctr else None,
+                               "counters": ctr["source"] if ctr else None,
                                "launch": list(hr2.hr2_get_launch_config(eng.ctx)),
                                "autotuned": {"candidates": len(tried), "best": list(best),
                                              "shape": "(warps per CTA, CTAs per SM, 128-point tiles per item, "
@@ -530,6 +540,8 @@ def run_extras(args, local, flush):
                                              "tiles_per_item_tried": sorted({c[2] for c in tried}),
                                              "fastest_ms": min(tried.values()) if tried else None,
                                              "default_ms": tried.get(autotune.DEFAULT_SHAPE)}}
+        if args.uneven_only:
+            return out
         # serving: 16 nested-sampling-like streams over the 12 setups, Poisson arrivals
         shapes = [(s.n_bins, s.n_nu, s.n_layers + 1) for s in wl.setups]
         res = []
@@ -801,12 +813,12 @@ def run_peaks(args, local):
 SM_MAX_MHZ = 2032.0
 
 
-def committed_counters() -> Optional[dict]:
+def committed_counters(path: str = PROFILE_TRAFFIC) -> Optional[dict]:
     """ncu counters of the forward kernel committed under profiles/ (DRAM bytes per launch
     and L2 throughput as a fraction of peak), if they belong to the current kernel source."""
-    if not os.path.exists(PROFILE_TRAFFIC):
+    if not os.path.exists(path):
         return None
-    with open(PROFILE_TRAFFIC) as f:
+    with open(path) as f:
         tr = json.load(f)
     if tr.get("kernel_source_hash") != _kernel_hash():
         return None
