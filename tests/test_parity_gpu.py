@@ -379,6 +379,16 @@ def test_batch_100_layers_reduced_with_lnl(eng, storage):
     for i in range(len(theta) - 4, len(theta)):
         ref = oracle.lnL(D, sig, ob_all[i])
         assert abs(lnl[i] - ref) < LNL_ATOL, (i, lnl[i], ref)
+    # far from the data (the prior draws) lnL is large and |dlnL| may exceed LNL_ATOL, but it
+    # must stay within what the flux tolerance allows: with |Dm_gpu - Dm| <= e_b per bin,
+    # e_b = tol (|Dm_b| + 1e-6 max|Dm|) (the relative-error gate with its floor),
+    # |dlnL| <= sum e_b |D_b - Dm_b| / s_b^2 + sum e_b^2 / (2 s_b^2)   (Eq. 19 expanded)
+    for i in range(len(theta) - 4):
+        ref = oracle.lnL(D, sig, ob_all[i])
+        e = tol * (np.abs(ob_all[i]) + 1e-6 * np.max(np.abs(ob_all[i])))
+        bound = np.sum(e * np.abs(D - ob_all[i]) / sig ** 2) + np.sum(e ** 2 / (2 * sig ** 2))
+        print("sample %d: lnL %.4e  dlnL %.3e  bound %.3e" % (i, ref, lnl[i] - ref, bound))
+        assert abs(lnl[i] - ref) <= bound + 1e-9 * abs(ref), (i, lnl[i] - ref, bound)
     # error inflation (Eqs. 22-23)
     eps = np.full(len(theta), np.log10(np.median(sig) ** 2))
     eps[0] = np.nan
