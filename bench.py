@@ -574,7 +574,7 @@ def run_extras(args, local, flush):
                           "latency": "arrival to lnL on the host (served requests; rejected ones counted)",
                           "loads": res}
     if not args.no_large:
-        out["large_tables"] = large_table_sweep(local)
+        out["large_tables"] = large_table_sweep(local, modes=("direct", "cached", "stream"))
     out["linear_sigma_option"] = run_linear_option(args, local, flush)
     out["parabolic_source_option"] = run_linear_option(args, local, flush, sc="parabolic")
     out["nested_sampling"] = run_nested(args, local)
@@ -710,8 +710,10 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
         t = eng.add_tables(wl.table, "fp16")
         # "direct": the FP16 tables read in place (batches up to the context's split_max_batch
         # in two passes), "direct1": the same in one pass always, "cached": the level-gridded
-        # operand
-        setups = {m: eng.add_setup(t, s, level_cache=(m == "cached")) for m in modes}
+        # operand, "stream": that operand built per call and group of tiles into a ring
+        # (batches of 64 and more; smaller ones read the tables directly, so they are skipped)
+        setups = {m: eng.add_setup(t, s, level_cache="stream" if m == "stream" else (m == "cached"))
+                  for m in modes}
         cfg0 = hr2.hr2_get_launch_config(eng.ctx)
         th_all, _ = wl.params(max(batches))
         # algorithmic bytes one model reads: on the direct path the FP16 corners (4 per level
@@ -723,15 +725,21 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
         algo = {"direct": (s.n_layers + 1) * 4 * s.n_nu * (len(s.species) + 1) * 2,
                 "cached": (s.n_layers + 1) * n_tiles * 128 * (len(s.species) + 2) * 8}
         algo["direct1"] = algo["direct"]
+        algo["stream"] = algo["cached"]
         for mode, h in setups.items():
             per_model_bytes = algo[mode]
             hr2.hr2_set_launch_config(eng.ctx, *cfg0[:4], 0 if mode == "direct1" else cfg0[4])
             for b in batches:
+                if mode == "stream" and b < 64:
+                    continue
                 th = torch.as_tensor(th_all[:b], device=dev)
                 sd = torch.zeros(b, dtype=torch.int32, device=dev)
                 bins = torch.empty((b, s.n_bins), dtype=torch.float32, device=dev)
+                torch.cuda.synchronize()
+                m0 = hr2.hr2_ctx_memory(eng.ctx)[0]
                 eng.forward([h], sd, th, bins)
                 torch.cuda.synchronize()
+                ring_bytes = hr2.hr2_ctx_memory(eng.ctx)[0] - m0   # the streamed path's ring and views
                 t0 = time.perf_counter()
                 eng.forward([h], sd, th, bins)
                 torch.cuda.synchronize()
@@ -747,7 +755,7 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
                 clk = cs.stop()
                 ms, n = hr2.hr2_profile_read(eng.ctx, True)
                 ms /= max(n, 1)
-                passes = 2 if mode != "cached" and b <= hr2.hr2_get_launch_config(eng.ctx)[4] else 1
+                passes = 2 if mode not in ("cached", "stream") and b <= hr2.hr2_get_launch_config(eng.ctx)[4] else 1
                 line = {"workload": wl.name, "mode": mode, "batch": b, "passes": passes, "kernel_ms": ms, "reps": reps,
                         "models_per_s": b / (ms / 1e3),
                         "algorithmic_bytes_per_model": per_model_bytes,
@@ -756,7 +764,10 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
                         "clocks": clk}
                 # counters per path: "direct2" the two-pass direct path, "direct" the one-pass one
                 key = "%s_b%d" % ("cached" if mode == "cached" else ("direct2" if passes == 2 else "direct"), b)
-                if counters and key in counters.get("dram_bytes_per_launch", {}):
+                line["operand_bytes"] = hr2.hr2_setup_memory(h)[1]
+                if mode == "stream":
+                    line["ring_bytes"] = ring_bytes
+                if counters and mode != "stream" and key in counters.get("dram_bytes_per_launch", {}):
                     dram = counters["dram_bytes_per_launch"][key]
                     line.update({"dram_bytes_per_launch": dram, "dram_gbs": dram / (ms / 1e3) / 1e9,
                                  "dram_hbm_frac": dram / (ms / 1e3) / 1e9 / hbm_peak,

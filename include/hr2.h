@@ -105,6 +105,9 @@ typedef enum {
 
 /* hr2_setup_desc.level_cache: build the level-gridded operand where it fits */
 #define HR2_LEVEL_CACHE_AUTO 2
+/* hr2_setup_desc.level_cache: build the operand at every evaluation, one
+ * group of tiles at a time, into a per-stream ring (see level_cache) */
+#define HR2_LEVEL_CACHE_STREAM 3
 
 /* Interpolation space of the opacity tables (Sect. 2.8 names the
  * interpolation of the tables but not the quantity interpolated). */
@@ -182,7 +185,20 @@ typedef struct {
                                  linear option, which needs the operand, then
                                  fails with HR2_ENOMEM).  hr2_setup_memory
                                  tells which was built.  One batch call takes
-                                 setups of a single kind.                        */
+                                 setups of a single kind.
+                                 HR2_LEVEL_CACHE_STREAM (log10 option only):
+                                 no operand is kept; a call with this setup
+                                 alone and at least 64 samples builds the
+                                 operand per group of consecutive 128-point
+                                 tiles into a ring in the stream's workspace
+                                 (FP32 arithmetic; at most 1 GiB unless
+                                 hr2_set_stream_group says otherwise) and
+                                 sweeps each group before the next is built,
+                                 which costs one operand build per call but
+                                 holds only the ring on the device; smaller
+                                 calls and calls that mix it with other setups
+                                 read the tables directly.  hr2_setup_memory
+                                 reports HR2_LEVEL_CACHE_STREAM for it.          */
   int interp;                 /* HR2_INTERP_LOG10 or HR2_INTERP_LINEAR.  With
                                  FP16 tables the linear option needs
                                  level_cache (the operand then holds the
@@ -444,6 +460,14 @@ int hr2_stream_check(hr2_ctx* ctx, void* stream);
  * device) left.  A 4-byte device-to-host copy; allocates nothing.  No
  * counterpart in the paper. */
 int hr2_noalloc_check(hr2_ctx* ctx, void* stream);
+
+/* Tiles per group of the streamed operand (HR2_LEVEL_CACHE_STREAM) for
+ * later calls: 0 (the default) sizes each group so that it holds about four
+ * work items per persistent CTA, with the ring at most 1 GiB; a positive
+ * count fixes it (the ring then holds that many tiles' operand, which the
+ * context's budget must allow).  No counterpart in the paper: it trades the
+ * ring's memory against the number of groups.  HR2_EINVAL for tiles < 0. */
+int hr2_set_stream_group(hr2_ctx* ctx, int tiles);
 
 /* hr2_set_wait_limit / hr2_get_wait_limit: SM clock cycles (>= 0) that a
  * device-side pipeline wait of the forward kernel may take before it gives

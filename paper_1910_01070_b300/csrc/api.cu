@@ -19,6 +19,14 @@
 
 using namespace hr2;
 
+namespace hr2 {
+// streamed level-gridded operand (kern_setup.cu)
+cudaError_t build_level_stream(const SetupDev* d_setup, int n_lev, int n_rows, int tile_lo, int n_tiles, float* ring,
+                               cudaStream_t s);
+cudaError_t build_stream_views(const SetupDev* d_setup, const float* ring, int group_tiles, int n_groups,
+                               SetupDev* views, cudaStream_t s);
+}  // namespace hr2
+
 // ------------------------------------------------------------ tracing
 // An NVTX range over the host side of an entry point (argument checks,
 // workspace, launches), named after it, so that a timeline profiler (or ncu's
@@ -71,6 +79,10 @@ struct Workspace {
   float* io_bins = nullptr;
   float* chi = nullptr;       // two-pass direct path: absorption coefficients
   size_t chi_cap = 0;         // floats
+  float* ring = nullptr;      // streamed operand: one group of tiles
+  size_t ring_cap = 0;        // floats
+  SetupDev* views = nullptr;  // streamed operand: one setup view per group
+  int views_cap = 0;
 };
 
 struct hr2_ctx {
@@ -79,6 +91,7 @@ struct hr2_ctx {
   size_t budget = 0;
   size_t used = 0;
   hr2_launch_cfg cfg{2, 8, 1, 0, kDefaultSplitMaxBatch};
+  int stream_group = 0;                        // tiles per group of the streamed operand (0: by batch)
   long long wait_limit = kDefaultWaitCycles;   // bounded device-side waits, SM clock cycles
   bool wait_fault = false;                     // test hook: first stages wait for bytes that never come
   std::mutex mu;
@@ -107,6 +120,8 @@ struct hr2_setup {
   SetupDev* dev = nullptr;
   std::vector<void*> mem;
   size_t operand_bytes = 0;
+  bool streamed = false;             // HR2_LEVEL_CACHE_STREAM: operand built per call, per group of tiles
+  SetupDev* dev_stream = nullptr;    // ... and the descriptor its batches are prepared with (cached records)
   int n_bins = 0;
   bool has_obs = false;
   double* d_obs = nullptr;  // [2][n_bins]: D then sigma
@@ -160,6 +175,8 @@ static void ws_free(hr2_ctx* ctx, Workspace* w) {
   dfree(ctx, w->io_lnl);
   dfree(ctx, w->io_bins);
   dfree(ctx, w->chi);
+  dfree(ctx, w->ring);
+  dfree(ctx, w->views);
   unsigned int* keep = w->h_counter;
   *w = Workspace();
   w->h_counter = keep;
@@ -249,6 +266,32 @@ static int ws_ensure_chi(hr2_ctx* ctx, cudaStream_t stream, Workspace* w, size_t
   return HR2_OK;
 }
 
+// The workspace's ring and setup views of the streamed operand, grown to at
+// least `floats` and `views` (outside stream capture).
+static int ws_ensure_stream(hr2_ctx* ctx, cudaStream_t stream, Workspace* w, size_t floats, int views) {
+  std::lock_guard<std::mutex> lk(ctx->mu);
+  if (w->ring_cap >= floats && w->views_cap >= views) return HR2_OK;
+  if (stream_capturing(stream))
+    return fail(HR2_EBUSY, "the streamed operand's ring must grow while the stream is capturing; call the batch once first");
+  HR2_CU(cudaStreamSynchronize(stream));
+  int rc;
+  if (w->ring_cap < floats) {
+    dfree(ctx, w->ring);
+    w->ring = nullptr;
+    w->ring_cap = 0;
+    if ((rc = dalloc_t(ctx, &w->ring, floats))) return rc;
+    w->ring_cap = floats;
+  }
+  if (w->views_cap < views) {
+    dfree(ctx, w->views);
+    w->views = nullptr;
+    w->views_cap = 0;
+    if ((rc = dalloc_t(ctx, &w->views, (size_t)views))) return rc;
+    w->views_cap = views;
+  }
+  return HR2_OK;
+}
+
 // ------------------------------------------------------------ contexts
 extern "C" int hr2_ctx_create(int device, size_t mem_budget_bytes, hr2_ctx** out) {
   if (!out) return fail(HR2_EINVAL, "out is NULL");
@@ -316,6 +359,13 @@ extern "C" int hr2_set_launch_config(hr2_ctx* ctx, const hr2_launch_cfg* cfg) {
   if (cfg->split_max_batch < 0 || cfg->split_max_batch > 65535)   // the absorption pass puts the batch on grid z
     return fail(HR2_EINVAL, "split_max_batch %d outside 0..65535", cfg->split_max_batch);
   ctx->cfg = *cfg;
+  return HR2_OK;
+}
+
+extern "C" int hr2_set_stream_group(hr2_ctx* ctx, int tiles) {
+  if (!ctx) return fail(HR2_EINVAL, "ctx is NULL");
+  if (tiles < 0) return fail(HR2_EINVAL, "tiles %d < 0", tiles);
+  ctx->stream_group = tiles;
   return HR2_OK;
 }
 
@@ -605,8 +655,11 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
     return fail(HR2_EINVAL, "obs_flux and obs_sigma must both be given or both be NULL");
   if (d->interp != HR2_INTERP_LOG10 && d->interp != HR2_INTERP_LINEAR)
     return fail(HR2_EINVAL, "interp %d is neither HR2_INTERP_LOG10 nor HR2_INTERP_LINEAR", d->interp);
-  if (d->interp == HR2_INTERP_LINEAR && th.storage == HR2_STORE_FP16_OFFSET && !d->level_cache)
-    return fail(HR2_EINVAL, "the linear interpolation option on FP16 tables needs level_cache");
+  if (d->interp == HR2_INTERP_LINEAR && th.storage == HR2_STORE_FP16_OFFSET &&
+      (!d->level_cache || d->level_cache == HR2_LEVEL_CACHE_STREAM))
+    return fail(HR2_EINVAL, "the linear interpolation option on FP16 tables needs level_cache (not streamed)");
+  if (d->level_cache == HR2_LEVEL_CACHE_STREAM && th.storage != HR2_STORE_FP16_OFFSET)
+    return fail(HR2_EINVAL, "the streamed operand needs FP16 tables");
   if (d->profile != HR2_PROFILE_FE && d->profile != HR2_PROFILE_MILNE)
     return fail(HR2_EINVAL, "profile %d is neither HR2_PROFILE_FE nor HR2_PROFILE_MILNE", d->profile);
   if (d->sc != HR2_SC_LINEAR && d->sc != HR2_SC_PARABOLIC)
@@ -791,7 +844,9 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
   // per tile, level, T cell and operand row (absorbers, then the two CIA
   // pairs): 2 kTileNu floats (row and T difference)
   const size_t per_tile = (size_t)h.n_lev * (h.n_species + 2) * (th.n_T - 1) * 2 * kTileNu;
-  bool want_operand = d->level_cache != 0 && th.storage == HR2_STORE_FP16_OFFSET;
+  const bool stream_op = d->level_cache == HR2_LEVEL_CACHE_STREAM;
+  bool want_operand = d->level_cache != 0 && !stream_op && th.storage == HR2_STORE_FP16_OFFSET;
+  if (stream_op) h.lvl32_tile_floats = (long long)per_tile;   // the ring's tile stride
   if (want_operand && d->level_cache == HR2_LEVEL_CACHE_AUTO) {
     // the operand where it fits the context's budget and half the free memory
     const size_t bytes = per_tile * h.n_tiles * sizeof(float);
@@ -827,6 +882,20 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
   if ((e = cudaMemcpy(st->dev, &h, sizeof(SetupDev), cudaMemcpyHostToDevice)) != cudaSuccess) {
     rc = fail(HR2_ECUDA, "setup descriptor: %s", cudaGetErrorString(e));
     goto fail_tmp;
+  }
+  if (d->level_cache == HR2_LEVEL_CACHE_STREAM) {
+    // the descriptor batches are prepared with on the streamed path: records
+    // and weights of the level-gridded sweep (the operand itself comes per
+    // group of tiles through the views); st->dev above stays the direct one
+    SetupDev hs = h;
+    hs.cached = 1;
+    if ((rc = dalloc_t(ctx, &st->dev_stream, 1))) goto fail_tmp;
+    track(st->dev_stream);
+    if ((e = cudaMemcpy(st->dev_stream, &hs, sizeof(SetupDev), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      rc = fail(HR2_ECUDA, "setup descriptor: %s", cudaGetErrorString(e));
+      goto fail_tmp;
+    }
+    st->streamed = true;
   }
   dfree(ctx, d_quad);
   dfree(ctx, d_edges);
@@ -880,7 +949,7 @@ extern "C" int hr2_setup_memory(const hr2_setup* s, size_t* bytes, size_t* opera
   }
   if (bytes) *bytes = total;
   if (operand_bytes) *operand_bytes = s->operand_bytes;
-  if (level_gridded) *level_gridded = s->host.cached;
+  if (level_gridded) *level_gridded = s->host.cached ? 1 : (s->streamed ? HR2_LEVEL_CACHE_STREAM : 0);
   return HR2_OK;
 }
 
@@ -986,6 +1055,107 @@ static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {
   return {w, ctas, st};
 }
 
+// Batches of at least this many samples on a single streamed setup take the
+// streamed operand; smaller ones (and mixed batches) read the tables directly.
+// On the 290001-point, 12-absorber tables one call costs about 14 ms of
+// operand build plus 0.155 ms per sample, against 0.394 ms per sample read
+// directly: equal near 60 samples.
+constexpr int kStreamMinBatch = 64;
+// largest ring of the streamed operand chosen automatically
+constexpr size_t kStreamRingMaxBytes = (size_t)1 << 30;
+
+// One batch on a setup created with HR2_LEVEL_CACHE_STREAM: the samples are
+// prepared once (records of the level-gridded sweep), then, per group of
+// consecutive tiles, the operand of the group is built into the stream's
+// ring (k_level_stream), the work of the group is planned and the persistent
+// forward kernel sweeps it through the group's setup view; the binning runs
+// once over the whole range.  Groups are sized so that each holds about four
+// work items per persistent CTA (or ctx->stream_group tiles), with the ring
+// at most kStreamRingMaxBytes.
+static int forward_streamed(hr2_ctx* ctx, const hr2_setup* st, BatchShape sh, const int* setup_of_sample,
+                            const double* params, int n, float* out_bins, int bins_ld, float* out_highres,
+                            int highres_ld, int* out_status, cudaStream_t s) {
+  sh.cached = 1;   // the sweep reads a level-gridded operand, from the ring
+  Workspace* w = nullptr;
+  int rc = ws_ensure(ctx, s, n, sh.max_lev, out_highres ? 0 : sh.max_nu, 0, 0, 0, &w);
+  if (rc) return rc;
+  const SetupDev& h = st->host;
+  const LaunchShape ls = shape_for(ctx, sh, n);
+  const int grid = ctx->n_sm * ls.ctas_per_sm;
+  const size_t per_tile = (size_t)h.lvl32_tile_floats;
+  int group = ctx->stream_group;
+  if (group <= 0) {
+    const long long sblocks = (n + ls.warps - 1) / ls.warps;
+    const long long tpi = std::max(1, ctx->cfg.tiles_per_item);
+    group = (int)std::min<long long>(h.n_tiles, (4LL * grid * tpi + sblocks - 1) / sblocks);
+    group = (int)std::min<size_t>((size_t)group, std::max<size_t>(1, kStreamRingMaxBytes / (per_tile * sizeof(float))));
+  }
+  group = std::max(1, std::min(group, h.n_tiles));
+  const int n_groups = (h.n_tiles + group - 1) / group;
+  if ((rc = ws_ensure_stream(ctx, s, w, (size_t)group * per_tile, n_groups))) return rc;
+  FwdArgs a{};
+  a.setups[0] = st->dev_stream;
+  a.n_setups = 1;
+  a.n = n;
+  a.setup_of_sample = setup_of_sample;
+  a.params = params;
+  a.perm = w->perm;
+  a.plan = w->plan;
+  a.counter = w->counter;
+  a.status = out_status;
+  a.recs = w->recs;
+  a.rec_ld = w->lev_cap;
+  a.samp = w->samp;
+  a.warps = ls.warps;
+  a.tiles_per_item = ctx->cfg.tiles_per_item;
+  a.err = (int*)(w->counter + 1);
+  a.wait_limit = ctx->wait_limit;
+  a.tx_extra = ctx->wait_fault ? 16u : 0u;
+  a.highres = out_highres ? out_highres : w->highres;
+  a.highres_ld = out_highres ? highres_ld : w->nu_cap;
+  fill_node_constants(a, 1, &st);
+  cudaError_t e;
+  if ((e = launch_prep(a, s)) != cudaSuccess) return fail(HR2_ECUDA, "prep launch: %s", cudaGetErrorString(e));
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (ctx->profiling) {
+    HR2_CU(cudaEventCreate(&ev.first));
+    if ((e = cudaEventCreate(&ev.second)) != cudaSuccess) {
+      cudaEventDestroy(ev.first);
+      return fail(HR2_ECUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+    }
+  }
+  auto launch_failed = [&](const char* what, cudaError_t err) {
+    if (ev.first) cudaEventDestroy(ev.first);
+    if (ev.second) cudaEventDestroy(ev.second);
+    return fail(HR2_ECUDA, "%s launch: %s", what, cudaGetErrorString(err));
+  };
+  // (the profiling events bracket every group: operand builds, plans and sweeps)
+  if (ev.first && (e = cudaEventRecord(ev.first, s)) != cudaSuccess) return launch_failed("event", e);
+  if ((e = build_stream_views(st->dev_stream, w->ring, group, n_groups, w->views, s)) != cudaSuccess)
+    return launch_failed("setup views", e);
+  for (int g = 0; g < n_groups; ++g) {
+    const int lo = g * group, cnt = std::min(group, h.n_tiles - lo);
+    if ((e = build_level_stream(st->dev_stream, h.n_lev, h.n_species + 2, lo, cnt, w->ring, s)) != cudaSuccess)
+      return launch_failed("streamed operand", e);
+    FwdArgs ag = a;
+    ag.setups[0] = w->views + g;
+    FwdArgs ap = ag;
+    if (g > 0) ap.err = nullptr;   // the first plan cleared the error word; later groups keep what it holds
+    if ((e = launch_plan(ap, w->perm, w->plan, s)) != cudaSuccess) return launch_failed("plan", e);
+    if ((e = launch_forward32(ag, sh.max_mu, grid, true, sh.linear != 0, sh.para != 0, sh.max_k, absorber_bound(sh),
+                              ls.stages, s)) != cudaSuccess)
+      return launch_failed("forward32", e);
+  }
+  if (ev.second && (e = cudaEventRecord(ev.second, s)) != cudaSuccess) return launch_failed("event", e);
+  if (ev.first) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->prof.push_back(ev);
+  }
+  if ((e = launch_bins(a, out_bins, bins_ld, false, s)) != cudaSuccess)
+    return fail(HR2_ECUDA, "bins launch: %s", cudaGetErrorString(e));
+  return HR2_OK;
+}
+
 extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups,
                                    const int* setup_of_sample, const double* params, int n, float* out_bins,
                                    int bins_ld, float* out_highres, int highres_ld, int* out_status, void* stream) {
@@ -1004,6 +1174,9 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
   if (fp64 && n > 65535) return fail(HR2_EINVAL, "the FP64 path takes at most 65535 samples per call");
   HR2_CU(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
+  if (n_setups == 1 && setups[0]->streamed && n >= kStreamMinBatch)
+    return forward_streamed(ctx, setups[0], sh, setup_of_sample, params, n, out_bins, bins_ld, out_highres, highres_ld,
+                            out_status, s);
   Workspace* w = nullptr;
   rc = ws_ensure(ctx, s, n, sh.max_lev, (!fp64 && !out_highres) ? sh.max_nu : 0, fp64 ? sh.max_nu : 0, 0, 0, &w);
   if (rc) return rc;

@@ -523,4 +523,101 @@ cudaError_t build_level_cache(const TablesDev* d_tab, const SetupDev& h, float* 
   return cudaGetLastError();
 }
 
+// ------------------------------------------ streamed level-gridded operand
+// The same operand as k_level_cache (layout, per tile: [level][T cell][row]
+// [kTileNu/2 pairs][4]), built at evaluation time for a group of n_tiles
+// consecutive tiles of setup S starting at its tile tile_lo, into ring
+// (tile tt of the group at ring + tt * S.lvl32_tile_floats), in FP32
+// arithmetic: g = log2(10) (v0 + w_p (v1 - v0)) of the FP16 rows v0, v1 of
+// the level's p cell (log10 option only).  One thread per (tile, level, row,
+// pair of columns) walks the T rows and writes each T cell's
+// {g[a], g[a+1] - g[a]} of its two columns as one 16-byte store, so that 64
+// threads write one cell's 1 KB block contiguously.
+__global__ void __launch_bounds__(64) k_level_stream(const SetupDev* __restrict__ sp, int tile_lo, int n_tiles,
+                                                     float* __restrict__ ring) {
+  const SetupDev& S = *sp;
+  const TablesDev& t = *S.tables;
+  const int q = threadIdx.x;                       // pair of columns within the tile
+  const int n_rows = S.n_species + 2;
+  int b = blockIdx.x;
+  const int s = b % n_rows;
+  b /= n_rows;
+  const int j = b % S.n_lev;
+  const int tt = b / S.n_lev;
+  if (tt >= n_tiles) return;
+  const int n_cells = t.n_T - 1;
+  const LevelDev lv = S.levels[j];
+  const float wp = (float)lv.wp64;
+  const float l2 = (float)kLog2_10;
+  const size_t col = (size_t)(S.tile0 + tile_lo + tt) * kTileNu + 2 * q;
+  const __half* base;
+  size_t a_step;
+  bool interp = true, zero = false;
+  if (s < S.n_species) {
+    base = t.sig16 + (((size_t)S.species[s] * t.n_T) * t.n_p + lv.pcell) * t.nu_pad + col;
+    a_step = (size_t)t.n_p * t.nu_pad;
+  } else {
+    const int pair = s - S.n_species;
+    base = t.cia16 + (size_t)pair * t.n_T * t.nu_pad + col;
+    a_step = (size_t)t.nu_pad;
+    interp = false;
+    zero = !t.has_cia[pair];
+  }
+  float4* out = reinterpret_cast<float4*>(ring + (size_t)tt * S.lvl32_tile_floats) +
+                (((size_t)j * n_cells) * n_rows + s) * (kTileNu / 2) + q;
+  const size_t cell_step = (size_t)n_rows * (kTileNu / 2);   // float4s from one T cell to the next
+  float2 gp = make_float2(0.f, 0.f);
+  for (int a = 0; a < t.n_T; ++a) {
+    float2 g = make_float2(0.f, 0.f);
+    if (!zero) {
+      const __half2 h0 = *reinterpret_cast<const __half2*>(base + a * a_step);
+      const float2 v0 = __half22float2(h0);
+      if (interp) {
+        const float2 v1 = __half22float2(*reinterpret_cast<const __half2*>(base + a * a_step + t.nu_pad));
+        g = make_float2(l2 * fmaf(wp, v1.x - v0.x, v0.x), l2 * fmaf(wp, v1.y - v0.y, v0.y));
+      } else {
+        g = make_float2(l2 * v0.x, l2 * v0.y);
+      }
+    }
+    if (a > 0) out[(size_t)(a - 1) * cell_step] = make_float4(gp.x, gp.y, g.x - gp.x, g.y - gp.y);
+    gp = g;
+  }
+}
+
+// One setup view per group of group_tiles tiles: the setup with its tile
+// range, wavenumber constants and operand narrowed to the group and the
+// operand read from the ring (the forward kernel then sees an ordinary
+// level-gridded setup of up to group_tiles tiles; its output columns stay
+// those of the whole setup, since they follow tile0 and nu_first).
+__global__ void k_stream_views(const SetupDev* __restrict__ sp, const float* ring, int group_tiles, int n_groups,
+                               SetupDev* views) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= n_groups) return;
+  SetupDev v = *sp;
+  const int lo = g * group_tiles;
+  v.tile0 = sp->tile0 + lo;
+  v.n_tiles = min(group_tiles, sp->n_tiles - lo);
+  v.nu_pair = sp->nu_pair + (size_t)lo * (kTileNu / 2);
+  v.c1n_pair = sp->c1n_pair + (size_t)lo * (kTileNu / 2);
+  v.lvl32 = ring;
+  v.cached = 1;
+  views[g] = v;
+}
+
+cudaError_t build_level_stream(const SetupDev* d_setup, int n_lev, int n_rows, int tile_lo, int n_tiles, float* ring,
+                               cudaStream_t s) {
+  const long long blocks = (long long)n_tiles * n_lev * n_rows;
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_level_stream<<<(unsigned)blocks, kTileNu / 2, 0, s>>>(d_setup, tile_lo, n_tiles, ring);
+  return cudaGetLastError();
+}
+
+cudaError_t build_stream_views(const SetupDev* d_setup, const float* ring, int group_tiles, int n_groups,
+                               SetupDev* views, cudaStream_t s) {
+  if (n_groups <= 0) return cudaSuccess;
+  k_stream_views<<<(n_groups + 127) / 128, 128, 0, s>>>(d_setup, ring, group_tiles, n_groups, views);
+  return cudaGetLastError();
+}
+
 }  // namespace hr2

@@ -27,6 +27,7 @@ HR2_P_LOGG, HR2_P_F, HR2_P_DIST, HR2_P_T0, HR2_P_X0, HR2_P_CLOUD, HR2_NPARAM = 0
 HR2_STORE_FP16_OFFSET, HR2_STORE_FP64 = 1, 2
 HR2_INTERP_LOG10, HR2_INTERP_LINEAR = 0, 1
 HR2_LEVEL_CACHE_AUTO = 2
+HR2_LEVEL_CACHE_STREAM = 3
 INTERP = {"log10": HR2_INTERP_LOG10, "linear": HR2_INTERP_LINEAR}
 HR2_PROFILE_FE, HR2_PROFILE_MILNE = 0, 1
 PROFILE = {"fe": HR2_PROFILE_FE, "milne": HR2_PROFILE_MILNE}
@@ -42,7 +43,7 @@ EXPORTED = [
     "hr2_profile_read", "hr2_stream_check", "hr2_nodes_from_b", "hr2_version",
     "hr2_ns_state_init", "hr2_ns_absorb", "hr2_ns_propose", "hr2_ns_finalize", "hr2_effective_temperature",
     "hr2_measure_unit_rate", "hr2_noalloc_check", "hr2_set_wait_limit", "hr2_get_wait_limit",
-    "hr2_set_wait_fault", "hr2_setup_memory",
+    "hr2_set_wait_fault", "hr2_setup_memory", "hr2_set_stream_group",
 ]
 
 
@@ -107,6 +108,7 @@ def lib():
                 "hr2_ctx_memory": (C.c_int, [_VP, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)]),
                 "hr2_set_launch_config": (C.c_int, [_VP, C.POINTER(LaunchCfg)]),
                 "hr2_get_launch_config": (C.c_int, [_VP, C.POINTER(LaunchCfg)]),
+                "hr2_set_stream_group": (C.c_int, [_VP, C.c_int]),
                 "hr2_reserve": (C.c_int, [_VP, _VP, C.c_int, C.c_int]),
                 "create_opacity_tables": (C.c_int, [_VP, C.POINTER(TableDesc), _DP, _DP, _DP, C.c_int,
                                                     C.POINTER(_VP)]),
@@ -223,6 +225,11 @@ def hr2_set_launch_config(ctx, warps_per_cta: int, ctas_per_sm: int, tiles_per_i
     _check(lib().hr2_set_launch_config(ctx, C.byref(cfg)), ctx)
 
 
+def hr2_set_stream_group(ctx, tiles: int):
+    """Tiles per group of the streamed operand for later calls (0: sized by the batch)."""
+    _check(lib().hr2_set_stream_group(ctx, int(tiles)), ctx)
+
+
 def hr2_get_launch_config(ctx):
     """(warps_per_cta, ctas_per_sm, tiles_per_item, stages, split_max_batch)."""
     cfg = LaunchCfg()
@@ -318,15 +325,23 @@ def hr2_setup_memory(setup):
     """(device bytes of the setup, bytes of its level-gridded operand, whether the operand was built)."""
     b, ob, lg = C.c_size_t(), C.c_size_t(), C.c_int()
     _check(lib().hr2_setup_memory(setup, C.byref(b), C.byref(ob), C.byref(lg)))
-    return b.value, ob.value, bool(lg.value)
+    return b.value, ob.value, lg.value == 1
+
+
+def hr2_setup_streamed(setup) -> bool:
+    """Whether the setup builds its operand per call (level_cache="stream")."""
+    b, ob, lg = C.c_size_t(), C.c_size_t(), C.c_int()
+    _check(lib().hr2_setup_memory(setup, C.byref(b), C.byref(ob), C.byref(lg)))
+    return lg.value == HR2_LEVEL_CACHE_STREAM
 
 
 def _level_cache_arg(v) -> int:
-    """level_cache as the ABI takes it: True/False, or "auto" (HR2_LEVEL_CACHE_AUTO)."""
+    """level_cache as the ABI takes it: True/False, "auto" (HR2_LEVEL_CACHE_AUTO) or
+    "stream" (HR2_LEVEL_CACHE_STREAM)."""
     if isinstance(v, str):
-        if v != "auto":
-            raise ValueError("level_cache must be a bool or 'auto'")
-        return HR2_LEVEL_CACHE_AUTO
+        if v not in ("auto", "stream"):
+            raise ValueError("level_cache must be a bool, 'auto' or 'stream'")
+        return HR2_LEVEL_CACHE_AUTO if v == "auto" else HR2_LEVEL_CACHE_STREAM
     return int(bool(v))
 
 

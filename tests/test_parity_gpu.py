@@ -692,3 +692,12 @@ def test_large_tables_sampled(eng):
         assert rel_flux_err(hi[i][idx], ref) <= FLUX_RTOL
         refb, _ = om.bins_at(theta[i], sel)
         assert rel_flux_err(bins[i][sel], refb) <= FLUX_RTOL
+    # the same batch on the streamed operand: no 62 GB operand, a ring of one group of tiles
+    s1 = eng.add_setup(t, wl.setups[0], level_cache="stream")
+    b1, h1, st1 = _run(eng, [s1], sid, theta)
+    assert np.all(st1 == 0)
+    for i in (0, 131):
+        ref, _ = om.top_flux_at(theta[i], idx)
+        assert rel_flux_err(h1[i][idx], ref) <= FLUX_RTOL
+        refb, _ = om.bins_at(theta[i], sel)
+        assert rel_flux_err(b1[i][sel], refb) <= FLUX_RTOL

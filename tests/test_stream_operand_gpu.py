@@ -1,0 +1,139 @@
+"""The streamed level-gridded operand (level_cache="stream") through the C ABI.
+
+A streamed setup keeps no operand: a call with it alone and at least 64
+samples builds the operand (the tables interpolated in p onto the levels,
+FP32 arithmetic) one group of tiles at a time into a per-stream ring and
+sweeps each group before building the next.  The oracle is the FP64 oracle on
+the tables as stored; the operand's own rounding differs from the
+level-gridded operand built once at creation (FP64 arithmetic), so the two
+agree to FP32 rounding, not bit for bit.  Per tile the arithmetic does not
+depend on how the tiles are grouped, so every grouping gives the same bits.
+"""
+import numpy as np
+import pytest
+
+from paper_1910_01070_b300 import hr2
+from paper_1910_01070_b300 import workloads as W
+from paper_1910_01070_b300.engine import Engine
+from tests.helpers import FLUX_RTOL, oracle_model, rel_flux_err, tables_as_stored
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def eng():
+    from paper_1910_01070_b300 import build
+    build.build()
+    e = Engine(0)
+    yield e
+    e.close()
+
+
+def _case():
+    # 8 tiles of 128 points (the last one ragged), 20 layers, 3 absorbers
+    spec = W.TableSpec(3, np.linspace(300.0, 3000.0, 7), np.linspace(-4.0, 2.0, 6), 5000.0, 1.0, 1100, seed=71)
+    setup = W.make_setup(spec, 5030.0, 5990.0, 20, [0, 1, 2], 4, 3, 2, 400.0, 24)
+    return spec, W.make_tables(spec), setup
+
+
+def _run(eng, s, setup, theta):
+    n = len(theta)
+    bins = torch.full((n, setup.n_bins), -1.0, dtype=torch.float32, device="cuda")
+    hi = torch.full((n, setup.n_nu), -1.0, dtype=torch.float32, device="cuda")
+    st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    sd = torch.zeros(n, dtype=torch.int32, device="cuda")
+    th = torch.as_tensor(theta, device="cuda")
+    hr2.forward_model_batch(eng.ctx, [s], sd, th, bins, hi, st)
+    hr2.hr2_stream_check(eng.ctx)
+    torch.cuda.synchronize()
+    return bins.cpu().numpy(), hi.cpu().numpy(), st.cpu().numpy()
+
+
+def test_streamed_setup_matches_oracle_over_several_groups(eng):
+    spec, tabs, setup = _case()
+    t = eng.add_tables(spec, "fp16", tabs)
+    s = eng.add_setup(t, setup, level_cache="stream")
+    assert hr2.hr2_setup_streamed(s)
+    b_, ob, lg = hr2.hr2_setup_memory(s)
+    assert ob == 0 and lg is False
+    theta = W.draw_params(setup, 64, 5, W.Prior())
+    hr2.hr2_set_stream_group(eng.ctx, 3)             # groups of 3, 3 and 2 tiles
+    try:
+        bins, hi, st = _run(eng, s, setup, theta)
+    finally:
+        hr2.hr2_set_stream_group(eng.ctx, 0)
+    assert np.all(st == 0)
+    om = oracle_model(tables_as_stored(tabs, "fp16"), setup)
+    for i in range(0, 64, 5):
+        ob_, otop, ok = om.forward(theta[i], want_top=True)
+        assert ok
+        assert rel_flux_err(hi[i], otop) <= FLUX_RTOL
+        assert rel_flux_err(bins[i], ob_) <= FLUX_RTOL
+
+
+def test_groupings_agree_bitwise_and_with_the_level_gridded_operand(eng):
+    spec, tabs, setup = _case()
+    t = eng.add_tables(spec, "fp16", tabs)
+    s_str = eng.add_setup(t, setup, level_cache="stream")
+    s_lvl = eng.add_setup(t, setup, level_cache=True)
+    theta = W.draw_params(setup, 64, 6, W.Prior())
+    out = {}
+    for g in (1, 3, 8, 0):
+        hr2.hr2_set_stream_group(eng.ctx, g)
+        try:
+            out[g] = _run(eng, s_str, setup, theta)
+        finally:
+            hr2.hr2_set_stream_group(eng.ctx, 0)
+    for g in (1, 3, 8):
+        assert np.array_equal(out[g][0], out[0][0])
+        assert np.array_equal(out[g][1], out[0][1])
+    bl, hl, stl = _run(eng, s_lvl, setup, theta)
+    assert np.all(stl == 0) and np.all(out[0][2] == 0)
+    # FP32 against FP64 arithmetic of the same operand: a few units of FP32 rounding
+    for i in range(64):
+        assert rel_flux_err(out[0][1][i], hl[i].astype(np.float64)) <= 2e-5
+        assert rel_flux_err(out[0][0][i], bl[i].astype(np.float64)) <= 2e-5
+
+
+def test_small_and_mixed_batches_read_the_tables_directly(eng):
+    """Below 64 samples, or beside another setup, a streamed setup is evaluated like a
+    setup without an operand: the same bits as one created with level_cache=False."""
+    spec, tabs, setup = _case()
+    t = eng.add_tables(spec, "fp16", tabs)
+    s_str = eng.add_setup(t, setup, level_cache="stream")
+    s_dir = eng.add_setup(t, setup, level_cache=False)
+    theta = W.draw_params(setup, 12, 7, W.Prior())
+    a = _run(eng, s_str, setup, theta)
+    b = _run(eng, s_dir, setup, theta)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # mixed with a direct setup in one call (40 samples, alternating)
+    theta = W.draw_params(setup, 40, 8, W.Prior())
+    sid = (np.arange(40) % 2).astype(np.int32)
+    n = 40
+    bins = torch.empty((n, setup.n_bins), dtype=torch.float32, device="cuda")
+    hi = torch.empty((n, setup.n_nu), dtype=torch.float32, device="cuda")
+    hr2.forward_model_batch(eng.ctx, [s_str, s_dir], torch.as_tensor(sid, device="cuda"),
+                            torch.as_tensor(theta, device="cuda"), bins, hi, None)
+    torch.cuda.synchronize()
+    h = hi.cpu().numpy()
+    assert np.all(np.isfinite(h))
+    b2 = _run(eng, s_dir, setup, theta)
+    assert np.array_equal(h, b2[1])
+
+
+def test_streamed_option_argument_errors(eng):
+    spec, tabs, setup = _case()
+    t64 = eng.add_tables(spec, "fp64", tabs)
+    with pytest.raises(hr2.Hr2Error) as ei:
+        eng.add_setup(t64, setup, level_cache="stream")
+    assert ei.value.code == hr2.HR2_EINVAL
+    t = eng.add_tables(spec, "fp16", tabs)
+    setup.interp = "linear"
+    with pytest.raises(hr2.Hr2Error) as ei:
+        eng.add_setup(t, setup, level_cache="stream")
+    assert ei.value.code == hr2.HR2_EINVAL
+    with pytest.raises(hr2.Hr2Error) as ei:
+        hr2.hr2_set_stream_group(eng.ctx, -1)
+    assert ei.value.code == hr2.HR2_EINVAL
