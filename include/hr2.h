@@ -181,9 +181,9 @@ typedef struct {
                                  bilinearly.  HR2_LEVEL_CACHE_AUTO: the
                                  operand if it fits both the context's budget
                                  (when one is set) and half the device's free
-                                 memory at creation, else the direct path (the
-                                 linear option, which needs the operand, then
-                                 fails with HR2_ENOMEM).  hr2_setup_memory
+                                 memory at creation, else the streamed operand
+                                 below (the linear option, which needs the
+                                 operand, then fails with HR2_ENOMEM).  hr2_setup_memory
                                  tells which was built.  One batch call takes
                                  setups of a single kind.
                                  HR2_LEVEL_CACHE_STREAM (log10 option only):
@@ -197,7 +197,9 @@ typedef struct {
                                  which costs one operand build per call but
                                  holds only the ring on the device; smaller
                                  calls and calls that mix it with other setups
-                                 read the tables directly.  hr2_setup_memory
+                                 read the tables directly, and so does a call
+                                 whose ring fits neither the context's budget
+                                 nor the device's memory.  hr2_setup_memory
                                  reports HR2_LEVEL_CACHE_STREAM for it.          */
   int interp;                 /* HR2_INTERP_LOG10 or HR2_INTERP_LINEAR.  With
                                  FP16 tables the linear option needs

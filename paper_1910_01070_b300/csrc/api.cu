@@ -844,9 +844,8 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
   // per tile, level, T cell and operand row (absorbers, then the two CIA
   // pairs): 2 kTileNu floats (row and T difference)
   const size_t per_tile = (size_t)h.n_lev * (h.n_species + 2) * (th.n_T - 1) * 2 * kTileNu;
-  const bool stream_op = d->level_cache == HR2_LEVEL_CACHE_STREAM;
+  bool stream_op = d->level_cache == HR2_LEVEL_CACHE_STREAM;
   bool want_operand = d->level_cache != 0 && !stream_op && th.storage == HR2_STORE_FP16_OFFSET;
-  if (stream_op) h.lvl32_tile_floats = (long long)per_tile;   // the ring's tile stride
   if (want_operand && d->level_cache == HR2_LEVEL_CACHE_AUTO) {
     // the operand where it fits the context's budget and half the free memory
     const size_t bytes = per_tile * h.n_tiles * sizeof(float);
@@ -861,6 +860,11 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
       goto fail_tmp;
     }
     want_operand = fits;
+    stream_op = !fits;   // the operand per call and group of tiles instead
+  }
+  if (stream_op) {
+    h.lvl32_tile_floats = (long long)per_tile;   // the ring's tile stride
+    st->streamed = true;
   }
   if (want_operand) {
     float* d_lvl = nullptr;
@@ -883,7 +887,7 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
     rc = fail(HR2_ECUDA, "setup descriptor: %s", cudaGetErrorString(e));
     goto fail_tmp;
   }
-  if (d->level_cache == HR2_LEVEL_CACHE_STREAM) {
+  if (st->streamed) {
     // the descriptor batches are prepared with on the streamed path: records
     // and weights of the level-gridded sweep (the operand itself comes per
     // group of tiles through the views); st->dev above stays the direct one
@@ -895,7 +899,6 @@ extern "C" int hr2_setup_create(hr2_ctx* ctx, const hr2_tables* tab, const hr2_s
       rc = fail(HR2_ECUDA, "setup descriptor: %s", cudaGetErrorString(e));
       goto fail_tmp;
     }
-    st->streamed = true;
   }
   dfree(ctx, d_quad);
   dfree(ctx, d_edges);
@@ -1063,6 +1066,8 @@ static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {
 constexpr int kStreamMinBatch = 64;
 // largest ring of the streamed operand chosen automatically
 constexpr size_t kStreamRingMaxBytes = (size_t)1 << 30;
+// forward_streamed: no ring fits; the caller evaluates the batch directly
+constexpr int kStreamFallback = 1;
 
 // One batch on a setup created with HR2_LEVEL_CACHE_STREAM: the samples are
 // prepared once (records of the level-gridded sweep), then, per group of
@@ -1091,8 +1096,23 @@ static int forward_streamed(hr2_ctx* ctx, const hr2_setup* st, BatchShape sh, co
     group = (int)std::min<size_t>((size_t)group, std::max<size_t>(1, kStreamRingMaxBytes / (per_tile * sizeof(float))));
   }
   group = std::max(1, std::min(group, h.n_tiles));
+  {
+    // within the context's budget (what the ring already holds counts as free)
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (ctx->budget) {
+      const size_t held = w->ring_cap * sizeof(float) + (size_t)w->views_cap * sizeof(SetupDev);
+      const size_t room = ctx->budget > ctx->used - std::min(ctx->used, held) ? ctx->budget - (ctx->used - std::min(ctx->used, held)) : 0;
+      const size_t views_b = (size_t)h.n_tiles * sizeof(SetupDev);
+      const size_t fit = room > views_b ? (room - views_b) / (per_tile * sizeof(float)) : 0;
+      group = (int)std::min<size_t>((size_t)group, fit);
+    }
+  }
+  if (group < 1) return kStreamFallback;
   const int n_groups = (h.n_tiles + group - 1) / group;
-  if ((rc = ws_ensure_stream(ctx, s, w, (size_t)group * per_tile, n_groups))) return rc;
+  if ((rc = ws_ensure_stream(ctx, s, w, (size_t)group * per_tile, n_groups))) {
+    if (rc == HR2_ENOMEM) return kStreamFallback;   // the call reads the tables directly
+    return rc;
+  }
   FwdArgs a{};
   a.setups[0] = st->dev_stream;
   a.n_setups = 1;
@@ -1174,9 +1194,12 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
   if (fp64 && n > 65535) return fail(HR2_EINVAL, "the FP64 path takes at most 65535 samples per call");
   HR2_CU(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  if (n_setups == 1 && setups[0]->streamed && n >= kStreamMinBatch)
-    return forward_streamed(ctx, setups[0], sh, setup_of_sample, params, n, out_bins, bins_ld, out_highres, highres_ld,
-                            out_status, s);
+  if (n_setups == 1 && setups[0]->streamed && n >= kStreamMinBatch) {
+    rc = forward_streamed(ctx, setups[0], sh, setup_of_sample, params, n, out_bins, bins_ld, out_highres, highres_ld,
+                          out_status, s);
+    if (rc != kStreamFallback) return rc;
+    t_last_error.clear();
+  }
   Workspace* w = nullptr;
   rc = ws_ensure(ctx, s, n, sh.max_lev, (!fp64 && !out_highres) ? sh.max_nu : 0, fp64 ? sh.max_nu : 0, 0, 0, &w);
   if (rc) return rc;

@@ -628,8 +628,9 @@ def test_memory_budget_admission():
 
 def test_level_gridded_operand_where_it_fits():
     """level_cache='auto' builds the level-gridded operand only where it fits the context's budget
-    (and half the free device memory); otherwise the setup evaluates the FP16 tables directly,
-    with the same results as a setup created without the operand.  The operand's size is
+    (and half the free device memory); otherwise the setup streams the operand (built per call
+    into a ring that fits the budget) and reads the FP16 tables directly below 64 samples, with
+    the same results as a setup created without the operand there.  The operand's size is
     levels x (T cells) x (absorbers + 2 CIA rows) x tiles of 128 points x 8 bytes."""
     spec, tabs = _absorber_spec(6, 77)
     setup = W.make_setup(spec, 5000.0, 5299.0, 24, range(6), 4, 3, 2, 300.0, 6)
@@ -646,6 +647,8 @@ def test_level_gridded_operand_where_it_fits():
         b2, ob2, lg2 = hr2.hr2_setup_memory(s_direct)
         assert not lg2 and ob2 == 0 and b2 == b - ob
         ref_direct = _run(big, [s_direct], sid, theta)
+        theta64 = W.draw_params(setup, 64, 72, W.Prior())
+        ref64 = _run(big, [s_direct], np.zeros(64, np.int32), theta64)
     with Engine(0) as probe:
         t = probe.add_tables(spec, "fp16", tabs)
         tables_bytes = probe.memory()[0]
@@ -654,8 +657,16 @@ def test_level_gridded_operand_where_it_fits():
         t = small.add_tables(spec, "fp16", tabs)
         s = small.add_setup(t, setup, level_cache="auto")
         assert hr2.hr2_setup_memory(s)[2] is False
+        assert hr2.hr2_setup_streamed(s)
         got = _run(small, [s], sid, theta)
         assert np.array_equal(got[0], ref_direct[0]) and np.array_equal(got[1], ref_direct[1])
+        # 64 samples stream the operand through a ring that fits what the budget leaves
+        got64 = _run(small, [s], np.zeros(64, np.int32), theta64)
+        used, budget = small.memory()
+        assert used <= budget
+        for i in range(64):
+            assert rel_flux_err(got64[1][i], ref64[1][i].astype(np.float64)) <= 2e-5
+            assert rel_flux_err(got64[0][i], ref64[0][i].astype(np.float64)) <= 2e-5
         with pytest.raises(hr2.Hr2Error) as ei:
             small.add_setup(t, dataclasses.replace(setup, interp="linear"), level_cache="auto")
         assert ei.value.code == hr2.HR2_ENOMEM
