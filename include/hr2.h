@@ -191,7 +191,7 @@ typedef struct {
                                  alone and at least 64 samples builds the
                                  operand per group of consecutive 128-point
                                  tiles into a ring in the stream's workspace
-                                 (FP32 arithmetic; at most 1 GiB unless
+                                 (FP32 arithmetic; at most 4 GiB unless
                                  hr2_set_stream_group says otherwise) and
                                  sweeps each group before the next is built,
                                  which costs one operand build per call but
@@ -464,8 +464,8 @@ int hr2_stream_check(hr2_ctx* ctx, void* stream);
 int hr2_noalloc_check(hr2_ctx* ctx, void* stream);
 
 /* Tiles per group of the streamed operand (HR2_LEVEL_CACHE_STREAM) for
- * later calls: 0 (the default) sizes each group so that it holds about four
- * work items per persistent CTA, with the ring at most 1 GiB; a positive
+ * later calls: 0 (the default) sizes each group so that it holds about eight
+ * work items per persistent CTA, with the ring at most 4 GiB; a positive
  * count fixes it (the ring then holds that many tiles' operand, which the
  * context's budget must allow).  No counterpart in the paper: it trades the
  * ring's memory against the number of groups.  HR2_EINVAL for tiles < 0. */

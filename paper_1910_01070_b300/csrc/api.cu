@@ -1064,8 +1064,9 @@ static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {
 // operand build plus 0.155 ms per sample, against 0.394 ms per sample read
 // directly: equal near 60 samples.
 constexpr int kStreamMinBatch = 64;
-// largest ring of the streamed operand chosen automatically
-constexpr size_t kStreamRingMaxBytes = (size_t)1 << 30;
+// largest ring of the streamed operand chosen automatically (on the
+// 290001-point tables at batch 64: 27.1 ms with 1 GiB, 22.4 ms with 4 GiB)
+constexpr size_t kStreamRingMaxBytes = (size_t)4 << 30;
 // forward_streamed: no ring fits; the caller evaluates the batch directly
 constexpr int kStreamFallback = 1;
 
@@ -1074,7 +1075,7 @@ constexpr int kStreamFallback = 1;
 // consecutive tiles, the operand of the group is built into the stream's
 // ring (k_level_stream), the work of the group is planned and the persistent
 // forward kernel sweeps it through the group's setup view; the binning runs
-// once over the whole range.  Groups are sized so that each holds about four
+// once over the whole range.  Groups are sized so that each holds about eight
 // work items per persistent CTA (or ctx->stream_group tiles), with the ring
 // at most kStreamRingMaxBytes.
 static int forward_streamed(hr2_ctx* ctx, const hr2_setup* st, BatchShape sh, const int* setup_of_sample,
@@ -1092,7 +1093,7 @@ static int forward_streamed(hr2_ctx* ctx, const hr2_setup* st, BatchShape sh, co
   if (group <= 0) {
     const long long sblocks = (n + ls.warps - 1) / ls.warps;
     const long long tpi = std::max(1, ctx->cfg.tiles_per_item);
-    group = (int)std::min<long long>(h.n_tiles, (4LL * grid * tpi + sblocks - 1) / sblocks);
+    group = (int)std::min<long long>(h.n_tiles, (8LL * grid * tpi + sblocks - 1) / sblocks);
     group = (int)std::min<size_t>((size_t)group, std::max<size_t>(1, kStreamRingMaxBytes / (per_tile * sizeof(float))));
   }
   group = std::max(1, std::min(group, h.n_tiles));
