@@ -407,7 +407,9 @@ def run_hr2(args, world, rank, local):
                            "l2": "flushed between timed steps (256 MB write outside the events)",
                            "launch": list(hr2.hr2_get_launch_config(eng.ctx))},
                 "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
-                "fp64_path": fp64, "e2e": e2e, "roofline": roofline, "hbm": hbm, "cpu_baseline": cpu, "clocks": clk,
+                "fp64_path": fp64, "e2e": e2e, "roofline": roofline, "hbm": hbm,
+                "effective_streaming": effective_streaming(setup, value),
+                "cpu_baseline": cpu, "clocks": clk,
                 "gpu_launches": 5 * args.steps}
         if graph:
             line["graph_replay"] = graph
@@ -417,6 +419,16 @@ def run_hr2(args, world, rank, local):
             line["speedup_vs_fp64_path"] = value / fp64["value"]
         print(json.dumps(line), flush=True)
     eng.close()
+
+
+def effective_streaming(setup, models_per_s: float) -> dict:
+    """Models/s times the table bytes one model interpolates from, (L+1) levels x 4 corners
+    x N_nu points x (K absorbers + 1/2 for the two CIA rows) x 2 bytes of FP16: the rate a
+    design without on-chip reuse would have to stream; above the HBM peak by the reuse."""
+    per_model = (setup.n_layers + 1) * 4 * setup.n_nu * (len(setup.species) + 0.5) * 2
+    return {"gbs": models_per_s * per_model / 1e9, "bytes_per_model": per_model,
+            "label": "effective streaming bandwidth (models/s x per-model algorithmic table bytes; "
+                     "not DRAM traffic, which is in hbm)"}
 
 
 def graph_replay_timing(eng, setups, pool, n, n_bins, n_nu, flush, local, reps=60):
