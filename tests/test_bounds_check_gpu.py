@@ -36,3 +36,18 @@ def test_parity_cases_pass_under_index_checks():
     assert r.returncode == 0, tail
     m = re.search(r"(\d+) passed", tail)
     assert m and int(m.group(1)) >= 20 and "failed" not in tail, tail
+
+
+def test_streamed_operand_cases_pass_under_index_checks():
+    """The streamed operand's cases: the forward kernel's operand reads through each group's
+    setup view (tile range and ring) checked against the view's bounds."""
+    from paper_1910_01070_b300 import build
+    lib = build.build(bounds_check=True)
+    env = dict(os.environ, HR2_LIBRARY=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_stream_operand_gpu.py"), "-q",
+                        "-m", "gpu", "-p", "no:cacheprovider"], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=1800)
+    tail = (r.stdout + r.stderr)[-3000:]
+    assert r.returncode == 0, tail
+    m = re.search(r"(\d+) passed", tail)
+    assert m and int(m.group(1)) >= 4 and "failed" not in tail, tail
