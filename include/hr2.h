@@ -199,7 +199,13 @@ typedef struct {
                                  calls and calls that mix it with other setups
                                  read the tables directly, and so does a call
                                  whose ring fits neither the context's budget
-                                 nor the device's memory.  hr2_setup_memory
+                                 nor the device's memory.  The ring and the
+                                 group descriptors are allocated by a call on
+                                 the stream that needs more than it holds,
+                                 never during stream capture: capture a
+                                 streamed batch only after one eager call of
+                                 the same size on that stream (HR2_EBUSY
+                                 otherwise).  hr2_setup_memory
                                  reports HR2_LEVEL_CACHE_STREAM for it.          */
   int interp;                 /* HR2_INTERP_LOG10 or HR2_INTERP_LINEAR.  With
                                  FP16 tables the linear option needs

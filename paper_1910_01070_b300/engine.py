@@ -40,6 +40,9 @@ class Engine:
         return h
 
     def add_setup(self, tables, s: W.SetupSpec, obs_flux=None, obs_sigma=None, level_cache=True):
+        """A setup on the engine's tables.  level_cache: True (the level-gridded operand, built
+        once), False (the FP16 tables read directly), "auto" (the operand where it fits, else
+        streamed) or "stream" (the operand built per call and group of tiles into a ring)."""
         h = hr2.hr2_setup_create(self.ctx, tables, s.nu_first, s.n_nu, s.n_layers, s.species, s.n_mu,
                                  s.fe_elements, s.fe_order, s.resolving_power, s.bin_edges, s.p_top, s.p_bot,
                                  s.r_he, s.radius_cm, obs_flux, obs_sigma, level_cache, s.interp, s.profile, s.cloud, s.sc)

@@ -137,3 +137,27 @@ def test_streamed_option_argument_errors(eng):
     with pytest.raises(hr2.Hr2Error) as ei:
         hr2.hr2_set_stream_group(eng.ctx, -1)
     assert ei.value.code == hr2.HR2_EINVAL
+
+
+def test_streamed_batch_replayed_from_a_cuda_graph(eng):
+    """graphs.CapturedBatch on a streamed setup: its eager warm-up calls allocate the
+    capture stream's ring, the capture records every group's build, plan and sweep, and a
+    replay gives the eager call's bits."""
+    from paper_1910_01070_b300 import graphs
+    spec, tabs, setup = _case()
+    t = eng.add_tables(spec, "fp16", tabs)
+    s = eng.add_setup(t, setup, level_cache="stream")
+    theta = W.draw_params(setup, 64, 9, W.Prior())
+    ref_b, _, st = _run(eng, s, setup, theta)
+    assert np.all(st == 0)
+    D, sig = W.mock_observation(ref_b[0].astype(np.float64), 9)
+    eng.set_observation(s, D, sig)
+    hr2.hr2_set_stream_group(eng.ctx, 3)
+    try:
+        cb = graphs.CapturedBatch(eng.ctx, [s], 64, setup.n_bins, setup.n_nu)
+        lnl, bins = cb.run(torch.as_tensor(theta), torch.zeros(64, dtype=torch.int32))
+        got = bins.cpu().numpy()
+    finally:
+        hr2.hr2_set_stream_group(eng.ctx, 0)
+    assert np.array_equal(got[:, : setup.n_bins], ref_b)
+    assert np.all(np.isfinite(lnl.cpu().numpy()))
