@@ -387,7 +387,11 @@ int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups
  * library allocate: a host application whose device memory belongs to
  * another allocator (a framework's caching pool that must account for every
  * byte), or a latency-critical evaluation loop that cannot accept the
- * device-wide synchronisation cudaMalloc may imply.
+ * device-wide synchronisation cudaMalloc may imply.  A setup created with
+ * HR2_LEVEL_CACHE_STREAM (or streamed by HR2_LEVEL_CACHE_AUTO) is read
+ * directly here at every batch size, since its ring would need an
+ * allocation: from 64 samples up forward_model_batch streams it instead, and
+ * the two agree to the FP32 rounding of the streamed operand.
  *
  * Its scratch (per-sample and per-level records, the work plan and the work
  * counter) lives in one statically sized device array of
@@ -415,7 +419,8 @@ int forward_model_batch_noalloc(hr2_ctx* ctx, int n_setups, const hr2_setup* con
  * (No counterpart in the paper.)  While enabled, every forward_model_batch
  * records a pair of CUDA events on its stream around the launch of the main
  * forward kernel (k_forward32 / k_forward64; with the two-pass direct path,
- * around both passes), so a caller can time that
+ * around both passes; with the streamed operand, around every group's
+ * build, plan and sweep), so a caller can time that
  * kernel alone inside a longer step.  hr2_profile_read waits for the
  * recorded events, returns the summed kernel time in ms and the number of
  * launches, and with reset != 0 forgets them. */
