@@ -1058,6 +1058,28 @@ static LaunchShape shape_for(const hr2_ctx* ctx, const BatchShape& sh, int n) {
   return {w, ctas, st};
 }
 
+// The fields of a batch's kernel arguments that come from the context, the
+// stream's workspace and the caller's inputs (setups, outputs and the
+// two-pass or streamed extras are the caller's).
+static void fill_batch_args(FwdArgs& a, const hr2_ctx* ctx, const Workspace* w, const LaunchShape& ls,
+                            const int* setup_of_sample, const double* params, int n, int* out_status) {
+  a.n = n;
+  a.setup_of_sample = setup_of_sample;
+  a.params = params;
+  a.perm = w->perm;
+  a.plan = w->plan;
+  a.counter = w->counter;
+  a.status = out_status;
+  a.recs = w->recs;
+  a.rec_ld = w->lev_cap;
+  a.samp = w->samp;
+  a.warps = ls.warps;
+  a.tiles_per_item = ctx->cfg.tiles_per_item;
+  a.err = (int*)(w->counter + 1);
+  a.wait_limit = ctx->wait_limit;
+  a.tx_extra = ctx->wait_fault ? 16u : 0u;
+}
+
 // Batches of at least this many samples on a single streamed setup take the
 // streamed operand; smaller ones (and mixed batches) read the tables directly.
 // On the 290001-point, 12-absorber tables one call costs about 14 ms of
@@ -1117,21 +1139,7 @@ static int forward_streamed(hr2_ctx* ctx, const hr2_setup* st, BatchShape sh, co
   FwdArgs a{};
   a.setups[0] = st->dev_stream;
   a.n_setups = 1;
-  a.n = n;
-  a.setup_of_sample = setup_of_sample;
-  a.params = params;
-  a.perm = w->perm;
-  a.plan = w->plan;
-  a.counter = w->counter;
-  a.status = out_status;
-  a.recs = w->recs;
-  a.rec_ld = w->lev_cap;
-  a.samp = w->samp;
-  a.warps = ls.warps;
-  a.tiles_per_item = ctx->cfg.tiles_per_item;
-  a.err = (int*)(w->counter + 1);
-  a.wait_limit = ctx->wait_limit;
-  a.tx_extra = ctx->wait_fault ? 16u : 0u;
+  fill_batch_args(a, ctx, w, ls, setup_of_sample, params, n, out_status);
   a.highres = out_highres ? out_highres : w->highres;
   a.highres_ld = out_highres ? highres_ld : w->nu_cap;
   fill_node_constants(a, 1, &st);
@@ -1207,22 +1215,8 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
   FwdArgs a{};
   for (int g = 0; g < n_setups; ++g) a.setups[g] = setups[g]->dev;
   a.n_setups = n_setups;
-  a.n = n;
-  a.setup_of_sample = setup_of_sample;
-  a.params = params;
-  a.perm = w->perm;
-  a.plan = w->plan;
-  a.counter = w->counter;
-  a.status = out_status;
-  a.recs = w->recs;
-  a.rec_ld = w->lev_cap;
-  a.samp = w->samp;
   const LaunchShape ls = shape_for(ctx, sh, n);
-  a.warps = ls.warps;
-  a.tiles_per_item = ctx->cfg.tiles_per_item;
-  a.err = (int*)(w->counter + 1);
-  a.wait_limit = ctx->wait_limit;
-  a.tx_extra = ctx->wait_fault ? 16u : 0u;
+  fill_batch_args(a, ctx, w, ls, setup_of_sample, params, n, out_status);
   fill_node_constants(a, n_setups, setups);
   // small batches on tables read in place run in two passes: the absorption
   // coefficients of every level first, in parallel, then the sweep; their
