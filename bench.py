@@ -56,7 +56,7 @@ def parse():
     p.add_argument("--sweep-large", action="store_true",
                    help="instead of the main line: batch sweep on the 290001-point, 12-absorber tables")
     p.add_argument("--sweep-nu", type=int, default=290001, help="wavenumber points of the swept tables")
-    p.add_argument("--sweep-modes", default="direct,cached")
+    p.add_argument("--sweep-modes", default="direct,cached,stream")
     p.add_argument("--sweep-batches", default="1,2,4,8,16,32,64,128,256")
     p.add_argument("--sweep-reps", type=int, default=0,
                    help="timed launches per sweep point (0: about 0.3 s worth, at least 3)")
@@ -778,7 +778,11 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
                 key = "%s_b%d" % ("cached" if mode == "cached" else ("direct2" if passes == 2 else "direct"), b)
                 line["operand_bytes"] = hr2.hr2_setup_memory(h)[1]
                 if mode == "stream":
-                    line["ring_bytes"] = ring_bytes
+                    # the operand every call writes (all T cells of every level and tile) and
+                    # its rate over the whole call
+                    build_b = (s.n_layers + 1) * n_tiles * 128 * (len(s.species) + 2) * 8 * (len(wl.table.T_grid) - 1)
+                    line.update({"ring_bytes": ring_bytes, "operand_build_bytes_per_call": build_b,
+                                 "operand_build_gbs_over_call": build_b / (ms / 1e3) / 1e9})
                 if counters and mode != "stream" and key in counters.get("dram_bytes_per_launch", {}):
                     dram = counters["dram_bytes_per_launch"][key]
                     line.update({"dram_bytes_per_launch": dram, "dram_gbs": dram / (ms / 1e3) / 1e9,
