@@ -21,8 +21,10 @@ using namespace hr2;
 
 namespace hr2 {
 // streamed level-gridded operand (kern_setup.cu)
-cudaError_t build_level_stream(const SetupDev* d_setup, int n_lev, int n_rows, int tile_lo, int n_tiles, float* ring,
-                               cudaStream_t s);
+cudaError_t build_level_stream(const SetupDev* d_setup, int n_lev, int n_rows, int tile_lo, int n_tiles,
+                               const unsigned char* mask, float* ring, cudaStream_t s);
+cudaError_t build_cell_mask(const LevRec* recs, int rec_ld, const SampleDev* samp, int n, int n_lev, int n_cells,
+                            unsigned char* mask, cudaStream_t s);
 cudaError_t build_stream_views(const SetupDev* d_setup, const float* ring, int group_tiles, int n_groups,
                                SetupDev* views, cudaStream_t s);
 }  // namespace hr2
@@ -83,6 +85,8 @@ struct Workspace {
   size_t ring_cap = 0;        // floats
   SetupDev* views = nullptr;  // streamed operand: one setup view per group
   int views_cap = 0;
+  unsigned char* cells = nullptr;   // streamed operand: the batch's (level, T cell) mask
+  size_t cells_cap = 0;
 };
 
 struct hr2_ctx {
@@ -177,6 +181,7 @@ static void ws_free(hr2_ctx* ctx, Workspace* w) {
   dfree(ctx, w->chi);
   dfree(ctx, w->ring);
   dfree(ctx, w->views);
+  dfree(ctx, w->cells);
   unsigned int* keep = w->h_counter;
   *w = Workspace();
   w->h_counter = keep;
@@ -266,11 +271,11 @@ static int ws_ensure_chi(hr2_ctx* ctx, cudaStream_t stream, Workspace* w, size_t
   return HR2_OK;
 }
 
-// The workspace's ring and setup views of the streamed operand, grown to at
-// least `floats` and `views` (outside stream capture).
-static int ws_ensure_stream(hr2_ctx* ctx, cudaStream_t stream, Workspace* w, size_t floats, int views) {
+// The workspace's ring, setup views and cell mask of the streamed operand,
+// grown to at least `floats`, `views` and `cells` (outside stream capture).
+static int ws_ensure_stream(hr2_ctx* ctx, cudaStream_t stream, Workspace* w, size_t floats, int views, size_t cells) {
   std::lock_guard<std::mutex> lk(ctx->mu);
-  if (w->ring_cap >= floats && w->views_cap >= views) return HR2_OK;
+  if (w->ring_cap >= floats && w->views_cap >= views && w->cells_cap >= cells) return HR2_OK;
   if (stream_capturing(stream))
     return fail(HR2_EBUSY, "the streamed operand's ring must grow while the stream is capturing; call the batch once first");
   HR2_CU(cudaStreamSynchronize(stream));
@@ -288,6 +293,13 @@ static int ws_ensure_stream(hr2_ctx* ctx, cudaStream_t stream, Workspace* w, siz
     w->views_cap = 0;
     if ((rc = dalloc_t(ctx, &w->views, (size_t)views))) return rc;
     w->views_cap = views;
+  }
+  if (w->cells_cap < cells) {
+    dfree(ctx, w->cells);
+    w->cells = nullptr;
+    w->cells_cap = 0;
+    if ((rc = dalloc_t(ctx, &w->cells, cells))) return rc;
+    w->cells_cap = cells;
   }
   return HR2_OK;
 }
@@ -1095,7 +1107,8 @@ constexpr int kStreamFallback = 1;
 // One batch on a setup created with HR2_LEVEL_CACHE_STREAM: the samples are
 // prepared once (records of the level-gridded sweep), then, per group of
 // consecutive tiles, the operand of the group is built into the stream's
-// ring (k_level_stream), the work of the group is planned and the persistent
+// ring (k_level_stream; only the (level, T cell) blocks some sample of the
+// batch sits in, from k_mark_cells), the work of the group is planned and the persistent
 // forward kernel sweeps it through the group's setup view; the binning runs
 // once over the whole range.  Groups are sized so that each holds about eight
 // work items per persistent CTA (or ctx->stream_group tiles), with the ring
@@ -1132,7 +1145,8 @@ static int forward_streamed(hr2_ctx* ctx, const hr2_setup* st, BatchShape sh, co
   }
   if (group < 1) return kStreamFallback;
   const int n_groups = (h.n_tiles + group - 1) / group;
-  if ((rc = ws_ensure_stream(ctx, s, w, (size_t)group * per_tile, n_groups))) {
+  const int n_cells = st->tables->host.n_T - 1;
+  if ((rc = ws_ensure_stream(ctx, s, w, (size_t)group * per_tile, n_groups, (size_t)h.n_lev * n_cells))) {
     if (rc == HR2_ENOMEM) return kStreamFallback;   // the call reads the tables directly
     return rc;
   }
@@ -1162,9 +1176,12 @@ static int forward_streamed(hr2_ctx* ctx, const hr2_setup* st, BatchShape sh, co
   if (ev.first && (e = cudaEventRecord(ev.first, s)) != cudaSuccess) return launch_failed("event", e);
   if ((e = build_stream_views(st->dev_stream, w->ring, group, n_groups, w->views, s)) != cudaSuccess)
     return launch_failed("setup views", e);
+  // the (level, T cell) pairs the batch's samples sit in: the only blocks built
+  if ((e = build_cell_mask(w->recs, w->lev_cap, w->samp, n, h.n_lev, n_cells, w->cells, s)) != cudaSuccess)
+    return launch_failed("cell mask", e);
   for (int g = 0; g < n_groups; ++g) {
     const int lo = g * group, cnt = std::min(group, h.n_tiles - lo);
-    if ((e = build_level_stream(st->dev_stream, h.n_lev, h.n_species + 2, lo, cnt, w->ring, s)) != cudaSuccess)
+    if ((e = build_level_stream(st->dev_stream, h.n_lev, h.n_species + 2, lo, cnt, w->cells, w->ring, s)) != cudaSuccess)
       return launch_failed("streamed operand", e);
     FwdArgs ag = a;
     ag.setups[0] = w->views + g;

@@ -1,6 +1,8 @@
 // kern_setup.cu -- device kernels run once per table or setup creation:
 // table quantisation, level grid, quadrature nodes and the combined
 // instrument-profile + binning operator W.  All in FP64.
+#include <algorithm>
+
 #include "hr2_internal.cuh"
 
 namespace hr2 {
@@ -532,8 +534,11 @@ cudaError_t build_level_cache(const TablesDev* d_tab, const SetupDev& h, float* 
 // the level's p cell (log10 option only).  One thread per (tile, level, row,
 // pair of columns) walks the T rows and writes each T cell's
 // {g[a], g[a+1] - g[a]} of its two columns as one 16-byte store, so that 64
-// threads write one cell's 1 KB block contiguously.
+// threads write one cell's 1 KB block contiguously.  With a cell mask
+// ([level][T cell], from k_mark_cells) only the cells some sample of the
+// batch sits in at that level are written: the sweep reads no other.
 __global__ void __launch_bounds__(64) k_level_stream(const SetupDev* __restrict__ sp, int tile_lo, int n_tiles,
+                                                     const unsigned char* __restrict__ mask,
                                                      float* __restrict__ ring) {
   const SetupDev& S = *sp;
   const TablesDev& t = *S.tables;
@@ -579,9 +584,35 @@ __global__ void __launch_bounds__(64) k_level_stream(const SetupDev* __restrict_
         g = make_float2(l2 * v0.x, l2 * v0.y);
       }
     }
-    if (a > 0) out[(size_t)(a - 1) * cell_step] = make_float4(gp.x, gp.y, g.x - gp.x, g.y - gp.y);
+    if (a > 0 && (!mask || mask[(size_t)j * n_cells + a - 1]))
+      out[(size_t)(a - 1) * cell_step] = make_float4(gp.x, gp.y, g.x - gp.x, g.y - gp.y);
     gp = g;
   }
+}
+
+// The T cells the batch's valid samples sit in, per level: mask[j * n_cells
+// + a] = 1 where some sample's record of level j holds cell a (records of the
+// level-gridded sweep, written by k_prep).  The mask starts at zero.
+__global__ void k_mark_cells(const LevRec* __restrict__ recs, int rec_ld, const SampleDev* __restrict__ samp, int n,
+                             int n_lev, int n_cells, unsigned char* mask) {
+  const long long total = (long long)n * n_lev;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / n_lev), j = (int)(idx % n_lev);
+    if (samp[i].status != 0) continue;
+    const int a = reinterpret_cast<const LevRecC*>(recs + (size_t)i * rec_ld)[j].acell;
+    if (a >= 0 && a < n_cells) mask[(size_t)j * n_cells + a] = 1;
+  }
+}
+
+cudaError_t build_cell_mask(const LevRec* recs, int rec_ld, const SampleDev* samp, int n, int n_lev, int n_cells,
+                            unsigned char* mask, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(mask, 0, (size_t)n_lev * n_cells, s);
+  if (e != cudaSuccess || n <= 0) return e;
+  const long long total = (long long)n * n_lev;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+  k_mark_cells<<<blocks, 256, 0, s>>>(recs, rec_ld, samp, n, n_lev, n_cells, mask);
+  return cudaGetLastError();
 }
 
 // One setup view per group of group_tiles tiles: the setup with its tile
@@ -604,12 +635,12 @@ __global__ void k_stream_views(const SetupDev* __restrict__ sp, const float* rin
   views[g] = v;
 }
 
-cudaError_t build_level_stream(const SetupDev* d_setup, int n_lev, int n_rows, int tile_lo, int n_tiles, float* ring,
-                               cudaStream_t s) {
+cudaError_t build_level_stream(const SetupDev* d_setup, int n_lev, int n_rows, int tile_lo, int n_tiles,
+                               const unsigned char* mask, float* ring, cudaStream_t s) {
   const long long blocks = (long long)n_tiles * n_lev * n_rows;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  k_level_stream<<<(unsigned)blocks, kTileNu / 2, 0, s>>>(d_setup, tile_lo, n_tiles, ring);
+  k_level_stream<<<(unsigned)blocks, kTileNu / 2, 0, s>>>(d_setup, tile_lo, n_tiles, mask, ring);
   return cudaGetLastError();
 }
 

@@ -161,3 +161,32 @@ def test_streamed_batch_replayed_from_a_cuda_graph(eng):
         hr2.hr2_set_stream_group(eng.ctx, 0)
     assert np.array_equal(got[:, : setup.n_bins], ref_b)
     assert np.all(np.isfinite(lnl.cpu().numpy()))
+
+
+def test_concentrated_batch_builds_only_the_cells_it_uses(eng):
+    """64 samples within 1 % of one draw sit in few T cells per level, so most of the ring's
+    blocks are not rebuilt for them and hold an earlier group's contents: the results still
+    match the level-gridded operand (FP32 rounding) and do not depend on the grouping."""
+    spec, tabs, setup = _case()
+    t = eng.add_tables(spec, "fp16", tabs)
+    s_str = eng.add_setup(t, setup, level_cache="stream")
+    s_lvl = eng.add_setup(t, setup, level_cache=True)
+    base = W.draw_params(setup, 1, 10, W.Prior())[0]
+    rng = np.random.default_rng(10)
+    theta = np.repeat(base[None, :], 64, axis=0)
+    theta[:, 3:10] *= 1.0 + 0.01 * rng.standard_normal((64, 7))
+    prior = W.draw_params(setup, 64, 11, W.Prior())
+    out = {}
+    for g in (2, 0):
+        hr2.hr2_set_stream_group(eng.ctx, g)
+        try:
+            _run(eng, s_str, setup, prior)          # fills the ring with other cells first
+            out[g] = _run(eng, s_str, setup, theta)
+        finally:
+            hr2.hr2_set_stream_group(eng.ctx, 0)
+    assert np.array_equal(out[2][0], out[0][0]) and np.array_equal(out[2][1], out[0][1])
+    bl, hl, _ = _run(eng, s_lvl, setup, theta)
+    assert np.all(out[0][2] == 0)
+    for i in range(64):
+        assert rel_flux_err(out[0][1][i], hl[i].astype(np.float64)) <= 2e-5
+        assert rel_flux_err(out[0][0][i], bl[i].astype(np.float64)) <= 2e-5
