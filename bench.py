@@ -723,7 +723,7 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
         # "direct": the FP16 tables read in place (batches up to the context's split_max_batch
         # in two passes), "direct1": the same in one pass always, "cached": the level-gridded
         # operand, "stream": that operand built per call and group of tiles into a ring
-        # (batches of 64 and more; smaller ones read the tables directly, so they are skipped)
+        # (batches of 32 and more; smaller ones read the tables directly, so they are skipped)
         setups = {m: eng.add_setup(t, s, level_cache="stream" if m == "stream" else (m == "cached"))
                   for m in modes}
         cfg0 = hr2.hr2_get_launch_config(eng.ctx)
@@ -742,7 +742,7 @@ def large_table_sweep(local, n_nu=290001, modes=("direct", "cached"), batches=(1
             per_model_bytes = algo[mode]
             hr2.hr2_set_launch_config(eng.ctx, *cfg0[:4], 0 if mode == "direct1" else cfg0[4])
             for b in batches:
-                if mode == "stream" and b < 64:
+                if mode == "stream" and b < 32:
                     continue
                 th = torch.as_tensor(th_all[:b], device=dev)
                 sd = torch.zeros(b, dtype=torch.int32, device=dev)

@@ -188,7 +188,7 @@ typedef struct {
                                  setups of a single kind.
                                  HR2_LEVEL_CACHE_STREAM (log10 option only):
                                  no operand is kept; a call with this setup
-                                 alone and at least 64 samples builds the
+                                 alone and at least 32 samples builds the
                                  operand per group of consecutive 128-point
                                  tiles into a ring in the stream's workspace
                                  (FP32 arithmetic; at most 4 GiB unless
@@ -390,7 +390,7 @@ int hr2_evaluate_host(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups
  * device-wide synchronisation cudaMalloc may imply.  A setup created with
  * HR2_LEVEL_CACHE_STREAM (or streamed by HR2_LEVEL_CACHE_AUTO) is read
  * directly here at every batch size, since its ring would need an
- * allocation: from 64 samples up forward_model_batch streams it instead, and
+ * allocation: from 32 samples up forward_model_batch streams it instead, and
  * the two agree to the FP32 rounding of the streamed operand.
  *
  * Its scratch (per-sample and per-level records, the work plan and the work

@@ -1094,10 +1094,10 @@ static void fill_batch_args(FwdArgs& a, const hr2_ctx* ctx, const Workspace* w, 
 
 // Batches of at least this many samples on a single streamed setup take the
 // streamed operand; smaller ones (and mixed batches) read the tables directly.
-// On the 290001-point, 12-absorber tables one call costs about 14 ms of
-// operand build plus 0.155 ms per sample, against 0.394 ms per sample read
-// directly: equal near 60 samples.
-constexpr int kStreamMinBatch = 64;
+// On the 290001-point, 12-absorber tables (a prior-drawn batch, about half of
+// the (level, T cell) blocks built): 12.4 ms at 32 samples against 13.0 ms
+// read directly, 15.1 against 19.4 ms at 48; below 32 the direct path wins.
+constexpr int kStreamMinBatch = 32;
 // largest ring of the streamed operand chosen automatically (on the
 // 290001-point tables at batch 64: 27.1 ms with 1 GiB, 22.4 ms with 4 GiB)
 constexpr size_t kStreamRingMaxBytes = (size_t)4 << 30;

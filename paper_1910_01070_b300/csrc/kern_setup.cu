@@ -571,10 +571,13 @@ __global__ void __launch_bounds__(64) k_level_stream(const SetupDev* __restrict_
   float4* out = reinterpret_cast<float4*>(ring + (size_t)tt * S.lvl32_tile_floats) +
                 (((size_t)j * n_cells) * n_rows + s) * (kTileNu / 2) + q;
   const size_t cell_step = (size_t)n_rows * (kTileNu / 2);   // float4s from one T cell to the next
+  const unsigned char* mrow = mask ? mask + (size_t)j * n_cells : nullptr;
   float2 gp = make_float2(0.f, 0.f);
   for (int a = 0; a < t.n_T; ++a) {
     float2 g = make_float2(0.f, 0.f);
-    if (!zero) {
+    // T row a enters the cells a-1 and a; with a mask it is read only if one of them is built
+    const bool need = !mrow || (a > 0 && mrow[a - 1]) || (a < n_cells && mrow[a]);
+    if (!zero && need) {
       const __half2 h0 = *reinterpret_cast<const __half2*>(base + a * a_step);
       const float2 v0 = __half22float2(h0);
       if (interp) {
@@ -584,7 +587,7 @@ __global__ void __launch_bounds__(64) k_level_stream(const SetupDev* __restrict_
         g = make_float2(l2 * v0.x, l2 * v0.y);
       }
     }
-    if (a > 0 && (!mask || mask[(size_t)j * n_cells + a - 1]))
+    if (a > 0 && (!mrow || mrow[a - 1]))
       out[(size_t)(a - 1) * cell_step] = make_float4(gp.x, gp.y, g.x - gp.x, g.y - gp.y);
     gp = g;
   }

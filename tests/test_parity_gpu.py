@@ -629,7 +629,7 @@ def test_memory_budget_admission():
 def test_level_gridded_operand_where_it_fits():
     """level_cache='auto' builds the level-gridded operand only where it fits the context's budget
     (and half the free device memory); otherwise the setup streams the operand (built per call
-    into a ring that fits the budget) and reads the FP16 tables directly below 64 samples, with
+    into a ring that fits the budget) and reads the FP16 tables directly below 32 samples, with
     the same results as a setup created without the operand there.  The operand's size is
     levels x (T cells) x (absorbers + 2 CIA rows) x tiles of 128 points x 8 bytes."""
     spec, tabs = _absorber_spec(6, 77)

@@ -1,6 +1,6 @@
 """The streamed level-gridded operand (level_cache="stream") through the C ABI.
 
-A streamed setup keeps no operand: a call with it alone and at least 64
+A streamed setup keeps no operand: a call with it alone and at least 32
 samples builds the operand (the tables interpolated in p onto the levels,
 FP32 arithmetic) one group of tiles at a time into a per-stream ring and
 sweeps each group before building the next.  The oracle is the FP64 oracle on
@@ -98,7 +98,7 @@ def test_groupings_agree_bitwise_and_with_the_level_gridded_operand(eng):
 
 
 def test_small_and_mixed_batches_read_the_tables_directly(eng):
-    """Below 64 samples, or beside another setup, a streamed setup is evaluated like a
+    """Below 32 samples, or beside another setup, a streamed setup is evaluated like a
     setup without an operand: the same bits as one created with level_cache=False."""
     spec, tabs, setup = _case()
     t = eng.add_tables(spec, "fp16", tabs)
