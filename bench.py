@@ -586,7 +586,7 @@ def run_extras(args, local, flush):
                           "latency": "arrival to lnL on the host (served requests; rejected ones counted)",
                           "loads": res}
     if not args.no_large:
-        out["large_tables"] = large_table_sweep(local, modes=("direct", "cached", "stream"))
+        out["large_tables"] = large_table_sweep(local, modes=("direct", "cached", "stream"), batches=(1, 64, 256))
     out["linear_sigma_option"] = run_linear_option(args, local, flush)
     out["parabolic_source_option"] = run_linear_option(args, local, flush, sc="parabolic")
     out["nested_sampling"] = run_nested(args, local)
