@@ -187,17 +187,20 @@ typedef struct {
                                  tells which was built.  One batch call takes
                                  setups of a single kind.
                                  HR2_LEVEL_CACHE_STREAM (log10 option only):
-                                 no operand is kept; a call with this setup
-                                 alone and at least 32 samples builds the
-                                 operand per group of consecutive 128-point
-                                 tiles into a ring in the stream's workspace
+                                 no operand is kept; a call of at least 32
+                                 samples whose setups are all streamed builds
+                                 their operands per group of consecutive
+                                 128-point tiles (only the level and T cell
+                                 blocks its samples use) into a ring in the
+                                 stream's workspace
                                  (FP32 arithmetic; at most 4 GiB unless
                                  hr2_set_stream_group says otherwise) and
                                  sweeps each group before the next is built,
                                  which costs one operand build per call but
                                  holds only the ring on the device; smaller
-                                 calls and calls that mix it with other setups
-                                 read the tables directly, and so does a call
+                                 calls and calls that mix it with setups of
+                                 another kind read the tables directly, and
+                                 so does a call
                                  whose ring fits neither the context's budget
                                  nor the device's memory.  The ring and the
                                  group descriptors are allocated by a call on

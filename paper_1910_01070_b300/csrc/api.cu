@@ -22,11 +22,10 @@ using namespace hr2;
 namespace hr2 {
 // streamed level-gridded operand (kern_setup.cu)
 cudaError_t build_level_stream(const SetupDev* d_setup, int n_lev, int n_rows, int tile_lo, int n_tiles,
-                               const unsigned char* mask, float* ring, cudaStream_t s);
-cudaError_t build_cell_mask(const LevRec* recs, int rec_ld, const SampleDev* samp, int n, int n_lev, int n_cells,
-                            unsigned char* mask, cudaStream_t s);
-cudaError_t build_stream_views(const SetupDev* d_setup, const float* ring, int group_tiles, int n_groups,
-                               SetupDev* views, cudaStream_t s);
+                               const unsigned char* mask, int mask_stride, float* ring, cudaStream_t s);
+cudaError_t build_cell_mask(const FwdArgs& a, int max_lev, int stride, unsigned char* mask, cudaStream_t s);
+cudaError_t build_stream_views(const SetupDev* d_setup, const float* ring, int group_tiles, int n_groups, int ord,
+                               int n_setups, SetupDev* views, cudaStream_t s);
 }  // namespace hr2
 
 // ------------------------------------------------------------ tracing
@@ -1104,59 +1103,67 @@ constexpr size_t kStreamRingMaxBytes = (size_t)4 << 30;
 // forward_streamed: no ring fits; the caller evaluates the batch directly
 constexpr int kStreamFallback = 1;
 
-// One batch on a setup created with HR2_LEVEL_CACHE_STREAM: the samples are
-// prepared once (records of the level-gridded sweep), then, per group of
-// consecutive tiles, the operand of the group is built into the stream's
-// ring (k_level_stream; only the (level, T cell) blocks some sample of the
-// batch sits in, from k_mark_cells), the work of the group is planned and the persistent
-// forward kernel sweeps it through the group's setup view; the binning runs
-// once over the whole range.  Groups are sized so that each holds about eight
-// work items per persistent CTA (or ctx->stream_group tiles), with the ring
-// at most kStreamRingMaxBytes.
-static int forward_streamed(hr2_ctx* ctx, const hr2_setup* st, BatchShape sh, const int* setup_of_sample,
-                            const double* params, int n, float* out_bins, int bins_ld, float* out_highres,
-                            int highres_ld, int* out_status, cudaStream_t s) {
+// One batch on setups created with HR2_LEVEL_CACHE_STREAM (all of the call's
+// setups): the samples are prepared once (records of the level-gridded
+// sweep), then, per group of consecutive tiles (the same count of each
+// setup's own tiles), each setup's operand of the group is built into its
+// section of the stream's ring (k_level_stream; only the (level, T cell)
+// blocks some sample of the batch sits in, from k_mark_cells), the work of
+// the group is planned and the persistent forward kernel sweeps it through
+// the group's setup views (a setup whose tiles are all behind has none);
+// the binning runs once over the whole range.  Groups are sized so that each
+// holds about eight work items per persistent CTA (or ctx->stream_group
+// tiles), with the ring at most kStreamRingMaxBytes.
+static int forward_streamed(hr2_ctx* ctx, int n_setups, const hr2_setup* const* setups, BatchShape sh,
+                            const int* setup_of_sample, const double* params, int n, float* out_bins, int bins_ld,
+                            float* out_highres, int highres_ld, int* out_status, cudaStream_t s) {
   sh.cached = 1;   // the sweep reads a level-gridded operand, from the ring
   Workspace* w = nullptr;
   int rc = ws_ensure(ctx, s, n, sh.max_lev, out_highres ? 0 : sh.max_nu, 0, 0, 0, &w);
   if (rc) return rc;
-  const SetupDev& h = st->host;
   const LaunchShape ls = shape_for(ctx, sh, n);
   const int grid = ctx->n_sm * ls.ctas_per_sm;
-  const size_t per_tile = (size_t)h.lvl32_tile_floats;
+  // floats of one tile of every setup's operand, and its section offsets
+  size_t per_tile_all = 0;
+  int max_cells = 1;
+  for (int g = 0; g < n_setups; ++g) {
+    per_tile_all += (size_t)setups[g]->host.lvl32_tile_floats;
+    max_cells = std::max(max_cells, setups[g]->tables->host.n_T - 1);
+  }
+  const int max_tiles = sh.max_tiles;
   int group = ctx->stream_group;
   if (group <= 0) {
     const long long sblocks = (n + ls.warps - 1) / ls.warps;
     const long long tpi = std::max(1, ctx->cfg.tiles_per_item);
-    group = (int)std::min<long long>(h.n_tiles, (8LL * grid * tpi + sblocks - 1) / sblocks);
-    group = (int)std::min<size_t>((size_t)group, std::max<size_t>(1, kStreamRingMaxBytes / (per_tile * sizeof(float))));
+    group = (int)std::min<long long>(max_tiles, (8LL * grid * tpi + sblocks - 1) / sblocks);
+    group = (int)std::min<size_t>((size_t)group, std::max<size_t>(1, kStreamRingMaxBytes / (per_tile_all * sizeof(float))));
   }
-  group = std::max(1, std::min(group, h.n_tiles));
+  group = std::max(1, std::min(group, max_tiles));
+  const size_t mask_bytes = (size_t)n_setups * sh.max_lev * max_cells;
   {
     // within the context's budget (what the ring already holds counts as free)
     std::lock_guard<std::mutex> lk(ctx->mu);
     if (ctx->budget) {
-      const size_t held = w->ring_cap * sizeof(float) + (size_t)w->views_cap * sizeof(SetupDev);
+      const size_t held = w->ring_cap * sizeof(float) + (size_t)w->views_cap * sizeof(SetupDev) + w->cells_cap;
       const size_t room = ctx->budget > ctx->used - std::min(ctx->used, held) ? ctx->budget - (ctx->used - std::min(ctx->used, held)) : 0;
-      const size_t views_b = (size_t)h.n_tiles * sizeof(SetupDev);
-      const size_t fit = room > views_b ? (room - views_b) / (per_tile * sizeof(float)) : 0;
+      const size_t fixed = (size_t)max_tiles * n_setups * sizeof(SetupDev) + mask_bytes;
+      const size_t fit = room > fixed ? (room - fixed) / (per_tile_all * sizeof(float)) : 0;
       group = (int)std::min<size_t>((size_t)group, fit);
     }
   }
   if (group < 1) return kStreamFallback;
-  const int n_groups = (h.n_tiles + group - 1) / group;
-  const int n_cells = st->tables->host.n_T - 1;
-  if ((rc = ws_ensure_stream(ctx, s, w, (size_t)group * per_tile, n_groups, (size_t)h.n_lev * n_cells))) {
+  const int n_groups = (max_tiles + group - 1) / group;
+  if ((rc = ws_ensure_stream(ctx, s, w, (size_t)group * per_tile_all, n_groups * n_setups, mask_bytes))) {
     if (rc == HR2_ENOMEM) return kStreamFallback;   // the call reads the tables directly
     return rc;
   }
   FwdArgs a{};
-  a.setups[0] = st->dev_stream;
-  a.n_setups = 1;
+  for (int g = 0; g < n_setups; ++g) a.setups[g] = setups[g]->dev_stream;
+  a.n_setups = n_setups;
   fill_batch_args(a, ctx, w, ls, setup_of_sample, params, n, out_status);
   a.highres = out_highres ? out_highres : w->highres;
   a.highres_ld = out_highres ? highres_ld : w->nu_cap;
-  fill_node_constants(a, 1, &st);
+  fill_node_constants(a, n_setups, setups);
   cudaError_t e;
   if ((e = launch_prep(a, s)) != cudaSuccess) return fail(HR2_ECUDA, "prep launch: %s", cudaGetErrorString(e));
   std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
@@ -1174,19 +1181,32 @@ static int forward_streamed(hr2_ctx* ctx, const hr2_setup* st, BatchShape sh, co
   };
   // (the profiling events bracket every group: operand builds, plans and sweeps)
   if (ev.first && (e = cudaEventRecord(ev.first, s)) != cudaSuccess) return launch_failed("event", e);
-  if ((e = build_stream_views(st->dev_stream, w->ring, group, n_groups, w->views, s)) != cudaSuccess)
-    return launch_failed("setup views", e);
-  // the (level, T cell) pairs the batch's samples sit in: the only blocks built
-  if ((e = build_cell_mask(w->recs, w->lev_cap, w->samp, n, h.n_lev, n_cells, w->cells, s)) != cudaSuccess)
-    return launch_failed("cell mask", e);
-  for (int g = 0; g < n_groups; ++g) {
-    const int lo = g * group, cnt = std::min(group, h.n_tiles - lo);
-    if ((e = build_level_stream(st->dev_stream, h.n_lev, h.n_species + 2, lo, cnt, w->cells, w->ring, s)) != cudaSuccess)
-      return launch_failed("streamed operand", e);
+  std::vector<size_t> off(n_setups);
+  size_t acc = 0;
+  for (int g = 0; g < n_setups; ++g) {
+    off[g] = acc;
+    acc += (size_t)group * setups[g]->host.lvl32_tile_floats;
+    if ((e = build_stream_views(setups[g]->dev_stream, w->ring + off[g], group, n_groups, g, n_setups, w->views, s)) !=
+        cudaSuccess)
+      return launch_failed("setup views", e);
+  }
+  // the (level, T cell) pairs the batch's samples sit in, per setup: the only blocks built
+  if ((e = build_cell_mask(a, sh.max_lev, max_cells, w->cells, s)) != cudaSuccess) return launch_failed("cell mask", e);
+  for (int q = 0; q < n_groups; ++q) {
+    const int lo = q * group;
     FwdArgs ag = a;
-    ag.setups[0] = w->views + g;
+    for (int g = 0; g < n_setups; ++g) {
+      const SetupDev& h = setups[g]->host;
+      const int cnt = std::min(group, h.n_tiles - lo);
+      if (cnt > 0 &&
+          (e = build_level_stream(setups[g]->dev_stream, h.n_lev, h.n_species + 2, lo, cnt,
+                                  w->cells + (size_t)g * sh.max_lev * max_cells, max_cells, w->ring + off[g], s)) !=
+              cudaSuccess)
+        return launch_failed("streamed operand", e);
+      ag.setups[g] = w->views + (size_t)q * n_setups + g;
+    }
     FwdArgs ap = ag;
-    if (g > 0) ap.err = nullptr;   // the first plan cleared the error word; later groups keep what it holds
+    if (q > 0) ap.err = nullptr;   // the first plan cleared the error word; later groups keep what it holds
     if ((e = launch_plan(ap, w->perm, w->plan, s)) != cudaSuccess) return launch_failed("plan", e);
     if ((e = launch_forward32(ag, sh.max_mu, grid, true, sh.linear != 0, sh.para != 0, sh.max_k, absorber_bound(sh),
                               ls.stages, s)) != cudaSuccess)
@@ -1220,9 +1240,11 @@ extern "C" int forward_model_batch(hr2_ctx* ctx, int n_setups, const hr2_setup* 
   if (fp64 && n > 65535) return fail(HR2_EINVAL, "the FP64 path takes at most 65535 samples per call");
   HR2_CU(cudaSetDevice(ctx->device));
   cudaStream_t s = (cudaStream_t)stream;
-  if (n_setups == 1 && setups[0]->streamed && n >= kStreamMinBatch) {
-    rc = forward_streamed(ctx, setups[0], sh, setup_of_sample, params, n, out_bins, bins_ld, out_highres, highres_ld,
-                          out_status, s);
+  bool all_streamed = true;
+  for (int g = 0; g < n_setups; ++g) all_streamed = all_streamed && setups[g]->streamed;
+  if (all_streamed && n >= kStreamMinBatch) {
+    rc = forward_streamed(ctx, n_setups, setups, sh, setup_of_sample, params, n, out_bins, bins_ld, out_highres,
+                          highres_ld, out_status, s);
     if (rc != kStreamFallback) return rc;
     t_last_error.clear();
   }

@@ -535,10 +535,11 @@ cudaError_t build_level_cache(const TablesDev* d_tab, const SetupDev& h, float* 
 // pair of columns) walks the T rows and writes each T cell's
 // {g[a], g[a+1] - g[a]} of its two columns as one 16-byte store, so that 64
 // threads write one cell's 1 KB block contiguously.  With a cell mask
-// ([level][T cell], from k_mark_cells) only the cells some sample of the
-// batch sits in at that level are written: the sweep reads no other.
+// (this setup's [level][mask_stride] bytes, from k_mark_cells) only the cells
+// some sample of the batch sits in at that level are written, from only the
+// T rows they need: the sweep reads no other.
 __global__ void __launch_bounds__(64) k_level_stream(const SetupDev* __restrict__ sp, int tile_lo, int n_tiles,
-                                                     const unsigned char* __restrict__ mask,
+                                                     const unsigned char* __restrict__ mask, int mask_stride,
                                                      float* __restrict__ ring) {
   const SetupDev& S = *sp;
   const TablesDev& t = *S.tables;
@@ -571,7 +572,7 @@ __global__ void __launch_bounds__(64) k_level_stream(const SetupDev* __restrict_
   float4* out = reinterpret_cast<float4*>(ring + (size_t)tt * S.lvl32_tile_floats) +
                 (((size_t)j * n_cells) * n_rows + s) * (kTileNu / 2) + q;
   const size_t cell_step = (size_t)n_rows * (kTileNu / 2);   // float4s from one T cell to the next
-  const unsigned char* mrow = mask ? mask + (size_t)j * n_cells : nullptr;
+  const unsigned char* mrow = mask ? mask + (size_t)j * mask_stride : nullptr;
   float2 gp = make_float2(0.f, 0.f);
   for (int a = 0; a < t.n_T; ++a) {
     float2 g = make_float2(0.f, 0.f);
@@ -593,64 +594,68 @@ __global__ void __launch_bounds__(64) k_level_stream(const SetupDev* __restrict_
   }
 }
 
-// The T cells the batch's valid samples sit in, per level: mask[j * n_cells
-// + a] = 1 where some sample's record of level j holds cell a (records of the
-// level-gridded sweep, written by k_prep).  The mask starts at zero.
-__global__ void k_mark_cells(const LevRec* __restrict__ recs, int rec_ld, const SampleDev* __restrict__ samp, int n,
-                             int n_lev, int n_cells, unsigned char* mask) {
-  const long long total = (long long)n * n_lev;
+// The T cells the batch's valid samples sit in, per setup and level:
+// mask[(g * max_lev + j) * stride + a] = 1 where some sample of setup g has
+// cell a in its record of level j (records of the level-gridded sweep,
+// written by k_prep).  The mask starts at zero.
+__global__ void k_mark_cells(FwdArgs a, int max_lev, int stride, unsigned char* mask) {
+  const long long total = (long long)a.n * max_lev;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx / n_lev), j = (int)(idx % n_lev);
-    if (samp[i].status != 0) continue;
-    const int a = reinterpret_cast<const LevRecC*>(recs + (size_t)i * rec_ld)[j].acell;
-    if (a >= 0 && a < n_cells) mask[(size_t)j * n_cells + a] = 1;
+    const int i = (int)(idx / max_lev), j = (int)(idx % max_lev);
+    const SampleDev& sd = a.samp[i];
+    if (sd.status != 0 || sd.setup < 0 || sd.setup >= a.n_setups) continue;
+    const SetupDev& S = *a.setups[sd.setup];
+    if (j >= S.n_lev) continue;
+    const int c = reinterpret_cast<const LevRecC*>(a.recs + (size_t)i * a.rec_ld)[j].acell;
+    if (c >= 0 && c < S.tables->n_T - 1 && c < stride) mask[((size_t)sd.setup * max_lev + j) * stride + c] = 1;
   }
 }
 
-cudaError_t build_cell_mask(const LevRec* recs, int rec_ld, const SampleDev* samp, int n, int n_lev, int n_cells,
-                            unsigned char* mask, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(mask, 0, (size_t)n_lev * n_cells, s);
-  if (e != cudaSuccess || n <= 0) return e;
-  const long long total = (long long)n * n_lev;
+cudaError_t build_cell_mask(const FwdArgs& a, int max_lev, int stride, unsigned char* mask, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(mask, 0, (size_t)a.n_setups * max_lev * stride, s);
+  if (e != cudaSuccess || a.n <= 0) return e;
+  const long long total = (long long)a.n * max_lev;
   const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
-  k_mark_cells<<<blocks, 256, 0, s>>>(recs, rec_ld, samp, n, n_lev, n_cells, mask);
+  k_mark_cells<<<blocks, 256, 0, s>>>(a, max_lev, stride, mask);
   return cudaGetLastError();
 }
 
-// One setup view per group of group_tiles tiles: the setup with its tile
-// range, wavenumber constants and operand narrowed to the group and the
-// operand read from the ring (the forward kernel then sees an ordinary
-// level-gridded setup of up to group_tiles tiles; its output columns stay
-// those of the whole setup, since they follow tile0 and nu_first).
+// One setup view per group of group_tiles tiles, for setup `ord` of a batch
+// of n_setups (views[g * n_setups + ord]): the setup with its tile range,
+// wavenumber constants and operand narrowed to the group and the operand
+// read from its section of the ring (the forward kernel then sees an
+// ordinary level-gridded setup of up to group_tiles tiles, none once the
+// setup's tiles are all behind; its output columns stay those of the whole
+// setup, since they follow tile0 and nu_first).
 __global__ void k_stream_views(const SetupDev* __restrict__ sp, const float* ring, int group_tiles, int n_groups,
-                               SetupDev* views) {
+                               int ord, int n_setups, SetupDev* views) {
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= n_groups) return;
   SetupDev v = *sp;
-  const int lo = g * group_tiles;
+  const int lo = min(g * group_tiles, sp->n_tiles);
   v.tile0 = sp->tile0 + lo;
   v.n_tiles = min(group_tiles, sp->n_tiles - lo);
   v.nu_pair = sp->nu_pair + (size_t)lo * (kTileNu / 2);
   v.c1n_pair = sp->c1n_pair + (size_t)lo * (kTileNu / 2);
   v.lvl32 = ring;
   v.cached = 1;
-  views[g] = v;
+  views[(size_t)g * n_setups + ord] = v;
 }
 
 cudaError_t build_level_stream(const SetupDev* d_setup, int n_lev, int n_rows, int tile_lo, int n_tiles,
-                               const unsigned char* mask, float* ring, cudaStream_t s) {
+                               const unsigned char* mask, int mask_stride, float* ring, cudaStream_t s) {
   const long long blocks = (long long)n_tiles * n_lev * n_rows;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  k_level_stream<<<(unsigned)blocks, kTileNu / 2, 0, s>>>(d_setup, tile_lo, n_tiles, mask, ring);
+  k_level_stream<<<(unsigned)blocks, kTileNu / 2, 0, s>>>(d_setup, tile_lo, n_tiles, mask, mask_stride, ring);
   return cudaGetLastError();
 }
 
-cudaError_t build_stream_views(const SetupDev* d_setup, const float* ring, int group_tiles, int n_groups,
-                               SetupDev* views, cudaStream_t s) {
+cudaError_t build_stream_views(const SetupDev* d_setup, const float* ring, int group_tiles, int n_groups, int ord,
+                               int n_setups, SetupDev* views, cudaStream_t s) {
   if (n_groups <= 0) return cudaSuccess;
-  k_stream_views<<<(n_groups + 127) / 128, 128, 0, s>>>(d_setup, ring, group_tiles, n_groups, views);
+  k_stream_views<<<(n_groups + 127) / 128, 128, 0, s>>>(d_setup, ring, group_tiles, n_groups, ord, n_setups, views);
   return cudaGetLastError();
 }
 

@@ -190,3 +190,55 @@ def test_concentrated_batch_builds_only_the_cells_it_uses(eng):
     for i in range(64):
         assert rel_flux_err(out[0][1][i], hl[i].astype(np.float64)) <= 2e-5
         assert rel_flux_err(out[0][0][i], bl[i].astype(np.float64)) <= 2e-5
+
+
+def test_several_streamed_setups_in_one_call(eng):
+    """Three streamed setups (8, 4 and 5 tiles; 20, 16 and 24 layers; 3, 2 and 1 absorbers)
+    mixed in one call stream together: per group each builds its own tiles into its section
+    of the ring, and a setup whose tiles are all behind takes no work.  Against the same
+    setups with the level-gridded operand (FP32 rounding), across groupings (bit for bit)
+    and against the oracle."""
+    spec, tabs, _ = _case()
+    specs = [W.make_setup(spec, 5030.0, 5990.0, 20, [0, 1, 2], 4, 3, 2, 400.0, 24),
+             W.make_setup(spec, 5000.0, 5400.0, 16, [0, 2], 4, 3, 2, 300.0, 10),
+             W.make_setup(spec, 5500.0, 6090.0, 24, [1], 4, 3, 2, 500.0, 16)]
+    t = eng.add_tables(spec, "fp16", tabs)
+    s_str = [eng.add_setup(t, sp, level_cache="stream") for sp in specs]
+    s_lvl = [eng.add_setup(t, sp, level_cache=True) for sp in specs]
+    n = 96
+    sid = (np.arange(n) % 3).astype(np.int32)
+    theta = np.concatenate([W.draw_params(specs[g], 1, 100 + i, W.Prior()) for i, g in enumerate(sid)])
+    nb = max(sp.n_bins for sp in specs)
+    nn = max(sp.n_nu for sp in specs)
+
+    def run(setups):
+        bins = torch.full((n, nb), -1.0, dtype=torch.float32, device="cuda")
+        hi = torch.full((n, nn), -1.0, dtype=torch.float32, device="cuda")
+        st = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+        hr2.forward_model_batch(eng.ctx, setups, torch.as_tensor(sid, device="cuda"),
+                                torch.as_tensor(theta, device="cuda"), bins, hi, st)
+        hr2.hr2_stream_check(eng.ctx)
+        torch.cuda.synchronize()
+        return bins.cpu().numpy(), hi.cpu().numpy(), st.cpu().numpy()
+
+    out = {}
+    for g in (2, 0):
+        hr2.hr2_set_stream_group(eng.ctx, g)
+        try:
+            out[g] = run(s_str)
+        finally:
+            hr2.hr2_set_stream_group(eng.ctx, 0)
+    assert np.all(out[0][2] == 0)
+    assert np.array_equal(out[2][0], out[0][0]) and np.array_equal(out[2][1], out[0][1])
+    bl, hl, _ = run(s_lvl)
+    stored = tables_as_stored(tabs, "fp16")
+    for i in range(n):
+        sp = specs[sid[i]]
+        assert rel_flux_err(out[0][1][i, : sp.n_nu], hl[i, : sp.n_nu].astype(np.float64)) <= 2e-5
+        assert rel_flux_err(out[0][0][i, : sp.n_bins], bl[i, : sp.n_bins].astype(np.float64)) <= 2e-5
+    for i in (0, 1, 2, 50, 94, 95):
+        sp = specs[sid[i]]
+        ob, otop, ok = oracle_model(stored, sp).forward(theta[i], want_top=True)
+        assert ok
+        assert rel_flux_err(out[0][1][i, : sp.n_nu], otop) <= FLUX_RTOL
+        assert rel_flux_err(out[0][0][i, : sp.n_bins], ob) <= FLUX_RTOL
